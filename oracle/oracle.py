@@ -1,0 +1,147 @@
+"""Python access to the FP64 CPU oracle (``laph_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke``
+and by the CPU-baseline leg of ``bench.py``.  The CUDA library never imports,
+links or runs anything in this folder.
+
+The oracle computes, for one timeslice, the LapH meson and baryon blocks
+formed from N complex colour vectors (paper, section "Innovations",
+subsection "QUDA": quark-antiquark doublets and three-quark triplets built
+from the LapH eigenvectors):
+
+    B[p][i,j,k] = sum_x exp(-2 pi i ((n_p.x) mod L)/L) eps_abc phi_i^a phi_j^b phi_k^c
+    M[p][i][j]  = sum_x exp(-2 pi i ((n_p.x) mod L)/L) conj(phi_i^a) phi_j^a
+
+in double precision with plain loops (see ``laph_oracle.c``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "laph_oracle.c")
+_LIB = os.path.join(_HERE, "liblaph_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``laph_oracle.c`` into ``liblaph_oracle.so`` (gcc, OpenMP, no fast-math).
+
+    ``LAPH_ORACLE_LIB`` names a different, already built library instead; the
+    mutation tests use it to load copies of the oracle with planted mistakes.
+    """
+    override = os.environ.get("LAPH_ORACLE_LIB")
+    if override:
+        return override
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=gnu11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            dp = ctypes.POINTER(ctypes.c_double)
+            ip = ctypes.POINTER(ctypes.c_int32)
+            lib.oracle_phase_table.argtypes = [ctypes.c_int, ip, ctypes.c_int, dp]
+            lib.oracle_phase_table.restype = None
+            lib.oracle_baryon_triples.argtypes = [dp, ctypes.c_int, ctypes.c_int, ip, ctypes.c_int,
+                                                  ctypes.c_int64, ip, dp]
+            lib.oracle_baryon_triples.restype = ctypes.c_int
+            lib.oracle_baryon_blocks.argtypes = [dp, ctypes.c_int, ctypes.c_int, ip, ctypes.c_int, dp]
+            lib.oracle_baryon_blocks.restype = ctypes.c_int
+            lib.oracle_meson_blocks.argtypes = [dp, ctypes.c_int, ctypes.c_int, ip, ctypes.c_int, dp]
+            lib.oracle_meson_blocks.restype = ctypes.c_int
+            lib.oracle_baryon_dense.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp]
+            lib.oracle_baryon_dense.restype = None
+            lib.oracle_num_threads.argtypes = []
+            lib.oracle_num_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _iptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _prep(phi: np.ndarray, L: int, momenta):
+    phi = np.ascontiguousarray(phi, dtype=np.complex128)
+    V = L ** 3
+    if phi.ndim != 3 or phi.shape[1] != V or phi.shape[2] != 3:
+        raise ValueError(f"phi must be [N][L^3][3], got {phi.shape} for L={L}")
+    mom = np.ascontiguousarray(np.asarray(momenta, dtype=np.int32).reshape(-1, 3))
+    return phi, mom
+
+
+def num_threads() -> int:
+    """OpenMP threads the oracle uses (OMP_NUM_THREADS, else all host cores)."""
+    return int(_load().oracle_num_threads())
+
+
+def phase_table(L: int, momenta) -> np.ndarray:
+    """complex128 [P][L^3]: exp(-2 pi i ((n_p.x) mod L)/L)."""
+    mom = np.ascontiguousarray(np.asarray(momenta, dtype=np.int32).reshape(-1, 3))
+    out = np.empty((mom.shape[0], L ** 3), dtype=np.complex128)
+    _load().oracle_phase_table(L, _iptr(mom), mom.shape[0], _dptr(out))
+    return out
+
+
+def baryon_blocks(phi: np.ndarray, L: int, momenta) -> np.ndarray:
+    """Packed baryon blocks, complex128 [P][C(N,3)], colex index C(k,3)+C(j,2)+i."""
+    phi, mom = _prep(phi, L, momenta)
+    N = phi.shape[0]
+    n3 = N * (N - 1) * (N - 2) // 6
+    out = np.zeros((mom.shape[0], n3), dtype=np.complex128)
+    if n3:
+        rc = _load().oracle_baryon_blocks(_dptr(phi), L, N, _iptr(mom), mom.shape[0], _dptr(out))
+        if rc != 0:
+            raise RuntimeError("oracle_baryon_blocks failed")
+    return out
+
+
+def baryon_triples(phi: np.ndarray, L: int, momenta, ijk) -> np.ndarray:
+    """B for arbitrary index triples (any order): complex128 [n][P]."""
+    phi, mom = _prep(phi, L, momenta)
+    ijk = np.ascontiguousarray(np.asarray(ijk, dtype=np.int32).reshape(-1, 3))
+    out = np.zeros((ijk.shape[0], mom.shape[0]), dtype=np.complex128)
+    if ijk.shape[0]:
+        rc = _load().oracle_baryon_triples(_dptr(phi), L, phi.shape[0], _iptr(mom), mom.shape[0],
+                                           ijk.shape[0], _iptr(ijk), _dptr(out))
+        if rc != 0:
+            raise RuntimeError("oracle_baryon_triples failed (bad index or allocation)")
+    return out
+
+
+def meson_blocks(phi: np.ndarray, L: int, momenta) -> np.ndarray:
+    """Meson blocks, complex128 [P][N][N]."""
+    phi, mom = _prep(phi, L, momenta)
+    N = phi.shape[0]
+    out = np.zeros((mom.shape[0], N, N), dtype=np.complex128)
+    rc = _load().oracle_meson_blocks(_dptr(phi), L, N, _iptr(mom), mom.shape[0], _dptr(out))
+    if rc != 0:
+        raise RuntimeError("oracle_meson_blocks failed")
+    return out
+
+
+def baryon_dense(packed: np.ndarray, N: int) -> np.ndarray:
+    """Dense antisymmetric tensor complex128 [P][N][N][N] from the packed form."""
+    packed = np.ascontiguousarray(packed, dtype=np.complex128)
+    P = packed.shape[0]
+    out = np.empty((P, N, N, N), dtype=np.complex128)
+    _load().oracle_baryon_dense(_dptr(packed), N, P, _dptr(out))
+    return out
