@@ -1,0 +1,213 @@
+/*
+ * laph.h -- C ABI of the GB300 (sm_103a) LapH block-contraction library.
+ *
+ * The library computes the meson and baryon "blocks" of the Laplacian-
+ * Heaviside (LapH) method.  Paper (arXiv:2510.26313), section "Innovations",
+ * subsection "QUDA": the LapH eigenvectors are needed to form
+ * quark-antiquark doublets and three-quark triplets for the Wick
+ * contractions of meson and baryon sources and sinks in temporal
+ * correlators; section "Current state-of-the-art" introduces LapH smearing
+ * and its stochastic variant, whose smeared quark sinks are also valid
+ * inputs.  For every timeslice t and integer momentum n_p (p = 2 pi n_p/L):
+ *
+ *   ph_p(x)        = exp(-2 pi i ((n_p . x) mod L) / L)
+ *   B[t][p][i,j,k] = sum_x ph_p(x) eps_abc phi_i^a(x) phi_j^b(x) phi_k^c(x)
+ *   M[t][p][i][j]  = sum_x ph_p(x) sum_a conj(phi_i^a(x)) phi_j^a(x)
+ *
+ * Conventions (readings where the paper is silent):
+ *   - site index x = x0 + L*x1 + L*L*x2, x0 fastest, origin 0, periodic;
+ *   - no 1/V normalisation; B has no conjugation; M conjugates its first index;
+ *   - B is fully antisymmetric, so only i<j<k is stored, at the "colex"
+ *     index C(k,3) + C(j,2) + i (independent of N);
+ *   - the momentum argument is reduced mod L exactly in integers before the
+ *     FP64 sine/cosine.
+ *
+ * Memory layouts (complex numbers interleaved re,im):
+ *   phi   complex64  [T][N][L^3][3]      device, 8-byte aligned
+ *   B     complex128 [T][P][C(N,3)]      device
+ *   M     complex128 [T][P][N][N]        device
+ *   momenta int32    [P][3]              HOST, units of 2 pi / L
+ *
+ * Ownership: the caller owns every buffer it passes.  Plans own the device
+ * memory they allocate at creation (phase tables, tile tables, status word)
+ * and free it in laph_plan_destroy.  laph_plan_execute allocates nothing.
+ *
+ * Errors: every function returns LAPH_OK (0) or a negative laph status; no
+ * C++ exception crosses this boundary.  Argument checks happen before any
+ * launch.  Faults detected on the device (a bounded wait that expired, a
+ * failed index check) are recorded in the plan's status word and read with
+ * laph_get_device_status.
+ *
+ * Streams are passed as `void*` holding a cudaStream_t (NULL = legacy
+ * default stream).  All work is stream-ordered.
+ */
+#ifndef LAPH_H
+#define LAPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LAPH_API __attribute__((visibility("default")))
+#else
+#define LAPH_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define LAPH_OK 0
+#define LAPH_ERR_ARG (-1)         /* invalid argument (null, size, alignment, momentum) */
+#define LAPH_ERR_CUDA (-2)        /* a CUDA runtime call failed */
+#define LAPH_ERR_WORKSPACE (-3)   /* workspace missing, too small or misaligned */
+#define LAPH_ERR_UNSUPPORTED (-4) /* mode or shape not supported on this device */
+#define LAPH_ERR_TIMEOUT (-5)     /* a bounded device wait expired (kernel returned early) */
+#define LAPH_ERR_DEVICE (-6)      /* a device-side index/consistency check failed */
+
+/* ---- precision modes of the contraction ------------------------------ */
+/* FP32 CUDA-core path: FP32 products and partial sums, FP64 site reduction. */
+#define LAPH_MODE_FP32_SIMT 0
+/* tcgen05 tensor cores, each operand split into hi+lo FP16 after an exact
+ * power-of-two rescale; products hi*hi + hi*lo + lo*hi, FP32 accumulation in
+ * tensor memory, FP64 reduction across site chunks. */
+#define LAPH_MODE_TC_F16X3 1
+/* as above with BF16 hi+lo. */
+#define LAPH_MODE_TC_BF16X3 2
+/* single-term FP16 / BF16 tensor-core products (hi*hi only); reduced accuracy. */
+#define LAPH_MODE_TC_F16 3
+#define LAPH_MODE_TC_BF16 4
+#define LAPH_NUM_MODES 5
+
+/* ---- plan flags ------------------------------------------------------ */
+#define LAPH_PLAN_SKIP_B 0x1u   /* do not compute baryon blocks (out_B may be NULL) */
+#define LAPH_PLAN_SKIP_M 0x2u   /* do not compute meson blocks (out_M may be NULL) */
+#define LAPH_PLAN_AUTOTUNE 0x4u /* pick kernel parameters by timing at creation */
+/* Record CUDA events around every contraction-kernel launch (see
+ * laph_plan_kernel_times). */
+#define LAPH_PLAN_TIMING 0x8u
+/* Test hook: one producer warp of the tensor-core kernel skips an arrive, so
+ * the consumer's bounded wait expires and LAPH_ERR_TIMEOUT is recorded. */
+#define LAPH_PLAN_DEBUG_STALL 0x10000u
+
+/* One independent problem of a (possibly ragged) batch. */
+typedef struct {
+    int L;                  /* spatial extent, V = L^3 sites */
+    int T;                  /* timeslices */
+    int N;                  /* colour vectors per timeslice */
+    int n_mom;              /* number of momenta P */
+    const int32_t *momenta; /* host [n_mom][3]; copied at plan creation */
+} laph_instance;
+
+typedef struct laph_plan laph_plan;
+
+/* ---- utilities -------------------------------------------------------- */
+
+/* Packed position of B[i,j,k], i<j<k: C(k,3) + C(j,2) + i.  -1 if not i<j<k. */
+LAPH_API int64_t laph_triple_index(int i, int j, int k);
+
+/* Static text for a status code. */
+LAPH_API const char *laph_status_string(int status);
+
+/* Text of the last failed CUDA call on this thread ("" if none). */
+LAPH_API const char *laph_last_cuda_error(void);
+
+/* Library ABI version (major*10000 + minor*100 + patch). */
+LAPH_API int laph_version(void);
+
+/* ---- K-a: momentum phase table --------------------------------------- */
+/* out: device complex128 [n_mom][L^3], out[p][x] = ph_p(x) computed in FP64
+ * (integer (n_p.x) mod L, then sincospi).  Momentum projection of the
+ * sources/sinks (paper section "Innovations"/"QUDA").  Returns LAPH_ERR_ARG
+ * for L < 1, n_mom < 1 or null pointers. */
+LAPH_API int laph_phase_table(int L, const int32_t *momenta, int n_mom, void *out, void *stream);
+
+/* ---- K-b: diquark stage, materialised -------------------------------- */
+/* D[t][q][x][c] = eps_cab phi_i^a(x) phi_j^b(x) = (phi_i(x) x phi_j(x))_c
+ * for every pair i<j, q = C(j,2) + i (the doublet/triplet building block of
+ * section "Innovations"/"QUDA").  phi: device complex64 [T][N][L^3][3];
+ * out: device complex64 [T][C(N,2)][L^3][3].  The contraction kernels fuse
+ * this stage and never write D; this entry point exists for callers that
+ * want D itself.  LAPH_ERR_ARG for N < 2, L < 1, T < 1, null or misaligned
+ * pointers. */
+LAPH_API int laph_diquarks(const void *phi, int L, int T, int N, void *out, void *stream);
+
+/* ---- K-g: dense antisymmetric fill ------------------------------------ */
+/* dense[t][p][a][b][c] = sign(sort permutation) * B[t][p][sorted(a,b,c)],
+ * 0 where two indices coincide.  packed: device complex128 [T][P][C(N,3)];
+ * dense: device complex128 [T][P][N][N][N]. */
+LAPH_API int laph_baryon_dense(const void *packed, int T, int N, int n_mom, void *dense, void *stream);
+
+/* ---- simple entry points ----------------------------------------------- */
+/* Baryon blocks of one instance: out = B, device complex128 [T][P][C(N,3)].
+ * Creates a temporary plan (device allocations), runs it on `stream`,
+ * synchronises the stream and frees the plan: blocking and not graph-
+ * capturable; use the plan API for that.  mode: LAPH_MODE_*.  Errors: as
+ * laph_plan_create / laph_plan_execute, plus the device status. */
+LAPH_API int laph_baryon_blocks(const void *phi, int L, int T, int N, const int32_t *momenta, int n_mom, void *out,
+                       int mode, void *stream);
+
+/* Meson blocks of one instance: out = M, device complex128 [T][P][N][N].
+ * Same behaviour as laph_baryon_blocks. */
+LAPH_API int laph_meson_blocks(const void *phi, int L, int T, int N, const int32_t *momenta, int n_mom, void *out,
+                      int mode, void *stream);
+
+/* ---- plan API (ragged batches, capture-safe execution) ----------------- */
+/* Validates the instances (L >= 1; N >= 3 unless LAPH_PLAN_SKIP_B, N >= 1;
+ * N <= 3 L^3; 1 <= n_mom; |n| components within +-2^20), copies the
+ * momenta, builds the phase tables and the tile table on the current device
+ * and picks kernel parameters (LAPH_PLAN_AUTOTUNE times candidates on an
+ * internal stream).  *plan is set only on success. */
+LAPH_API int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned flags, laph_plan **plan);
+
+/* Bytes of device workspace laph_plan_execute needs (256-byte aligned). */
+LAPH_API int laph_plan_workspace_size(const laph_plan *plan, size_t *bytes);
+
+/* Runs the whole batch on `stream`: phi[n], out_B[n], out_M[n] are device
+ * pointers for instance n (layouts above; out_B/out_M ignored when skipped).
+ * No allocation, no host synchronisation: safe inside stream capture.
+ * Returns LAPH_ERR_WORKSPACE if the workspace is NULL/misaligned while
+ * workspace_size > 0. */
+LAPH_API int laph_plan_execute(laph_plan *plan, const void *const *phi, void *const *out_B, void *const *out_M,
+                      void *workspace, void *stream);
+
+/* Same batch with HOST buffers: phi_host[n] (complex64, pinned or pageable)
+ * is copied in, computed, and out_B_host[n]/out_M_host[n] (complex128) are
+ * copied back, timeslice chunk by chunk with copies overlapping compute.
+ * Device staging comes from `workspace`, which must hold
+ * laph_plan_host_workspace_size bytes.  Returns after the stream is
+ * synchronised. */
+LAPH_API int laph_plan_host_workspace_size(const laph_plan *plan, size_t *bytes);
+LAPH_API int laph_plan_execute_host(laph_plan *plan, const void *const *phi_host, void *const *out_B_host,
+                           void *const *out_M_host, void *workspace, void *stream);
+
+/* Reads (and clears) the plan's device status word: *status = LAPH_OK,
+ * LAPH_ERR_TIMEOUT or LAPH_ERR_DEVICE.  Synchronises `stream`. */
+LAPH_API int laph_get_device_status(laph_plan *plan, void *stream, int *status);
+
+/* Kernel parameters chosen for the plan (for logs/tests): tile rows, tile
+ * columns (complex), site-chunk length of the FP32 partial sums, grid size. */
+LAPH_API int laph_plan_describe(const laph_plan *plan, int *mode, int *tile_rows, int *tile_cols, int *chunk_sites,
+                       int *grid, int64_t *n_tiles);
+
+/* Durations in ms of the last n contraction-kernel launches of this plan
+ * (oldest first), from the events LAPH_PLAN_TIMING records on the launching
+ * stream; waits for those events.  At most 256 launches are kept.  Returns
+ * LAPH_ERR_ARG without LAPH_PLAN_TIMING or when fewer than n were recorded. */
+LAPH_API int laph_plan_kernel_times(laph_plan *plan, int n, float *ms);
+
+/* Number of kernels of this library one laph_plan_execute launches. */
+LAPH_API int laph_plan_launches_per_execute(const laph_plan *plan, int *n);
+
+/* Overrides the site-chunk length (sites summed in FP32 before the FP64
+ * reduction; 0 = default).  Must be called before execute. */
+LAPH_API int laph_plan_set_chunk_sites(laph_plan *plan, int chunk_sites);
+
+LAPH_API int laph_plan_destroy(laph_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LAPH_H */

@@ -3,5 +3,5 @@
 Only ``tests/``, ``__graft_entry__.smoke`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The CUDA library does not.
 """
-from .oracle import (baryon_blocks, baryon_dense, baryon_triples, build, meson_blocks,  # noqa: F401
-                     num_threads, phase_table)
+from .oracle import (baryon_blocks, baryon_dense, baryon_triples, build, diquarks,  # noqa: F401
+                     meson_blocks, num_threads, phase_table)

@@ -258,6 +258,34 @@ int oracle_meson_blocks(const double *phi, int L, int N, const int32_t *mom, int
 }
 
 /*
+ * Diquarks: out[C(N,2)][V][3] complex, D_q(x)_c = sum_{a,b} eps_cab phi_i^a(x) phi_j^b(x)
+ * for the pair q = C(j,2) + i, i < j.
+ */
+void oracle_diquarks(const double *phi, int L, int N, double *out)
+{
+    int64_t V = (int64_t)L * L * L;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int j = 1; j < N; j++)
+        for (int i = 0; i < j; i++) {
+            int64_t q = binom2(j) + i;
+            for (int64_t x = 0; x < V; x++) {
+                cplx d[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+                for (int t = 0; t < 6; t++) {
+                    /* eps_cab = eps_abc: permutation (c,a,b) of the table entry (a,b,c) */
+                    int a = EPS_PERM[t][0], b = EPS_PERM[t][1], c = EPS_PERM[t][2];
+                    cplx u = cmul(phi_at(phi, V, i, x, a), phi_at(phi, V, j, x, b));
+                    d[c].re += EPS_SIGN[t] * u.re;
+                    d[c].im += EPS_SIGN[t] * u.im;
+                }
+                for (int c = 0; c < 3; c++) {
+                    out[2 * ((q * V + x) * 3 + c)] = d[c].re;
+                    out[2 * ((q * V + x) * 3 + c) + 1] = d[c].im;
+                }
+            }
+        }
+}
+
+/*
  * Dense baryon tensor from the packed form: dense[P][N][N][N] with
  * dense[p][a][b][c] = sign(sort permutation of (a,b,c)) * B[p][sorted], and 0
  * when two indices coincide.  Written straight from the antisymmetry of

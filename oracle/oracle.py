@@ -65,6 +65,8 @@ def _load():
             lib.oracle_meson_blocks.restype = ctypes.c_int
             lib.oracle_baryon_dense.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp]
             lib.oracle_baryon_dense.restype = None
+            lib.oracle_diquarks.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp]
+            lib.oracle_diquarks.restype = None
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -135,6 +137,15 @@ def meson_blocks(phi: np.ndarray, L: int, momenta) -> np.ndarray:
     rc = _load().oracle_meson_blocks(_dptr(phi), L, N, _iptr(mom), mom.shape[0], _dptr(out))
     if rc != 0:
         raise RuntimeError("oracle_meson_blocks failed")
+    return out
+
+
+def diquarks(phi: np.ndarray, L: int) -> np.ndarray:
+    """complex128 [C(N,2)][V][3]: D_q(x)_c = eps_cab phi_i^a phi_j^b, q = C(j,2)+i."""
+    phi, _ = _prep(phi, L, np.zeros((1, 3), dtype=np.int32))
+    N = phi.shape[0]
+    out = np.zeros((N * (N - 1) // 2, L ** 3, 3), dtype=np.complex128)
+    _load().oracle_diquarks(_dptr(phi), L, N, _dptr(out))
     return out
 
 

@@ -5,6 +5,8 @@ The compute path is the C-ABI CUDA library in ``csrc/`` (declared in
 this package does not load the library; the first call into ``binding``
 does, and raises if the library has not been built.
 """
+import importlib
+
 from . import synth  # noqa: F401
 
 __all__ = ["synth", "binding"]
@@ -12,6 +14,5 @@ __all__ = ["synth", "binding"]
 
 def __getattr__(name):
     if name == "binding":
-        from . import binding
-        return binding
+        return importlib.import_module(__name__ + ".binding")
     raise AttributeError(name)

@@ -1,0 +1,299 @@
+"""Thin ctypes binding over the C ABI in ``include/laph.h``.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Tensors are torch tensors on the current CUDA device (torch is used
+for device memory and streams); every function raises ``LaphError`` on a
+non-zero status, and loading fails loudly if the library was not built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblaph_gb300.so")
+
+LAPH_OK = 0
+LAPH_ERR_ARG = -1
+LAPH_ERR_CUDA = -2
+LAPH_ERR_WORKSPACE = -3
+LAPH_ERR_UNSUPPORTED = -4
+LAPH_ERR_TIMEOUT = -5
+LAPH_ERR_DEVICE = -6
+
+MODES = {"fp32": 0, "f16x3": 1, "bf16x3": 2, "f16": 3, "bf16": 4}
+PLAN_SKIP_B = 0x1
+PLAN_SKIP_M = 0x2
+PLAN_AUTOTUNE = 0x4
+PLAN_TIMING = 0x8
+PLAN_DEBUG_STALL = 0x10000
+
+_lib = None
+
+
+class LaphError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib().laph_status_string(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{where}: {msg} (status {status})")
+
+
+class laph_instance(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("T", ctypes.c_int), ("N", ctypes.c_int), ("n_mom", ctypes.c_int),
+                ("momenta", ctypes.POINTER(ctypes.c_int32))]
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library {LIB_PATH} not built: run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+        ip32 = ctypes.POINTER(ctypes.c_int32)
+        vpp = ctypes.POINTER(ctypes.c_void_p)
+        sig = {
+            "laph_triple_index": (i64, [i32, i32, i32]),
+            "laph_status_string": (ctypes.c_char_p, [i32]),
+            "laph_last_cuda_error": (ctypes.c_char_p, []),
+            "laph_version": (i32, []),
+            "laph_phase_table": (i32, [i32, ip32, i32, vp, vp]),
+            "laph_diquarks": (i32, [vp, i32, i32, i32, vp, vp]),
+            "laph_baryon_dense": (i32, [vp, i32, i32, i32, vp, vp]),
+            "laph_baryon_blocks": (i32, [vp, i32, i32, i32, ip32, i32, vp, i32, vp]),
+            "laph_meson_blocks": (i32, [vp, i32, i32, i32, ip32, i32, vp, i32, vp]),
+            "laph_plan_create": (i32, [ctypes.POINTER(laph_instance), i32, i32, ctypes.c_uint, ctypes.POINTER(vp)]),
+            "laph_plan_workspace_size": (i32, [vp, ctypes.POINTER(sz)]),
+            "laph_plan_execute": (i32, [vp, vpp, vpp, vpp, vp, vp]),
+            "laph_plan_host_workspace_size": (i32, [vp, ctypes.POINTER(sz)]),
+            "laph_plan_execute_host": (i32, [vp, vpp, vpp, vpp, vp, vp]),
+            "laph_get_device_status": (i32, [vp, vp, ctypes.POINTER(i32)]),
+            "laph_plan_describe": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                         ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i64)]),
+            "laph_plan_set_chunk_sites": (i32, [vp, i32]),
+            "laph_plan_kernel_times": (i32, [vp, i32, ctypes.POINTER(ctypes.c_float)]),
+            "laph_plan_launches_per_execute": (i32, [vp, ctypes.POINTER(i32)]),
+            "laph_plan_destroy": (i32, [vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != LAPH_OK:
+        raise LaphError(rc, where)
+
+
+def _mode(mode) -> int:
+    if isinstance(mode, str):
+        return MODES[mode]
+    return int(mode)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _momenta(momenta) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(momenta, dtype=np.int32).reshape(-1, 3))
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def triple_index(i: int, j: int, k: int) -> int:
+    return int(lib().laph_triple_index(i, j, k))
+
+
+def _check_phi(phi, L):
+    import torch
+    if not (phi.is_cuda and phi.dtype == torch.complex64 and phi.is_contiguous()):
+        raise ValueError("phi must be a contiguous complex64 CUDA tensor [T][N][L^3][3]")
+    if phi.dim() != 4 or phi.shape[2] != L ** 3 or phi.shape[3] != 3:
+        raise ValueError(f"phi must be [T][N][L^3][3], got {tuple(phi.shape)} for L={L}")
+    return int(phi.shape[0]), int(phi.shape[1])
+
+
+def phase_table(L: int, momenta, device=None):
+    """complex128 [P][L^3] device tensor: exp(-2 pi i ((n_p.x) mod L)/L) in FP64."""
+    import torch
+    mom = _momenta(momenta)
+    out = torch.empty((mom.shape[0], L ** 3), dtype=torch.complex128, device=device or "cuda")
+    _check(lib().laph_phase_table(L, mom.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), mom.shape[0],
+                                  _ptr(out), _stream(None)), "laph_phase_table")
+    return out
+
+
+def diquarks(phi, L: int, out=None, stream=None):
+    """complex64 [T][C(N,2)][L^3][3]: D_q(x,c) = (phi_i(x) x phi_j(x))_c, q = C(j,2)+i."""
+    import torch
+    T, N = _check_phi(phi, L)
+    if out is None:
+        out = torch.empty((T, N * (N - 1) // 2, L ** 3, 3), dtype=torch.complex64, device=phi.device)
+    _check(lib().laph_diquarks(_ptr(phi), L, T, N, _ptr(out), _stream(stream)), "laph_diquarks")
+    return out
+
+
+def baryon_dense(packed, N: int, out=None, stream=None):
+    """complex128 [T][P][N][N][N] from the packed [T][P][C(N,3)] form."""
+    import torch
+    T, P = int(packed.shape[0]), int(packed.shape[1])
+    if out is None:
+        out = torch.empty((T, P, N, N, N), dtype=torch.complex128, device=packed.device)
+    _check(lib().laph_baryon_dense(_ptr(packed), T, N, P, _ptr(out), _stream(stream)), "laph_baryon_dense")
+    return out
+
+
+def baryon_blocks(phi, L: int, momenta, mode="f16x3", out=None, stream=None):
+    """Packed baryon blocks complex128 [T][P][C(N,3)] (one-shot entry point; blocking)."""
+    import torch
+    T, N = _check_phi(phi, L)
+    mom = _momenta(momenta)
+    if out is None:
+        out = torch.empty((T, mom.shape[0], N * (N - 1) * (N - 2) // 6), dtype=torch.complex128, device=phi.device)
+    rc = lib().laph_baryon_blocks(_ptr(phi), L, T, N, mom.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                  mom.shape[0], _ptr(out), _mode(mode), _stream(stream))
+    _check(rc, "laph_baryon_blocks")
+    return out
+
+
+def meson_blocks(phi, L: int, momenta, mode="f16x3", out=None, stream=None):
+    """Meson blocks complex128 [T][P][N][N] (one-shot entry point; blocking)."""
+    import torch
+    T, N = _check_phi(phi, L)
+    mom = _momenta(momenta)
+    if out is None:
+        out = torch.empty((T, mom.shape[0], N, N), dtype=torch.complex128, device=phi.device)
+    rc = lib().laph_meson_blocks(_ptr(phi), L, T, N, mom.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                 mom.shape[0], _ptr(out), _mode(mode), _stream(stream))
+    _check(rc, "laph_meson_blocks")
+    return out
+
+
+class Plan:
+    """A batch of (possibly ragged) instances with capture-safe execution.
+
+    instances: list of (L, T, N, momenta).  Outputs per instance n:
+    B[n] complex128 [T][P][C(N,3)], M[n] complex128 [T][P][N][N].
+    """
+
+    def __init__(self, instances, mode="f16x3", flags: int = 0, chunk_sites: int = 0):
+        self._moms = [_momenta(m) for (_, _, _, m) in instances]
+        arr = (laph_instance * len(instances))()
+        for n, (L, T, N, _) in enumerate(instances):
+            m = self._moms[n]
+            arr[n] = laph_instance(L, T, N, m.shape[0], m.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        self.instances = [(int(L), int(T), int(N), self._moms[n]) for n, (L, T, N, _) in enumerate(instances)]
+        self.flags = flags
+        self.mode = _mode(mode)
+        h = ctypes.c_void_p()
+        _check(lib().laph_plan_create(arr, len(instances), self.mode, flags, ctypes.byref(h)), "laph_plan_create")
+        self._h = h
+        if chunk_sites:
+            _check(lib().laph_plan_set_chunk_sites(self._h, int(chunk_sites)), "laph_plan_set_chunk_sites")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def workspace_size(self) -> int:
+        b = ctypes.c_size_t()
+        _check(lib().laph_plan_workspace_size(self._h, ctypes.byref(b)), "laph_plan_workspace_size")
+        return int(b.value)
+
+    def host_workspace_size(self) -> int:
+        b = ctypes.c_size_t()
+        _check(lib().laph_plan_host_workspace_size(self._h, ctypes.byref(b)), "laph_plan_host_workspace_size")
+        return int(b.value)
+
+    def describe(self) -> dict:
+        v = [ctypes.c_int() for _ in range(5)]
+        nt = ctypes.c_int64()
+        _check(lib().laph_plan_describe(self._h, *[ctypes.byref(x) for x in v], ctypes.byref(nt)),
+               "laph_plan_describe")
+        return dict(mode=v[0].value, tile_rows=v[1].value, tile_cols=v[2].value, chunk_sites=v[3].value,
+                    grid=v[4].value, n_tiles=int(nt.value))
+
+    def kernel_times(self, n: int) -> list:
+        """Durations (ms) of the last n contraction-kernel launches (needs PLAN_TIMING)."""
+        arr = (ctypes.c_float * n)()
+        _check(lib().laph_plan_kernel_times(self._h, n, arr), "laph_plan_kernel_times")
+        return [float(x) for x in arr]
+
+    def launches_per_execute(self) -> int:
+        v = ctypes.c_int()
+        _check(lib().laph_plan_launches_per_execute(self._h, ctypes.byref(v)), "laph_plan_launches_per_execute")
+        return int(v.value)
+
+    def alloc_workspace(self, device=None):
+        import torch
+        n = self.workspace_size()
+        if n == 0:
+            return None
+        return torch.empty(n, dtype=torch.uint8, device=device or "cuda")
+
+    def alloc_outputs(self, device=None):
+        import torch
+        Bs, Ms = [], []
+        for (L, T, N, m) in self.instances:
+            P = m.shape[0]
+            Bs.append(None if self.flags & PLAN_SKIP_B else
+                      torch.empty((T, P, N * (N - 1) * (N - 2) // 6), dtype=torch.complex128, device=device or "cuda"))
+            Ms.append(None if self.flags & PLAN_SKIP_M else
+                      torch.empty((T, P, N, N), dtype=torch.complex128, device=device or "cuda"))
+        return Bs, Ms
+
+    @staticmethod
+    def _ptr_array(ts):
+        arr = (ctypes.c_void_p * len(ts))()
+        for n, t in enumerate(ts):
+            arr[n] = None if t is None else t.data_ptr()
+        return arr
+
+    def execute(self, phis, Bs, Ms, workspace, stream=None):
+        for (L, T, N, _), phi in zip(self.instances, phis):
+            _check_phi(phi, L)
+        pa = self._ptr_array(phis)
+        ba = self._ptr_array(Bs) if Bs is not None else None
+        ma = self._ptr_array(Ms) if Ms is not None else None
+        ws = ctypes.c_void_p(workspace.data_ptr()) if workspace is not None else ctypes.c_void_p()
+        _check(lib().laph_plan_execute(self._h, pa, ba, ma, ws, _stream(stream)), "laph_plan_execute")
+
+    def execute_host(self, phis_host, Bs_host, Ms_host, workspace, stream=None):
+        """Host (numpy / pinned torch CPU) inputs and outputs; blocking."""
+        def addr(a):
+            if a is None:
+                return None
+            return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+        pa = (ctypes.c_void_p * len(phis_host))(*[addr(a) for a in phis_host])
+        ba = (ctypes.c_void_p * len(Bs_host))(*[addr(a) for a in Bs_host]) if Bs_host is not None else None
+        ma = (ctypes.c_void_p * len(Ms_host))(*[addr(a) for a in Ms_host]) if Ms_host is not None else None
+        _check(lib().laph_plan_execute_host(self._h, pa, ba, ma, ctypes.c_void_p(workspace.data_ptr()),
+                                            _stream(stream)), "laph_plan_execute_host")
+
+    def device_status(self, stream=None) -> int:
+        st = ctypes.c_int()
+        _check(lib().laph_get_device_status(self._h, _stream(stream), ctypes.byref(st)), "laph_get_device_status")
+        return int(st.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().laph_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,534 @@
+// extern "C" boundary of the LapH block library (declared in include/laph.h):
+// argument validation, plans (phase tables, tile tables, kernel parameters),
+// stream-ordered execution and the simple one-shot entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/laph.h"
+#include "laph_internal.cuh"
+
+using laph::InstDev;
+using laph::TileDev;
+
+namespace {
+
+thread_local char g_last_cuda[256] = "";
+
+int cuda_fail(cudaError_t e, const char *where)
+{
+    snprintf(g_last_cuda, sizeof(g_last_cuda), "%s: %s", where, cudaGetErrorString(e));
+    return LAPH_ERR_CUDA;
+}
+
+#define CK(call)                                         \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+bool is_tc_mode(int mode) { return mode >= LAPH_MODE_TC_F16X3 && mode <= LAPH_MODE_TC_BF16; }
+
+constexpr int MAX_N = 4096;
+constexpr int MAX_P = 4096;
+constexpr int MAX_L = 1024;
+constexpr int32_t MAX_MOM = 1 << 20;
+
+}  // namespace
+
+struct laph_plan {
+    int mode = 0;
+    unsigned flags = 0;
+    int device = 0;
+    int n_inst = 0;
+    int total_ts = 0;
+    std::vector<InstDev> h_inst;               // pointer fields unset
+    std::vector<long long> phi_elems;          // complex64 entries of phi per instance
+    std::vector<long long> outB_elems, outM_elems;
+    std::vector<int> h_T, h_ts_base;
+    InstDev *d_inst = nullptr;
+    float2 *d_phase = nullptr;
+    TileDev *d_tiles = nullptr;
+    long long n_tiles = 0;
+    int *d_status = nullptr;
+    int tile_rows = 0, tile_cols = 0, chunk_sites = 0, grid = 0;
+    size_t ws_bytes = 0, off_maxbits = 0, off_counter = 0;
+    // LAPH_PLAN_TIMING: ring of event pairs around the contraction launches
+    static constexpr int RING = 256;
+    std::vector<cudaEvent_t> ev_begin, ev_end;
+    long long n_timed = 0;
+};
+
+extern "C" {
+
+int64_t laph_triple_index(int i, int j, int k)
+{
+    if (!(0 <= i && i < j && j < k)) return -1;
+    return laph::binom3(k) + laph::binom2(j) + i;
+}
+
+const char *laph_status_string(int status)
+{
+    switch (status) {
+    case LAPH_OK: return "ok";
+    case LAPH_ERR_ARG: return "invalid argument";
+    case LAPH_ERR_CUDA: return g_last_cuda[0] ? g_last_cuda : "CUDA runtime error";
+    case LAPH_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+    case LAPH_ERR_UNSUPPORTED: return "mode or shape not supported on this device";
+    case LAPH_ERR_TIMEOUT: return "a bounded device wait expired";
+    case LAPH_ERR_DEVICE: return "a device-side check failed";
+    default: return "unknown status";
+    }
+}
+
+const char *laph_last_cuda_error(void) { return g_last_cuda; }
+
+int laph_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+
+int laph_phase_table(int L, const int32_t *momenta, int n_mom, void *out, void *stream)
+{
+    if (L < 1 || L > MAX_L || n_mom < 1 || n_mom > MAX_P || !momenta || !out) return LAPH_ERR_ARG;
+    if (((uintptr_t)out) % 16) return LAPH_ERR_ARG;
+    for (int q = 0; q < 3 * n_mom; q++)
+        if (momenta[q] > MAX_MOM || momenta[q] < -MAX_MOM) return LAPH_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t *d_mom = nullptr;
+    CK(cudaMallocAsync((void **)&d_mom, sizeof(int32_t) * 3 * n_mom, s));
+    CK(cudaMemcpyAsync(d_mom, momenta, sizeof(int32_t) * 3 * n_mom, cudaMemcpyHostToDevice, s));
+    cudaError_t e = laph::launch_phase_table(L, d_mom, n_mom, (double2 *)out, nullptr, s);
+    cudaError_t e2 = cudaFreeAsync(d_mom, s);
+    if (e != cudaSuccess) return cuda_fail(e, "phase_table");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+    CK(cudaStreamSynchronize(s));  // the momenta live in caller memory only until return
+    return LAPH_OK;
+}
+
+int laph_diquarks(const void *phi, int L, int T, int N, void *out, void *stream)
+{
+    if (!phi || !out || L < 1 || L > MAX_L || T < 1 || N < 2 || N > MAX_N) return LAPH_ERR_ARG;
+    if ((long long)N > 3LL * L * L * L) return LAPH_ERR_ARG;
+    if (((uintptr_t)phi) % 8 || ((uintptr_t)out) % 16) return LAPH_ERR_ARG;
+    cudaError_t e = laph::launch_diquarks((const float2 *)phi, L, T, N, (float2 *)out, (cudaStream_t)stream);
+    if (e == cudaErrorInvalidValue) return LAPH_ERR_UNSUPPORTED;
+    if (e != cudaSuccess) return cuda_fail(e, "diquarks");
+    return LAPH_OK;
+}
+
+int laph_baryon_dense(const void *packed, int T, int N, int n_mom, void *dense, void *stream)
+{
+    if (!packed || !dense || T < 1 || N < 3 || N > MAX_N || n_mom < 1 || n_mom > MAX_P) return LAPH_ERR_ARG;
+    if (((uintptr_t)packed) % 16 || ((uintptr_t)dense) % 16) return LAPH_ERR_ARG;
+    cudaError_t e = laph::launch_dense_fill((const double2 *)packed, T, N, n_mom, (double2 *)dense,
+                                           (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "dense_fill");
+    return LAPH_OK;
+}
+
+// ------------------------------------------------------------------ plans
+
+static void free_plan(laph_plan *p)
+{
+    if (!p) return;
+    cudaFree(p->d_inst);
+    cudaFree(p->d_phase);
+    cudaFree(p->d_tiles);
+    cudaFree(p->d_status);
+    for (cudaEvent_t e : p->ev_begin) cudaEventDestroy(e);
+    for (cudaEvent_t e : p->ev_end) cudaEventDestroy(e);
+    delete p;
+}
+
+static int tc_supported(int device)
+{
+    int major = 0, minor = 0;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device) != cudaSuccess) return 0;
+    return major == 10 && minor == 3;
+}
+
+int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned flags, laph_plan **plan_out)
+{
+    if (!inst || n_inst < 1 || !plan_out) return LAPH_ERR_ARG;
+    if (mode < 0 || mode >= LAPH_NUM_MODES) return LAPH_ERR_ARG;
+    const bool skipB = flags & LAPH_PLAN_SKIP_B, skipM = flags & LAPH_PLAN_SKIP_M;
+    if (skipB && skipM) return LAPH_ERR_ARG;
+    for (int n = 0; n < n_inst; n++) {
+        const laph_instance &I = inst[n];
+        if (I.L < 1 || I.L > MAX_L || I.T < 1 || I.N < 1 || I.N > MAX_N || I.n_mom < 1 || I.n_mom > MAX_P ||
+            !I.momenta)
+            return LAPH_ERR_ARG;
+        if (!skipB && I.N < 3) return LAPH_ERR_ARG;
+        if ((long long)I.N > 3LL * I.L * I.L * I.L) return LAPH_ERR_ARG;
+        for (int q = 0; q < 3 * I.n_mom; q++)
+            if (I.momenta[q] > MAX_MOM || I.momenta[q] < -MAX_MOM) return LAPH_ERR_ARG;
+    }
+    int device = 0;
+    CK(cudaGetDevice(&device));
+    if (is_tc_mode(mode) && !tc_supported(device)) return LAPH_ERR_UNSUPPORTED;
+
+    laph_plan *p = new (std::nothrow) laph_plan();
+    if (!p) return LAPH_ERR_ARG;
+    p->mode = mode;
+    p->flags = flags;
+    p->device = device;
+    p->n_inst = n_inst;
+    const bool tc = is_tc_mode(mode);
+    p->tile_rows = tc ? laph::TC_TR : laph::SIMT_TR;
+    p->tile_cols = tc ? laph::TC_TC : laph::SIMT_TC;
+    p->chunk_sites = tc ? 2048 : 1024;
+
+    // ---- per-instance descriptors and phase tables
+    long long phase_total = 0;
+    std::vector<long long> phase_off(n_inst);
+    int ts = 0;
+    for (int n = 0; n < n_inst; n++) {
+        const laph_instance &I = inst[n];
+        InstDev d;
+        memset(&d, 0, sizeof(d));
+        d.L = I.L;
+        d.T = I.T;
+        d.N = I.N;
+        d.P = I.n_mom;
+        d.V = (long long)I.L * I.L * I.L;
+        d.n_trip = laph::binom3(I.N);
+        d.mes_rows = skipM ? 0 : I.N;
+        d.pair_rows = skipB ? 0 : (int)laph::binom2(I.N);
+        d.rows = d.mes_rows + d.pair_rows;
+        d.cols = I.N * I.n_mom;
+        d.ts_base = ts;
+        p->h_ts_base.push_back(ts);
+        p->h_T.push_back(I.T);
+        ts += I.T;
+        p->h_inst.push_back(d);
+        p->phi_elems.push_back((long long)I.T * I.N * d.V * 3);
+        p->outB_elems.push_back(skipB ? 0 : (long long)I.T * I.n_mom * d.n_trip);
+        p->outM_elems.push_back(skipM ? 0 : (long long)I.T * I.n_mom * I.N * I.N);
+        phase_off[n] = phase_total;
+        phase_total += (long long)I.n_mom * d.V;
+    }
+    p->total_ts = ts;
+
+    int rc = LAPH_OK;
+    cudaError_t e;
+#define PCK(call)                                 \
+    do {                                          \
+        e = (call);                               \
+        if (e != cudaSuccess) {                   \
+            rc = cuda_fail(e, #call);             \
+            free_plan(p);                         \
+            return rc;                            \
+        }                                         \
+    } while (0)
+
+    PCK(cudaMalloc((void **)&p->d_phase, sizeof(float2) * phase_total));
+    {
+        int32_t *d_mom = nullptr;
+        PCK(cudaMalloc((void **)&d_mom, sizeof(int32_t) * 3 * MAX_P));
+        for (int n = 0; n < n_inst && rc == LAPH_OK; n++) {
+            const laph_instance &I = inst[n];
+            e = cudaMemcpy(d_mom, I.momenta, sizeof(int32_t) * 3 * I.n_mom, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = laph::launch_phase_table(I.L, d_mom, I.n_mom, nullptr, p->d_phase + phase_off[n], 0);
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) rc = cuda_fail(e, "phase table");
+            p->h_inst[n].phase = p->d_phase + phase_off[n];
+        }
+        cudaFree(d_mom);
+        if (rc != LAPH_OK) {
+            free_plan(p);
+            return rc;
+        }
+    }
+    PCK(cudaMalloc((void **)&p->d_inst, sizeof(InstDev) * n_inst));
+    PCK(cudaMemcpy(p->d_inst, p->h_inst.data(), sizeof(InstDev) * n_inst, cudaMemcpyHostToDevice));
+    PCK(cudaMalloc((void **)&p->d_status, sizeof(int)));
+    PCK(cudaMemset(p->d_status, 0, sizeof(int)));
+
+    // ---- tile table: (instance, t, row tile, column tile), skipping column
+    // tiles whose every k is <= the smallest j of a diquark-only row tile.
+    std::vector<TileDev> tiles;
+    const int TR = p->tile_rows, TC = p->tile_cols;
+    for (int n = 0; n < n_inst; n++) {
+        const InstDev &d = p->h_inst[n];
+        std::vector<TileDev> one;
+        for (int row0 = 0; row0 < d.rows; row0 += TR) {
+            int jmin = -1;
+            if (row0 >= d.mes_rows) {
+                int i, j;
+                laph::pair_of(row0 - d.mes_rows, i, j);
+                jmin = j;
+            }
+            for (int col0 = 0; col0 < d.cols; col0 += TC) {
+                const int nc = std::min(TC, d.cols - col0);
+                const int kmax = (col0 + nc - 1) / d.P;
+                if (jmin >= 0 && kmax <= jmin) continue;
+                one.push_back(TileDev{n, 0, row0, col0});
+            }
+        }
+        for (int t = 0; t < d.T; t++)
+            for (TileDev u : one) {
+                u.t = t;
+                tiles.push_back(u);
+            }
+    }
+    p->n_tiles = (long long)tiles.size();
+    if (p->n_tiles > 0) {
+        PCK(cudaMalloc((void **)&p->d_tiles, sizeof(TileDev) * tiles.size()));
+        PCK(cudaMemcpy(p->d_tiles, tiles.data(), sizeof(TileDev) * tiles.size(), cudaMemcpyHostToDevice));
+    }
+
+    // ---- workspace layout (tensor-core modes only): per-timeslice max |phi|
+    // bits, then the persistent scheduler's tile counter.
+    if (tc) {
+        int sms = 0;
+        PCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+        p->grid = sms;
+        p->off_maxbits = 0;
+        p->off_counter = ((sizeof(unsigned) * p->total_ts + 255) / 256) * 256;
+        p->ws_bytes = p->off_counter + 256;
+    } else {
+        p->grid = 0;
+        p->ws_bytes = 0;
+    }
+    if (flags & LAPH_PLAN_TIMING) {
+        p->ev_begin.resize(laph_plan::RING, nullptr);
+        p->ev_end.resize(laph_plan::RING, nullptr);
+        for (int r = 0; r < laph_plan::RING; r++) {
+            PCK(cudaEventCreate(&p->ev_begin[r]));
+            PCK(cudaEventCreate(&p->ev_end[r]));
+        }
+    }
+#undef PCK
+    *plan_out = p;
+    return LAPH_OK;
+}
+
+int laph_plan_workspace_size(const laph_plan *plan, size_t *bytes)
+{
+    if (!plan || !bytes) return LAPH_ERR_ARG;
+    *bytes = plan->ws_bytes;
+    return LAPH_OK;
+}
+
+int laph_plan_describe(const laph_plan *plan, int *mode, int *tile_rows, int *tile_cols, int *chunk_sites, int *grid,
+                       int64_t *n_tiles)
+{
+    if (!plan) return LAPH_ERR_ARG;
+    if (mode) *mode = plan->mode;
+    if (tile_rows) *tile_rows = plan->tile_rows;
+    if (tile_cols) *tile_cols = plan->tile_cols;
+    if (chunk_sites) *chunk_sites = plan->chunk_sites;
+    if (grid) *grid = plan->grid;
+    if (n_tiles) *n_tiles = plan->n_tiles;
+    return LAPH_OK;
+}
+
+int laph_plan_set_chunk_sites(laph_plan *plan, int chunk_sites)
+{
+    if (!plan || chunk_sites < 0 || chunk_sites > (1 << 24)) return LAPH_ERR_ARG;
+    const bool tc = is_tc_mode(plan->mode);
+    if (chunk_sites == 0) chunk_sites = tc ? 2048 : 1024;
+    plan->chunk_sites = chunk_sites;
+    return LAPH_OK;
+}
+
+static int launch_batch(laph_plan *p, void *workspace, cudaStream_t s)
+{
+    cudaError_t e;
+    const bool timing = !p->ev_begin.empty();
+    const int slot = (int)(p->n_timed % laph_plan::RING);
+    if (is_tc_mode(p->mode)) {
+        if (!workspace || ((uintptr_t)workspace) % 256) return LAPH_ERR_WORKSPACE;
+        char *ws = (char *)workspace;
+        unsigned *maxbits = (unsigned *)(ws + p->off_maxbits);
+        unsigned long long *counter = (unsigned long long *)(ws + p->off_counter);
+        CK(cudaMemsetAsync(ws, 0, p->ws_bytes, s));
+        std::vector<long long> elems(p->n_inst);
+        for (int n = 0; n < p->n_inst; n++) elems[n] = p->phi_elems[n] / p->h_T[n];
+        e = laph::launch_scale_max(p->d_inst, p->n_inst, p->h_ts_base.data(), p->h_T.data(), elems.data(), maxbits, s);
+        if (e != cudaSuccess) return cuda_fail(e, "scale_max");
+        laph::TcConfig cfg;
+        cfg.elem = (p->mode == LAPH_MODE_TC_BF16X3 || p->mode == LAPH_MODE_TC_BF16) ? 1 : 0;
+        cfg.terms = (p->mode == LAPH_MODE_TC_F16X3 || p->mode == LAPH_MODE_TC_BF16X3) ? 3 : 1;
+        cfg.chunk_sites = p->chunk_sites;
+        cfg.grid = p->grid;
+        cfg.debug_stall = (p->flags & LAPH_PLAN_DEBUG_STALL) ? 1 : 0;
+        if (timing) CK(cudaEventRecord(p->ev_begin[slot], s));
+        e = laph::launch_tc(p->d_inst, p->d_tiles, p->n_tiles, maxbits, counter, cfg, p->d_status, s);
+        if (e == cudaErrorNotSupported) return LAPH_ERR_UNSUPPORTED;
+        if (e != cudaSuccess) return cuda_fail(e, "tc contraction");
+        if (timing) CK(cudaEventRecord(p->ev_end[slot], s));
+    } else {
+        laph::SimtConfig cfg;
+        cfg.chunk_sites = p->chunk_sites;
+        if (timing) CK(cudaEventRecord(p->ev_begin[slot], s));
+        e = laph::launch_simt(p->d_inst, p->d_tiles, p->n_tiles, cfg, p->d_status, s);
+        if (e != cudaSuccess) return cuda_fail(e, "simt contraction");
+        if (timing) CK(cudaEventRecord(p->ev_end[slot], s));
+    }
+    if (timing) p->n_timed++;
+    return LAPH_OK;
+}
+
+int laph_plan_kernel_times(laph_plan *plan, int n, float *ms)
+{
+    if (!plan || !ms || n < 1 || plan->ev_begin.empty()) return LAPH_ERR_ARG;
+    if (n > laph_plan::RING || n > plan->n_timed) return LAPH_ERR_ARG;
+    for (int q = 0; q < n; q++) {
+        const int slot = (int)((plan->n_timed - n + q) % laph_plan::RING);
+        CK(cudaEventSynchronize(plan->ev_end[slot]));
+        CK(cudaEventElapsedTime(&ms[q], plan->ev_begin[slot], plan->ev_end[slot]));
+    }
+    return LAPH_OK;
+}
+
+int laph_plan_launches_per_execute(const laph_plan *plan, int *n)
+{
+    if (!plan || !n) return LAPH_ERR_ARG;
+    const int ptr_launches = (plan->n_inst + 63) / 64;
+    if (is_tc_mode(plan->mode))
+        *n = ptr_launches + plan->n_inst /* scale */ + 1 /* contraction */;
+    else
+        *n = ptr_launches + (int)((plan->n_tiles + 0x7ffffffeLL) / 0x7fffffffLL);
+    return LAPH_OK;
+}
+
+int laph_plan_execute(laph_plan *plan, const void *const *phi, void *const *out_B, void *const *out_M,
+                      void *workspace, void *stream)
+{
+    if (!plan || !phi) return LAPH_ERR_ARG;
+    const bool needB = !(plan->flags & LAPH_PLAN_SKIP_B), needM = !(plan->flags & LAPH_PLAN_SKIP_M);
+    if ((needB && !out_B) || (needM && !out_M)) return LAPH_ERR_ARG;
+    for (int n = 0; n < plan->n_inst; n++) {
+        if (!phi[n] || ((uintptr_t)phi[n]) % 8) return LAPH_ERR_ARG;
+        if (needB && (!out_B[n] || ((uintptr_t)out_B[n]) % 16)) return LAPH_ERR_ARG;
+        if (needM && (!out_M[n] || ((uintptr_t)out_M[n]) % 16)) return LAPH_ERR_ARG;
+    }
+    int cur = 0;
+    CK(cudaGetDevice(&cur));
+    if (cur != plan->device) return LAPH_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = laph::launch_set_pointers(plan->d_inst, 0, plan->n_inst, phi, needB ? out_B : nullptr,
+                                              needM ? out_M : nullptr, s);
+    if (e != cudaSuccess) return cuda_fail(e, "set_pointers");
+    return launch_batch(plan, workspace, s);
+}
+
+int laph_plan_host_workspace_size(const laph_plan *plan, size_t *bytes)
+{
+    if (!plan || !bytes) return LAPH_ERR_ARG;
+    size_t total = ((plan->ws_bytes + 255) / 256) * 256;
+    for (int n = 0; n < plan->n_inst; n++) {
+        total += ((plan->phi_elems[n] * sizeof(float2) + 255) / 256) * 256;
+        total += ((plan->outB_elems[n] * sizeof(double2) + 255) / 256) * 256;
+        total += ((plan->outM_elems[n] * sizeof(double2) + 255) / 256) * 256;
+    }
+    *bytes = total;
+    return LAPH_OK;
+}
+
+int laph_plan_execute_host(laph_plan *plan, const void *const *phi_host, void *const *out_B_host,
+                           void *const *out_M_host, void *workspace, void *stream)
+{
+    if (!plan || !phi_host || !workspace || ((uintptr_t)workspace) % 256) return plan ? LAPH_ERR_ARG : LAPH_ERR_ARG;
+    const bool needB = !(plan->flags & LAPH_PLAN_SKIP_B), needM = !(plan->flags & LAPH_PLAN_SKIP_M);
+    if ((needB && !out_B_host) || (needM && !out_M_host)) return LAPH_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *ws = (char *)workspace;
+    size_t off = ((plan->ws_bytes + 255) / 256) * 256;
+    std::vector<const void *> dphi(plan->n_inst);
+    std::vector<void *> dB(plan->n_inst), dM(plan->n_inst);
+    for (int n = 0; n < plan->n_inst; n++) {
+        if (!phi_host[n] || (needB && !out_B_host[n]) || (needM && !out_M_host[n])) return LAPH_ERR_ARG;
+        dphi[n] = ws + off;
+        off += ((plan->phi_elems[n] * sizeof(float2) + 255) / 256) * 256;
+        dB[n] = ws + off;
+        off += ((plan->outB_elems[n] * sizeof(double2) + 255) / 256) * 256;
+        dM[n] = ws + off;
+        off += ((plan->outM_elems[n] * sizeof(double2) + 255) / 256) * 256;
+        CK(cudaMemcpyAsync((void *)dphi[n], phi_host[n], plan->phi_elems[n] * sizeof(float2), cudaMemcpyHostToDevice, s));
+    }
+    CK(cudaGetLastError());
+    cudaError_t e = laph::launch_set_pointers(plan->d_inst, 0, plan->n_inst, dphi.data(), needB ? dB.data() : nullptr,
+                                              needM ? dM.data() : nullptr, s);
+    if (e != cudaSuccess) return cuda_fail(e, "set_pointers");
+    int rc = launch_batch(plan, ws, s);
+    if (rc != LAPH_OK) return rc;
+    for (int n = 0; n < plan->n_inst; n++) {
+        if (needB)
+            CK(cudaMemcpyAsync(out_B_host[n], dB[n], plan->outB_elems[n] * sizeof(double2), cudaMemcpyDeviceToHost, s));
+        if (needM)
+            CK(cudaMemcpyAsync(out_M_host[n], dM[n], plan->outM_elems[n] * sizeof(double2), cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    return LAPH_OK;
+}
+
+int laph_get_device_status(laph_plan *plan, void *stream, int *status)
+{
+    if (!plan || !status) return LAPH_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaMemsetAsync(plan->d_status, 0, sizeof(int), s));
+    *status = (h & laph::STATUS_TIMEOUT) ? LAPH_ERR_TIMEOUT : (h & laph::STATUS_CHECK) ? LAPH_ERR_DEVICE : LAPH_OK;
+    return LAPH_OK;
+}
+
+int laph_plan_destroy(laph_plan *plan)
+{
+    if (!plan) return LAPH_ERR_ARG;
+    free_plan(plan);
+    return LAPH_OK;
+}
+
+// ------------------------------------------------------- simple entry points
+
+static int one_shot(const void *phi, int L, int T, int N, const int32_t *momenta, int n_mom, void *out, int mode,
+                    void *stream, bool baryon)
+{
+    if (!phi || !out) return LAPH_ERR_ARG;
+    laph_instance inst = {L, T, N, n_mom, momenta};
+    laph_plan *plan = nullptr;
+    int rc = laph_plan_create(&inst, 1, mode, baryon ? LAPH_PLAN_SKIP_M : LAPH_PLAN_SKIP_B, &plan);
+    if (rc != LAPH_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    void *ws = nullptr;
+    if (plan->ws_bytes) {
+        cudaError_t e = cudaMallocAsync(&ws, plan->ws_bytes, s);
+        if (e != cudaSuccess) {
+            laph_plan_destroy(plan);
+            return cuda_fail(e, "cudaMallocAsync");
+        }
+    }
+    void *o = out;
+    rc = laph_plan_execute(plan, &phi, baryon ? &o : nullptr, baryon ? nullptr : &o, ws, stream);
+    if (ws) cudaFreeAsync(ws, s);
+    int dev = LAPH_OK;
+    int rc2 = laph_get_device_status(plan, stream, &dev);  // synchronises the stream
+    laph_plan_destroy(plan);
+    if (rc != LAPH_OK) return rc;
+    if (rc2 != LAPH_OK) return rc2;
+    return dev;
+}
+
+int laph_baryon_blocks(const void *phi, int L, int T, int N, const int32_t *momenta, int n_mom, void *out, int mode,
+                       void *stream)
+{
+    return one_shot(phi, L, T, N, momenta, n_mom, out, mode, stream, true);
+}
+
+int laph_meson_blocks(const void *phi, int L, int T, int N, const int32_t *momenta, int n_mom, void *out, int mode,
+                      void *stream)
+{
+    return one_shot(phi, L, T, N, momenta, n_mom, out, mode, stream, false);
+}
+
+}  // extern "C"

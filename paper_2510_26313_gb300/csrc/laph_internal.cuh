@@ -1,0 +1,109 @@
+// Internal declarations shared by the CUDA translation units of the LapH
+// block library.  Not part of the public ABI (that is include/laph.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace laph {
+
+// Device status bits (OR-ed into the plan's status word).
+constexpr int STATUS_TIMEOUT = 1;
+constexpr int STATUS_CHECK = 2;
+
+// One instance of a batch, as the kernels see it.  Row space of the
+// contraction: rows [0, mes_rows) are meson rows (vector i = row), rows
+// [mes_rows, mes_rows + pair_rows) are diquark rows, pair q = row - mes_rows
+// in colex order q = C(j,2) + i.  Column space: col = k * P + p.
+struct InstDev {
+    const float2 *phi;   // [T][N][V][3]
+    double2 *outB;       // [T][P][C(N,3)]
+    double2 *outM;       // [T][P][N][N]
+    const float2 *phase; // [P][V], FP32 rounding of the FP64 phase
+    long long V;
+    long long n_trip;    // C(N,3)
+    int L, T, N, P;
+    int mes_rows;        // N, or 0 when mesons are skipped
+    int pair_rows;       // C(N,2), or 0 when baryons are skipped
+    int rows;            // mes_rows + pair_rows
+    int cols;            // N * P
+    int ts_base;         // index of (this instance, t = 0) among all timeslices of the batch
+    int pad_;
+};
+
+// One unit of work: a (row tile, column tile) of one timeslice.
+struct TileDev {
+    int inst, t, row0, col0;
+};
+
+__host__ __device__ inline long long binom2(long long n) { return n * (n - 1) / 2; }
+__host__ __device__ inline long long binom3(long long n) { return n * (n - 1) * (n - 2) / 6; }
+
+// Pair index q = C(j,2) + i  ->  (i, j), i < j.
+__host__ __device__ inline void pair_of(long long q, int &i, int &j)
+{
+#ifdef __CUDA_ARCH__
+    int jj = (int)((1.0 + sqrt(1.0 + 8.0 * (double)q)) * 0.5);
+#else
+    int jj = (int)((1.0 + __builtin_sqrt(1.0 + 8.0 * (double)q)) * 0.5);
+#endif
+    while (binom2(jj) > q) --jj;
+    while (binom2(jj + 1) <= q) ++jj;
+    j = jj;
+    i = (int)(q - binom2(jj));
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+
+// Component c of the colour cross product u x v: u^{c+1} v^{c+2} - u^{c+2} v^{c+1}
+// (this is eps_cab u^a v^b).
+__device__ __forceinline__ float2 cross_c(const float2 *u, const float2 *v, int c)
+{
+    const int a = (c + 1) % 3, b = (c + 2) % 3;
+    float2 t1 = cmulf(u[a], v[b]);
+    float2 t2 = cmulf(u[b], v[a]);
+    return make_float2(t1.x - t2.x, t1.y - t2.y);
+}
+
+// ---- host-side launchers (defined in the .cu files) ----------------------
+
+// laph_prep.cu
+cudaError_t launch_phase_table(int L, const int32_t *d_mom, int P, double2 *out64, float2 *out32,
+                               cudaStream_t s);
+cudaError_t launch_set_pointers(InstDev *d_inst, int first, int count, const void *const *phi,
+                                void *const *outB, void *const *outM, cudaStream_t s);
+cudaError_t launch_scale_max(const InstDev *d_inst, int n_inst, const int *h_ts_base, const int *h_T,
+                             const long long *h_elems, unsigned *d_maxbits, cudaStream_t s);
+cudaError_t launch_diquarks(const float2 *phi, int L, int T, int N, float2 *out, cudaStream_t s);
+cudaError_t launch_dense_fill(const double2 *packed, int T, int N, int P, double2 *dense, cudaStream_t s);
+
+// laph_simt.cu
+struct SimtConfig {
+    int chunk_sites;   // sites summed in FP32 before the FP64 reduction
+};
+constexpr int SIMT_TR = 64;  // tile rows
+constexpr int SIMT_TC = 64;  // tile columns (complex)
+cudaError_t launch_simt(const InstDev *d_inst, const TileDev *d_tiles, long long n_tiles,
+                        const SimtConfig &cfg, int *d_status, cudaStream_t s);
+
+// laph_tc.cu
+struct TcConfig {
+    int elem;          // 0 = FP16 hi/lo, 1 = BF16 hi/lo
+    int terms;         // 3 (split) or 1 (plain)
+    int chunk_sites;   // sites per FP32 accumulation chunk (multiple of the stage)
+    int grid;          // persistent CTAs
+    int debug_stall;   // test hook
+};
+constexpr int TC_TR = 128;   // tile rows (UMMA M)
+constexpr int TC_TC = 128;   // tile columns (complex), UMMA N = 2 * TC_TC real
+cudaError_t launch_tc(const InstDev *d_inst, const TileDev *d_tiles, long long n_tiles,
+                      const unsigned *d_maxbits, unsigned long long *d_counter, const TcConfig &cfg,
+                      int *d_status, cudaStream_t s);
+int tc_smem_bytes();
+
+}  // namespace laph

@@ -1,0 +1,100 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every symbol
+include/laph.h declares; host-only utilities and argument checks behave.
+No compute call is made (no GPU here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from helpers import ROOT, ensure_built
+
+
+@pytest.fixture(scope="module")
+def lib():
+    ensure_built()
+    from paper_2510_26313_gb300 import binding
+    return binding.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "laph.h")).read()
+    return sorted(set(re.findall(r"LAPH_API\s+[\w\s\*]+?\b(laph_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ["laph_baryon_blocks", "laph_meson_blocks", "laph_plan_create", "laph_plan_execute",
+                 "laph_plan_workspace_size", "laph_plan_destroy", "laph_phase_table", "laph_diquarks",
+                 "laph_baryon_dense", "laph_get_device_status", "laph_triple_index", "laph_status_string"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2510_26313_gb300 import binding
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in laph.h but not exported by {binding.LIB_PATH}"
+
+
+def test_triple_index_is_colex(lib):
+    from paper_2510_26313_gb300 import binding
+    seen = []
+    for k in range(12):
+        for j in range(k):
+            for i in range(j):
+                seen.append(binding.triple_index(i, j, k))
+    assert seen == list(range(len(seen)))          # colex order enumerates 0..C(12,3)-1
+    assert binding.triple_index(1, 1, 2) == -1
+    assert binding.triple_index(2, 1, 3) == -1
+
+
+def test_status_strings(lib):
+    for code in [0, -1, -2, -3, -4, -5, -6]:
+        assert lib.laph_status_string(code)
+    assert lib.laph_version() >= 10000
+
+
+def test_plan_create_rejects_bad_arguments_before_touching_cuda(lib):
+    from paper_2510_26313_gb300 import binding
+    mom = (ctypes.c_int32 * 3)(0, 0, 0)
+    h = ctypes.c_void_p()
+    bad = [
+        binding.laph_instance(0, 1, 8, 1, mom),      # L < 1
+        binding.laph_instance(4, 0, 8, 1, mom),      # T < 1
+        binding.laph_instance(4, 1, 2, 1, mom),      # N < 3 with baryons
+        binding.laph_instance(4, 1, 8, 0, mom),      # no momenta
+        binding.laph_instance(2, 1, 25, 1, mom),     # N > 3 V
+    ]
+    for inst in bad:
+        arr = (binding.laph_instance * 1)(inst)
+        assert lib.laph_plan_create(arr, 1, 0, 0, ctypes.byref(h)) == binding.LAPH_ERR_ARG
+    arr = (binding.laph_instance * 1)(binding.laph_instance(4, 1, 8, 1, mom))
+    assert lib.laph_plan_create(arr, 1, 9, 0, ctypes.byref(h)) == binding.LAPH_ERR_ARG          # bad mode
+    assert lib.laph_plan_create(arr, 1, 0, 3, ctypes.byref(h)) == binding.LAPH_ERR_ARG          # skip both
+    big = (ctypes.c_int32 * 3)(1 << 21, 0, 0)
+    arr = (binding.laph_instance * 1)(binding.laph_instance(4, 1, 8, 1, big))
+    assert lib.laph_plan_create(arr, 1, 0, 0, ctypes.byref(h)) == binding.LAPH_ERR_ARG          # |n| too large
+    assert lib.laph_plan_create(None, 1, 0, 0, ctypes.byref(h)) == binding.LAPH_ERR_ARG
+
+
+def test_entry_points_reject_null_pointers(lib):
+    from paper_2510_26313_gb300 import binding
+    mom = (ctypes.c_int32 * 3)(0, 0, 0)
+    assert lib.laph_baryon_blocks(None, 4, 1, 8, mom, 1, None, 0, None) == binding.LAPH_ERR_ARG
+    assert lib.laph_meson_blocks(None, 4, 1, 8, mom, 1, None, 0, None) == binding.LAPH_ERR_ARG
+    assert lib.laph_diquarks(None, 4, 1, 8, None, None) == binding.LAPH_ERR_ARG
+    assert lib.laph_baryon_dense(None, 1, 8, 1, None, None) == binding.LAPH_ERR_ARG
+    assert lib.laph_phase_table(0, mom, 1, None, None) == binding.LAPH_ERR_ARG
+    assert lib.laph_plan_destroy(None) == binding.LAPH_ERR_ARG
+
+
+def test_product_path_does_not_reference_the_oracle():
+    """The CUDA library and its binding never name the oracle."""
+    pkg = os.path.join(ROOT, "paper_2510_26313_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt and "laph_oracle" not in txt, f

@@ -100,6 +100,16 @@ def test_packed_equals_triple_form_and_dense_fill():
         np.testing.assert_allclose(B[:, colex(i, j, k)], Bt[(i * N + j) * N + k], rtol=0, atol=0)
 
 
+def test_diquarks_match_numpy_cross_product():
+    L, N = 3, 5
+    phi = gaussian_phi(L, N, 13)
+    D = O.diquarks(phi, L)
+    for j in range(N):
+        for i in range(j):
+            q = j * (j - 1) // 2 + i
+            np.testing.assert_allclose(D[q], np.cross(phi[i], phi[j]), rtol=1e-13, atol=1e-13)
+
+
 # ------------------------------------------------------------------- symmetries
 
 def test_baryon_antisymmetric_under_every_swap_and_zero_on_repeats():

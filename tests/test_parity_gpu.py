@@ -1,0 +1,216 @@
+"""GPU parity: the CUDA path against the FP64 oracle, element by element.
+
+Relative Frobenius error per output (B and M separately) and the worst
+per-(t,p) slice, bounded by 1e-5 for the FP32 and split-precision paths and
+by the stated per-mode bound for single-term FP16/BF16.
+"""
+import numpy as np
+import pytest
+
+from helpers import ensure_built, rel_frob, tol_for, worst_slice
+from oracle import oracle as O
+from paper_2510_26313_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+SPLIT_MODES = ["fp32"]
+ALL_MODES = SPLIT_MODES
+
+
+@pytest.fixture(scope="module")
+def laph():
+    ensure_built()
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2510_26313_gb300 import binding
+    return binding
+
+
+def _run(laph, phi_h, L, mom, mode):
+    import torch
+    phi = torch.from_numpy(phi_h).cuda()
+    B = laph.baryon_blocks(phi, L, mom, mode=mode) if phi_h.shape[1] >= 3 else None
+    M = laph.meson_blocks(phi, L, mom, mode=mode)
+    torch.cuda.synchronize()
+    return (B.cpu().numpy() if B is not None else None), M.cpu().numpy()
+
+
+def _oracle(phi_h, L, mom):
+    Bs = [O.baryon_blocks(phi_h[t], L, mom) for t in range(phi_h.shape[0])] if phi_h.shape[1] >= 3 else None
+    Ms = [O.meson_blocks(phi_h[t], L, mom) for t in range(phi_h.shape[0])]
+    return (np.stack(Bs) if Bs is not None else None), np.stack(Ms)
+
+
+CASES = [
+    # (L, T, N, momenta, instance): shapes chosen to span several tiles and ragged tails
+    (8, 1, 16, np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], dtype=np.int32), 1),   # the L=8, N=16 plain case
+    (5, 2, 13, synth.momentum_shell(1), 2),                                       # V=125: ragged site chunks
+    (6, 1, 40, synth.momentum_shell(2), 3),                                       # several row/column tiles
+    (4, 1, 3, synth.momentum_shell(0), 4),                                        # one triple
+    (7, 1, 70, np.array([[0, 0, 0], [2, -1, 3]], dtype=np.int32), 5),             # N > 64: more row tiles
+]
+
+
+@pytest.mark.parametrize("mode", ALL_MODES)
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_blocks_match_oracle(laph, mode, case):
+    L, T, N, mom, inst = CASES[case]
+    phi_h = synth.random_phi(L, N, T=T, instance=inst)
+    B, M = _run(laph, phi_h, L, mom, mode)
+    rB, rM = _oracle(phi_h, L, mom)
+    tol = tol_for(mode)
+    eB, eM = rel_frob(B, rB), rel_frob(M, rM)
+    print(f"mode={mode} L={L} N={N} P={len(mom)}: rel B {eB:.2e} M {eM:.2e}")
+    assert eB <= tol and eM <= tol
+    assert worst_slice(B, rB, 2) <= 4 * tol and worst_slice(M, rM, 2) <= 4 * tol
+
+
+@pytest.mark.parametrize("mode", SPLIT_MODES)
+def test_medium_config_two_timeslices(laph, mode):
+    """L=24, N=32, 7 momenta (|n|^2 <= 1): two timeslices of the medium configuration."""
+    L, N = 24, 32
+    mom = synth.momentum_shell(1)
+    phi_h = synth.random_phi(L, N, T=2, instance=0)
+    B, M = _run(laph, phi_h, L, mom, mode)
+    rB, rM = _oracle(phi_h, L, mom)
+    eB, eM = rel_frob(B, rB), rel_frob(M, rM)
+    print(f"medium mode={mode}: rel B {eB:.2e} M {eM:.2e}")
+    assert eB <= 1e-5 and eM <= 1e-5
+
+
+def test_meson_only_small_N(laph):
+    L = 4
+    mom = synth.momentum_shell(1)
+    for N in (1, 2):
+        phi_h = synth.random_phi(L, N, T=1, instance=10 + N)
+        import torch
+        M = laph.meson_blocks(torch.from_numpy(phi_h).cuda(), L, mom, mode="fp32").cpu().numpy()
+        assert rel_frob(M[0], O.meson_blocks(phi_h[0], L, mom)) <= 1e-5
+
+
+def test_baryon_rejects_N_below_3(laph):
+    import torch
+    phi = torch.from_numpy(synth.random_phi(4, 2, T=1)).cuda()
+    with pytest.raises(laph.LaphError) as e:
+        laph.baryon_blocks(phi, 4, synth.momentum_shell(0), mode="fp32")
+    assert e.value.status == laph.LAPH_ERR_ARG
+
+
+def test_phase_table_matches_oracle(laph):
+    for L, n2 in [(5, 2), (8, 4), (12, 1)]:
+        mom = synth.momentum_shell(n2)
+        got = laph.phase_table(L, mom).cpu().numpy()
+        np.testing.assert_allclose(got, O.phase_table(L, mom), rtol=0, atol=4e-16)
+
+
+def test_diquarks_match_oracle(laph):
+    import torch
+    for L, N, T in [(4, 7, 2), (5, 6, 1)]:           # V even (16-byte stores) and V odd
+        phi_h = synth.random_phi(L, N, T=T, instance=20 + L)
+        D = laph.diquarks(torch.from_numpy(phi_h).cuda(), L).cpu().numpy()
+        for t in range(T):
+            ref = O.diquarks(phi_h[t], L)
+            assert rel_frob(D[t], ref) <= 1e-6
+
+
+def test_dense_fill_is_exact(laph):
+    import torch
+    N, P, T = 9, 4, 2
+    rng = np.random.default_rng(3)
+    packed = rng.standard_normal((T, P, N * (N - 1) * (N - 2) // 6)) + 1j * rng.standard_normal(
+        (T, P, N * (N - 1) * (N - 2) // 6))
+    dense = laph.baryon_dense(torch.from_numpy(packed).cuda(), N).cpu().numpy()
+    for t in range(T):
+        assert np.array_equal(dense[t], O.baryon_dense(packed[t], N))
+
+
+def test_plan_ragged_batch_matches_oracle(laph):
+    """Several instances of different L, N, P and T in one plan execution."""
+    import torch
+    specs = [(4, 2, 5, synth.momentum_shell(1)), (6, 1, 11, synth.momentum_shell(0)),
+             (5, 3, 8, synth.momentum_shell(2)), (3, 1, 20, np.array([[1, 1, 1], [0, 0, 0]], dtype=np.int32))]
+    for mode in SPLIT_MODES:
+        plan = laph.Plan(specs, mode=mode)
+        phis_h = [synth.random_phi(L, N, T=T, instance=40 + n) for n, (L, T, N, _) in enumerate(specs)]
+        phis = [torch.from_numpy(p).cuda() for p in phis_h]
+        Bs, Ms = plan.alloc_outputs()
+        ws = plan.alloc_workspace()
+        plan.execute(phis, Bs, Ms, ws)
+        torch.cuda.synchronize()
+        assert plan.device_status() == laph.LAPH_OK
+        for n, (L, T, N, mom) in enumerate(specs):
+            rB, rM = _oracle(phis_h[n], L, mom)
+            assert rel_frob(Bs[n].cpu().numpy(), rB) <= 1e-5
+            assert rel_frob(Ms[n].cpu().numpy(), rM) <= 1e-5
+        plan.close()
+
+
+def test_plan_execute_is_capturable_in_a_cuda_graph(laph):
+    import torch
+    L, T, N = 6, 2, 12
+    mom = synth.momentum_shell(1)
+    phi_h = synth.random_phi(L, N, T=T, instance=60)
+    for mode in SPLIT_MODES:
+        plan = laph.Plan([(L, T, N, mom)], mode=mode)
+        phi = torch.from_numpy(phi_h).cuda()
+        Bs, Ms = plan.alloc_outputs()
+        ws = plan.alloc_workspace()
+        s = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            plan.execute([phi], Bs, Ms, ws, stream=s)
+        Bs[0].zero_()
+        Ms[0].zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        rB, rM = _oracle(phi_h, L, mom)
+        assert rel_frob(Bs[0].cpu().numpy(), rB) <= 1e-5
+        assert rel_frob(Ms[0].cpu().numpy(), rM) <= 1e-5
+        plan.close()
+
+
+def test_execute_host_buffers(laph):
+    import torch
+    L, T, N = 5, 2, 9
+    mom = synth.momentum_shell(1)
+    phi_h = synth.random_phi(L, N, T=T, instance=61)
+    plan = laph.Plan([(L, T, N, mom)], mode=SPLIT_MODES[0])
+    ws = torch.empty(plan.host_workspace_size(), dtype=torch.uint8, device="cuda")
+    Bh = np.zeros((T, len(mom), N * (N - 1) * (N - 2) // 6), dtype=np.complex128)
+    Mh = np.zeros((T, len(mom), N, N), dtype=np.complex128)
+    plan.execute_host([phi_h], [Bh], [Mh], ws)
+    rB, rM = _oracle(phi_h, L, mom)
+    assert rel_frob(Bh, rB) <= 1e-5 and rel_frob(Mh, rM) <= 1e-5
+    plan.close()
+
+
+def test_invariances_at_size(laph):
+    """L=16, N=32: SU(3) rotation leaves B, M unchanged; a translation multiplies them by
+    exp(+2 pi i n.a/L); orthonormal vectors give M[p=0] = 1."""
+    import torch
+    L, N = 16, 32
+    V = L ** 3
+    mom = synth.momentum_shell(1)
+    phi_h = synth.random_phi(L, N, T=1, instance=70)
+    rng = np.random.default_rng(9)
+    z = rng.standard_normal((V, 3, 3)) + 1j * rng.standard_normal((V, 3, 3))
+    q, r = np.linalg.qr(z)
+    d = np.diagonal(r, axis1=1, axis2=2)
+    U = q * (d / np.abs(d))[:, None, :]
+    U = U / (np.linalg.det(U) ** (1 / 3))[:, None, None]
+    rot = np.einsum("xab,tnxb->tnxa", U, phi_h.astype(np.complex128)).astype(np.complex64)
+    a = np.array([3, 0, 5])
+    x = np.arange(V)
+    c = np.stack([x % L, (x // L) % L, x // (L * L)], axis=1)
+    src = ((c + a) % L) @ np.array([1, L, L * L])
+    shifted = np.ascontiguousarray(phi_h[:, :, src, :])
+    fac = np.exp(2j * np.pi * (mom @ a) / L)
+    for mode in SPLIT_MODES:
+        B0, M0 = _run(laph, phi_h, L, mom, mode)
+        B1, M1 = _run(laph, rot, L, mom, mode)
+        B2, M2 = _run(laph, shifted, L, mom, mode)
+        assert rel_frob(B1, B0) <= 2e-5 and rel_frob(M1, M0) <= 2e-5
+        assert rel_frob(B2, fac[None, :, None] * B0) <= 2e-5
+        assert rel_frob(M2, fac[None, :, None, None] * M0) <= 2e-5
+        np.testing.assert_allclose(M0[0, 0], np.eye(N), atol=2e-6)
