@@ -38,8 +38,13 @@ bool is_tc_mode(int mode) { return mode >= LAPH_MODE_TC_F16X3 && mode <= LAPH_MO
 
 constexpr int MAX_N = 4096;
 constexpr int MAX_P = 4096;
-constexpr int MAX_L = 1024;
+constexpr int MAX_L = 512;
 constexpr int32_t MAX_MOM = 1 << 20;
+// Sites summed between the reductions of partial sums: FP32 CUDA-core sums
+// (round to nearest) on the FP32 path; tensor-core FP32 accumulation, whose
+// error grows linearly with the number of additions, on the split path.
+constexpr int SIMT_DEFAULT_CHUNK = 1024;
+constexpr int TC_DEFAULT_CHUNK = 128;
 
 }  // namespace
 
@@ -59,7 +64,8 @@ struct laph_plan {
     long long n_tiles = 0;
     int *d_status = nullptr;
     int tile_rows = 0, tile_cols = 0, chunk_sites = 0, grid = 0;
-    size_t ws_bytes = 0, off_maxbits = 0, off_counter = 0;
+    int max_staged = 0, max_P = 0;
+    size_t ws_bytes = 0, off_maxbits = 0, off_counter = 0, ws_zero_bytes = 0;
     // LAPH_PLAN_TIMING: ring of event pairs around the contraction launches
     static constexpr int RING = 256;
     std::vector<cudaEvent_t> ev_begin, ev_end;
@@ -182,7 +188,7 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
     const bool tc = is_tc_mode(mode);
     p->tile_rows = tc ? laph::TC_TR : laph::SIMT_TR;
     p->tile_cols = tc ? laph::TC_TC : laph::SIMT_TC;
-    p->chunk_sites = tc ? 2048 : 1024;
+    p->chunk_sites = tc ? TC_DEFAULT_CHUNK : SIMT_DEFAULT_CHUNK;
 
     // ---- per-instance descriptors and phase tables
     long long phase_total = 0;
@@ -197,6 +203,8 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
         d.N = I.N;
         d.P = I.n_mom;
         d.V = (long long)I.L * I.L * I.L;
+        d.Vs = d.V + (d.V & 1);
+        d.pad_off = -1;
         d.n_trip = laph::binom3(I.N);
         d.mes_rows = skipM ? 0 : I.N;
         d.pair_rows = skipB ? 0 : (int)laph::binom2(I.N);
@@ -211,7 +219,7 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
         p->outB_elems.push_back(skipB ? 0 : (long long)I.T * I.n_mom * d.n_trip);
         p->outM_elems.push_back(skipM ? 0 : (long long)I.T * I.n_mom * I.N * I.N);
         phase_off[n] = phase_total;
-        phase_total += (long long)I.n_mom * d.V;
+        phase_total += (long long)I.n_mom * d.Vs;
     }
     p->total_ts = ts;
 
@@ -228,6 +236,7 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
     } while (0)
 
     PCK(cudaMalloc((void **)&p->d_phase, sizeof(float2) * phase_total));
+    PCK(cudaMemset(p->d_phase, 0, sizeof(float2) * phase_total));
     {
         int32_t *d_mom = nullptr;
         PCK(cudaMalloc((void **)&d_mom, sizeof(int32_t) * 3 * MAX_P));
@@ -264,13 +273,30 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
                 laph::pair_of(row0 - d.mes_rows, i, j);
                 jmin = j;
             }
+            // contiguous range of vectors used by the rows of this tile
+            int v_lo = d.N, v_hi = -1;
+            for (int g = row0; g < std::min(row0 + TR, d.rows); g++) {
+                if (g < d.mes_rows) {
+                    v_lo = std::min(v_lo, g);
+                    v_hi = std::max(v_hi, g);
+                } else {
+                    int i, j;
+                    laph::pair_of(g - d.mes_rows, i, j);
+                    v_lo = std::min(v_lo, i);
+                    v_hi = std::max(v_hi, j);
+                }
+            }
+            const int nv = v_hi - v_lo + 1;
             for (int col0 = 0; col0 < d.cols; col0 += TC) {
                 const int nc = std::min(TC, d.cols - col0);
-                const int kmax = (col0 + nc - 1) / d.P;
+                const int kmin = col0 / d.P, kmax = (col0 + nc - 1) / d.P;
                 if (jmin >= 0 && kmax <= jmin) continue;
-                one.push_back(TileDev{n, 0, row0, col0});
+                const int nk = kmax - kmin + 1;
+                p->max_staged = std::max(p->max_staged, nv + nk);
+                one.push_back(TileDev{n, 0, row0, col0, v_lo, nv, kmin, nk, nc, 0, 0, 0});
             }
         }
+        p->max_P = std::max(p->max_P, d.P);
         for (int t = 0; t < d.T; t++)
             for (TileDev u : one) {
                 u.t = t;
@@ -278,6 +304,10 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
             }
     }
     p->n_tiles = (long long)tiles.size();
+    if (tc && (p->max_staged > laph::TC_MAX_STAGED || p->max_P > laph::TC_MAX_P)) {
+        free_plan(p);
+        return LAPH_ERR_UNSUPPORTED;
+    }
     if (p->n_tiles > 0) {
         PCK(cudaMalloc((void **)&p->d_tiles, sizeof(TileDev) * tiles.size()));
         PCK(cudaMemcpy(p->d_tiles, tiles.data(), sizeof(TileDev) * tiles.size(), cudaMemcpyHostToDevice));
@@ -291,7 +321,17 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
         p->grid = sms;
         p->off_maxbits = 0;
         p->off_counter = ((sizeof(unsigned) * p->total_ts + 255) / 256) * 256;
-        p->ws_bytes = p->off_counter + 256;
+        size_t off = p->off_counter + 256;
+        p->ws_zero_bytes = off;
+        for (int n = 0; n < n_inst; n++) {
+            InstDev &d = p->h_inst[n];
+            if (d.V & 1) {
+                d.pad_off = (long long)off;
+                off += (((size_t)d.T * d.N * d.Vs * 3 * sizeof(float2) + 255) / 256) * 256;
+            }
+        }
+        p->ws_bytes = off;
+        PCK(cudaMemcpy(p->d_inst, p->h_inst.data(), sizeof(InstDev) * n_inst, cudaMemcpyHostToDevice));
     } else {
         p->grid = 0;
         p->ws_bytes = 0;
@@ -333,7 +373,7 @@ int laph_plan_set_chunk_sites(laph_plan *plan, int chunk_sites)
 {
     if (!plan || chunk_sites < 0 || chunk_sites > (1 << 24)) return LAPH_ERR_ARG;
     const bool tc = is_tc_mode(plan->mode);
-    if (chunk_sites == 0) chunk_sites = tc ? 2048 : 1024;
+    if (chunk_sites == 0) chunk_sites = tc ? TC_DEFAULT_CHUNK : SIMT_DEFAULT_CHUNK;
     plan->chunk_sites = chunk_sites;
     return LAPH_OK;
 }
@@ -348,7 +388,12 @@ static int launch_batch(laph_plan *p, void *workspace, cudaStream_t s)
         char *ws = (char *)workspace;
         unsigned *maxbits = (unsigned *)(ws + p->off_maxbits);
         unsigned long long *counter = (unsigned long long *)(ws + p->off_counter);
-        CK(cudaMemsetAsync(ws, 0, p->ws_bytes, s));
+        CK(cudaMemsetAsync(ws, 0, p->ws_zero_bytes, s));
+        for (int n = 0; n < p->n_inst; n++)
+            if (p->h_inst[n].pad_off >= 0) {
+                e = laph::launch_pad_phi(p->d_inst, n, p->h_inst[n], s);
+                if (e != cudaSuccess) return cuda_fail(e, "pad_phi");
+            }
         std::vector<long long> elems(p->n_inst);
         for (int n = 0; n < p->n_inst; n++) elems[n] = p->phi_elems[n] / p->h_T[n];
         e = laph::launch_scale_max(p->d_inst, p->n_inst, p->h_ts_base.data(), p->h_T.data(), elems.data(), maxbits, s);
@@ -358,6 +403,8 @@ static int launch_batch(laph_plan *p, void *workspace, cudaStream_t s)
         cfg.terms = (p->mode == LAPH_MODE_TC_F16X3 || p->mode == LAPH_MODE_TC_BF16X3) ? 3 : 1;
         cfg.chunk_sites = p->chunk_sites;
         cfg.grid = p->grid;
+        cfg.max_staged = p->max_staged;
+        cfg.max_P = p->max_P;
         cfg.debug_stall = (p->flags & LAPH_PLAN_DEBUG_STALL) ? 1 : 0;
         if (timing) CK(cudaEventRecord(p->ev_begin[slot], s));
         e = laph::launch_tc(p->d_inst, p->d_tiles, p->n_tiles, maxbits, counter, cfg, p->d_status, s);
@@ -414,8 +461,11 @@ int laph_plan_execute(laph_plan *plan, const void *const *phi, void *const *out_
     CK(cudaGetDevice(&cur));
     if (cur != plan->device) return LAPH_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    if (is_tc_mode(plan->mode))
+        for (int n = 0; n < plan->n_inst; n++)
+            if (((uintptr_t)phi[n]) % 16) return LAPH_ERR_ARG;  // 16-byte vector loads
     cudaError_t e = laph::launch_set_pointers(plan->d_inst, 0, plan->n_inst, phi, needB ? out_B : nullptr,
-                                              needM ? out_M : nullptr, s);
+                                              needM ? out_M : nullptr, workspace, s);
     if (e != cudaSuccess) return cuda_fail(e, "set_pointers");
     return launch_batch(plan, workspace, s);
 }
@@ -456,7 +506,7 @@ int laph_plan_execute_host(laph_plan *plan, const void *const *phi_host, void *c
     }
     CK(cudaGetLastError());
     cudaError_t e = laph::launch_set_pointers(plan->d_inst, 0, plan->n_inst, dphi.data(), needB ? dB.data() : nullptr,
-                                              needM ? dM.data() : nullptr, s);
+                                              needM ? dM.data() : nullptr, ws, s);
     if (e != cudaSuccess) return cuda_fail(e, "set_pointers");
     int rc = launch_batch(plan, ws, s);
     if (rc != LAPH_OK) return rc;

@@ -19,8 +19,12 @@ struct InstDev {
     const float2 *phi;   // [T][N][V][3]
     double2 *outB;       // [T][P][C(N,3)]
     double2 *outM;       // [T][P][N][N]
-    const float2 *phase; // [P][V], FP32 rounding of the FP64 phase
+    const float2 *phase; // [P][Vs], FP32 rounding of the FP64 phase
+    const float2 *phi_tc;// phi as the tensor-core kernel reads it: [T][N][Vs][3], 16-byte aligned vectors
+    float2 *phi_pad;     // workspace copy used when V is odd (Vs = V + 1), else null
+    long long pad_off;   // byte offset of phi_pad in the workspace, -1 when V is even
     long long V;
+    long long Vs;        // site stride of phi_tc and of the phase table: V rounded up to even
     long long n_trip;    // C(N,3)
     int L, T, N, P;
     int mes_rows;        // N, or 0 when mesons are skipped
@@ -31,9 +35,15 @@ struct InstDev {
     int pad_;
 };
 
-// One unit of work: a (row tile, column tile) of one timeslice.
+// One unit of work: a (row tile, column tile) of one timeslice.  v_lo and nv
+// give the contiguous range of vector indices the tile's rows use (the
+// tensor-core path stages exactly these vectors in shared memory).
 struct TileDev {
     int inst, t, row0, col0;
+    int v_lo, nv;        // vectors used by the rows: [v_lo, v_lo + nv)
+    int k_lo, nk;        // vectors used by the columns: [k_lo, k_lo + nk)
+    int ncols;           // valid columns of the tile
+    int pad0, pad1, pad2;
 };
 
 __host__ __device__ inline long long binom2(long long n) { return n * (n - 1) / 2; }
@@ -76,11 +86,12 @@ __device__ __forceinline__ float2 cross_c(const float2 *u, const float2 *v, int 
 cudaError_t launch_phase_table(int L, const int32_t *d_mom, int P, double2 *out64, float2 *out32,
                                cudaStream_t s);
 cudaError_t launch_set_pointers(InstDev *d_inst, int first, int count, const void *const *phi,
-                                void *const *outB, void *const *outM, cudaStream_t s);
+                                void *const *outB, void *const *outM, void *workspace, cudaStream_t s);
 cudaError_t launch_scale_max(const InstDev *d_inst, int n_inst, const int *h_ts_base, const int *h_T,
                              const long long *h_elems, unsigned *d_maxbits, cudaStream_t s);
 cudaError_t launch_diquarks(const float2 *phi, int L, int T, int N, float2 *out, cudaStream_t s);
 cudaError_t launch_dense_fill(const double2 *packed, int T, int N, int P, double2 *dense, cudaStream_t s);
+cudaError_t launch_pad_phi(const InstDev *d_inst, int inst, const InstDev &h, cudaStream_t s);
 
 // laph_simt.cu
 struct SimtConfig {
@@ -95,12 +106,16 @@ cudaError_t launch_simt(const InstDev *d_inst, const TileDev *d_tiles, long long
 struct TcConfig {
     int elem;          // 0 = FP16 hi/lo, 1 = BF16 hi/lo
     int terms;         // 3 (split) or 1 (plain)
-    int chunk_sites;   // sites per FP32 accumulation chunk (multiple of the stage)
+    int chunk_sites;   // sites accumulated by the tensor core between FP32 drains
     int grid;          // persistent CTAs
+    int max_staged;    // largest number of staged vectors (nv + nk) of any tile
+    int max_P;         // largest momentum count of any instance
     int debug_stall;   // test hook
 };
 constexpr int TC_TR = 128;   // tile rows (UMMA M)
-constexpr int TC_TC = 128;   // tile columns (complex), UMMA N = 2 * TC_TC real
+constexpr int TC_TC = 96;    // tile columns (complex), UMMA N = 2 * TC_TC real
+constexpr int TC_MAX_STAGED = 160;  // staged vectors (rows' + columns') per tile
+constexpr int TC_MAX_P = 64;    // momenta per instance supported by the kernel
 cudaError_t launch_tc(const InstDev *d_inst, const TileDev *d_tiles, long long n_tiles,
                       const unsigned *d_maxbits, unsigned long long *d_counter, const TcConfig &cfg,
                       int *d_status, cudaStream_t s);

@@ -10,7 +10,7 @@ namespace laph {
 // ph_p(x) = exp(-2 pi i r / L), r = (n_p . x) mod L in [0, L), evaluated in
 // FP64 with sincospi on the exactly reduced integer argument (momentum
 // projection of section "Innovations"/"QUDA").
-__global__ void phase_table_kernel(int L, const int32_t *__restrict__ mom, int P, long long V,
+__global__ void phase_table_kernel(int L, const int32_t *__restrict__ mom, int P, long long V, long long Vs,
                                    double2 *__restrict__ out64, float2 *__restrict__ out32)
 {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -23,16 +23,17 @@ __global__ void phase_table_kernel(int L, const int32_t *__restrict__ mom, int P
     double s, c;
     sincospi(-2.0 * (double)r / (double)L, &s, &c);
     if (out64) out64[idx] = make_double2(c, s);
-    if (out32) out32[idx] = make_float2((float)c, (float)s);
+    if (out32) out32[p * Vs + x] = make_float2((float)c, (float)s);
 }
 
 cudaError_t launch_phase_table(int L, const int32_t *d_mom, int P, double2 *out64, float2 *out32, cudaStream_t s)
 {
     const long long V = (long long)L * L * L;
+    const long long Vs = V + (V & 1);
     const long long n = (long long)P * V;
     const int bs = 256;
     const long long nb = (n + bs - 1) / bs;
-    phase_table_kernel<<<(unsigned)nb, bs, 0, s>>>(L, d_mom, P, V, out64, out32);
+    phase_table_kernel<<<(unsigned)nb, bs, 0, s>>>(L, d_mom, P, V, Vs, out64, out32);
     return cudaGetLastError();
 }
 
@@ -42,6 +43,7 @@ cudaError_t launch_phase_table(int L, const int32_t *d_mom, int P, double2 *out6
 constexpr int PTR_BATCH = 64;
 struct PtrBatch {
     int first, count;
+    char *ws;
     const void *phi[PTR_BATCH];
     void *outB[PTR_BATCH];
     void *outM[PTR_BATCH];
@@ -55,14 +57,22 @@ __global__ void set_pointers_kernel(InstDev *d_inst, PtrBatch b)
         I.phi = (const float2 *)b.phi[n];
         I.outB = (double2 *)b.outB[n];
         I.outM = (double2 *)b.outM[n];
+        if (I.pad_off >= 0 && b.ws) {
+            I.phi_pad = (float2 *)(b.ws + I.pad_off);
+            I.phi_tc = I.phi_pad;
+        } else {
+            I.phi_pad = nullptr;
+            I.phi_tc = I.phi;
+        }
     }
 }
 
 cudaError_t launch_set_pointers(InstDev *d_inst, int first, int count, const void *const *phi, void *const *outB,
-                                void *const *outM, cudaStream_t s)
+                                void *const *outM, void *workspace, cudaStream_t s)
 {
     for (int base = 0; base < count; base += PTR_BATCH) {
         PtrBatch b;
+        b.ws = (char *)workspace;
         b.first = first + base;
         b.count = count - base < PTR_BATCH ? count - base : PTR_BATCH;
         for (int n = 0; n < b.count; n++) {
@@ -117,6 +127,30 @@ cudaError_t launch_scale_max(const InstDev *d_inst, int n_inst, const int *h_ts_
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// ---------------------------------------------------------------- padding
+// For odd V the tensor-core kernel reads a copy of phi with one zero site
+// appended to every vector, so that every vector starts 16-byte aligned.
+__global__ void pad_phi_kernel(const InstDev *__restrict__ d_inst, int inst)
+{
+    const InstDev &I = d_inst[inst];
+    const long long nvec = (long long)I.T * I.N;
+    const long long per = I.Vs * 3;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nvec * per;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long v = e / per, k = e - v * per;
+        I.phi_pad[e] = k < I.V * 3 ? I.phi[v * I.V * 3 + k] : make_float2(0.f, 0.f);
+    }
+}
+
+cudaError_t launch_pad_phi(const InstDev *d_inst, int inst, const InstDev &h, cudaStream_t s)
+{
+    const long long n = (long long)h.T * h.N * h.Vs * 3;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    pad_phi_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_inst, inst);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- K-b

@@ -109,7 +109,7 @@ simt_kernel(const InstDev *__restrict__ insts, const TileDev *__restrict__ tiles
             float2 o[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
             if (xin && bk[m] >= 0) {
                 const float2 *w = phit + ((long long)bk[m] * V + x) * 3;
-                const float2 phv = __ldg(ph + (long long)bp[m] * V + x);
+                const float2 phv = __ldg(ph + (long long)bp[m] * I.Vs + x);
 #pragma unroll
                 for (int c = 0; c < 3; c++) o[c] = cmulf(phv, __ldg(w + c));
             }

@@ -213,4 +213,4 @@ def test_invariances_at_size(laph):
         assert rel_frob(B1, B0) <= 2e-5 and rel_frob(M1, M0) <= 2e-5
         assert rel_frob(B2, fac[None, :, None] * B0) <= 2e-5
         assert rel_frob(M2, fac[None, :, None, None] * M0) <= 2e-5
-        np.testing.assert_allclose(M0[0, 0], np.eye(N), atol=2e-6)
+        np.testing.assert_allclose(M0[0, 0], np.eye(N), atol=2e-6 if mode == "fp32" else 1e-5)
