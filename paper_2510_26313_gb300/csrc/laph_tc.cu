@@ -94,15 +94,17 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+// Waits up to about `hint_ns` for the phase with the given parity to
+// complete; the warp is suspended meanwhile instead of spinning.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity, uint32_t hint_ns = 20000u)
 {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
         : "memory");
     return ok != 0;
 }
@@ -259,28 +261,24 @@ struct Ctx {
 };
 
 // Warp-wide bounded wait (every lane calls it; the result is warp-uniform).
+// Each try_wait suspends the warp until the phase completes or about 20 us
+// pass; between those wake-ups the abort flag and the time limit are checked.
 __device__ __forceinline__ bool warp_wait(const Ctx &c, uint64_t *bar, uint32_t parity)
 {
-    long long t0 = 0;
-    bool started = false;
+    if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+    const long long t0 = clock64();
     while (true) {
-        const bool ok = mbar_try_wait(bar, parity);
-        if (__all_sync(0xffffffffu, ok)) return true;
+        if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
         const int ab = *(volatile int *)&c.S->abort;
         if (__any_sync(0xffffffffu, ab != 0)) return false;
-        if (!started) {
-            t0 = clock64();
-            started = true;
-        } else {
-            int expired = (clock64() - t0) > WAIT_LIMIT;
-            expired = __shfl_sync(0xffffffffu, expired, 0);
-            if (expired) {
-                if (c.lane == 0) {
-                    *(volatile int *)&c.S->abort = 1;
-                    atomicOr(c.status, STATUS_TIMEOUT);
-                }
-                return false;
+        int expired = (clock64() - t0) > WAIT_LIMIT;
+        expired = __shfl_sync(0xffffffffu, expired, 0);
+        if (expired) {
+            if (c.lane == 0) {
+                *(volatile int *)&c.S->abort = 1;
+                atomicOr(c.status, STATUS_TIMEOUT);
             }
+            return false;
         }
     }
 }
@@ -390,7 +388,9 @@ template <int ELEM, int TERMS>
 __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
 {
     extern __shared__ uint8_t smem_raw[];
-    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // align to 1024 bytes by offsetting the __shared__ array itself, so that
+    // the compiler keeps every derived pointer in the shared address space
+    uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     uint8_t *bstage = smem;
     uint8_t *stage_buf = smem + kp.nb * STAGE_BYTES;
     Shared *S = reinterpret_cast<Shared *>(stage_buf + kp.nstg * kp.stg_bytes);
