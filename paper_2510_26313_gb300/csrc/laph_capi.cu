@@ -60,11 +60,12 @@ struct laph_plan {
     std::vector<int> h_T, h_ts_base;
     InstDev *d_inst = nullptr;
     float2 *d_phase = nullptr;
+    float2 *d_phase_blk = nullptr;
     TileDev *d_tiles = nullptr;
     long long n_tiles = 0;
     int *d_status = nullptr;
     int tile_rows = 0, tile_cols = 0, chunk_sites = 0, grid = 0;
-    int max_staged = 0, max_P = 0;
+    int max_staged = 0, max_P = 0, max_phb = 0;
     size_t ws_bytes = 0, off_maxbits = 0, off_counter = 0, ws_zero_bytes = 0;
     // LAPH_PLAN_TIMING: ring of event pairs around the contraction launches
     static constexpr int RING = 256;
@@ -144,6 +145,7 @@ static void free_plan(laph_plan *p)
     if (!p) return;
     cudaFree(p->d_inst);
     cudaFree(p->d_phase);
+    cudaFree(p->d_phase_blk);
     cudaFree(p->d_tiles);
     cudaFree(p->d_status);
     for (cudaEvent_t e : p->ev_begin) cudaEventDestroy(e);
@@ -204,7 +206,9 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
         d.P = I.n_mom;
         d.V = (long long)I.L * I.L * I.L;
         d.Vs = d.V + (d.V & 1);
-        d.pad_off = -1;
+        d.blk_off = -1;
+        d.nblk = (int)((d.V + laph::TC_BS - 1) / laph::TC_BS);
+        d.phb_stride = ((I.n_mom * laph::TC_PHROW * 8 + 15) / 16) * 2;
         d.n_trip = laph::binom3(I.N);
         d.mes_rows = skipM ? 0 : I.N;
         d.pair_rows = skipB ? 0 : (int)laph::binom2(I.N);
@@ -325,10 +329,34 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
         p->ws_zero_bytes = off;
         for (int n = 0; n < n_inst; n++) {
             InstDev &d = p->h_inst[n];
-            if (d.V & 1) {
-                d.pad_off = (long long)off;
-                off += (((size_t)d.T * d.N * d.Vs * 3 * sizeof(float2) + 255) / 256) * 256;
-            }
+            d.blk_off = (long long)off;
+            off += (((size_t)d.T * d.nblk * d.N * laph::TC_SLOT * sizeof(float2) + 255) / 256) * 256;
+            p->max_phb = std::max(p->max_phb, d.phb_stride);
+        }
+        // phase tables in the site-blocked layout (plan-owned)
+        long long phb_total = 0;
+        std::vector<long long> phb_off(n_inst);
+        for (int n = 0; n < n_inst; n++) {
+            phb_off[n] = phb_total;
+            phb_total += (long long)p->h_inst[n].nblk * p->h_inst[n].phb_stride;
+        }
+        PCK(cudaMalloc((void **)&p->d_phase_blk, sizeof(float2) * phb_total));
+        int32_t *d_mom = nullptr;
+        PCK(cudaMalloc((void **)&d_mom, sizeof(int32_t) * 3 * MAX_P));
+        for (int n = 0; n < n_inst && rc == LAPH_OK; n++) {
+            const laph_instance &I = inst[n];
+            InstDev &d = p->h_inst[n];
+            e = cudaMemcpy(d_mom, I.momenta, sizeof(int32_t) * 3 * I.n_mom, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = laph::launch_phase_blocks(I.L, d_mom, I.n_mom, d.nblk, d.phb_stride, p->d_phase_blk + phb_off[n], 0);
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) rc = cuda_fail(e, "phase blocks");
+            d.phase_blk = p->d_phase_blk + phb_off[n];
+        }
+        cudaFree(d_mom);
+        if (rc != LAPH_OK) {
+            free_plan(p);
+            return rc;
         }
         p->ws_bytes = off;
         PCK(cudaMemcpy(p->d_inst, p->h_inst.data(), sizeof(InstDev) * n_inst, cudaMemcpyHostToDevice));
@@ -389,22 +417,21 @@ static int launch_batch(laph_plan *p, void *workspace, cudaStream_t s)
         unsigned *maxbits = (unsigned *)(ws + p->off_maxbits);
         unsigned long long *counter = (unsigned long long *)(ws + p->off_counter);
         CK(cudaMemsetAsync(ws, 0, p->ws_zero_bytes, s));
-        for (int n = 0; n < p->n_inst; n++)
-            if (p->h_inst[n].pad_off >= 0) {
-                e = laph::launch_pad_phi(p->d_inst, n, p->h_inst[n], s);
-                if (e != cudaSuccess) return cuda_fail(e, "pad_phi");
-            }
         std::vector<long long> elems(p->n_inst);
         for (int n = 0; n < p->n_inst; n++) elems[n] = p->phi_elems[n] / p->h_T[n];
         e = laph::launch_scale_max(p->d_inst, p->n_inst, p->h_ts_base.data(), p->h_T.data(), elems.data(), maxbits, s);
         if (e != cudaSuccess) return cuda_fail(e, "scale_max");
+        for (int n = 0; n < p->n_inst; n++) {
+            e = laph::launch_blockify(p->d_inst, n, p->h_inst[n], maxbits, s);
+            if (e != cudaSuccess) return cuda_fail(e, "blockify");
+        }
         laph::TcConfig cfg;
         cfg.elem = (p->mode == LAPH_MODE_TC_BF16X3 || p->mode == LAPH_MODE_TC_BF16) ? 1 : 0;
         cfg.terms = (p->mode == LAPH_MODE_TC_F16X3 || p->mode == LAPH_MODE_TC_BF16X3) ? 3 : 1;
         cfg.chunk_sites = p->chunk_sites;
         cfg.grid = p->grid;
         cfg.max_staged = p->max_staged;
-        cfg.max_P = p->max_P;
+        cfg.max_phb = p->max_phb;
         cfg.debug_stall = (p->flags & LAPH_PLAN_DEBUG_STALL) ? 1 : 0;
         if (timing) CK(cudaEventRecord(p->ev_begin[slot], s));
         e = laph::launch_tc(p->d_inst, p->d_tiles, p->n_tiles, maxbits, counter, cfg, p->d_status, s);
@@ -440,7 +467,7 @@ int laph_plan_launches_per_execute(const laph_plan *plan, int *n)
     if (!plan || !n) return LAPH_ERR_ARG;
     const int ptr_launches = (plan->n_inst + 63) / 64;
     if (is_tc_mode(plan->mode))
-        *n = ptr_launches + plan->n_inst /* scale */ + 1 /* contraction */;
+        *n = ptr_launches + 2 * plan->n_inst /* scale, blockify */ + 1 /* contraction */;
     else
         *n = ptr_launches + (int)((plan->n_tiles + 0x7ffffffeLL) / 0x7fffffffLL);
     return LAPH_OK;
@@ -461,9 +488,6 @@ int laph_plan_execute(laph_plan *plan, const void *const *phi, void *const *out_
     CK(cudaGetDevice(&cur));
     if (cur != plan->device) return LAPH_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    if (is_tc_mode(plan->mode))
-        for (int n = 0; n < plan->n_inst; n++)
-            if (((uintptr_t)phi[n]) % 16) return LAPH_ERR_ARG;  // 16-byte vector loads
     cudaError_t e = laph::launch_set_pointers(plan->d_inst, 0, plan->n_inst, phi, needB ? out_B : nullptr,
                                               needM ? out_M : nullptr, workspace, s);
     if (e != cudaSuccess) return cuda_fail(e, "set_pointers");

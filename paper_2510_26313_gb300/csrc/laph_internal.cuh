@@ -16,24 +16,34 @@ constexpr int STATUS_CHECK = 2;
 // [mes_rows, mes_rows + pair_rows) are diquark rows, pair q = row - mes_rows
 // in colex order q = C(j,2) + i.  Column space: col = k * P + p.
 struct InstDev {
-    const float2 *phi;   // [T][N][V][3]
-    double2 *outB;       // [T][P][C(N,3)]
-    double2 *outM;       // [T][P][N][N]
-    const float2 *phase; // [P][Vs], FP32 rounding of the FP64 phase
-    const float2 *phi_tc;// phi as the tensor-core kernel reads it: [T][N][Vs][3], 16-byte aligned vectors
-    float2 *phi_pad;     // workspace copy used when V is odd (Vs = V + 1), else null
-    long long pad_off;   // byte offset of phi_pad in the workspace, -1 when V is even
+    const float2 *phi;       // [T][N][V][3]
+    double2 *outB;           // [T][P][C(N,3)]
+    double2 *outM;           // [T][P][N][N]
+    const float2 *phase;     // [P][Vs], FP32 rounding of the FP64 phase (FP32 path)
+    const float2 *phase_blk; // tensor-core path: per site block, P rows of TC_PHROW entries (row stride TC_PHROW)
+    float2 *phi_blk;         // tensor-core path: scaled, site-blocked copy of phi in the workspace
     long long V;
-    long long Vs;        // site stride of phi_tc and of the phase table: V rounded up to even
-    long long n_trip;    // C(N,3)
+    long long Vs;            // V rounded up to even: row stride of `phase`
+    long long n_trip;        // C(N,3)
+    long long blk_off;       // byte offset of phi_blk in the workspace (-1: none)
     int L, T, N, P;
-    int mes_rows;        // N, or 0 when mesons are skipped
-    int pair_rows;       // C(N,2), or 0 when baryons are skipped
-    int rows;            // mes_rows + pair_rows
-    int cols;            // N * P
-    int ts_base;         // index of (this instance, t = 0) among all timeslices of the batch
+    int mes_rows;            // N, or 0 when mesons are skipped
+    int pair_rows;           // C(N,2), or 0 when baryons are skipped
+    int rows;                // mes_rows + pair_rows
+    int cols;                // N * P
+    int ts_base;             // index of (this instance, t = 0) among all timeslices of the batch
+    int nblk;                // site blocks: ceil(V / TC_BS)
+    int phb_stride;          // float2 entries per site block of phase_blk (P * TC_PHROW rounded up to 16 bytes)
     int pad_;
 };
+
+// Site-blocked layout of the tensor-core path.  phi_blk[t][b][n][TC_SLOT]:
+// entry 3*o + c of slot (b, n) is 2^s phi_n^c(x = TC_BS*b + o) (zero past V),
+// the last two entries are padding.  All vectors of one block are contiguous,
+// so the rows' (or columns') vectors of a tile arrive with one bulk copy.
+constexpr int TC_BS = 8;                      // sites per block
+constexpr int TC_SLOT = 3 * TC_BS + 2;        // complex entries per (block, vector): 208 bytes
+constexpr int TC_PHROW = TC_BS + 3;           // complex entries per (block, momentum): 88 bytes
 
 // One unit of work: a (row tile, column tile) of one timeslice.  v_lo and nv
 // give the contiguous range of vector indices the tile's rows use (the
@@ -87,11 +97,23 @@ cudaError_t launch_phase_table(int L, const int32_t *d_mom, int P, double2 *out6
                                cudaStream_t s);
 cudaError_t launch_set_pointers(InstDev *d_inst, int first, int count, const void *const *phi,
                                 void *const *outB, void *const *outM, void *workspace, cudaStream_t s);
+// Power-of-two exponent s with max|phi| * 2^s in [0.5, 1), from the FP32 bits of max|phi|.
+__host__ __device__ inline int scale_exp(unsigned maxbits)
+{
+    if (maxbits == 0) return 0;
+    int E = (int)((maxbits >> 23) & 0xff);
+    if (E == 0) E = 1;
+    int s = 126 - E;
+    return s > 100 ? 100 : (s < -100 ? -100 : s);
+}
 cudaError_t launch_scale_max(const InstDev *d_inst, int n_inst, const int *h_ts_base, const int *h_T,
                              const long long *h_elems, unsigned *d_maxbits, cudaStream_t s);
 cudaError_t launch_diquarks(const float2 *phi, int L, int T, int N, float2 *out, cudaStream_t s);
 cudaError_t launch_dense_fill(const double2 *packed, int T, int N, int P, double2 *dense, cudaStream_t s);
-cudaError_t launch_pad_phi(const InstDev *d_inst, int inst, const InstDev &h, cudaStream_t s);
+cudaError_t launch_blockify(const InstDev *d_inst, int inst, const InstDev &h, const unsigned *d_maxbits,
+                            cudaStream_t s);
+cudaError_t launch_phase_blocks(int L, const int32_t *d_mom, int P, int nblk, int phb_stride, float2 *out,
+                                cudaStream_t s);
 
 // laph_simt.cu
 struct SimtConfig {
@@ -109,7 +131,7 @@ struct TcConfig {
     int chunk_sites;   // sites accumulated by the tensor core between FP32 drains
     int grid;          // persistent CTAs
     int max_staged;    // largest number of staged vectors (nv + nk) of any tile
-    int max_P;         // largest momentum count of any instance
+    int max_phb;       // largest phase-block stride (float2 entries) of any instance
     int debug_stall;   // test hook
 };
 constexpr int TC_TR = 128;   // tile rows (UMMA M)

@@ -57,13 +57,7 @@ __global__ void set_pointers_kernel(InstDev *d_inst, PtrBatch b)
         I.phi = (const float2 *)b.phi[n];
         I.outB = (double2 *)b.outB[n];
         I.outM = (double2 *)b.outM[n];
-        if (I.pad_off >= 0 && b.ws) {
-            I.phi_pad = (float2 *)(b.ws + I.pad_off);
-            I.phi_tc = I.phi_pad;
-        } else {
-            I.phi_pad = nullptr;
-            I.phi_tc = I.phi;
-        }
+        I.phi_blk = (I.blk_off >= 0 && b.ws) ? (float2 *)(b.ws + I.blk_off) : nullptr;
     }
 }
 
@@ -129,27 +123,75 @@ cudaError_t launch_scale_max(const InstDev *d_inst, int n_inst, const int *h_ts_
     return cudaSuccess;
 }
 
-// ---------------------------------------------------------------- padding
-// For odd V the tensor-core kernel reads a copy of phi with one zero site
-// appended to every vector, so that every vector starts 16-byte aligned.
-__global__ void pad_phi_kernel(const InstDev *__restrict__ d_inst, int inst)
+// ---------------------------------------------------------------- site blocks
+// Scaled, site-blocked copy of phi for the tensor-core path:
+// phi_blk[t][b][n][e] = 2^s_t phi[t][n][8b + e/3][e%3] for e < 24 (zero past V),
+// e = 24, 25 padding.  Memory bound: one read of phi, one write of the copy.
+__global__ void blockify_kernel(const InstDev *__restrict__ d_inst, int inst, const unsigned *__restrict__ maxbits)
 {
     const InstDev &I = d_inst[inst];
-    const long long nvec = (long long)I.T * I.N;
-    const long long per = I.Vs * 3;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nvec * per;
-         e += (long long)gridDim.x * blockDim.x) {
-        const long long v = e / per, k = e - v * per;
-        I.phi_pad[e] = k < I.V * 3 ? I.phi[v * I.V * 3 + k] : make_float2(0.f, 0.f);
+    const long long total = (long long)I.T * I.nblk * I.N * TC_SLOT;
+    const long long V = I.V;
+    for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < total; o += (long long)gridDim.x * blockDim.x) {
+        const long long chunk = o / TC_SLOT;
+        const int e = (int)(o - chunk * TC_SLOT);
+        const int n = (int)(chunk % I.N);
+        const long long tb = chunk / I.N;
+        const int b = (int)(tb % I.nblk);
+        const int t = (int)(tb / I.nblk);
+        const long long x = (long long)TC_BS * b + e / 3;
+        float2 v = make_float2(0.f, 0.f);
+        if (e < 3 * TC_BS && x < V) {
+            const float sc = __int_as_float((127 + scale_exp(maxbits[I.ts_base + t])) << 23);
+            const float2 f = __ldg(I.phi + (((long long)t * I.N + n) * V + x) * 3 + e % 3);
+            v = make_float2(f.x * sc, f.y * sc);
+        }
+        I.phi_blk[o] = v;
     }
 }
 
-cudaError_t launch_pad_phi(const InstDev *d_inst, int inst, const InstDev &h, cudaStream_t s)
+cudaError_t launch_blockify(const InstDev *d_inst, int inst, const InstDev &h, const unsigned *d_maxbits, cudaStream_t s)
 {
-    const long long n = (long long)h.T * h.N * h.Vs * 3;
+    const long long n = (long long)h.T * h.nblk * h.N * TC_SLOT;
     long long blocks = (n + 255) / 256;
-    if (blocks > 152 * 32) blocks = 152 * 32;
-    pad_phi_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_inst, inst);
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    blockify_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_inst, inst, d_maxbits);
+    return cudaGetLastError();
+}
+
+// Phase table in the site-blocked layout: out[b * phb_stride + p * TC_PHROW + o]
+// = ph_p(8b + o) for o < 8 and 8b + o < V, zero elsewhere (FP64 sincospi of the
+// exactly reduced argument, rounded to FP32).
+__global__ void phase_blocks_kernel(int L, const int32_t *__restrict__ mom, int P, long long V, int nblk, int phb_stride,
+                                    float2 *__restrict__ out)
+{
+    const long long total = (long long)nblk * phb_stride;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long b = idx / phb_stride;
+        const int w = (int)(idx - b * phb_stride);
+        const int p = w / TC_PHROW, o = w - p * TC_PHROW;
+        const long long x = (long long)TC_BS * b + o;
+        float2 v = make_float2(0.f, 0.f);
+        if (p < P && o < TC_BS && x < V) {
+            const long long x0 = x % L, x1 = (x / L) % L, x2 = x / ((long long)L * L);
+            long long r = ((long long)mom[3 * p] * x0 + (long long)mom[3 * p + 1] * x1 + (long long)mom[3 * p + 2] * x2) % L;
+            if (r < 0) r += L;
+            double sn, cs;
+            sincospi(-2.0 * (double)r / (double)L, &sn, &cs);
+            v = make_float2((float)cs, (float)sn);
+        }
+        out[idx] = v;
+    }
+}
+
+cudaError_t launch_phase_blocks(int L, const int32_t *d_mom, int P, int nblk, int phb_stride, float2 *out, cudaStream_t s)
+{
+    const long long V = (long long)L * L * L;
+    const long long n = (long long)nblk * phb_stride;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    phase_blocks_kernel<<<(unsigned)blocks, 256, 0, s>>>(L, d_mom, P, V, nblk, phb_stride, out);
     return cudaGetLastError();
 }
 

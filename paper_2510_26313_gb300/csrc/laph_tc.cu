@@ -9,33 +9,33 @@
 // K; every complex column becomes two real B rows,
 //   re-row [Psi_re, -Psi_im]  ->  C_re,    im-row [Psi_im, Psi_re]  ->  C_im.
 //
-// Precision: phi is rescaled by an exact power of two per timeslice; every
-// operand value v is split into hi = RN16(v), lo = RN16(v - hi) (FP16 or
-// BF16); the tensor core accumulates hi*hi + hi*lo + lo*hi (hi*hi only in the
-// plain modes) in FP32.  The tensor core's FP32 accumulation does not round
-// to nearest, so its error grows with the number of additions; the
-// accumulator is therefore drained every `chunk_stages` K stages into a
-// second tensor-memory region of FP32 running sums kept by CUDA cores with
-// round-to-nearest, and at the end of a tile the sums are scaled back and
-// written to the complex128 output in FP64.
+// Precision: the operands are built from a copy of phi rescaled by an exact
+// power of two per timeslice; every operand value v is split into
+// hi = RN16(v), lo = RN16(v - hi) (FP16 or BF16); the tensor core
+// accumulates hi*hi + hi*lo + lo*hi (hi*hi only in the plain modes) in FP32.
+// Its FP32 accumulation does not round to nearest, so its error grows with
+// the number of additions; the accumulator is drained every `chunk_stages`
+// K stages into a second tensor-memory region of FP32 running sums kept by
+// CUDA cores with round-to-nearest, and at the end of a tile the sums are
+// scaled back and written to the complex128 output in FP64.
 //
 // Tile: 128 rows x 96 complex columns (UMMA M = 128, N = 192), K stage = 32
 // complex entries (one 128-byte swizzled row of FP16 per operand row).
 // Tensor memory (512 columns): ACC [0,192) | SUM [192,384) | A slots 2 x 64.
-// Shared memory: NB B stages (hi+lo, 48 KB each) and 2 staging buffers that
-// hold, per stage, the 12-site windows of every vector the tile's rows use
-// and the phases of those sites.
+// Shared memory: NB B stages (hi+lo, 48 KB each) and a ring of NR site-block
+// buffers, each holding, for one block of TC_BS sites, the block slots of the
+// tile's row vectors, of its column vectors and the block's phase rows --
+// three bulk copies from the site-blocked, pre-scaled copy of phi.
 //
-// Warp roles (512 threads, persistent CTAs, static tile order):
-//   0-3   A producers: thread = tile row = TMEM lane; reads its vectors'
-//         windows from the staging buffer, forms the 32 K entries of the
-//         stage (diquark or conj(phi)), splits and tcgen05.st's them;
-//   4-9   B producers: (column, 4-entry K group) units; phi_k from global
-//         memory with coalesced loads, phase from the staging buffer;
-//         writes hi/lo words in the 128B-swizzled K-major layout;
-//   10-13 epilogue: drains ACC into SUM, writes the output at tile end;
-//   14    loader: cp.async of the staging windows, completion on an mbarrier;
-//   15    TMEM allocation and single-thread MMA issue.
+// Warp roles (704 threads, persistent CTAs, static tile order):
+//   0-7   A producers: two warps per TMEM lane quadrant, each forms 16 of the
+//         stage's 32 K entries of its row (diquark or conj(phi)), splits and
+//         tcgen05.st's them;
+//   8-15  B producers: (column, 4-entry K group) units; Psi from the block
+//         buffers; hi/lo words in the 128B-swizzled K-major layout;
+//   16-19 epilogue: drains ACC into SUM, writes the output at tile end;
+//   20    loader: bulk copies of the site blocks, completion on mbarriers;
+//   21    TMEM allocation and single-thread MMA issue.
 // Every wait on an mbarrier is bounded; on expiry the CTA records
 // STATUS_TIMEOUT, raises a shared abort flag and all roles return.
 #include <cuda_bf16.h>
@@ -46,20 +46,22 @@
 namespace laph {
 namespace {
 
-constexpr int NTHREADS = 512;
-constexpr int WARP_B0 = 4;
-constexpr int N_BWARPS = 6;
-constexpr int WARP_E0 = 10;
-constexpr int WARP_LOAD = 14;
-constexpr int WARP_MMA = 15;
+constexpr int NTHREADS = 704;
+constexpr int WARP_B0 = 8;
+constexpr int N_AWARPS = 8;
+constexpr int N_BWARPS = 8;
+constexpr int B_UNITS = 3;                    // (column, K group) units per B producer thread: 96 x 8 / 256
+constexpr int WARP_E0 = 16;
+constexpr int WARP_LOAD = 20;
+constexpr int WARP_MMA = 21;
 constexpr int KSTAGE = 32;                    // complex K entries per stage (= 64 real)
+constexpr int KHALF = 16;                     // K entries per A producer warp per stage
 constexpr int B_ROWS = 2 * TC_TC;             // real B rows per tile (192)
 constexpr int B_BYTES = B_ROWS * 128;         // one of hi/lo
 constexpr int STAGE_BYTES = 2 * B_BYTES;      // hi + lo
-constexpr int WIN_SITES = 14;                 // staged sites per stage (from the even site <= x0)
-constexpr int WIN = 3 * WIN_SITES;            // staged complex entries per vector
-constexpr int VEC_STRIDE = WIN * 8;           // 336 B = 84 words: LDS.128 of 8 consecutive slots hit distinct banks
-constexpr int PH_STRIDE = WIN_SITES * 8;      // 112 B = 28 words, likewise
+constexpr int SLOT_BYTES = TC_SLOT * 8;       // 208 B = 52 words: LDS.128 of 8 consecutive slots hit distinct banks
+constexpr int PHROW_BYTES = TC_PHROW * 8;     // 88 B = 22 words: LDS.64 of 16 consecutive rows hit distinct banks
+constexpr int MAX_NB = 3, MAX_NR = 6;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t ACC_COL = 0;
 constexpr uint32_t SUM_COL = 192;
@@ -68,12 +70,13 @@ constexpr uint32_t A_SLOT_COLS = 64;          // 32 columns hi + 32 columns lo
 constexpr long long WAIT_LIMIT = 4000000000LL; // cycles (about 2 s at the top clock)
 
 static_assert(TC_TR == 128 && TC_TC == 96, "layout assumes 128 x 96 tiles");
+static_assert(TC_BS == 8, "block arithmetic assumes 8-site blocks");
 static_assert(A_COL + 2 * A_SLOT_COLS == TMEM_COLS, "tensor memory budget");
 
 struct Shared {
-    uint64_t stg_full[3], stg_empty[3];
+    uint64_t blk_full[MAX_NR], blk_empty[MAX_NR];
     uint64_t a_full[2], a_empty[2];
-    uint64_t b_full[3], b_empty[3];
+    uint64_t b_full[MAX_NB], b_empty[MAX_NB];
     uint64_t acc_full, acc_empty;
     uint64_t done;
     uint32_t tmem_base;
@@ -181,6 +184,32 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32
         : "memory");
 }
 
+__device__ __forceinline__ void tmem_st2(uint32_t taddr, uint32_t v0, uint32_t v1)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(taddr), "r"(v0), "r"(v1) : "memory");
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
 {
     asm volatile(
@@ -240,15 +269,6 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
     }
 }
 
-// Power-of-two exponent s with max|phi| * 2^s in [0.5, 1).
-__device__ __forceinline__ int scale_exp(unsigned maxbits)
-{
-    if (maxbits == 0) return 0;
-    int E = (int)((maxbits >> 23) & 0xff);
-    if (E == 0) E = 1;
-    int s = 126 - E;
-    return s > 100 ? 100 : (s < -100 ? -100 : s);
-}
 __device__ __forceinline__ float pow2f(int s) { return __int_as_float((127 + s) << 23); }
 __device__ __forceinline__ double pow2d(int s) { return __longlong_as_double((long long)(1023 + s) << 52); }
 
@@ -263,7 +283,7 @@ struct Ctx {
 // Warp-wide bounded wait (every lane calls it; the result is warp-uniform).
 // Each try_wait suspends the warp until the phase completes or about 20 us
 // pass; between those wake-ups the abort flag and the time limit are checked.
-__device__ __forceinline__ bool warp_wait(const Ctx &c, uint64_t *bar, uint32_t parity)
+__device__ __noinline__ bool warp_wait(const Ctx &c, uint64_t *bar, uint32_t parity)
 {
     if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
     const long long t0 = clock64();
@@ -283,88 +303,106 @@ __device__ __forceinline__ bool warp_wait(const Ctx &c, uint64_t *bar, uint32_t 
     }
 }
 
+// ------------------------------------------------------------ site blocks
+
+// Which site blocks of the current tile a warp has waited for / released.
+// Every consumer warp waits for and releases every block of a tile in order,
+// so that the ring's phases stay consistent.
+struct BlockTrack {
+    uint32_t gbase;  // global index of the tile's first block
+    int waited, released;
+};
+
+__device__ __noinline__ bool wait_blocks(const Ctx &c, BlockTrack &tr, int upto, int NR)
+{
+    while (tr.waited < upto) {
+        const uint32_t g = tr.gbase + tr.waited;
+        if (!warp_wait(c, &c.S->blk_full[g % NR], (g / NR) & 1u)) return false;
+        tr.waited++;
+    }
+    return true;
+}
+
+__device__ __noinline__ void release_blocks(const Ctx &c, BlockTrack &tr, int upto, int NR)
+{
+    if (upto > tr.waited) upto = tr.waited;
+    if (tr.released < upto) {
+        __syncwarp();
+        while (tr.released < upto) {
+            const uint32_t g = tr.gbase + tr.released;
+            if (c.lane == 0) mbar_arrive(&c.S->blk_empty[g % NR]);
+            tr.released++;
+        }
+    }
+}
+
 // ------------------------------------------------------------ A producer
 
-// Staged windows hold WIN_SITES sites starting at the even site x0e <= x0
-// (x0 = first site of the stage).  OFF = kappa0 - 3*x0e in [0, 5] is the
-// window position of the stage's first K entry, so K entry kl of the stage is
-// window entry kl + OFF.
-
-// Pair row: the stage's K entries from the windows of phi_i (wi) and phi_j
-// (wj), read two sites (three 16-byte loads) at a time.
-template <int ELEM, int OFF>
-__device__ __forceinline__ void a_pair(const float2 *wi, const float2 *wj, float sc2, uint32_t (&hi)[32],
-                                       uint32_t (&lo)[32])
+// Component c of the colour cross product u x v as eight fused operations.
+__device__ __forceinline__ float2 cross8(const float2 *u, const float2 *v, int c)
 {
-#pragma unroll
-    for (int m = 0; m < WIN_SITES / 2; m++) {
-        if (6 * m - OFF > KSTAGE - 1) break;
-        if (6 * m + 5 - OFF < 0) continue;
+    const int a = (c + 1) % 3, b = (c + 2) % 3;
+    float re = u[a].x * v[b].x;
+    re = fmaf(-u[a].y, v[b].y, re);
+    re = fmaf(-u[b].x, v[a].x, re);
+    re = fmaf(u[b].y, v[a].y, re);
+    float im = u[a].x * v[b].y;
+    im = fmaf(u[a].y, v[b].x, im);
+    im = fmaf(-u[b].x, v[a].y, im);
+    im = fmaf(-u[b].y, v[a].x, im);
+    return make_float2(re, im);
+}
+
+// The 16 K entries [ks, ks+16) of a stage for one row, written straight to
+// tensor memory (hi at ta, lo at ta + 32).  Site pairs (2 sites = 6 K entries
+// = three 16-byte loads per vector) pf..pf+3 cover the entries, pf = ks / 6;
+// ks is even, so every pair's entries fall into whole column pairs that are
+// either all inside [0, 16) or all outside.  The loop is kept rolled so that
+// its code stays small.  kind: 2 diquark row, 1 meson row (conj(phi_i)), 0
+// no row (loads suppressed, zeros written).
+template <int ELEM>
+__device__ __forceinline__ void a_half(int kind, int ks, const uint8_t *base0, const uint8_t *base1, int b0,
+                                       int nblk, int si, int sj, uint32_t ta)
+{
+    const int pf = ks / 6;
+#pragma unroll 1
+    for (int m = 0; m < 4; m++) {
+        const int kl0 = 6 * (pf + m) - ks;          // entry index of the pair's first K entry (even)
+        if (kl0 >= KHALF) break;
+        const int xg = 2 * (pf + m);                // first site of the pair
+        const int b = xg >> 3;
+        const bool in = b < nblk && kind != 0;
+        const uint8_t *base = ((b == b0) ? base0 : base1) + (xg & 7) * 24;
+        const float4 *wi = reinterpret_cast<const float4 *>(base + si * SLOT_BYTES);
+        const float4 *wj = reinterpret_cast<const float4 *>(base + sj * SLOT_BYTES);
         float2 u[6], v[6];
 #pragma unroll
         for (int h = 0; h < 3; h++) {
-            const float4 a = *reinterpret_cast<const float4 *>(wi + 6 * m + 2 * h);
-            const float4 b = *reinterpret_cast<const float4 *>(wj + 6 * m + 2 * h);
+            const float4 a = in ? wi[h] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 bb = in ? wj[h] : make_float4(0.f, 0.f, 0.f, 0.f);
             u[2 * h] = make_float2(a.x, a.y);
             u[2 * h + 1] = make_float2(a.z, a.w);
-            v[2 * h] = make_float2(b.x, b.y);
-            v[2 * h + 1] = make_float2(b.z, b.w);
+            v[2 * h] = make_float2(bb.x, bb.y);
+            v[2 * h + 1] = make_float2(bb.z, bb.w);
         }
 #pragma unroll
-        for (int s = 0; s < 2; s++) {
+        for (int e = 0; e < 6; e += 2) {
+            const int kl = kl0 + e;
+            if (kl < 0 || kl >= KHALF) continue;    // uniform over the warp
+            uint32_t h0, l0, h1, l1;
 #pragma unroll
-            for (int c = 0; c < 3; c++) {
-                const int kl = 3 * (2 * m + s) + c - OFF;
-                if (kl < 0 || kl >= KSTAGE) continue;
-                const float2 d = cross_c(u + 3 * s, v + 3 * s, c);
-                split2<ELEM>(d.x * sc2, d.y * sc2, hi[kl], lo[kl]);
+            for (int f = 0; f < 2; f++) {
+                const int q = e + f;
+                const float2 dq = cross8(u + 3 * (q / 3), v + 3 * (q / 3), q % 3);
+                const float2 d = kind == 2 ? dq : make_float2(u[q].x, -u[q].y);   // diquark or conj(phi_i)
+                if (f == 0)
+                    split2<ELEM>(d.x, d.y, h0, l0);
+                else
+                    split2<ELEM>(d.x, d.y, h1, l1);
             }
+            tmem_st2(ta + kl, h0, h1);
+            tmem_st2(ta + 32 + kl, l0, l1);
         }
-    }
-}
-
-// Meson row: conj(phi_i) at window entries kl + OFF.
-template <int ELEM, int OFF>
-__device__ __forceinline__ void a_meson(const float2 *wi, float sc, uint32_t (&hi)[32], uint32_t (&lo)[32])
-{
-#pragma unroll
-    for (int f = OFF / 2; f <= (OFF + KSTAGE - 1) / 2; f++) {
-        const float4 a = *reinterpret_cast<const float4 *>(wi + 2 * f);
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const int kl = 2 * f + h - OFF;
-            if (kl < 0 || kl >= KSTAGE) continue;
-            const float re = h ? a.z : a.x, im = h ? a.w : a.y;
-            split2<ELEM>(re * sc, -im * sc, hi[kl], lo[kl]);
-        }
-    }
-}
-
-template <int ELEM, int OFF>
-__device__ __forceinline__ void produce_a_off(int kind, const float2 *wi, const float2 *wj, float sc,
-                                              uint32_t (&hi)[32], uint32_t (&lo)[32])
-{
-    if (kind == 2)
-        a_pair<ELEM, OFF>(wi, wj, sc * sc, hi, lo);
-    else if (kind == 1)
-        a_meson<ELEM, OFF>(wi, sc, hi, lo);
-    else {
-#pragma unroll
-        for (int kl = 0; kl < KSTAGE; kl++) hi[kl] = lo[kl] = 0u;
-    }
-}
-
-template <int ELEM>
-__device__ __forceinline__ void produce_a(int kind, int off, const float2 *wi, const float2 *wj, float sc,
-                                          uint32_t (&hi)[32], uint32_t (&lo)[32])
-{
-    switch (off) {
-    case 0: produce_a_off<ELEM, 0>(kind, wi, wj, sc, hi, lo); break;
-    case 1: produce_a_off<ELEM, 1>(kind, wi, wj, sc, hi, lo); break;
-    case 2: produce_a_off<ELEM, 2>(kind, wi, wj, sc, hi, lo); break;
-    case 3: produce_a_off<ELEM, 3>(kind, wi, wj, sc, hi, lo); break;
-    case 4: produce_a_off<ELEM, 4>(kind, wi, wj, sc, hi, lo); break;
-    default: produce_a_off<ELEM, 5>(kind, wi, wj, sc, hi, lo); break;
     }
 }
 
@@ -377,10 +415,10 @@ struct KParams {
     int *status;
     int n_tiles;
     int chunk_stages;
-    int stg_bytes;   // bytes of one staging buffer
-    int ph_off;      // offset of the phase rows inside a staging buffer
-    int nb;          // B stage buffers (2 or 3)
-    int nstg;        // staging buffers (2 or 3)
+    int blk_bytes;   // bytes of one site-block buffer
+    int ph_off;      // offset of the phase rows inside a block buffer
+    int nb;          // B stage buffers
+    int nr;          // site-block buffers
     int debug_stall;
 };
 
@@ -392,19 +430,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
     // the compiler keeps every derived pointer in the shared address space
     uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     uint8_t *bstage = smem;
-    uint8_t *stage_buf = smem + kp.nb * STAGE_BYTES;
-    Shared *S = reinterpret_cast<Shared *>(stage_buf + kp.nstg * kp.stg_bytes);
+    uint8_t *bbuf = smem + kp.nb * STAGE_BYTES;
+    Shared *S = reinterpret_cast<Shared *>(bbuf + kp.nr * kp.blk_bytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int NB = kp.nb, NS = kp.nstg;
+    const int NB = kp.nb, NR = kp.nr;
     Ctx c{S, kp.status, lane};
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NS; s++) {
-            mbar_init(&S->stg_full[s], 1);
-            mbar_init(&S->stg_empty[s], 4 + N_BWARPS);
+        for (int s = 0; s < NR; s++) {
+            mbar_init(&S->blk_full[s], 1);
+            mbar_init(&S->blk_empty[s], N_AWARPS + N_BWARPS);
         }
         for (int s = 0; s < 2; s++) {
-            mbar_init(&S->a_full[s], 4);
+            mbar_init(&S->a_full[s], N_AWARPS);
             mbar_init(&S->a_empty[s], 1);
         }
         for (int s = 0; s < NB; s++) {
@@ -428,48 +466,38 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
 
     if (warp == WARP_LOAD) {
         // ---------------------------------------------------------- loader
-        uint32_t g = 0;
+        uint32_t gb = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < kp.n_tiles && ok; tile += gridDim.x) {
             const TileDev td = kp.tiles[tile];
             const InstDev &I = kp.insts[td.inst];
-            const long long Vs = I.Vs;
-            const int K = (int)(3 * I.V);
-            const int P = I.P;
-            const float2 *phit = I.phi_tc + (long long)td.t * I.N * Vs * 3;
-            const int n_st = (K + KSTAGE - 1) / KSTAGE;
-            const int nsl = td.nv + td.nk;
-            for (int st = 0; st < n_st; st++, g++) {
-                const int buf = g % NS;
-                if (!warp_wait(c, &S->stg_empty[buf], ((g / NS) & 1u) ^ 1u)) {
+            const uint32_t bytesA = td.nv * SLOT_BYTES, bytesB = td.nk * SLOT_BYTES;
+            const uint32_t bytesP = (uint32_t)I.phb_stride * 8u;
+            for (int b = 0; b < I.nblk; b++) {
+                const uint32_t g = gb + b;
+                const int slot = g % NR;
+                if (!warp_wait(c, &S->blk_empty[slot], ((g / NR) & 1u) ^ 1u)) {
                     ok = false;
                     break;
                 }
-                uint8_t *base = stage_buf + buf * kp.stg_bytes;
-                const long long x0e = (long long)((st * KSTAGE) / 3) & ~1LL;
-                const int nsite = (int)((Vs - x0e) < WIN_SITES ? (Vs - x0e) : WIN_SITES);  // even
-                const uint32_t vbytes = 24u * nsite, pbytes = 8u * nsite;
-                if (lane == 0) mbar_arrive_expect_tx(&S->stg_full[buf], vbytes * nsl + pbytes * P);
-                __syncwarp();
-                for (int idx = lane; idx < nsl + P; idx += 32) {
-                    if (idx < nsl) {
-                        const int vec = idx < td.nv ? td.v_lo + idx : td.k_lo + (idx - td.nv);
-                        bulk_g2s(base + idx * VEC_STRIDE, phit + ((long long)vec * Vs + x0e) * 3, vbytes,
-                                 &S->stg_full[buf]);
-                    } else {
-                        const int p = idx - nsl;
-                        bulk_g2s(base + kp.ph_off + p * PH_STRIDE, I.phase + (long long)p * Vs + x0e, pbytes,
-                                 &S->stg_full[buf]);
-                    }
+                if (lane == 0) {
+                    uint8_t *base = bbuf + slot * kp.blk_bytes;
+                    const float2 *blk = I.phi_blk + ((long long)td.t * I.nblk + b) * I.N * TC_SLOT;
+                    mbar_arrive_expect_tx(&S->blk_full[slot], bytesA + bytesB + bytesP);
+                    bulk_g2s(base, blk + (long long)td.v_lo * TC_SLOT, bytesA, &S->blk_full[slot]);
+                    bulk_g2s(base + bytesA, blk + (long long)td.k_lo * TC_SLOT, bytesB, &S->blk_full[slot]);
+                    bulk_g2s(base + kp.ph_off, I.phase_blk + (long long)b * I.phb_stride, bytesP, &S->blk_full[slot]);
                 }
+                __syncwarp();
             }
+            gb += I.nblk;
         }
     } else if (warp < WARP_B0) {
         // ---------------------------------------------------------- A producers
-        const int quad = warp & 3;
+        const int quad = warp & 3, half = warp >> 2;
         const int r = quad * 32 + lane;
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
-        uint32_t g = 0;
+        uint32_t g = 0, gb = 0;
         bool stalled = false, ok = true;
         for (int tile = blockIdx.x; tile < kp.n_tiles && ok; tile += gridDim.x) {
             const TileDev td = kp.tiles[tile];
@@ -487,34 +515,28 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
                 }
             }
             const int si = kind ? vi - td.v_lo : 0, sj = kind == 2 ? vj - td.v_lo : 0;
-            const float sc = pow2f(scale_exp(kp.maxbits[I.ts_base + td.t]));
+            const int nblk = I.nblk;
+            BlockTrack tr{gb, 0, 0};
             const int n_st = (K + KSTAGE - 1) / KSTAGE;
             for (int st = 0; st < n_st; st++, g++) {
                 const int sa = g & 1;
-                const int buf = g % NS;
-                if (!warp_wait(c, &S->a_empty[sa], ((g >> 1) & 1u) ^ 1u) ||
-                    !warp_wait(c, &S->stg_full[buf], (g / NS) & 1u)) {
+                const int ks = st * KSTAGE + KHALF * half;
+                const int pf = ks / 6;
+                const int bneed = min(nblk - 1, (2 * pf + 7) >> 3);
+                if (!warp_wait(c, &S->a_empty[sa], ((g >> 1) & 1u) ^ 1u) || !wait_blocks(c, tr, bneed + 1, NR)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const int kap0 = st * KSTAGE;
-                const int off = kap0 - 3 * (((kap0 / 3)) & ~1);
-                const uint8_t *base = stage_buf + buf * kp.stg_bytes;
-                const float2 *wi = reinterpret_cast<const float2 *>(base + si * VEC_STRIDE);
-                const float2 *wj = reinterpret_cast<const float2 *>(base + sj * VEC_STRIDE);
-                uint32_t hi[32], lo[32];
-                produce_a<ELEM>(kind, off, wi, wj, sc, hi, lo);
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&S->stg_empty[buf]);
-                if (kap0 + KSTAGE > K) {  // last stage of the tile: entries past 3V are zero
-#pragma unroll
-                    for (int kl = 0; kl < KSTAGE; kl++)
-                        if (kap0 + kl >= K) hi[kl] = lo[kl] = 0u;
-                }
-                const uint32_t ta = tmem + lane_base + A_COL + (uint32_t)sa * A_SLOT_COLS;
-                tmem_st32(ta, hi);
-                tmem_st32(ta + 32, lo);
+                // buffers of the (at most two) site blocks this half stage reads
+                const int b0 = (2 * pf) >> 3;
+                const int r0 = (int)((tr.gbase + b0) % NR);
+                const uint8_t *base0 = bbuf + r0 * kp.blk_bytes;
+                const uint8_t *base1 = bbuf + (r0 + 1 == NR ? 0 : r0 + 1) * kp.blk_bytes;
+                const uint32_t ta = tmem + lane_base + A_COL + (uint32_t)sa * A_SLOT_COLS + KHALF * half;
+                a_half<ELEM>(kind, ks, base0, base1, b0, nblk, si, sj, ta);
+                // blocks the next stage does not need (sites before its first) are free
+                release_blocks(c, tr, (((st + 1) * KSTAGE) / 3) >> 3, NR);
                 tmem_wait_st();
                 tc_fence_before();
                 __syncwarp();
@@ -522,11 +544,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
                 if (skip) stalled = true;
                 if (lane == 0 && !skip) mbar_arrive(&S->a_full[sa]);
             }
+            if (ok && wait_blocks(c, tr, nblk, NR)) release_blocks(c, tr, nblk, NR);
+            gb += nblk;
         }
     } else if (warp < WARP_E0) {
         // ---------------------------------------------------------- B producers
-        const int tb = (warp - WARP_B0) * 32 + lane;  // 0..191
-        uint32_t g = 0;
+        const int tb = (warp - WARP_B0) * 32 + lane;  // 0..255
+        uint32_t g = 0, gb = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < kp.n_tiles && ok; tile += gridDim.x) {
             const TileDev td = kp.tiles[tile];
@@ -535,13 +559,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
             const int P = I.P;
             const int ncols = td.ncols;
             const int ncols_pad = (ncols + 7) & ~7;
-            const float sc = pow2f(scale_exp(kp.maxbits[I.ts_base + td.t]));
-            // four units per thread: unit u = tb + 192 m -> column cu = u / 8, K group q = u % 8
-            int kslot[4], pp[4], cu[4], qq[4];
-            bool valid[4], write[4];
+            const int nblk = I.nblk;
+            // B_UNITS units per thread: unit u = tb + 256 m -> column cu = u / 8, K group q = u % 8
+            int koff[B_UNITS], poff[B_UNITS], cu[B_UNITS], qq[B_UNITS];
+            bool valid[B_UNITS], write[B_UNITS];
 #pragma unroll
-            for (int m = 0; m < 4; m++) {
-                const int u = tb + 192 * m;
+            for (int m = 0; m < B_UNITS; m++) {
+                const int u = tb + 256 * m;
                 cu[m] = u >> 3;
                 qq[m] = u & 7;
                 valid[m] = cu[m] < ncols;
@@ -551,41 +575,62 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
                     k = (td.col0 + cu[m]) / P;
                     p = td.col0 + cu[m] - k * P;
                 }
-                kslot[m] = td.nv + (k - td.k_lo);
-                pp[m] = p;
+                koff[m] = (td.nv + (k - td.k_lo)) * SLOT_BYTES;
+                poff[m] = kp.ph_off + p * PHROW_BYTES;
             }
+            BlockTrack tr{gb, 0, 0};
             const int n_st = (K + KSTAGE - 1) / KSTAGE;
             for (int st = 0; st < n_st; st++, g++) {
                 const int sb = g % NB;
-                const int buf = g % NS;
-                if (!warp_wait(c, &S->b_empty[sb], ((g / NB) & 1u) ^ 1u) ||
-                    !warp_wait(c, &S->stg_full[buf], (g / NS) & 1u)) {
+                const int kap0 = st * KSTAGE;
+                const int bneed = min(nblk - 1, ((kap0 + KSTAGE - 1) / 3) >> 3);
+                if (!warp_wait(c, &S->b_empty[sb], ((g / NB) & 1u) ^ 1u) || !wait_blocks(c, tr, bneed + 1, NR)) {
                     ok = false;
                     break;
                 }
-                const int kap0 = st * KSTAGE;
-                const int off = kap0 - 3 * (((kap0 / 3)) & ~1);
-                const uint8_t *base = stage_buf + buf * kp.stg_bytes;
+                // buffers of the (at most three) site blocks of this stage; block b
+                // holds K entries [24 b, 24 b + 24)
+                const int b0 = kap0 / 24;
+                const int r0 = (int)((tr.gbase + b0) % NR);
+                const int r1 = r0 + 1 == NR ? 0 : r0 + 1;
+                const int r2 = r1 + 1 == NR ? 0 : r1 + 1;
+                const uint8_t *base0 = bbuf + r0 * kp.blk_bytes, *base1 = bbuf + r1 * kp.blk_bytes,
+                              *base2 = bbuf + r2 * kp.blk_bytes;
                 uint8_t *bhi = bstage + sb * STAGE_BYTES;
                 uint8_t *blo = bhi + B_BYTES;
-#pragma unroll
-                for (int m = 0; m < 4; m++) {
+#pragma unroll 1
+                for (int m = 0; m < B_UNITS; m++) {
                     if (!write[m]) continue;
-                    const float2 *wk = reinterpret_cast<const float2 *>(base + kslot[m] * VEC_STRIDE);
-                    const float2 *wp = reinterpret_cast<const float2 *>(base + kp.ph_off + pp[m] * PH_STRIDE);
-                    const int e0 = 4 * qq[m] + off;  // window entry of this group's first K entry
+                    const int k4 = kap0 + 4 * qq[m];
+                    const int rb = k4 / 24 - b0;        // block of the first entry, relative to b0
+                    int e = k4 - 24 * (b0 + rb);        // entry within the block: 3 * site + colour
+                    const uint8_t *base = rb == 0 ? base0 : (rb == 1 ? base1 : base2);
+                    const uint8_t *nbase = rb == 0 ? base1 : base2;   // next block, if the group crosses
+                    int cc = e % 3;
+                    const uint8_t *pf_ = base + koff[m] + e * 8;          // phi_k entry
+                    const uint8_t *pp_ = base + poff[m] + (e / 3) * 8;    // phase of its site
                     uint32_t rh[4], rl[4], ih[4], il[4];
 #pragma unroll
                     for (int v = 0; v < 4; v++) {
-                        const int e = e0 + v;
                         float2 psi = make_float2(0.f, 0.f);
-                        if (valid[m] && kap0 + 4 * qq[m] + v < K) psi = cmulf(wp[e / 3], wk[e]);
+                        if (valid[m] && k4 + v < K)
+                            psi = cmulf(*reinterpret_cast<const float2 *>(pp_), *reinterpret_cast<const float2 *>(pf_));
                         uint32_t h, l;
-                        split2<ELEM>(psi.x * sc, psi.y * sc, h, l);
+                        split2<ELEM>(psi.x, psi.y, h, l);
                         rh[v] = h ^ 0x80000000u;            // (re, -im)
                         rl[v] = l ^ 0x80000000u;
                         ih[v] = __byte_perm(h, 0, 0x1032);  // (im, re)
                         il[v] = __byte_perm(l, 0, 0x1032);
+                        pf_ += 8;
+                        if (++cc == 3) {
+                            cc = 0;
+                            pp_ += 8;
+                        }
+                        if (++e == 3 * TC_BS) {             // next site block
+                            e = 0;
+                            pf_ = nbase + koff[m];
+                            pp_ = nbase + poff[m];
+                        }
                     }
                     const int n0 = 2 * cu[m];
                     *reinterpret_cast<uint4 *>(bhi + swz(n0, qq[m])) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
@@ -593,12 +638,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
                     *reinterpret_cast<uint4 *>(blo + swz(n0, qq[m])) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
                     *reinterpret_cast<uint4 *>(blo + swz(n0 + 1, qq[m])) = make_uint4(il[0], il[1], il[2], il[3]);
                 }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&S->stg_empty[buf]);
+                release_blocks(c, tr, (((st + 1) * KSTAGE) / 3) >> 3, NR);
                 fence_async_smem();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&S->b_full[sb]);
             }
+            if (ok && wait_blocks(c, tr, nblk, NR)) release_blocks(c, tr, nblk, NR);
+            gb += nblk;
         }
     } else if (warp < WARP_LOAD) {
         // ---------------------------------------------------------- epilogue
@@ -633,17 +679,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
                     break;
                 }
                 tc_fence_after();
-                for (int b = 0; b * 32 < n_real; b++) {
-                    uint32_t va[32], vs[32];
-                    tmem_ld32(tmem + lane_base + ACC_COL + 32u * b, va);
-                    if (ch > 0) tmem_ld32(tmem + lane_base + SUM_COL + 32u * b, vs);
+                for (int b = 0; b * 16 < n_real; b++) {
+                    uint32_t va[16], vs[16];
+                    tmem_ld16(tmem + lane_base + ACC_COL + 16u * b, va);
+                    if (ch > 0) tmem_ld16(tmem + lane_base + SUM_COL + 16u * b, vs);
                     tmem_wait_ld();
                     if (ch > 0) {
 #pragma unroll
-                        for (int e = 0; e < 32; e++)
+                        for (int e = 0; e < 16; e++)
                             va[e] = __float_as_uint(__uint_as_float(va[e]) + __uint_as_float(vs[e]));
                     }
-                    tmem_st32(tmem + lane_base + SUM_COL + 32u * b, va);
+                    tmem_st16(tmem + lane_base + SUM_COL + 16u * b, va);
                 }
                 tmem_wait_st();
                 tc_fence_before();
@@ -653,13 +699,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
             if (!ok) break;
             // tile done: FP32 sums -> FP64 output, scale undone
             const long long tP = (long long)td.t * I.P;
-            for (int b = 0; b * 32 < n_real; b++) {
-                uint32_t v[32];
-                tmem_ld32(tmem + lane_base + SUM_COL + 32u * b, v);
+            for (int b = 0; b * 16 < n_real; b++) {
+                uint32_t v[16];
+                tmem_ld16(tmem + lane_base + SUM_COL + 16u * b, v);
                 tmem_wait_ld();
-#pragma unroll
-                for (int u = 0; u < 16; u++) {
-                    const int cc = 16 * b + u;
+#pragma unroll 1
+                for (int u = 0; u < 8; u++) {
+                    const int cc = 8 * b + u;
                     if (!rvalid || cc >= ncols) continue;
                     const int col = td.col0 + cc;
                     const int k = col / I.P, p = col - k * I.P;
@@ -701,15 +747,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
                 tc_fence_after();
                 if (lane == 0) {
                     const uint32_t a_hi = tmem + A_COL + (uint32_t)sa * A_SLOT_COLS, a_lo = a_hi + 32;
-                    const uint32_t b_hi = smem_u32(bstage + sb * STAGE_BYTES), b_lo = b_hi + B_BYTES;
+                    // descriptor start addresses advance 32 bytes (2 units of 16) per K step
+                    const uint64_t dhi = desc_sw128(smem_u32(bstage + sb * STAGE_BYTES));
+                    const uint64_t dlo = dhi + (uint64_t)(B_BYTES >> 4);
                     const uint32_t d = tmem + ACC_COL;
 #pragma unroll
                     for (int ks = 0; ks < 4; ks++) {
                         const uint32_t acc = (chunk_start && ks == 0) ? 0u : 1u;
-                        mma_ts(d, a_hi + 8 * ks, desc_sw128(b_hi + 32 * ks), idesc, acc);
+                        mma_ts(d, a_hi + 8 * ks, dhi + 2 * ks, idesc, acc);
                         if (TERMS == 3) {
-                            mma_ts(d, a_hi + 8 * ks, desc_sw128(b_lo + 32 * ks), idesc, 1u);
-                            mma_ts(d, a_lo + 8 * ks, desc_sw128(b_hi + 32 * ks), idesc, 1u);
+                            mma_ts(d, a_hi + 8 * ks, dlo + 2 * ks, idesc, 1u);
+                            mma_ts(d, a_lo + 8 * ks, dhi + 2 * ks, idesc, 1u);
                         }
                     }
                     mma_commit(&S->a_empty[sa]);
@@ -734,13 +782,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
     }
 }
 
-int stg_bytes_for(int max_staged, int max_P)
+int blk_bytes_for(int max_staged, int max_phb)
 {
-    const int b = max_staged * VEC_STRIDE + max_P * PH_STRIDE;
+    const int b = max_staged * SLOT_BYTES + max_phb * 8;
     return (b + 127) & ~127;
 }
 
-int smem_for(int nb, int nstg, int stg_bytes) { return nb * STAGE_BYTES + nstg * stg_bytes + (int)sizeof(Shared) + 1024; }
+int smem_for(int nb, int nr, int blk_bytes) { return nb * STAGE_BYTES + nr * blk_bytes + (int)sizeof(Shared) + 1024; }
 
 constexpr int SMEM_LIMIT = 227 * 1024;
 
@@ -756,18 +804,18 @@ cudaError_t launch_one(const InstDev *d_inst, const TileDev *d_tiles, long long 
     kp.n_tiles = (int)n_tiles;
     kp.chunk_stages = (cfg.chunk_sites * 3) / KSTAGE;
     if (kp.chunk_stages < 1) kp.chunk_stages = 1;
-    kp.stg_bytes = stg_bytes_for(cfg.max_staged, cfg.max_P);
-    kp.ph_off = cfg.max_staged * VEC_STRIDE;
+    kp.blk_bytes = blk_bytes_for(cfg.max_staged, cfg.max_phb);
+    kp.ph_off = cfg.max_staged * SLOT_BYTES;
     kp.debug_stall = cfg.debug_stall;
-    // deepest buffering that fits: staging 3 then B stages 3
-    const int choices[4][2] = {{3, 3}, {2, 3}, {3, 2}, {2, 2}};
+    // deepest buffering that fits (a stage reads up to three site blocks)
+    const int choices[5][2] = {{3, 6}, {3, 5}, {3, 4}, {2, 5}, {2, 4}};
     int smem = 0;
     kp.nb = 0;
-    for (int ch = 0; ch < 4; ch++) {
-        const int need = smem_for(choices[ch][0], choices[ch][1], kp.stg_bytes);
+    for (int ch = 0; ch < 5; ch++) {
+        const int need = smem_for(choices[ch][0], choices[ch][1], kp.blk_bytes);
         if (need <= SMEM_LIMIT) {
             kp.nb = choices[ch][0];
-            kp.nstg = choices[ch][1];
+            kp.nr = choices[ch][1];
             smem = need;
             break;
         }
@@ -783,14 +831,14 @@ cudaError_t launch_one(const InstDev *d_inst, const TileDev *d_tiles, long long 
 
 }  // namespace
 
-int tc_smem_bytes() { return smem_for(2, 2, stg_bytes_for(TC_MAX_STAGED, TC_MAX_P)); }
+int tc_smem_bytes() { return smem_for(2, 4, blk_bytes_for(TC_MAX_STAGED, ((TC_MAX_P * TC_PHROW * 8 + 15) / 16) * 2)); }
 
 cudaError_t launch_tc(const InstDev *d_inst, const TileDev *d_tiles, long long n_tiles, const unsigned *d_maxbits,
                       unsigned long long *d_counter, const TcConfig &cfg, int *d_status, cudaStream_t s)
 {
     (void)d_counter;
     if (n_tiles <= 0) return cudaSuccess;
-    if (n_tiles > 0x7fffffffLL || cfg.max_staged > TC_MAX_STAGED || cfg.max_P > TC_MAX_P) return cudaErrorNotSupported;
+    if (n_tiles > 0x7fffffffLL || cfg.max_staged > TC_MAX_STAGED) return cudaErrorNotSupported;
     if (cfg.elem == 0 && cfg.terms == 3) return launch_one<0, 3>(d_inst, d_tiles, n_tiles, d_maxbits, cfg, d_status, s);
     if (cfg.elem == 1 && cfg.terms == 3) return launch_one<1, 3>(d_inst, d_tiles, n_tiles, d_maxbits, cfg, d_status, s);
     if (cfg.elem == 0 && cfg.terms == 1) return launch_one<0, 1>(d_inst, d_tiles, n_tiles, d_maxbits, cfg, d_status, s);
