@@ -206,6 +206,33 @@ LAPH_API int laph_plan_set_chunk_sites(laph_plan *plan, int chunk_sites);
 
 LAPH_API int laph_plan_destroy(laph_plan *plan);
 
+/* ---- allocation-free entry point -------------------------------------- */
+/* The paper has no counterpart to this function: it serves callers that may
+ * not allocate device memory.  It computes B and/or M of one instance with
+ * the FP32 CUDA-core contraction (LAPH_MODE_FP32_SIMT) and allocates
+ * nothing: no cudaMalloc, no cudaFree, no allocating library routine.  Its
+ * scratch (descriptor, momenta, tile table, FP32 phase table) lives in one
+ * file-scope device array of LAPH_NOALLOC_SCRATCH_BYTES bytes, which every
+ * GPU that loads the library holds until the process exits.
+ *   phi    device complex64 [T][N][L^3][3], 8-byte aligned;
+ *   out_B  device complex128 [T][P][C(N,3)] or NULL (baryons skipped);
+ *   out_M  device complex128 [T][P][N][N] or NULL (mesons skipped);
+ *          at least one of them non-NULL, each 16-byte aligned; the caller
+ *          owns both and the outputs need no clearing;
+ *   momenta HOST int32 [n_mom][3], read before the function returns.
+ * Limits: 1 <= n_mom <= 64, N >= 3 when out_B is given, N <= 3 L^3, and the
+ * scratch (about 8 * n_mom * L^3 bytes of phase table plus 48 bytes per
+ * (row tile, column tile, timeslice)) must fit the array: larger inputs
+ * return LAPH_ERR_WORKSPACE before any launch.  Asynchronous on `stream`.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call outside any stream capture.
+ * Every call shares the array and leaves its contents behind; each call
+ * rewrites what it reads, but calls that may overlap on the GPU (different
+ * streams or threads without ordering between them) race on the array. */
+#define LAPH_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+LAPH_API int laph_blocks_noalloc(const void *phi, int L, int T, int N, const int32_t *momenta, int n_mom, void *out_B,
+                                 void *out_M, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

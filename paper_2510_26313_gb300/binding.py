@@ -77,6 +77,7 @@ def lib() -> ctypes.CDLL:
             "laph_plan_kernel_times": (i32, [vp, i32, ctypes.POINTER(ctypes.c_float)]),
             "laph_plan_launches_per_execute": (i32, [vp, ctypes.POINTER(i32)]),
             "laph_plan_destroy": (i32, [vp]),
+            "laph_blocks_noalloc": (i32, [vp, i32, i32, i32, ip32, i32, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -179,6 +180,22 @@ def meson_blocks(phi, L: int, momenta, mode="f16x3", out=None, stream=None):
                                  mom.shape[0], _ptr(out), _mode(mode), _stream(stream))
     _check(rc, "laph_meson_blocks")
     return out
+
+
+def blocks_noalloc(phi, L: int, momenta, out_B, out_M, stream=None):
+    """FP32 B and/or M into caller-owned outputs with no device allocation.
+
+    out_B: complex128 [T][P][C(N,3)] or None; out_M: complex128 [T][P][N][N]
+    or None.  Asynchronous on `stream`; the library's fixed scratch array is
+    shared by all calls, so calls must not overlap on the GPU.
+    """
+    T, N = _check_phi(phi, L)
+    mom = _momenta(momenta)
+    rc = lib().laph_blocks_noalloc(_ptr(phi), L, T, N, mom.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   mom.shape[0], _ptr(out_B) if out_B is not None else None,
+                                   _ptr(out_M) if out_M is not None else None, _stream(stream))
+    _check(rc, "laph_blocks_noalloc")
+    return out_B, out_M
 
 
 class Plan:
