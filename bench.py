@@ -245,7 +245,9 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    kernel_ms = plan.kernel_times(args.steps)
+    n_con = plan.contraction_launches()
+    kernel_ms = plan.kernel_times(args.steps * n_con)
+    operand_ms = plan.operand_times(args.steps * n_con) if args.mode != "fp32" else []
     if world > 1:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -254,7 +256,7 @@ def main():
 
     flops_step = T * flops_per_timeslice(L, N, P)
     value = world * flops_step / (ms / 1e3) / 1e12
-    k_avg = statistics.mean(kernel_ms)
+    k_avg = sum(kernel_ms) / args.steps          # contraction kernel time per step (all chunks)
     achieved = flops_step / (k_avg / 1e3) / 1e12
     peaks, peak_src = measured_peaks()
     tc = args.mode != "fp32"
@@ -264,6 +266,15 @@ def main():
                 "frac": achieved / peak, "traffic": None,
                 "peak_source": f"{peak_src} bf16 dense sustained (cuBLAS); FP16 runs at the bf16 rate",
                 "note": "achieved counts algorithmic flops; the 3-term split executes 3x that on the tensor pipe"}
+        # B-operand stage images: HBM-bound, algorithmic bytes = images written + phi read once
+        n_ct = -(-(N * P) // 96)
+        n_st = -(-(3 * V) // 32)
+        psi_bytes = T * (n_ct * n_st * 49152 + N * V * 3 * 8)
+        o_avg = sum(operand_ms) / args.steps
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        roof["operand_kernel"] = {"name": "psi_kernel", "ms_per_step": o_avg, "bound": "hbm",
+                                  "achieved": psi_bytes / (o_avg / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                                  "frac": psi_bytes / (o_avg / 1e3) / 1e9 / hbm}
     else:
         # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock
         smax = float(peaks.get("sm_max_mhz", 2070.0))

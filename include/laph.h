@@ -90,6 +90,9 @@ extern "C" {
 /* Test hook: one producer warp of the tensor-core kernel skips an arrive, so
  * the consumer's bounded wait expires and LAPH_ERR_TIMEOUT is recorded. */
 #define LAPH_PLAN_DEBUG_STALL 0x10000u
+/* Test hook: every (instance, timeslice) becomes its own chunk of the
+ * tensor-core path, so that small batches exercise the chunked execution. */
+#define LAPH_PLAN_CHUNK_PER_TIMESLICE 0x20000u
 
 /* One independent problem of a (possibly ragged) batch. */
 typedef struct {
@@ -193,9 +196,20 @@ LAPH_API int laph_plan_describe(const laph_plan *plan, int *mode, int *tile_rows
 
 /* Durations in ms of the last n contraction-kernel launches of this plan
  * (oldest first), from the events LAPH_PLAN_TIMING records on the launching
- * stream; waits for those events.  At most 256 launches are kept.  Returns
- * LAPH_ERR_ARG without LAPH_PLAN_TIMING or when fewer than n were recorded. */
+ * stream around each launch; waits for those events.  At most 256 launches
+ * are kept.  Returns LAPH_ERR_ARG without LAPH_PLAN_TIMING or when fewer
+ * than n were recorded. */
 LAPH_API int laph_plan_kernel_times(laph_plan *plan, int n, float *ms);
+
+/* Same for the launches that build the tensor-core path's B operand (the
+ * phased vectors ph_p phi_k, split and laid out as shared-memory stage
+ * images), one per chunk of timeslices.  LAPH_ERR_ARG for the FP32 mode. */
+LAPH_API int laph_plan_operand_times(laph_plan *plan, int n, float *ms);
+
+/* Contraction-kernel launches per laph_plan_execute: the tensor-core path
+ * processes the batch's timeslices in chunks whose B-operand images fit its
+ * workspace (at most 24 GiB), one launch per chunk. */
+LAPH_API int laph_plan_contraction_launches(const laph_plan *plan, int *n);
 
 /* Number of kernels of this library one laph_plan_execute launches. */
 LAPH_API int laph_plan_launches_per_execute(const laph_plan *plan, int *n);

@@ -29,6 +29,7 @@ PLAN_SKIP_M = 0x2
 PLAN_AUTOTUNE = 0x4
 PLAN_TIMING = 0x8
 PLAN_DEBUG_STALL = 0x10000
+PLAN_CHUNK_PER_TIMESLICE = 0x20000
 
 _lib = None
 
@@ -75,6 +76,8 @@ def lib() -> ctypes.CDLL:
                                          ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i64)]),
             "laph_plan_set_chunk_sites": (i32, [vp, i32]),
             "laph_plan_kernel_times": (i32, [vp, i32, ctypes.POINTER(ctypes.c_float)]),
+            "laph_plan_operand_times": (i32, [vp, i32, ctypes.POINTER(ctypes.c_float)]),
+            "laph_plan_contraction_launches": (i32, [vp, ctypes.POINTER(i32)]),
             "laph_plan_launches_per_execute": (i32, [vp, ctypes.POINTER(i32)]),
             "laph_plan_destroy": (i32, [vp]),
             "laph_blocks_noalloc": (i32, [vp, i32, i32, i32, ip32, i32, vp, vp, vp]),
@@ -247,6 +250,18 @@ class Plan:
         arr = (ctypes.c_float * n)()
         _check(lib().laph_plan_kernel_times(self._h, n, arr), "laph_plan_kernel_times")
         return [float(x) for x in arr]
+
+    def operand_times(self, n: int) -> list:
+        """Durations (ms) of the last n B-operand launches of the tensor-core path (needs PLAN_TIMING)."""
+        arr = (ctypes.c_float * n)()
+        _check(lib().laph_plan_operand_times(self._h, n, arr), "laph_plan_operand_times")
+        return [float(x) for x in arr]
+
+    def contraction_launches(self) -> int:
+        """Contraction-kernel launches per execute (one per chunk of timeslices)."""
+        v = ctypes.c_int()
+        _check(lib().laph_plan_contraction_launches(self._h, ctypes.byref(v)), "laph_plan_contraction_launches")
+        return int(v.value)
 
     def launches_per_execute(self) -> int:
         v = ctypes.c_int()

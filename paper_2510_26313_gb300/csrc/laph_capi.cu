@@ -45,6 +45,9 @@ constexpr int32_t MAX_MOM = 1 << 20;
 // error grows linearly with the number of additions, on the split path.
 constexpr int SIMT_DEFAULT_CHUNK = 1024;
 constexpr int TC_DEFAULT_CHUNK = 128;
+// Largest B-operand buffer of the tensor-core path: the timeslices of a batch
+// are processed in chunks whose stage images fit in it.
+constexpr size_t PSI_CAP_BYTES = 24ull << 30;
 
 }  // namespace
 
@@ -60,17 +63,26 @@ struct laph_plan {
     std::vector<int> h_T, h_ts_base;
     InstDev *d_inst = nullptr;
     float2 *d_phase = nullptr;
-    float2 *d_phase_blk = nullptr;
     TileDev *d_tiles = nullptr;
     long long n_tiles = 0;
     int *d_status = nullptr;
     int tile_rows = 0, tile_cols = 0, chunk_sites = 0, grid = 0;
-    int max_staged = 0, max_P = 0, max_phb = 0;
-    size_t ws_bytes = 0, off_maxbits = 0, off_counter = 0, ws_zero_bytes = 0;
+    int max_staged = 0, max_P = 0;
+    size_t ws_bytes = 0, off_maxbits = 0, ws_zero_bytes = 0;
+    // tensor-core path: chunks of (instance, timeslice) units and their B-operand images
+    laph::PsiUnit *d_units = nullptr;
+    struct Chunk {
+        int unit0, n_units;
+        long long n_jobs;
+        long long tile0, n_tiles;
+    };
+    std::vector<Chunk> chunks;
+    size_t off_psi = 0;
     // LAPH_PLAN_TIMING: ring of event pairs around the contraction launches
     static constexpr int RING = 256;
-    std::vector<cudaEvent_t> ev_begin, ev_end;
-    long long n_timed = 0;
+    // (contraction launches; pv_* for the B-operand launches of the tensor-core path)
+    std::vector<cudaEvent_t> ev_begin, ev_end, pv_begin, pv_end;
+    long long n_timed = 0, n_ptimed = 0;
 };
 
 extern "C" {
@@ -145,11 +157,13 @@ static void free_plan(laph_plan *p)
     if (!p) return;
     cudaFree(p->d_inst);
     cudaFree(p->d_phase);
-    cudaFree(p->d_phase_blk);
+    cudaFree(p->d_units);
     cudaFree(p->d_tiles);
     cudaFree(p->d_status);
     for (cudaEvent_t e : p->ev_begin) cudaEventDestroy(e);
     for (cudaEvent_t e : p->ev_end) cudaEventDestroy(e);
+    for (cudaEvent_t e : p->pv_begin) cudaEventDestroy(e);
+    for (cudaEvent_t e : p->pv_end) cudaEventDestroy(e);
     delete p;
 }
 
@@ -208,12 +222,13 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
         d.Vs = d.V + (d.V & 1);
         d.blk_off = -1;
         d.nblk = (int)((d.V + laph::TC_BS - 1) / laph::TC_BS);
-        d.phb_stride = ((I.n_mom * laph::TC_PHROW * 8 + 15) / 16) * 2;
         d.n_trip = laph::binom3(I.N);
         d.mes_rows = skipM ? 0 : I.N;
         d.pair_rows = skipB ? 0 : (int)laph::binom2(I.N);
         d.rows = d.mes_rows + d.pair_rows;
         d.cols = I.N * I.n_mom;
+        d.n_ct = (d.cols + laph::TC_TC - 1) / laph::TC_TC;
+        d.n_st = (int)((3 * d.V + laph::TC_KSTAGE - 1) / laph::TC_KSTAGE);
         d.ts_base = ts;
         p->h_ts_base.push_back(ts);
         p->h_T.push_back(I.T);
@@ -263,52 +278,88 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
     PCK(cudaMalloc((void **)&p->d_status, sizeof(int)));
     PCK(cudaMemset(p->d_status, 0, sizeof(int)));
 
-    // ---- tile table: (instance, t, row tile, column tile), skipping column
+    // ---- tile table: (instance, t, column tile, row tile), skipping column
     // tiles whose every k is <= the smallest j of a diquark-only row tile.
+    // The tensor-core path processes the (instance, t) units in chunks whose
+    // B-operand images fit the Psi buffer; the tiles of one column tile are
+    // consecutive, so the CTAs that share a stage image run side by side.
     std::vector<TileDev> tiles;
+    std::vector<laph::PsiUnit> units;
     const int TR = p->tile_rows, TC = p->tile_cols;
+    size_t psi_total = 0;
+    for (int n = 0; n < n_inst; n++) {
+        const InstDev &d = p->h_inst[n];
+        psi_total += (size_t)d.T * d.n_ct * d.n_st * laph::TC_STAGE_BYTES;
+    }
+    const long long n_chunks_wanted = tc ? (long long)((psi_total + PSI_CAP_BYTES - 1) / PSI_CAP_BYTES) : 1;
+    const size_t psi_target = tc ? (psi_total + n_chunks_wanted - 1) / (size_t)n_chunks_wanted : 0;
+    size_t psi_max = 0;
+    laph_plan::Chunk cur{0, 0, 0, 0, 0};
+    size_t cur_bytes = 0;
     for (int n = 0; n < n_inst; n++) {
         const InstDev &d = p->h_inst[n];
         std::vector<TileDev> one;
-        for (int row0 = 0; row0 < d.rows; row0 += TR) {
-            int jmin = -1;
-            if (row0 >= d.mes_rows) {
-                int i, j;
-                laph::pair_of(row0 - d.mes_rows, i, j);
-                jmin = j;
-            }
-            // contiguous range of vectors used by the rows of this tile
-            int v_lo = d.N, v_hi = -1;
-            for (int g = row0; g < std::min(row0 + TR, d.rows); g++) {
-                if (g < d.mes_rows) {
-                    v_lo = std::min(v_lo, g);
-                    v_hi = std::max(v_hi, g);
-                } else {
+        for (int col0 = 0; col0 < d.cols; col0 += TC) {
+            const int nc = std::min(TC, d.cols - col0);
+            const int kmin = col0 / d.P, kmax = (col0 + nc - 1) / d.P;
+            for (int row0 = 0; row0 < d.rows; row0 += TR) {
+                int jmin = -1;
+                if (row0 >= d.mes_rows) {
                     int i, j;
-                    laph::pair_of(g - d.mes_rows, i, j);
-                    v_lo = std::min(v_lo, i);
-                    v_hi = std::max(v_hi, j);
+                    laph::pair_of(row0 - d.mes_rows, i, j);
+                    jmin = j;
                 }
-            }
-            const int nv = v_hi - v_lo + 1;
-            for (int col0 = 0; col0 < d.cols; col0 += TC) {
-                const int nc = std::min(TC, d.cols - col0);
-                const int kmin = col0 / d.P, kmax = (col0 + nc - 1) / d.P;
                 if (jmin >= 0 && kmax <= jmin) continue;
-                const int nk = kmax - kmin + 1;
-                p->max_staged = std::max(p->max_staged, nv + nk);
-                one.push_back(TileDev{n, 0, row0, col0, v_lo, nv, kmin, nk, nc, 0, 0, 0});
+                // contiguous range of vectors used by the rows of this tile
+                int v_lo = d.N, v_hi = -1;
+                for (int g = row0; g < std::min(row0 + TR, d.rows); g++) {
+                    if (g < d.mes_rows) {
+                        v_lo = std::min(v_lo, g);
+                        v_hi = std::max(v_hi, g);
+                    } else {
+                        int i, j;
+                        laph::pair_of(g - d.mes_rows, i, j);
+                        v_lo = std::min(v_lo, i);
+                        v_hi = std::max(v_hi, j);
+                    }
+                }
+                const int nv = v_hi - v_lo + 1;
+                p->max_staged = std::max(p->max_staged, tc ? nv : nv + (kmax - kmin + 1));
+                const long long psi_ct = (long long)(col0 / TC) * d.n_st * laph::TC_STAGE_BYTES;
+                one.push_back(TileDev{n, 0, row0, col0, v_lo, nv, kmin, kmax - kmin + 1, nc, 0, psi_ct});
             }
         }
         p->max_P = std::max(p->max_P, d.P);
-        for (int t = 0; t < d.T; t++)
+        const size_t unit_bytes = (size_t)d.n_ct * d.n_st * laph::TC_STAGE_BYTES;
+        for (int t = 0; t < d.T; t++) {
+            if (tc) {
+                if (cur.n_units > 0 && (cur_bytes + unit_bytes > psi_target || (flags & LAPH_PLAN_CHUNK_PER_TIMESLICE))) {
+                    p->chunks.push_back(cur);
+                    psi_max = std::max(psi_max, cur_bytes);
+                    cur = laph_plan::Chunk{(int)units.size(), 0, 0, (long long)tiles.size(), 0};
+                    cur_bytes = 0;
+                }
+                units.push_back(laph::PsiUnit{n, t, (long long)cur_bytes, cur.n_jobs});
+                cur.n_units++;
+                cur.n_jobs += (long long)d.n_ct * ((d.n_st + laph::TC_PSI_GROUP - 1) / laph::TC_PSI_GROUP);
+            }
             for (TileDev u : one) {
                 u.t = t;
+                if (tc) u.psi_off += (long long)cur_bytes;
                 tiles.push_back(u);
             }
+            if (tc) {
+                cur.n_tiles += (long long)one.size();
+                cur_bytes += unit_bytes;
+            }
+        }
+    }
+    if (tc && cur.n_units > 0) {
+        p->chunks.push_back(cur);
+        psi_max = std::max(psi_max, cur_bytes);
     }
     p->n_tiles = (long long)tiles.size();
-    if (tc && (p->max_staged > laph::TC_MAX_STAGED || p->max_P > laph::TC_MAX_P)) {
+    if (tc && p->max_staged > laph::TC_MAX_STAGED) {
         free_plan(p);
         return LAPH_ERR_UNSUPPORTED;
     }
@@ -316,48 +367,28 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
         PCK(cudaMalloc((void **)&p->d_tiles, sizeof(TileDev) * tiles.size()));
         PCK(cudaMemcpy(p->d_tiles, tiles.data(), sizeof(TileDev) * tiles.size(), cudaMemcpyHostToDevice));
     }
+    if (!units.empty()) {
+        PCK(cudaMalloc((void **)&p->d_units, sizeof(laph::PsiUnit) * units.size()));
+        PCK(cudaMemcpy(p->d_units, units.data(), sizeof(laph::PsiUnit) * units.size(), cudaMemcpyHostToDevice));
+    }
 
     // ---- workspace layout (tensor-core modes only): per-timeslice max |phi|
-    // bits, then the persistent scheduler's tile counter.
+    // bits (cleared by every execute), the site-blocked copies of phi, then
+    // the B-operand images of one chunk.
     if (tc) {
         int sms = 0;
         PCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
         p->grid = sms;
         p->off_maxbits = 0;
-        p->off_counter = ((sizeof(unsigned) * p->total_ts + 255) / 256) * 256;
-        size_t off = p->off_counter + 256;
+        size_t off = ((sizeof(unsigned) * p->total_ts + 255) / 256) * 256;
         p->ws_zero_bytes = off;
         for (int n = 0; n < n_inst; n++) {
             InstDev &d = p->h_inst[n];
             d.blk_off = (long long)off;
             off += (((size_t)d.T * d.nblk * d.N * laph::TC_SLOT * sizeof(float2) + 255) / 256) * 256;
-            p->max_phb = std::max(p->max_phb, d.phb_stride);
         }
-        // phase tables in the site-blocked layout (plan-owned)
-        long long phb_total = 0;
-        std::vector<long long> phb_off(n_inst);
-        for (int n = 0; n < n_inst; n++) {
-            phb_off[n] = phb_total;
-            phb_total += (long long)p->h_inst[n].nblk * p->h_inst[n].phb_stride;
-        }
-        PCK(cudaMalloc((void **)&p->d_phase_blk, sizeof(float2) * phb_total));
-        int32_t *d_mom = nullptr;
-        PCK(cudaMalloc((void **)&d_mom, sizeof(int32_t) * 3 * MAX_P));
-        for (int n = 0; n < n_inst && rc == LAPH_OK; n++) {
-            const laph_instance &I = inst[n];
-            InstDev &d = p->h_inst[n];
-            e = cudaMemcpy(d_mom, I.momenta, sizeof(int32_t) * 3 * I.n_mom, cudaMemcpyHostToDevice);
-            if (e == cudaSuccess)
-                e = laph::launch_phase_blocks(I.L, d_mom, I.n_mom, d.nblk, d.phb_stride, p->d_phase_blk + phb_off[n], 0);
-            if (e == cudaSuccess) e = cudaDeviceSynchronize();
-            if (e != cudaSuccess) rc = cuda_fail(e, "phase blocks");
-            d.phase_blk = p->d_phase_blk + phb_off[n];
-        }
-        cudaFree(d_mom);
-        if (rc != LAPH_OK) {
-            free_plan(p);
-            return rc;
-        }
+        p->off_psi = off;
+        off += ((psi_max + 255) / 256) * 256;
         p->ws_bytes = off;
         PCK(cudaMemcpy(p->d_inst, p->h_inst.data(), sizeof(InstDev) * n_inst, cudaMemcpyHostToDevice));
     } else {
@@ -367,9 +398,13 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
     if (flags & LAPH_PLAN_TIMING) {
         p->ev_begin.resize(laph_plan::RING, nullptr);
         p->ev_end.resize(laph_plan::RING, nullptr);
+        p->pv_begin.resize(laph_plan::RING, nullptr);
+        p->pv_end.resize(laph_plan::RING, nullptr);
         for (int r = 0; r < laph_plan::RING; r++) {
             PCK(cudaEventCreate(&p->ev_begin[r]));
             PCK(cudaEventCreate(&p->ev_end[r]));
+            PCK(cudaEventCreate(&p->pv_begin[r]));
+            PCK(cudaEventCreate(&p->pv_end[r]));
         }
     }
 #undef PCK
@@ -410,12 +445,10 @@ static int launch_batch(laph_plan *p, void *workspace, cudaStream_t s)
 {
     cudaError_t e;
     const bool timing = !p->ev_begin.empty();
-    const int slot = (int)(p->n_timed % laph_plan::RING);
     if (is_tc_mode(p->mode)) {
         if (!workspace || ((uintptr_t)workspace) % 256) return LAPH_ERR_WORKSPACE;
         char *ws = (char *)workspace;
         unsigned *maxbits = (unsigned *)(ws + p->off_maxbits);
-        unsigned long long *counter = (unsigned long long *)(ws + p->off_counter);
         CK(cudaMemsetAsync(ws, 0, p->ws_zero_bytes, s));
         std::vector<long long> elems(p->n_inst);
         for (int n = 0; n < p->n_inst; n++) elems[n] = p->phi_elems[n] / p->h_T[n];
@@ -431,34 +464,71 @@ static int launch_batch(laph_plan *p, void *workspace, cudaStream_t s)
         cfg.chunk_sites = p->chunk_sites;
         cfg.grid = p->grid;
         cfg.max_staged = p->max_staged;
-        cfg.max_phb = p->max_phb;
         cfg.debug_stall = (p->flags & LAPH_PLAN_DEBUG_STALL) ? 1 : 0;
-        if (timing) CK(cudaEventRecord(p->ev_begin[slot], s));
-        e = laph::launch_tc(p->d_inst, p->d_tiles, p->n_tiles, maxbits, counter, cfg, p->d_status, s);
-        if (e == cudaErrorNotSupported) return LAPH_ERR_UNSUPPORTED;
-        if (e != cudaSuccess) return cuda_fail(e, "tc contraction");
-        if (timing) CK(cudaEventRecord(p->ev_end[slot], s));
+        uint8_t *psi = (uint8_t *)(ws + p->off_psi);
+        for (const laph_plan::Chunk &c : p->chunks) {
+            const int ps = (int)(p->n_ptimed % laph_plan::RING), cs = (int)(p->n_timed % laph_plan::RING);
+            if (timing) CK(cudaEventRecord(p->pv_begin[ps], s));
+            e = laph::launch_psi(p->d_inst, p->d_units + c.unit0, c.n_units, c.n_jobs, maxbits, cfg.elem, psi, s);
+            if (e != cudaSuccess) return cuda_fail(e, "psi");
+            if (timing) {
+                CK(cudaEventRecord(p->pv_end[ps], s));
+                p->n_ptimed++;
+                CK(cudaEventRecord(p->ev_begin[cs], s));
+            }
+            e = laph::launch_tc(p->d_inst, p->d_tiles + c.tile0, c.n_tiles, maxbits, psi, cfg, p->d_status, s);
+            if (e == cudaErrorNotSupported) return LAPH_ERR_UNSUPPORTED;
+            if (e != cudaSuccess) return cuda_fail(e, "tc contraction");
+            if (timing) {
+                CK(cudaEventRecord(p->ev_end[cs], s));
+                p->n_timed++;
+            }
+        }
     } else {
         laph::SimtConfig cfg;
         cfg.chunk_sites = p->chunk_sites;
-        if (timing) CK(cudaEventRecord(p->ev_begin[slot], s));
+        const int cs = (int)(p->n_timed % laph_plan::RING);
+        if (timing) CK(cudaEventRecord(p->ev_begin[cs], s));
         e = laph::launch_simt(p->d_inst, p->d_tiles, p->n_tiles, cfg, p->d_status, s);
         if (e != cudaSuccess) return cuda_fail(e, "simt contraction");
-        if (timing) CK(cudaEventRecord(p->ev_end[slot], s));
+        if (timing) {
+            CK(cudaEventRecord(p->ev_end[cs], s));
+            p->n_timed++;
+        }
     }
-    if (timing) p->n_timed++;
+    return LAPH_OK;
+}
+
+static int ring_times(const std::vector<cudaEvent_t> &b, const std::vector<cudaEvent_t> &e, long long count, int n,
+                      float *ms)
+{
+    if (!ms || n < 1 || b.empty()) return LAPH_ERR_ARG;
+    if (n > laph_plan::RING || n > count) return LAPH_ERR_ARG;
+    for (int q = 0; q < n; q++) {
+        const int slot = (int)((count - n + q) % laph_plan::RING);
+        CK(cudaEventSynchronize(e[slot]));
+        CK(cudaEventElapsedTime(&ms[q], b[slot], e[slot]));
+    }
     return LAPH_OK;
 }
 
 int laph_plan_kernel_times(laph_plan *plan, int n, float *ms)
 {
-    if (!plan || !ms || n < 1 || plan->ev_begin.empty()) return LAPH_ERR_ARG;
-    if (n > laph_plan::RING || n > plan->n_timed) return LAPH_ERR_ARG;
-    for (int q = 0; q < n; q++) {
-        const int slot = (int)((plan->n_timed - n + q) % laph_plan::RING);
-        CK(cudaEventSynchronize(plan->ev_end[slot]));
-        CK(cudaEventElapsedTime(&ms[q], plan->ev_begin[slot], plan->ev_end[slot]));
-    }
+    if (!plan) return LAPH_ERR_ARG;
+    return ring_times(plan->ev_begin, plan->ev_end, plan->n_timed, n, ms);
+}
+
+int laph_plan_operand_times(laph_plan *plan, int n, float *ms)
+{
+    if (!plan) return LAPH_ERR_ARG;
+    return ring_times(plan->pv_begin, plan->pv_end, plan->n_ptimed, n, ms);
+}
+
+int laph_plan_contraction_launches(const laph_plan *plan, int *n)
+{
+    if (!plan || !n) return LAPH_ERR_ARG;
+    *n = is_tc_mode(plan->mode) ? (int)plan->chunks.size()
+                                : (int)((plan->n_tiles + 0x7ffffffeLL) / 0x7fffffffLL);
     return LAPH_OK;
 }
 
@@ -467,7 +537,7 @@ int laph_plan_launches_per_execute(const laph_plan *plan, int *n)
     if (!plan || !n) return LAPH_ERR_ARG;
     const int ptr_launches = (plan->n_inst + 63) / 64;
     if (is_tc_mode(plan->mode))
-        *n = ptr_launches + 2 * plan->n_inst /* scale, blockify */ + 1 /* contraction */;
+        *n = ptr_launches + 2 * plan->n_inst /* scale, blockify */ + 2 * (int)plan->chunks.size() /* psi, contraction */;
     else
         *n = ptr_launches + (int)((plan->n_tiles + 0x7ffffffeLL) / 0x7fffffffLL);
     return LAPH_OK;

@@ -19,8 +19,7 @@ struct InstDev {
     const float2 *phi;       // [T][N][V][3]
     double2 *outB;           // [T][P][C(N,3)]
     double2 *outM;           // [T][P][N][N]
-    const float2 *phase;     // [P][Vs], FP32 rounding of the FP64 phase (FP32 path)
-    const float2 *phase_blk; // tensor-core path: per site block, P rows of TC_PHROW entries (row stride TC_PHROW)
+    const float2 *phase;     // [P][Vs], FP32 rounding of the FP64 phase
     float2 *phi_blk;         // tensor-core path: scaled, site-blocked copy of phi in the workspace
     long long V;
     long long Vs;            // V rounded up to even: row stride of `phase`
@@ -33,7 +32,8 @@ struct InstDev {
     int cols;                // N * P
     int ts_base;             // index of (this instance, t = 0) among all timeslices of the batch
     int nblk;                // site blocks: ceil(V / TC_BS)
-    int phb_stride;          // float2 entries per site block of phase_blk (P * TC_PHROW rounded up to 16 bytes)
+    int n_ct;                // column tiles of the tensor-core path: ceil(cols / TC_TC)
+    int n_st;                // K stages of the tensor-core path: one per site block (= nblk)
     int pad_;
 };
 
@@ -43,17 +43,28 @@ struct InstDev {
 // so the rows' (or columns') vectors of a tile arrive with one bulk copy.
 constexpr int TC_BS = 8;                      // sites per block
 constexpr int TC_SLOT = 3 * TC_BS + 2;        // complex entries per (block, vector): 208 bytes
-constexpr int TC_PHROW = TC_BS + 3;           // complex entries per (block, momentum): 88 bytes
 
 // One unit of work: a (row tile, column tile) of one timeslice.  v_lo and nv
 // give the contiguous range of vector indices the tile's rows use (the
-// tensor-core path stages exactly these vectors in shared memory).
+// tensor-core path stages exactly these vectors in shared memory); psi_off is
+// the byte offset of the tile's B operand stages in the Psi buffer.
 struct TileDev {
     int inst, t, row0, col0;
     int v_lo, nv;        // vectors used by the rows: [v_lo, v_lo + nv)
     int k_lo, nk;        // vectors used by the columns: [k_lo, k_lo + nk)
     int ncols;           // valid columns of the tile
-    int pad0, pad1, pad2;
+    int pad0;
+    long long psi_off;
+};
+
+// One (instance, timeslice) of a chunk of the tensor-core path: its Psi
+// operand occupies n_ct * n_st stage images from byte psi_off of the chunk's
+// Psi buffer; job0 is the index of its first (column tile, stage group) job
+// within the chunk.
+struct PsiUnit {
+    int inst, t;
+    long long psi_off;
+    long long job0;
 };
 
 __host__ __device__ inline long long binom2(long long n) { return n * (n - 1) / 2; }
@@ -112,8 +123,6 @@ cudaError_t launch_diquarks(const float2 *phi, int L, int T, int N, float2 *out,
 cudaError_t launch_dense_fill(const double2 *packed, int T, int N, int P, double2 *dense, cudaStream_t s);
 cudaError_t launch_blockify(const InstDev *d_inst, int inst, const InstDev &h, const unsigned *d_maxbits,
                             cudaStream_t s);
-cudaError_t launch_phase_blocks(int L, const int32_t *d_mom, int P, int nblk, int phb_stride, float2 *out,
-                                cudaStream_t s);
 
 // laph_simt.cu
 struct SimtConfig {
@@ -130,16 +139,20 @@ struct TcConfig {
     int terms;         // 3 (split) or 1 (plain)
     int chunk_sites;   // sites accumulated by the tensor core between FP32 drains
     int grid;          // persistent CTAs
-    int max_staged;    // largest number of staged vectors (nv + nk) of any tile
-    int max_phb;       // largest phase-block stride (float2 entries) of any instance
+    int max_staged;    // largest number of staged row vectors (nv) of any tile
     int debug_stall;   // test hook
 };
 constexpr int TC_TR = 128;   // tile rows (UMMA M)
 constexpr int TC_TC = 96;    // tile columns (complex), UMMA N = 2 * TC_TC real
-constexpr int TC_MAX_STAGED = 160;  // staged vectors (rows' + columns') per tile
-constexpr int TC_MAX_P = 64;    // momenta per instance supported by the kernel
+constexpr int TC_KSTAGE = 3 * TC_BS;  // complex K entries per stage: one site block
+constexpr int TC_STAGE_BYTES = 2 * (2 * TC_TC) * (2 * TC_KSTAGE) * 2;  // one B stage image: hi + lo, 192 rows x 48 FP16 each
+constexpr int TC_MAX_STAGED = 160;  // staged row vectors per tile
+constexpr int TC_PSI_GROUP = 16;    // stages per job of the B-operand pass
+// Psi stage images of a chunk: jobs [0, n_jobs) over the units [0, n_units).
+cudaError_t launch_psi(const InstDev *d_inst, const PsiUnit *d_units, int n_units, long long n_jobs,
+                       const unsigned *d_maxbits, int elem, uint8_t *psi, cudaStream_t s);
 cudaError_t launch_tc(const InstDev *d_inst, const TileDev *d_tiles, long long n_tiles,
-                      const unsigned *d_maxbits, unsigned long long *d_counter, const TcConfig &cfg,
+                      const unsigned *d_maxbits, const uint8_t *psi, const TcConfig &cfg,
                       int *d_status, cudaStream_t s);
 int tc_smem_bytes();
 

@@ -159,42 +159,6 @@ cudaError_t launch_blockify(const InstDev *d_inst, int inst, const InstDev &h, c
     return cudaGetLastError();
 }
 
-// Phase table in the site-blocked layout: out[b * phb_stride + p * TC_PHROW + o]
-// = ph_p(8b + o) for o < 8 and 8b + o < V, zero elsewhere (FP64 sincospi of the
-// exactly reduced argument, rounded to FP32).
-__global__ void phase_blocks_kernel(int L, const int32_t *__restrict__ mom, int P, long long V, int nblk, int phb_stride,
-                                    float2 *__restrict__ out)
-{
-    const long long total = (long long)nblk * phb_stride;
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const long long b = idx / phb_stride;
-        const int w = (int)(idx - b * phb_stride);
-        const int p = w / TC_PHROW, o = w - p * TC_PHROW;
-        const long long x = (long long)TC_BS * b + o;
-        float2 v = make_float2(0.f, 0.f);
-        if (p < P && o < TC_BS && x < V) {
-            const long long x0 = x % L, x1 = (x / L) % L, x2 = x / ((long long)L * L);
-            long long r = ((long long)mom[3 * p] * x0 + (long long)mom[3 * p + 1] * x1 + (long long)mom[3 * p + 2] * x2) % L;
-            if (r < 0) r += L;
-            double sn, cs;
-            sincospi(-2.0 * (double)r / (double)L, &sn, &cs);
-            v = make_float2((float)cs, (float)sn);
-        }
-        out[idx] = v;
-    }
-}
-
-cudaError_t launch_phase_blocks(int L, const int32_t *d_mom, int P, int nblk, int phb_stride, float2 *out, cudaStream_t s)
-{
-    const long long V = (long long)L * L * L;
-    const long long n = (long long)nblk * phb_stride;
-    long long blocks = (n + 255) / 256;
-    if (blocks > 152 * 64) blocks = 152 * 64;
-    phase_blocks_kernel<<<(unsigned)blocks, 256, 0, s>>>(L, d_mom, P, V, nblk, phb_stride, out);
-    return cudaGetLastError();
-}
-
 // ---------------------------------------------------------------- K-b
 // D[t][q][x][c] = (phi_i(x) x phi_j(x))_c for q = C(j,2) + i.  One block per
 // (site block of SB sites, timeslice): phi of all N vectors for those sites

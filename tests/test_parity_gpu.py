@@ -129,8 +129,12 @@ def test_plan_ragged_batch_matches_oracle(laph):
     import torch
     specs = [(4, 2, 5, synth.momentum_shell(1)), (6, 1, 11, synth.momentum_shell(0)),
              (5, 3, 8, synth.momentum_shell(2)), (3, 1, 20, np.array([[1, 1, 1], [0, 0, 0]], dtype=np.int32))]
-    for mode in SPLIT_MODES:
-        plan = laph.Plan(specs, mode=mode)
+    runs = [(mode, 0) for mode in SPLIT_MODES] + [("f16x3", laph.PLAN_CHUNK_PER_TIMESLICE)]
+    for mode, flags in runs:
+        plan = laph.Plan(specs, mode=mode, flags=flags)
+        if flags:
+            # every (instance, timeslice) is its own chunk: one B-operand pass and one contraction each
+            assert plan.contraction_launches() == sum(T for _, T, _, _ in specs)
         phis_h = [synth.random_phi(L, N, T=T, instance=40 + n) for n, (L, T, N, _) in enumerate(specs)]
         phis = [torch.from_numpy(p).cuda() for p in phis_h]
         Bs, Ms = plan.alloc_outputs()
@@ -150,8 +154,9 @@ def test_plan_execute_is_capturable_in_a_cuda_graph(laph):
     L, T, N = 6, 2, 12
     mom = synth.momentum_shell(1)
     phi_h = synth.random_phi(L, N, T=T, instance=60)
-    for mode in SPLIT_MODES:
-        plan = laph.Plan([(L, T, N, mom)], mode=mode)
+    runs = [(mode, 0) for mode in SPLIT_MODES] + [("bf16x3", laph.PLAN_CHUNK_PER_TIMESLICE)]
+    for mode, flags in runs:
+        plan = laph.Plan([(L, T, N, mom)], mode=mode, flags=flags)
         phi = torch.from_numpy(phi_h).cuda()
         Bs, Ms = plan.alloc_outputs()
         ws = plan.alloc_workspace()
