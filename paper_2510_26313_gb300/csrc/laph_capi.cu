@@ -279,26 +279,21 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
     PCK(cudaMemset(p->d_status, 0, sizeof(int)));
 
     // ---- tile table: (instance, t, column tile, row tile), skipping column
-    // tiles whose every k is <= the smallest j of a diquark-only row tile.
-    // The tensor-core path processes the (instance, t) units in chunks whose
-    // B-operand images fit the Psi buffer; the tiles of one column tile are
-    // consecutive, so the CTAs that share a stage image run side by side.
+    // tiles whose every k is <= the smallest j of a diquark-only row tile;
+    // in the remaining tiles of such a row tile the leading columns with
+    // k <= that j are skipped in steps of 8 (cskip).  The tensor-core path
+    // processes the (instance, t) units in chunks whose B-operand images fit
+    // the Psi buffer; the tiles of one column tile are consecutive, so the
+    // CTAs that share a stage image run side by side.
     std::vector<TileDev> tiles;
     std::vector<laph::PsiUnit> units;
     const int TR = p->tile_rows, TC = p->tile_cols;
+    std::vector<std::vector<TileDev>> ones(n_inst);
+    std::vector<size_t> unit_bytes(n_inst);
     size_t psi_total = 0;
     for (int n = 0; n < n_inst; n++) {
         const InstDev &d = p->h_inst[n];
-        psi_total += (size_t)d.T * d.n_ct * d.n_st * laph::TC_STAGE_BYTES;
-    }
-    const long long n_chunks_wanted = tc ? (long long)((psi_total + PSI_CAP_BYTES - 1) / PSI_CAP_BYTES) : 1;
-    const size_t psi_target = tc ? (psi_total + n_chunks_wanted - 1) / (size_t)n_chunks_wanted : 0;
-    size_t psi_max = 0;
-    laph_plan::Chunk cur{0, 0, 0, 0, 0};
-    size_t cur_bytes = 0;
-    for (int n = 0; n < n_inst; n++) {
-        const InstDev &d = p->h_inst[n];
-        std::vector<TileDev> one;
+        std::vector<TileDev> &one = ones[n];
         for (int col0 = 0; col0 < d.cols; col0 += TC) {
             const int nc = std::min(TC, d.cols - col0);
             const int kmin = col0 / d.P, kmax = (col0 + nc - 1) / d.P;
@@ -326,14 +321,54 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
                 const int nv = v_hi - v_lo + 1;
                 p->max_staged = std::max(p->max_staged, tc ? nv : nv + (kmax - kmin + 1));
                 const long long psi_ct = (long long)(col0 / TC) * d.n_st * laph::TC_STAGE_BYTES;
-                one.push_back(TileDev{n, 0, row0, col0, v_lo, nv, kmin, kmax - kmin + 1, nc, 0, psi_ct});
+                int cskip = 0;
+                if (tc && jmin >= 0) {
+                    const int lead = std::max(0, std::min(nc, (jmin + 1) * d.P - col0));
+                    cskip = (lead / 8) * 8;
+                }
+                one.push_back(TileDev{n, 0, row0, col0, v_lo, nv, kmin, kmax - kmin + 1, nc, cskip, psi_ct});
             }
         }
         p->max_P = std::max(p->max_P, d.P);
-        const size_t unit_bytes = (size_t)d.n_ct * d.n_st * laph::TC_STAGE_BYTES;
+        unit_bytes[n] = (size_t)d.n_ct * d.n_st * laph::TC_STAGE_BYTES;
+        psi_total += (size_t)d.T * unit_bytes[n];
+    }
+    int sms = 0;
+    PCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    // units per chunk: one instance -> the count (within the cap) that
+    // leaves the fewest partly filled waves of persistent CTAs; several
+    // instances -> chunks filled in order up to an even share of the total.
+    long long per_chunk = 0;
+    size_t psi_target = 0;
+    if (tc && (flags & LAPH_PLAN_CHUNK_PER_TIMESLICE)) {
+        per_chunk = 1;
+    } else if (tc && n_inst == 1) {
+        const long long U = p->h_inst[0].T, tpu = (long long)ones[0].size();
+        const long long n_max = std::max(1LL, std::min(U, (long long)(PSI_CAP_BYTES / std::max<size_t>(unit_bytes[0], 1))));
+        long long best = -1, best_rounds = 0;
+        for (long long n = 1; n <= n_max; n++) {
+            const long long full = U / n, rest = U % n;
+            const long long rounds = full * ((n * tpu + sms - 1) / sms) + (rest * tpu + sms - 1) / sms;
+            if (best < 0 || rounds <= best_rounds) {
+                best = n;
+                best_rounds = rounds;
+            }
+        }
+        per_chunk = best;
+    } else if (tc) {
+        const long long n_chunks = (long long)((psi_total + PSI_CAP_BYTES - 1) / PSI_CAP_BYTES);
+        psi_target = (psi_total + n_chunks - 1) / (size_t)std::max(1LL, n_chunks);
+    }
+    size_t psi_max = 0;
+    laph_plan::Chunk cur{0, 0, 0, 0, 0};
+    size_t cur_bytes = 0;
+    for (int n = 0; n < n_inst; n++) {
+        const InstDev &d = p->h_inst[n];
+        const std::vector<TileDev> &one = ones[n];
         for (int t = 0; t < d.T; t++) {
             if (tc) {
-                if (cur.n_units > 0 && (cur_bytes + unit_bytes > psi_target || (flags & LAPH_PLAN_CHUNK_PER_TIMESLICE))) {
+                const bool full = per_chunk > 0 ? cur.n_units >= per_chunk : cur_bytes + unit_bytes[n] > psi_target;
+                if (cur.n_units > 0 && full) {
                     p->chunks.push_back(cur);
                     psi_max = std::max(psi_max, cur_bytes);
                     cur = laph_plan::Chunk{(int)units.size(), 0, 0, (long long)tiles.size(), 0};
@@ -350,7 +385,7 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
             }
             if (tc) {
                 cur.n_tiles += (long long)one.size();
-                cur_bytes += unit_bytes;
+                cur_bytes += unit_bytes[n];
             }
         }
     }
@@ -376,8 +411,6 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
     // bits (cleared by every execute), the site-blocked copies of phi, then
     // the B-operand images of one chunk.
     if (tc) {
-        int sms = 0;
-        PCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
         p->grid = sms;
         p->off_maxbits = 0;
         size_t off = ((sizeof(unsigned) * p->total_ts + 255) / 256) * 256;

@@ -53,7 +53,7 @@ struct TileDev {
     int v_lo, nv;        // vectors used by the rows: [v_lo, v_lo + nv)
     int k_lo, nk;        // vectors used by the columns: [k_lo, k_lo + nk)
     int ncols;           // valid columns of the tile
-    int pad0;
+    int cskip;           // leading columns no row of the tile needs (multiple of 8; tensor-core path)
     long long psi_off;
 };
 

@@ -33,13 +33,15 @@
 // warp fills a stage with two bulk copies completing on one mbarrier, and
 // the MMA's commit frees it.
 //
-// Warp roles (448 threads, persistent CTAs, static tile order):
-//   0-7   A producers: two warps per TMEM lane quadrant; warp half h forms
-//         the 12 K entries of sites 4h..4h+3 of its row (diquark or
-//         conj(phi)), splits them and tcgen05.st's them into the A slot;
-//   8-11  epilogue: drains ACC into SUM, writes the output at tile end;
-//   12    loader: the stage ring's bulk copies;
-//   13    TMEM allocation and single-thread MMA issue.
+// Warp roles (704 threads, persistent CTAs, static tile order):
+//   0-15  A producers in two groups of eight; group g forms the stages whose
+//         global index has parity g, in A slot g, so that two stages are
+//         formed at once.  Within a group, two warps per TMEM lane quadrant:
+//         warp half h forms the 12 K entries of sites 4h..4h+3 of its row
+//         (diquark or conj(phi)), splits them and tcgen05.st's them;
+//   16-19 epilogue: drains ACC into SUM, writes the output at tile end;
+//   20    loader: the stage ring's bulk copies;
+//   21    TMEM allocation and single-thread MMA issue.
 // Every wait on an mbarrier is bounded; on expiry the CTA records
 // STATUS_TIMEOUT, raises a shared abort flag and all roles return.
 #include <cuda_bf16.h>
@@ -50,11 +52,11 @@
 namespace laph {
 namespace {
 
-constexpr int NTHREADS = 448;
-constexpr int N_AWARPS = 8;
-constexpr int WARP_E0 = 8;
-constexpr int WARP_LOAD = 12;
-constexpr int WARP_MMA = 13;
+constexpr int NTHREADS = 704;
+constexpr int N_AGROUP = 8;                           // A producer warps per group (one stage)
+constexpr int N_AWARPS = 2 * N_AGROUP;
+constexpr int WARP_LOAD = 20;
+constexpr int WARP_MMA = 21;
 constexpr int KSTAGE = TC_KSTAGE;                     // complex K entries per stage (one site block)
 constexpr int KSTEPS = 2 * KSTAGE / 16;               // MMA k-steps per stage
 constexpr int B_ROWS = 2 * TC_TC;                     // real B rows per tile (192)
@@ -75,7 +77,8 @@ constexpr long long WAIT_LIMIT = 4000000000LL;        // cycles (about 2 s at th
 static_assert(TC_TR == 128 && TC_TC == 96, "layout assumes 128 x 96 tiles");
 static_assert(TC_BS == 8 && KSTAGE == 24 && KSTEPS == 3, "a stage is one 8-site block");
 static_assert(BIMG_BYTES == TC_STAGE_BYTES, "stage image size");
-static_assert(A_LO + KSTAGE <= A_SLOT_COLS && A_COL + 2 * A_SLOT_COLS == TMEM_COLS, "tensor memory budget");
+static_assert(A_LO + KSTAGE <= A_SLOT_COLS && SUM_COL + 192 <= A_COL && A_COL + 2 * A_SLOT_COLS == TMEM_COLS,
+              "tensor memory budget");
 
 struct Shared {
     uint64_t full[MAX_NS], empty[MAX_NS];
@@ -324,27 +327,31 @@ struct Ring {
 template <int ELEM>
 __device__ __forceinline__ void a_quarter(int kind, const uint8_t *pu, const uint8_t *pv, uint32_t ta)
 {
-    float2 u[12], v[12];
-#pragma unroll
-    for (int h = 0; h < 6; h++) {
-        const float4 a = reinterpret_cast<const float4 *>(pu)[h];
-        const float4 b = reinterpret_cast<const float4 *>(pv)[h];
-        u[2 * h] = make_float2(a.x, a.y);
-        u[2 * h + 1] = make_float2(a.z, a.w);
-        v[2 * h] = make_float2(b.x, b.y);
-        v[2 * h + 1] = make_float2(b.z, b.w);
-    }
     uint32_t hi[12], lo[12];
 #pragma unroll
-    for (int e = 0; e < 12; e++) {
-        float2 d;
-        if (kind == 2)
-            d = cross8(u + 3 * (e / 3), v + 3 * (e / 3), e % 3);
-        else if (kind == 1)
-            d = make_float2(u[e].x, -u[e].y);
-        else
-            d = make_float2(0.f, 0.f);
-        split2<ELEM>(d.x, d.y, hi[e], lo[e]);
+    for (int m = 0; m < 2; m++) {
+        // two sites = 6 entries = three 16-byte loads per vector
+        float2 u[6], v[6];
+#pragma unroll
+        for (int h = 0; h < 3; h++) {
+            const float4 a = reinterpret_cast<const float4 *>(pu)[3 * m + h];
+            const float4 b = reinterpret_cast<const float4 *>(pv)[3 * m + h];
+            u[2 * h] = make_float2(a.x, a.y);
+            u[2 * h + 1] = make_float2(a.z, a.w);
+            v[2 * h] = make_float2(b.x, b.y);
+            v[2 * h + 1] = make_float2(b.z, b.w);
+        }
+#pragma unroll
+        for (int e = 0; e < 6; e++) {
+            float2 d;
+            if (kind == 2)
+                d = cross8(u + 3 * (e / 3), v + 3 * (e / 3), e % 3);
+            else if (kind == 1)
+                d = make_float2(u[e].x, -u[e].y);
+            else
+                d = make_float2(0.f, 0.f);
+            split2<ELEM>(d.x, d.y, hi[6 * m + e], lo[6 * m + e]);
+        }
     }
 #pragma unroll
     for (int q = 0; q < 3; q++) {
@@ -386,7 +393,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
             mbar_init(&S->empty[s], 1);
         }
         for (int s = 0; s < 2; s++) {
-            mbar_init(&S->a_full[s], N_AWARPS);
+            mbar_init(&S->a_full[s], N_AGROUP);
             mbar_init(&S->a_empty[s], 1);
         }
         mbar_init(&S->acc_full, 1);
@@ -433,10 +440,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
         }
     } else if (warp < N_AWARPS) {
         // ---------------------------------------------------------- A producers
-        const int quad = warp & 3, half = warp >> 2;
+        const int quad = warp & 3, half = (warp >> 2) & 1, grp = warp >> 3;
         const int r = quad * 32 + lane;
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
-        Ring rs{0, 0}, ra{0, 0};
+        const uint32_t ta0 = tmem + lane_base + A_COL + (uint32_t)grp * A_SLOT_COLS + 12u * half;
+        uint32_t G = 0;   // global index of the tile's first stage
         bool stalled = false, ok = true;
         for (int tile = blockIdx.x; tile < kp.n_tiles && ok; tile += gridDim.x) {
             const TileDev td = kp.tiles[tile];
@@ -456,24 +464,34 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
             const int si = kind ? vi - td.v_lo : 0, sj = kind == 2 ? vj - td.v_lo : 0;
             const int off_u = BIMG_BYTES + si * SLOT_BYTES + half * HALF_BYTES;
             const int off_v = BIMG_BYTES + sj * SLOT_BYTES + half * HALF_BYTES;
-            for (int st = 0; st < nst; st++) {
-                if (!warp_wait(c, &S->a_empty[ra.slot], ra.phase ^ 1u) || !warp_wait(c, &S->full[rs.slot], rs.phase)) {
+            // this group's stages: global index Gs = G + st with parity grp
+            int st = (grp - (int)(G & 1u)) & 1;
+            const uint32_t Gs = G + st;
+            int s = (int)(Gs % (uint32_t)NS);
+            uint32_t ph = (Gs / (uint32_t)NS) & 1u;  // stage ring phase
+            uint32_t pa = (Gs >> 1) & 1u;            // A slot phase: uses of slot grp so far
+            for (; st < nst; st += 2) {
+                if (!warp_wait(c, &S->a_empty[grp], pa ^ 1u) || !warp_wait(c, &S->full[s], ph)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint8_t *buf = smem + rs.slot * kp.stage_bytes;
-                const uint32_t ta = tmem + lane_base + A_COL + (uint32_t)ra.slot * A_SLOT_COLS + 12u * half;
-                a_quarter<ELEM>(kind, buf + off_u, buf + off_v, ta);
+                const uint8_t *buf = smem + s * kp.stage_bytes;
+                a_quarter<ELEM>(kind, buf + off_u, buf + off_v, ta0);
                 tmem_wait_st();
                 tc_fence_before();
                 __syncwarp();
                 const bool skip = kp.debug_stall && !stalled && blockIdx.x == 0 && warp == 0;
                 if (skip) stalled = true;
-                if (lane == 0 && !skip) mbar_arrive(&S->a_full[ra.slot]);
-                rs.next(NS);
-                ra.next(2);
+                if (lane == 0 && !skip) mbar_arrive(&S->a_full[grp]);
+                pa ^= 1u;
+                s += 2;
+                if (s >= NS) {
+                    s -= NS;
+                    ph ^= 1u;
+                }
             }
+            G += (uint32_t)nst;
         }
     } else if (warp < WARP_LOAD) {
         // ---------------------------------------------------------- epilogue
@@ -485,8 +503,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
         for (int tile = blockIdx.x; tile < kp.n_tiles && ok; tile += gridDim.x) {
             const TileDev td = kp.tiles[tile];
             const InstDev &I = kp.insts[td.inst];
-            const int ncols = td.ncols;
-            const int n_real = 2 * ((ncols + 7) & ~7);
+            const int ncols = td.ncols, cskip = td.cskip;
+            const int n_real = 2 * ((ncols + 7) & ~7) - 2 * cskip;   // accumulator columns: tile columns cskip..
             const int gr = td.row0 + r;
             const bool rvalid = gr < I.rows;
             const bool meson = gr < I.mes_rows;
@@ -535,7 +553,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
                 tmem_wait_ld();
 #pragma unroll 1
                 for (int u = 0; u < 8; u++) {
-                    const int cc = 8 * b + u;
+                    const int cc = cskip + 8 * b + u;
                     if (!rvalid || cc >= ncols) continue;
                     const int col = td.col0 + cc;
                     const int k = col / P, p = col - k * P;
@@ -560,8 +578,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
             const TileDev td = kp.tiles[tile];
             const InstDev &I = kp.insts[td.inst];
             const int nst = I.nblk;
-            const int n_real = 2 * ((td.ncols + 7) & ~7);
+            // the first cskip columns (2 cskip real B rows, 64 bytes per column in
+            // every atom column) are not needed by any row of the tile
+            const int n_real = 2 * ((td.ncols + 7) & ~7) - 2 * td.cskip;
             const uint32_t idesc = idesc_f16(n_real, ELEM);
+            const uint64_t bskip = (uint64_t)(td.cskip * 64) >> 4;
             int cs = 0;   // stage within the current accumulation chunk
             for (int st = 0; st < nst; st++) {
                 const bool chunk_start = cs == 0;
@@ -578,7 +599,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
                 if (lane == 0) {
                     const uint32_t a_hi = tmem + A_COL + (uint32_t)ra.slot * A_SLOT_COLS, a_lo = a_hi + A_LO;
                     // descriptor start addresses advance one atom column (in units of 16 bytes) per k-step
-                    const uint64_t dhi = desc_sw32(smem_u32(smem + rs.slot * kp.stage_bytes));
+                    const uint64_t dhi = desc_sw32(smem_u32(smem + rs.slot * kp.stage_bytes)) + bskip;
                     const uint64_t dlo = dhi + (uint64_t)(B_BYTES >> 4);
                     const uint32_t d = tmem + ACC_COL;
 #pragma unroll
