@@ -103,17 +103,17 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Waits up to about `hint_ns` for the phase with the given parity to
-// complete; the warp is suspended meanwhile instead of spinning.
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity, uint32_t hint_ns = 20000u)
+// Tests the phase with the given parity for completion; the warp may be
+// suspended for a system-dependent time while it is incomplete.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     return ok != 0;
 }
@@ -276,9 +276,9 @@ struct Ctx {
     int lane;
 };
 
-// Slow path of a warp-wide bounded wait.  Each try_wait suspends the warp
-// until the phase completes or about 20 us pass; between those wake-ups the
-// abort flag and the time limit are checked.
+// Slow path of a warp-wide bounded wait.  Between the try_waits (each may
+// suspend the warp for a while) the abort flag and the time limit are
+// checked.
 __device__ __noinline__ bool warp_wait_slow(Shared *S, int *status, int lane, uint64_t *bar, uint32_t parity)
 {
     const long long t0 = clock64();
