@@ -68,7 +68,7 @@ struct laph_plan {
     int *d_status = nullptr;
     int tile_rows = 0, tile_cols = 0, chunk_sites = 0, grid = 0;
     int max_staged = 0, max_P = 0;
-    size_t ws_bytes = 0, off_maxbits = 0, ws_zero_bytes = 0;
+    size_t ws_bytes = 0, off_maxbits = 0, off_counter = 0, ws_zero_bytes = 0;
     // tensor-core path: chunks of (instance, timeslice) units and their B-operand images
     laph::PsiUnit *d_units = nullptr;
     struct Chunk {
@@ -359,10 +359,19 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
         const long long n_chunks = (long long)((psi_total + PSI_CAP_BYTES - 1) / PSI_CAP_BYTES);
         psi_target = (psi_total + n_chunks - 1) / (size_t)std::max(1LL, n_chunks);
     }
+    // instances in decreasing order of work per timeslice (stages x tiles),
+    // so that the dynamically scheduled tiles of a chunk start with the longest
+    std::vector<int> order(n_inst);
+    for (int n = 0; n < n_inst; n++) order[n] = n;
+    if (tc)
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            return (long long)p->h_inst[a].n_st * (long long)ones[a].size() >
+                   (long long)p->h_inst[b].n_st * (long long)ones[b].size();
+        });
     size_t psi_max = 0;
     laph_plan::Chunk cur{0, 0, 0, 0, 0};
     size_t cur_bytes = 0;
-    for (int n = 0; n < n_inst; n++) {
+    for (int n : order) {
         const InstDev &d = p->h_inst[n];
         const std::vector<TileDev> &one = ones[n];
         for (int t = 0; t < d.T; t++) {
@@ -408,12 +417,13 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
     }
 
     // ---- workspace layout (tensor-core modes only): per-timeslice max |phi|
-    // bits (cleared by every execute), the site-blocked copies of phi, then
-    // the B-operand images of one chunk.
+    // bits and one tile counter per chunk (both cleared by every execute), the
+    // site-blocked copies of phi, then the B-operand images of one chunk.
     if (tc) {
         p->grid = sms;
         p->off_maxbits = 0;
-        size_t off = ((sizeof(unsigned) * p->total_ts + 255) / 256) * 256;
+        p->off_counter = ((sizeof(unsigned) * p->total_ts + 255) / 256) * 256;
+        size_t off = p->off_counter + ((sizeof(unsigned) * p->chunks.size() + 255) / 256) * 256;
         p->ws_zero_bytes = off;
         for (int n = 0; n < n_inst; n++) {
             InstDev &d = p->h_inst[n];
@@ -499,7 +509,9 @@ static int launch_batch(laph_plan *p, void *workspace, cudaStream_t s)
         cfg.max_staged = p->max_staged;
         cfg.debug_stall = (p->flags & LAPH_PLAN_DEBUG_STALL) ? 1 : 0;
         uint8_t *psi = (uint8_t *)(ws + p->off_psi);
-        for (const laph_plan::Chunk &c : p->chunks) {
+        unsigned *counters = (unsigned *)(ws + p->off_counter);
+        for (size_t ci = 0; ci < p->chunks.size(); ci++) {
+            const laph_plan::Chunk &c = p->chunks[ci];
             const int ps = (int)(p->n_ptimed % laph_plan::RING), cs = (int)(p->n_timed % laph_plan::RING);
             if (timing) CK(cudaEventRecord(p->pv_begin[ps], s));
             e = laph::launch_psi(p->d_inst, p->d_units + c.unit0, c.n_units, c.n_jobs, maxbits, cfg.elem, psi, s);
@@ -509,7 +521,8 @@ static int launch_batch(laph_plan *p, void *workspace, cudaStream_t s)
                 p->n_ptimed++;
                 CK(cudaEventRecord(p->ev_begin[cs], s));
             }
-            e = laph::launch_tc(p->d_inst, p->d_tiles + c.tile0, c.n_tiles, maxbits, psi, cfg, p->d_status, s);
+            e = laph::launch_tc(p->d_inst, p->d_tiles + c.tile0, c.n_tiles, maxbits, psi, counters + ci, cfg, p->d_status,
+                                s);
             if (e == cudaErrorNotSupported) return LAPH_ERR_UNSUPPORTED;
             if (e != cudaSuccess) return cuda_fail(e, "tc contraction");
             if (timing) {

@@ -151,8 +151,9 @@ constexpr int TC_PSI_GROUP = 16;    // stages per job of the B-operand pass
 // Psi stage images of a chunk: jobs [0, n_jobs) over the units [0, n_units).
 cudaError_t launch_psi(const InstDev *d_inst, const PsiUnit *d_units, int n_units, long long n_jobs,
                        const unsigned *d_maxbits, int elem, uint8_t *psi, cudaStream_t s);
+// counter: a zeroed word of device memory; persistent CTAs claim tiles with it.
 cudaError_t launch_tc(const InstDev *d_inst, const TileDev *d_tiles, long long n_tiles,
-                      const unsigned *d_maxbits, const uint8_t *psi, const TcConfig &cfg,
+                      const unsigned *d_maxbits, const uint8_t *psi, unsigned *counter, const TcConfig &cfg,
                       int *d_status, cudaStream_t s);
 int tc_smem_bytes();
 

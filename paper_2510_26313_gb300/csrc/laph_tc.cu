@@ -33,14 +33,15 @@
 // warp fills a stage with two bulk copies completing on one mbarrier, and
 // the MMA's commit frees it.
 //
-// Warp roles (704 threads, persistent CTAs, static tile order):
+// Warp roles (704 threads, persistent CTAs; the loader claims tiles from a
+// global counter and hands them to the other roles through a small ring):
 //   0-15  A producers in two groups of eight; group g forms the stages whose
 //         global index has parity g, in A slot g, so that two stages are
 //         formed at once.  Within a group, two warps per TMEM lane quadrant:
 //         warp half h forms the 12 K entries of sites 4h..4h+3 of its row
 //         (diquark or conj(phi)), splits them and tcgen05.st's them;
 //   16-19 epilogue: drains ACC into SUM, writes the output at tile end;
-//   20    loader: the stage ring's bulk copies;
+//   20    loader: claims the next tile, then the stage ring's bulk copies;
 //   21    TMEM allocation and single-thread MMA issue.
 // Every wait on an mbarrier is bounded; on expiry the CTA records
 // STATUS_TIMEOUT, raises a shared abort flag and all roles return.
@@ -66,6 +67,8 @@ constexpr int BIMG_BYTES = 2 * B_BYTES;               // hi + lo
 constexpr int SLOT_BYTES = TC_SLOT * 8;               // 208 B = 52 words: LDS.128 of 8 consecutive slots hit distinct banks
 constexpr int HALF_BYTES = (TC_BS / 2) * 3 * 8;       // 4 sites x 3 colours: one A warp's share of a slot
 constexpr int MAX_NS = 6;
+constexpr int TRING = 4;                              // tile ring entries
+constexpr int N_TILE_READERS = N_AWARPS + 4 + 1;     // A producers, epilogue, MMA
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t ACC_COL = 0;
 constexpr uint32_t SUM_COL = 192;
@@ -82,6 +85,8 @@ static_assert(A_LO + KSTAGE <= A_SLOT_COLS && SUM_COL + 192 <= A_COL && A_COL + 
 
 struct Shared {
     uint64_t full[MAX_NS], empty[MAX_NS];
+    uint64_t tfull[TRING], tempty[TRING];
+    int tile_ring[TRING];
     uint64_t a_full[2], a_empty[2];
     uint64_t acc_full, acc_empty;
     uint64_t done;
@@ -318,6 +323,21 @@ struct Ring {
     }
 };
 
+// Next tile of this CTA from the tile ring (-1: no more tiles).  Every
+// reader warp takes every entry in order and frees it at once.
+__device__ __forceinline__ int next_tile(const Ctx c, Ring &rt, bool &ok)
+{
+    if (!warp_wait(c, &c.S->tfull[rt.slot], rt.phase)) {
+        ok = false;
+        return -1;
+    }
+    const int t = *(volatile int *)&c.S->tile_ring[rt.slot];
+    __syncwarp();
+    if (c.lane == 0) mbar_arrive(&c.S->tempty[rt.slot]);
+    rt.next(TRING);
+    return t;
+}
+
 // ------------------------------------------------------------ A producer
 
 // The 12 K entries of sites 4h..4h+3 of one row, from the block slots of
@@ -367,6 +387,7 @@ struct KParams {
     const TileDev *tiles;
     const unsigned *maxbits;
     const uint8_t *psi;   // B stage images of the chunk
+    unsigned *counter;    // tile counter of this launch (zero at launch)
     int *status;
     int n_tiles;
     int chunk_stages;
@@ -392,6 +413,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
             mbar_init(&S->full[s], 1);
             mbar_init(&S->empty[s], 1);
         }
+        for (int s = 0; s < TRING; s++) {
+            mbar_init(&S->tfull[s], 1);
+            mbar_init(&S->tempty[s], N_TILE_READERS);
+        }
         for (int s = 0; s < 2; s++) {
             mbar_init(&S->a_full[s], N_AGROUP);
             mbar_init(&S->a_empty[s], 1);
@@ -413,9 +438,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
 
     if (warp == WARP_LOAD) {
         // ---------------------------------------------------------- loader
-        Ring rs{0, 0};
+        Ring rs{0, 0}, rt{0, 0};
         bool ok = true;
-        for (int tile = blockIdx.x; tile < kp.n_tiles && ok; tile += gridDim.x) {
+        while (ok) {
+            if (!warp_wait(c, &S->tempty[rt.slot], rt.phase ^ 1u)) break;
+            int tile = 0;
+            if (lane == 0) {
+                tile = (int)atomicAdd(kp.counter, 1u);
+                if (tile >= kp.n_tiles) tile = -1;
+                *(volatile int *)&S->tile_ring[rt.slot] = tile;
+                mbar_arrive(&S->tfull[rt.slot]);
+            }
+            tile = __shfl_sync(0xffffffffu, tile, 0);
+            rt.next(TRING);
+            if (tile < 0) break;
             const TileDev td = kp.tiles[tile];
             const InstDev &I = kp.insts[td.inst];
             const int nst = I.nblk;
@@ -446,7 +482,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
         const uint32_t ta0 = tmem + lane_base + A_COL + (uint32_t)grp * A_SLOT_COLS + 12u * half;
         uint32_t G = 0;   // global index of the tile's first stage
         bool stalled = false, ok = true;
-        for (int tile = blockIdx.x; tile < kp.n_tiles && ok; tile += gridDim.x) {
+        Ring rt{0, 0};
+        while (ok) {
+            const int tile = next_tile(c, rt, ok);
+            if (tile < 0) break;
             const TileDev td = kp.tiles[tile];
             const InstDev &I = kp.insts[td.inst];
             const int nst = I.nblk;
@@ -500,7 +539,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
         uint32_t gc = 0;
         bool ok = true;
-        for (int tile = blockIdx.x; tile < kp.n_tiles && ok; tile += gridDim.x) {
+        Ring rt{0, 0};
+        while (ok) {
+            const int tile = next_tile(c, rt, ok);
+            if (tile < 0) break;
             const TileDev td = kp.tiles[tile];
             const InstDev &I = kp.insts[td.inst];
             const int ncols = td.ncols, cskip = td.cskip;
@@ -574,7 +616,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
         Ring rs{0, 0}, ra{0, 0};
         uint32_t gc = 0;
         bool issued = false, ok = true;
-        for (int tile = blockIdx.x; tile < kp.n_tiles && ok; tile += gridDim.x) {
+        Ring rt{0, 0};
+        while (ok) {
+            const int tile = next_tile(c, rt, ok);
+            if (tile < 0) break;
             const TileDev td = kp.tiles[tile];
             const InstDev &I = kp.insts[td.inst];
             const int nst = I.nblk;
@@ -739,13 +784,14 @@ int smem_for(int ns, int stage_bytes) { return ns * stage_bytes + (int)sizeof(Sh
 
 template <int ELEM, int TERMS>
 cudaError_t launch_one(const InstDev *d_inst, const TileDev *d_tiles, long long n_tiles, const unsigned *maxbits,
-                       const uint8_t *psi, const TcConfig &cfg, int *status, cudaStream_t s)
+                       const uint8_t *psi, unsigned *counter, const TcConfig &cfg, int *status, cudaStream_t s)
 {
     KParams kp;
     kp.insts = d_inst;
     kp.tiles = d_tiles;
     kp.maxbits = maxbits;
     kp.psi = psi;
+    kp.counter = counter;
     kp.status = status;
     kp.n_tiles = (int)n_tiles;
     kp.chunk_stages = (cfg.chunk_sites * 3) / KSTAGE;
@@ -775,18 +821,18 @@ cudaError_t launch_one(const InstDev *d_inst, const TileDev *d_tiles, long long 
 int tc_smem_bytes() { return smem_for(2, stage_bytes_for(TC_MAX_STAGED)); }
 
 cudaError_t launch_tc(const InstDev *d_inst, const TileDev *d_tiles, long long n_tiles, const unsigned *d_maxbits,
-                      const uint8_t *psi, const TcConfig &cfg, int *d_status, cudaStream_t s)
+                      const uint8_t *psi, unsigned *counter, const TcConfig &cfg, int *d_status, cudaStream_t s)
 {
     if (n_tiles <= 0) return cudaSuccess;
     if (n_tiles > 0x7fffffffLL || cfg.max_staged > TC_MAX_STAGED) return cudaErrorNotSupported;
     if (cfg.elem == 0 && cfg.terms == 3)
-        return launch_one<0, 3>(d_inst, d_tiles, n_tiles, d_maxbits, psi, cfg, d_status, s);
+        return launch_one<0, 3>(d_inst, d_tiles, n_tiles, d_maxbits, psi, counter, cfg, d_status, s);
     if (cfg.elem == 1 && cfg.terms == 3)
-        return launch_one<1, 3>(d_inst, d_tiles, n_tiles, d_maxbits, psi, cfg, d_status, s);
+        return launch_one<1, 3>(d_inst, d_tiles, n_tiles, d_maxbits, psi, counter, cfg, d_status, s);
     if (cfg.elem == 0 && cfg.terms == 1)
-        return launch_one<0, 1>(d_inst, d_tiles, n_tiles, d_maxbits, psi, cfg, d_status, s);
+        return launch_one<0, 1>(d_inst, d_tiles, n_tiles, d_maxbits, psi, counter, cfg, d_status, s);
     if (cfg.elem == 1 && cfg.terms == 1)
-        return launch_one<1, 1>(d_inst, d_tiles, n_tiles, d_maxbits, psi, cfg, d_status, s);
+        return launch_one<1, 1>(d_inst, d_tiles, n_tiles, d_maxbits, psi, counter, cfg, d_status, s);
     return cudaErrorNotSupported;
 }
 
