@@ -178,6 +178,83 @@ def run_reference(args):
     return 0
 
 
+def run_ragged(args):
+    """--workload ragged: 200 ragged instances (L in {16,24,32}, N in [24,96], P in {1,7,19,33},
+    T in 1..8) in one plan; the same instances as 200 separate plans for comparison."""
+    import torch
+    from paper_2510_26313_gb300 import binding as laph
+    torch.cuda.set_device(0)
+    insts = synth.ragged_instances(200)
+    specs = [(i.L, i.T, i.N, i.momenta) for i in insts]
+    flops_step = sum(i.T * flops_per_timeslice(i.L, i.N, i.P) for i in insts)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(synth.SEED_BASE)
+    phis = []
+    for i in insts:
+        z = torch.randn((i.T, i.N, i.V, 3, 2), generator=gen, device="cuda", dtype=torch.float32)
+        phis.append(torch.view_as_complex(z).contiguous() / math.sqrt(3 * i.V))
+    plan = laph.Plan(specs, mode=args.mode, flags=laph.PLAN_TIMING, chunk_sites=args.chunk_sites)
+    Bs, Ms = plan.alloc_outputs()
+    ws = plan.alloc_workspace()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        plan.execute(phis, Bs, Ms, ws, stream=stream)
+    torch.cuda.synchronize()
+    if plan.device_status() != laph.LAPH_OK:
+        raise RuntimeError("device status not OK after warm-up")
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.execute(phis, Bs, Ms, ws, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    n_con = plan.contraction_launches()
+    k_ms = sum(plan.kernel_times(args.steps * n_con)) / args.steps
+    # accuracy on the smallest instances (timeslice 0) against the FP64 oracle
+    rel = []
+    if not args.no_cpu_baseline:
+        small = sorted(range(len(insts)), key=lambda n: insts[n].T * flops_per_timeslice(insts[n].L, insts[n].N, insts[n].P))[:3]
+        for n in small:
+            B0, M0, _, _, _ = oracle_sample(phis[n][0].cpu().numpy().astype(np.complex64), insts[n].L, insts[n].momenta)
+            rel.append({"instance": n, "B": rel_frob(Bs[n][0].cpu().numpy(), B0), "M": rel_frob(Ms[n][0].cpu().numpy(), M0)})
+    # the same instances, one plan each, executed back to back
+    del ws
+    torch.cuda.empty_cache()
+    single = [laph.Plan([sp], mode=args.mode, chunk_sites=args.chunk_sites) for sp in specs]
+    sws = torch.empty(max(pl.workspace_size() for pl in single), dtype=torch.uint8, device="cuda")  # shared, stream-ordered
+    for n, pl in enumerate(single):
+        pl.execute([phis[n]], [Bs[n]], [Ms[n]], sws, stream=stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for n, pl in enumerate(single):
+        pl.execute([phis[n]], [Bs[n]], [Ms[n]], sws, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_single = e0.elapsed_time(e1)
+    peaks, _ = measured_peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    line = {
+        "metric": "ragged batch complex TFLOP/s (200 instances, one plan)", "value": flops_step / (ms / 1e3) / 1e12,
+        "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": f"{args.mode}->f32/f64",
+        "data": "synthetic (seeded complex Gaussian, not orthonormalised)",
+        "config": {"workload": "200 ragged instances: L in {16,24,32}, N in [24,96], P in {1,7,19,33}, T in 1..8",
+                   "timeslices": sum(i.T for i in insts), "mode": args.mode},
+        "roofline": {"bound": "tensor", "achieved": flops_step / (k_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                     "frac": flops_step / (k_ms / 1e3) / 1e12 / peak, "traffic": None},
+        "per_instance_plans": {"ms_per_step": ms_single, "value": flops_step / (ms_single / 1e3) / 1e12},
+        "gpu_launches": plan.launches_per_execute() * args.steps, "clocks": clk, "rel_err": rel,
+        "contraction_launches": n_con, "kernel_ms": k_ms,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -185,7 +262,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="f16x3")
-    ap.add_argument("--workload", default="metric", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="metric", choices=sorted(WORKLOADS) + ["ragged"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -194,6 +271,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "ragged":
+        return run_ragged(args)
 
     import torch
     import torch.distributed as dist
