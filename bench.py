@@ -361,6 +361,41 @@ def main():
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None, "peak_source": "152 SMs x 128 FP32 FMA lanes x 2 x max SM clock"}
 
+    # ---- the memory-bound stages on their own (outside the timed region):
+    # materialised diquarks D (K-b) on 4 timeslices and the dense sign fill (K-g)
+    aux = None
+    if rank == 0:
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        Td = min(4, T)
+        npair = N * (N - 1) // 2
+        D = torch.empty((Td, npair, V, 3), dtype=torch.complex64, device="cuda")
+        dense = torch.empty((Td, P, N, N, N), dtype=torch.complex128, device="cuda")
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        laph.diquarks(phi[:Td], L, out=D)
+        laph.baryon_dense(Bs[0][:Td], N, out=dense)
+        torch.cuda.synchronize()
+        reps = 3
+        ev[0].record(stream)
+        for _ in range(reps):
+            laph.diquarks(phi[:Td], L, out=D)
+        ev[1].record(stream)
+        for _ in range(reps):
+            laph.baryon_dense(Bs[0][:Td], N, out=dense)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        dq_ms = ev[0].elapsed_time(ev[1]) / reps
+        df_ms = ev[1].elapsed_time(ev[2]) / reps
+        dq_bytes = Td * N * V * 3 * 8 + D.numel() * 8
+        df_bytes = Td * P * (N * (N - 1) * (N - 2) // 6) * 16 + dense.numel() * 16
+        aux = {
+            "diquark_kernel": {"timeslices": Td, "ms": dq_ms, "bytes": dq_bytes, "achieved": dq_bytes / (dq_ms / 1e3) / 1e9,
+                               "peak": hbm, "unit": "GB/s", "frac": dq_bytes / (dq_ms / 1e3) / 1e9 / hbm},
+            "dense_fill_kernel": {"timeslices": Td, "ms": df_ms, "bytes": df_bytes,
+                                  "achieved": df_bytes / (df_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                                  "frac": df_bytes / (df_ms / 1e3) / 1e9 / hbm},
+        }
+        del D, dense
+
     # ---- accuracy and CPU baseline on timeslice 0 (rank 0 only)
     rel = None
     cpu = None
@@ -409,6 +444,7 @@ def main():
                        "mode": args.mode, "l2": "inputs larger than L2 (phi %.2f GB)" % (phi_h.nbytes / 1e9),
                        "parallelism": f"replicas x{world} (independent timeslice batches)"},
             "roofline": roof,
+            "aux_kernels": aux,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": plan.launches_per_execute() * args.steps,

@@ -161,97 +161,161 @@ cudaError_t launch_blockify(const InstDev *d_inst, int inst, const InstDev &h, c
 
 // ---------------------------------------------------------------- K-b
 // D[t][q][x][c] = (phi_i(x) x phi_j(x))_c for q = C(j,2) + i.  One block per
-// (site block of SB sites, timeslice): phi of all N vectors for those sites
-// is staged in shared memory with 16-byte loads, then every warp writes whole
-// pairs, SB*3 complex numbers per pair, as contiguous 16-byte stores.
-__global__ void diquark_kernel(const float2 *__restrict__ phi, int N, long long V, int SB, float2 *__restrict__ out)
+// (block of DQ_SB = 64 sites, timeslice): phi of all N vectors for those
+// sites is staged in shared memory, then every warp takes one pair at a time
+// and each lane forms two whole sites (6 complex, three 16-byte loads per
+// vector, 48 FMAs).  The lane's 48 bytes go through a per-warp shared buffer
+// so that each global store instruction writes 512 contiguous bytes.
+constexpr int DQ_SB = 64;
+constexpr int DQ_THREADS = 256;
+
+__global__ void __launch_bounds__(DQ_THREADS) diquark_kernel(const float2 *__restrict__ phi, int N, long long V,
+                                                             float2 *__restrict__ out)
 {
-    extern __shared__ float2 sphi[];  // [N][SB*3]
+    extern __shared__ float4 dq_smem[];
+    float2 *sphi = reinterpret_cast<float2 *>(dq_smem);          // [N][DQ_SB][3]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = DQ_THREADS / 32;
+    float4 *xbuf = dq_smem + (size_t)N * DQ_SB * 3 / 2 + warp * 96; // per warp: 96 x 16 bytes
     const int t = blockIdx.y;
-    const long long x0 = (long long)blockIdx.x * SB;
-    const int nsite = (int)((V - x0) < SB ? (V - x0) : SB);
-    const int w3 = SB * 3;
+    const long long x0 = (long long)blockIdx.x * DQ_SB;
+    const int nsite = (int)((V - x0) < DQ_SB ? (V - x0) : DQ_SB);
+    const bool aligned = (V & 1) == 0;   // 16-byte aligned rows of phi and D
     const float2 *src = phi + (long long)t * N * V * 3;
-    // stage: vector n, complex e in [0, nsite*3)
-    for (int idx = threadIdx.x; idx < N * w3; idx += blockDim.x) {
-        const int n = idx / w3, e = idx - n * w3;
-        sphi[idx] = e < nsite * 3 ? __ldg(src + ((long long)n * V + x0) * 3 + e) : make_float2(0.f, 0.f);
+    const int w3 = DQ_SB * 3;
+    // stage phi[t][n][x0 .. x0+nsite)[3], zero past V
+    if (aligned) {
+        const int q4 = w3 / 2;   // float4 per vector
+        for (int idx = threadIdx.x; idx < N * q4; idx += DQ_THREADS) {
+            const int n = idx / q4, e = idx - n * q4;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (2 * e < nsite * 3) v = __ldg(reinterpret_cast<const float4 *>(src + ((long long)n * V + x0) * 3) + e);
+            dq_smem[idx] = v;
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < N * w3; idx += DQ_THREADS) {
+            const int n = idx / w3, e = idx - n * w3;
+            sphi[idx] = e < nsite * 3 ? __ldg(src + ((long long)n * V + x0) * 3 + e) : make_float2(0.f, 0.f);
+        }
     }
     __syncthreads();
     const long long pairs = binom2(N);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-    const bool vec4 = ((V & 1) == 0) && (nsite == SB);  // 16-byte aligned whole rows
+    int i = 0, j = 1;
+    if (warp < pairs) pair_of(warp, i, j);
     for (long long q = warp; q < pairs; q += nwarp) {
-        int i, j;
-        pair_of(q, i, j);
-        const float2 *u = sphi + i * w3, *v = sphi + j * w3;
-        float2 *dst = out + (((long long)t * pairs + q) * V + x0) * 3;
-        if (vec4) {
-            for (int f = lane; f < w3 / 2; f += 32) {
-                float2 r[2];
+        // sites 2 lane, 2 lane + 1 of vectors i and j
+        const float4 *u4 = reinterpret_cast<const float4 *>(sphi + ((long long)i * DQ_SB + 2 * lane) * 3);
+        const float4 *v4 = reinterpret_cast<const float4 *>(sphi + ((long long)j * DQ_SB + 2 * lane) * 3);
+        float2 u[6], v[6];
 #pragma unroll
-                for (int h = 0; h < 2; h++) {
-                    const int e = 2 * f + h, x = e / 3, c = e - 3 * x;
-                    r[h] = cross_c(u + 3 * x, v + 3 * x, c);
-                }
-                reinterpret_cast<float4 *>(dst)[f] = make_float4(r[0].x, r[0].y, r[1].x, r[1].y);
-            }
+        for (int h = 0; h < 3; h++) {
+            const float4 a = u4[h], b = v4[h];
+            u[2 * h] = make_float2(a.x, a.y);
+            u[2 * h + 1] = make_float2(a.z, a.w);
+            v[2 * h] = make_float2(b.x, b.y);
+            v[2 * h + 1] = make_float2(b.z, b.w);
+        }
+        float2 d[6];
+#pragma unroll
+        for (int e = 0; e < 6; e++) d[e] = cross_c(u + 3 * (e / 3), v + 3 * (e / 3), e % 3);
+        float2 *dst = out + (((long long)t * pairs + q) * V + x0) * 3;
+        if (aligned && nsite == DQ_SB) {
+            // transpose through the warp's buffer: lane l holds float4 3l..3l+2 of the pair's 96
+#pragma unroll
+            for (int h = 0; h < 3; h++) xbuf[3 * lane + h] = make_float4(d[2 * h].x, d[2 * h].y, d[2 * h + 1].x, d[2 * h + 1].y);
+            __syncwarp();
+#pragma unroll
+            for (int h = 0; h < 3; h++) reinterpret_cast<float4 *>(dst)[32 * h + lane] = xbuf[32 * h + lane];
+            __syncwarp();
         } else {
-            for (int e = lane; e < nsite * 3; e += 32) {
-                const int x = e / 3, c = e - 3 * x;
-                dst[e] = cross_c(u + 3 * x, v + 3 * x, c);
+#pragma unroll
+            for (int e = 0; e < 6; e++)
+                if (6 * lane + e < nsite * 3) dst[6 * lane + e] = d[e];
+        }
+        // next pair of this warp: q + nwarp
+        const long long qn = q + nwarp;
+        if (qn < pairs) {
+            i += nwarp;
+            while (i >= j) {
+                i -= j;
+                j++;
             }
         }
+    }
+}
+
+// Vector counts whose staged sites do not fit in shared memory: one thread per
+// output entry, operands read from global memory.
+__global__ void diquark_generic_kernel(const float2 *__restrict__ phi, int N, long long V, long long total,
+                                       float2 *__restrict__ out)
+{
+    const long long pairs = binom2(N);
+    for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < total; o += (long long)gridDim.x * blockDim.x) {
+        const long long e = o % (3 * V), r = o / (3 * V);
+        const long long q = r % pairs, t = r / pairs;
+        int i, j;
+        pair_of(q, i, j);
+        const long long x = e / 3;
+        const int c = (int)(e - 3 * x);
+        const float2 *u = phi + ((t * N + i) * V + x) * 3, *v = phi + ((t * N + j) * V + x) * 3;
+        float2 uu[3] = {__ldg(u), __ldg(u + 1), __ldg(u + 2)}, vv[3] = {__ldg(v), __ldg(v + 1), __ldg(v + 2)};
+        out[o] = cross_c(uu, vv, c);
     }
 }
 
 cudaError_t launch_diquarks(const float2 *phi, int L, int T, int N, float2 *out, cudaStream_t s)
 {
     const long long V = (long long)L * L * L;
-    int SB = 32;
-    while (SB > 2 && (long long)N * SB * 3 * 8 > 160 * 1024) SB /= 2;
-    const size_t smem = (size_t)N * SB * 3 * sizeof(float2);
-    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)N * DQ_SB * 3 * sizeof(float2) + (DQ_THREADS / 32) * 96 * 16;
+    if (smem > 227 * 1024) {
+        const long long total = (long long)T * binom2(N) * 3 * V;
+        long long blocks = (total + 255) / 256;
+        if (blocks > 152 * 64) blocks = 152 * 64;
+        diquark_generic_kernel<<<(unsigned)blocks, 256, 0, s>>>(phi, N, V, total, out);
+        return cudaGetLastError();
+    }
     cudaError_t e = cudaFuncSetAttribute(diquark_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 g((unsigned)((V + SB - 1) / SB), (unsigned)T);
-    diquark_kernel<<<g, 256, smem, s>>>(phi, N, V, SB, out);
+    dim3 g((unsigned)((V + DQ_SB - 1) / DQ_SB), (unsigned)T);
+    diquark_kernel<<<g, DQ_THREADS, smem, s>>>(phi, N, V, out);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- K-g
 // dense[t][p][a][b][c] = sign * packed[t][p][C(k,3)+C(j,2)+i] with (i,j,k) the
-// sorted (a,b,c) and sign the parity of the sort; 0 on a repeated index.
-__global__ void dense_fill_kernel(const double2 *__restrict__ packed, int N, long long n_trip, long long total,
-                                  double2 *__restrict__ dense)
+// sorted (a,b,c) and sign the parity of the sort (the product of the signs
+// of b-a, c-a and c-b); 0 on a repeated index.  Block (a, tp) writes the N*N
+// entries (b, c) of row a, c fastest; no branches depend on the indices.
+__global__ void __launch_bounds__(256) dense_fill_kernel(const double2 *__restrict__ packed, int N, long long n_trip,
+                                                         long long tp0, double2 *__restrict__ dense)
 {
-    const long long n3 = (long long)N * N * N;
-    for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < total; o += (long long)gridDim.x * blockDim.x) {
-        const long long tp = o / n3;
-        const long long r = o - tp * n3;
-        int a = (int)(r / ((long long)N * N)), b = (int)((r / N) % N), c = (int)(r % N);
-        double sgn = 1.0;
-        int t0;
-        if (a > b) { t0 = a; a = b; b = t0; sgn = -sgn; }
-        if (b > c) { t0 = b; b = c; c = t0; sgn = -sgn; }
-        if (a > b) { t0 = a; a = b; b = t0; sgn = -sgn; }
-        double2 v = make_double2(0.0, 0.0);
-        if (a != b && b != c) {
-            const double2 s = packed[tp * n_trip + binom3(c) + binom2(b) + a];
-            v = make_double2(sgn * s.x, sgn * s.y);
-        }
-        dense[o] = v;
+    const int a = blockIdx.x;
+    const long long tp = tp0 + blockIdx.y;
+    const double2 *pk = packed + tp * n_trip;
+    double2 *row = dense + (tp * N + a) * (long long)N * N;
+    const int nn = N * N;
+#pragma unroll 4
+    for (int r = threadIdx.x; r < nn; r += 256) {
+        const int b = r / N, c = r - b * N;
+        const int lo = min(a, min(b, c)), hi = max(a, max(b, c)), mid = a + b + c - lo - hi;
+        const bool neg = (b < a) ^ (c < a) ^ (c < b);
+        const bool rep = (a == b) | (b == c) | (a == c);
+        const long long idx = binom3(hi) + binom2(mid) + lo;
+        const double2 w = rep ? make_double2(0.0, 0.0) : __ldg(pk + idx);
+        row[r] = (neg && !rep) ? make_double2(-w.x, -w.y) : w;
     }
 }
 
 cudaError_t launch_dense_fill(const double2 *packed, int T, int N, int P, double2 *dense, cudaStream_t s)
 {
-    const long long total = (long long)T * P * N * N * N;
-    long long blocks = (total + 255) / 256;
-    if (blocks > 152 * 64) blocks = 152 * 64;
-    if (blocks < 1) blocks = 1;
-    dense_fill_kernel<<<(unsigned)blocks, 256, 0, s>>>(packed, N, binom3(N), total, dense);
-    return cudaGetLastError();
+    const long long TP = (long long)T * P;
+    for (long long tp0 = 0; tp0 < TP; tp0 += 65535) {
+        const long long n = TP - tp0 < 65535 ? TP - tp0 : 65535;
+        dim3 g((unsigned)N, (unsigned)n);
+        dense_fill_kernel<<<g, 256, 0, s>>>(packed, N, binom3(N), tp0, dense);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace laph

@@ -105,7 +105,9 @@ def test_phase_table_matches_oracle(laph):
 
 def test_diquarks_match_oracle(laph):
     import torch
-    for L, N, T in [(4, 7, 2), (5, 6, 1)]:           # V even (16-byte stores) and V odd
+    # V even with whole 64-site blocks (transposed 16-byte stores), V odd, a partial last
+    # block with many pairs per warp, and a vector count beyond the shared-memory window
+    for L, N, T in [(4, 7, 2), (5, 6, 1), (6, 40, 1), (4, 150, 1)]:
         phi_h = synth.random_phi(L, N, T=T, instance=20 + L)
         D = laph.diquarks(torch.from_numpy(phi_h).cuda(), L).cpu().numpy()
         for t in range(T):
