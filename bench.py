@@ -36,6 +36,8 @@ WORKLOADS = {
     "metric": (32, 64, 64, 2),
     "medium": (24, 48, 32, 1),
     "small": (8, 1, 16, None),
+    # a case small enough for full ncu captures (inputs still larger than L2 once staged)
+    "profile": (24, 2, 64, 2),
 }
 METRIC = "baryon+meson block complex TFLOP/s at L=32,N=64,Np=19; tensor-pipe %; rel err vs FP64"
 

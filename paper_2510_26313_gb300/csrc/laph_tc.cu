@@ -303,6 +303,22 @@ __device__ __noinline__ bool warp_wait_slow(Shared *S, int *status, int lane, ui
     }
 }
 
+// Bounded wait that ignores the abort flag: used at exit to let the bulk
+// copies a warp issued land before the CTA's shared memory is released.
+__device__ __noinline__ void drain_wait(Shared *S, int *status, int lane, uint64_t *bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (!__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) {
+        if (clock64() - t0 > WAIT_LIMIT) {
+            if (lane == 0) {
+                *(volatile int *)&S->abort = 1;
+                atomicOr(status, STATUS_TIMEOUT);
+            }
+            return;
+        }
+    }
+}
+
 // Warp-wide bounded wait (every lane calls it; the result is warp-uniform).
 __device__ __forceinline__ bool warp_wait(const Ctx c, uint64_t *bar, uint32_t parity)
 {
@@ -439,6 +455,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
     if (warp == WARP_LOAD) {
         // ---------------------------------------------------------- loader
         Ring rs{0, 0}, rt{0, 0};
+        uint32_t n_issued = 0;   // stages whose copies were issued
         bool ok = true;
         while (ok) {
             if (!warp_wait(c, &S->tempty[rt.slot], rt.phase ^ 1u)) break;
@@ -472,8 +489,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
                 }
                 __syncwarp();
                 rs.next(NS);
+                n_issued++;
             }
         }
+        // the copies of the last NS issued stages may still be in flight (after
+        // an abort nobody consumed them): wait until they have landed
+        for (uint32_t k = n_issued > (uint32_t)NS ? n_issued - NS : 0; k < n_issued; k++)
+            drain_wait(S, kp.status, lane, &S->full[k % NS], (k / NS) & 1u);
     } else if (warp < N_AWARPS) {
         // ---------------------------------------------------------- A producers
         const int quad = warp & 3, half = (warp >> 2) & 1, grp = warp >> 3;

@@ -221,3 +221,23 @@ def test_invariances_at_size(laph):
         assert rel_frob(B2, fac[None, :, None] * B0) <= 2e-5
         assert rel_frob(M2, fac[None, :, None, None] * M0) <= 2e-5
         np.testing.assert_allclose(M0[0, 0], np.eye(N), atol=2e-6 if mode == "fp32" else 1e-5)
+
+
+def test_stalled_producer_times_out_and_context_stays_usable(laph):
+    """A producer warp that never arrives (the plan's stall hook) makes the MMA's bounded wait
+    expire: the kernel records a timeout, every role returns, and the context stays usable."""
+    import torch
+    L, T, N = 4, 1, 10
+    mom = synth.momentum_shell(1)
+    phi_h = synth.random_phi(L, N, T=T, instance=90)
+    phi = torch.from_numpy(phi_h).cuda()
+    plan = laph.Plan([(L, T, N, mom)], mode="f16x3", flags=laph.PLAN_DEBUG_STALL)
+    Bs, Ms = plan.alloc_outputs()
+    ws = plan.alloc_workspace()
+    plan.execute([phi], Bs, Ms, ws)
+    torch.cuda.synchronize()
+    assert plan.device_status() == laph.LAPH_ERR_TIMEOUT
+    plan.close()
+    B, M = _run(laph, phi_h, L, mom, "f16x3")
+    rB, rM = _oracle(phi_h, L, mom)
+    assert rel_frob(B, rB) <= 1e-5 and rel_frob(M, rM) <= 1e-5
