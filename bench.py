@@ -117,6 +117,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(ms: float, device) -> float:
+    """The largest of a per-rank duration over all ranks of the process group (the duration
+    itself for one rank): the job's time is its slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(flops_per_rank: float, ms: float, world: int) -> float:
+    """Whole-job TFLOP/s: every rank processes its own batch of the same size."""
+    return world * flops_per_rank / (ms / 1e3) / 1e12
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -329,14 +346,11 @@ def main():
     n_con = plan.contraction_launches()
     kernel_ms = plan.kernel_times(args.steps * n_con)
     operand_ms = plan.operand_times(args.steps * n_con) if args.mode != "fp32" else []
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, "cuda")
     status = plan.device_status()
 
     flops_step = T * flops_per_timeslice(L, N, P)
-    value = world * flops_step / (ms / 1e3) / 1e12
+    value = weak_scaling_value(flops_step, ms, world)
     k_avg = sum(kernel_ms) / args.steps          # contraction kernel time per step (all chunks)
     achieved = flops_step / (k_avg / 1e3) / 1e12
     peaks, peak_src = measured_peaks()
@@ -426,11 +440,8 @@ def main():
             plan.execute_host([phi_pin], Bh, Mh, hws, stream=stream)
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-        if world > 1:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * flops_step / e2e_s / 1e12, "unit": "TFLOP/s",
+        e2e_s = max_over_ranks(e2e_s, "cuda")
+        e2e = {"value": weak_scaling_value(flops_step, 1e3 * e2e_s, world), "unit": "TFLOP/s",
                "h2d_bytes_per_step": int(phi_pin.numel() * 8),
                "d2h_bytes_per_step": int(Bh[0].numel() * 16 + Mh[0].numel() * 16),
                "ms_per_step": 1e3 * e2e_s}

@@ -4,6 +4,8 @@ Relative Frobenius error per output (B and M separately) and the worst
 per-(t,p) slice, bounded by 1e-5 for the FP32 and split-precision paths and
 by the stated per-mode bound for single-term FP16/BF16.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -241,3 +243,61 @@ def test_stalled_producer_times_out_and_context_stays_usable(laph):
     B, M = _run(laph, phi_h, L, mom, "f16x3")
     rB, rM = _oracle(phi_h, L, mom)
     assert rel_frob(B, rB) <= 1e-5 and rel_frob(M, rM) <= 1e-5
+
+
+def _sampled_triples(N, n, seed):
+    rng = np.random.default_rng(seed)
+    trip = sorted({tuple(int(v) for v in sorted(rng.choice(N, 3, replace=False))) for _ in range(n)})
+    idx = [math.comb(k, 3) + math.comb(j, 2) + i for (i, j, k) in trip]
+    return trip, idx
+
+
+def test_metric_workload_sampled_parity(laph):
+    """L=32, T=64, N=64, P=19 (|n|^2 <= 2), the benchmark's inputs and its chunked launch
+    configuration: sampled baryon triples and whole meson blocks of the first and last
+    timeslices against the oracle."""
+    import torch
+    L, T, N = 32, 64, 64
+    mom = synth.momentum_shell(2)
+    phi_h = synth.random_phi(L, N, T=T, instance=0)
+    plan = laph.Plan([(L, T, N, mom)], mode="f16x3")
+    assert plan.contraction_launches() > 1
+    phi = torch.from_numpy(phi_h).cuda()
+    Bs, Ms = plan.alloc_outputs()
+    ws = plan.alloc_workspace()
+    plan.execute([phi], Bs, Ms, ws)
+    torch.cuda.synchronize()
+    assert plan.device_status() == laph.LAPH_OK
+    trip, idx = _sampled_triples(N, 400, 5)
+    for t in (0, T - 1):
+        ref = O.baryon_triples(phi_h[t], L, mom, trip)                 # [n][P]
+        got = Bs[0][t][:, idx].cpu().numpy().T
+        assert rel_frob(got, ref) <= 1e-5
+        assert rel_frob(Ms[0][t].cpu().numpy(), O.meson_blocks(phi_h[t], L, mom)) <= 1e-5
+    plan.close()
+
+
+def test_large_streamed_shape_sampled_parity(laph):
+    """L=48, N=128, 33 momenta (|n|^2 <= 4): one timeslice per chunk, 128 staged row vectors.
+    Sampled triples, and the meson blocks of a subset of vectors (M[i][j] depends only on
+    vectors i and j)."""
+    import torch
+    L, T, N = 48, 1, 128
+    mom = synth.momentum_shell(4)
+    assert mom.shape[0] == 33
+    phi_h = synth.random_phi(L, N, T=T, instance=7)
+    plan = laph.Plan([(L, T, N, mom)], mode="f16x3")
+    phi = torch.from_numpy(phi_h).cuda()
+    Bs, Ms = plan.alloc_outputs()
+    ws = plan.alloc_workspace()
+    plan.execute([phi], Bs, Ms, ws)
+    torch.cuda.synchronize()
+    assert plan.device_status() == laph.LAPH_OK
+    trip, idx = _sampled_triples(N, 200, 6)
+    ref = O.baryon_triples(phi_h[0], L, mom, trip)
+    assert rel_frob(Bs[0][0][:, idx].cpu().numpy().T, ref) <= 1e-5
+    sub = np.sort(np.random.default_rng(8).choice(N, 12, replace=False))
+    rM = O.meson_blocks(phi_h[0][sub], L, mom)
+    gM = Ms[0][0].cpu().numpy()[:, sub][:, :, sub]
+    assert rel_frob(gM, rM) <= 1e-5
+    plan.close()
