@@ -71,6 +71,10 @@ struct laph_plan {
     size_t ws_bytes = 0, off_maxbits = 0, off_counter = 0, ws_zero_bytes = 0;
     // tensor-core path: chunks of (instance, timeslice) units and their B-operand images
     laph::PsiUnit *d_units = nullptr;
+    std::vector<laph::PsiUnit> h_units;
+    // laph_plan_execute_host: copy streams and per-chunk events, made on first use
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    std::vector<cudaEvent_t> ev_in, ev_out;
     struct Chunk {
         int unit0, n_units;
         long long n_jobs;
@@ -158,6 +162,10 @@ static void free_plan(laph_plan *p)
     cudaFree(p->d_inst);
     cudaFree(p->d_phase);
     cudaFree(p->d_units);
+    for (cudaEvent_t e : p->ev_in) cudaEventDestroy(e);
+    for (cudaEvent_t e : p->ev_out) cudaEventDestroy(e);
+    if (p->h2d) cudaStreamDestroy(p->h2d);
+    if (p->d2h) cudaStreamDestroy(p->d2h);
     cudaFree(p->d_tiles);
     cudaFree(p->d_status);
     for (cudaEvent_t e : p->ev_begin) cudaEventDestroy(e);
@@ -411,6 +419,7 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
         PCK(cudaMalloc((void **)&p->d_tiles, sizeof(TileDev) * tiles.size()));
         PCK(cudaMemcpy(p->d_tiles, tiles.data(), sizeof(TileDev) * tiles.size(), cudaMemcpyHostToDevice));
     }
+    p->h_units = units;
     if (!units.empty()) {
         PCK(cudaMalloc((void **)&p->d_units, sizeof(laph::PsiUnit) * units.size()));
         PCK(cudaMemcpy(p->d_units, units.data(), sizeof(laph::PsiUnit) * units.size(), cudaMemcpyHostToDevice));
@@ -484,6 +493,65 @@ int laph_plan_set_chunk_sites(laph_plan *plan, int chunk_sites)
     return LAPH_OK;
 }
 
+static laph::TcConfig tc_config(const laph_plan *p)
+{
+    laph::TcConfig cfg;
+    cfg.elem = (p->mode == LAPH_MODE_TC_BF16X3 || p->mode == LAPH_MODE_TC_BF16) ? 1 : 0;
+    cfg.terms = (p->mode == LAPH_MODE_TC_F16X3 || p->mode == LAPH_MODE_TC_BF16X3) ? 3 : 1;
+    cfg.chunk_sites = p->chunk_sites;
+    cfg.grid = p->grid;
+    cfg.max_staged = p->max_staged;
+    cfg.debug_stall = (p->flags & LAPH_PLAN_DEBUG_STALL) ? 1 : 0;
+    return cfg;
+}
+
+// B-operand pass and contraction of chunk ci (tensor-core path), with the
+// timing events of LAPH_PLAN_TIMING around each launch.
+static int launch_tc_chunk(laph_plan *p, char *ws, size_t ci, const laph::TcConfig &cfg, cudaStream_t s)
+{
+    cudaError_t e;
+    const bool timing = !p->ev_begin.empty();
+    unsigned *maxbits = (unsigned *)(ws + p->off_maxbits);
+    uint8_t *psi = (uint8_t *)(ws + p->off_psi);
+    unsigned *counters = (unsigned *)(ws + p->off_counter);
+    const laph_plan::Chunk &c = p->chunks[ci];
+    const int ps = (int)(p->n_ptimed % laph_plan::RING), cs = (int)(p->n_timed % laph_plan::RING);
+    if (timing) CK(cudaEventRecord(p->pv_begin[ps], s));
+    e = laph::launch_psi(p->d_inst, p->d_units + c.unit0, c.n_units, c.n_jobs, maxbits, cfg.elem, psi, s);
+    if (e != cudaSuccess) return cuda_fail(e, "psi");
+    if (timing) {
+        CK(cudaEventRecord(p->pv_end[ps], s));
+        p->n_ptimed++;
+        CK(cudaEventRecord(p->ev_begin[cs], s));
+    }
+    e = laph::launch_tc(p->d_inst, p->d_tiles + c.tile0, c.n_tiles, maxbits, psi, counters + ci, cfg, p->d_status, s);
+    if (e == cudaErrorNotSupported) return LAPH_ERR_UNSUPPORTED;
+    if (e != cudaSuccess) return cuda_fail(e, "tc contraction");
+    if (timing) {
+        CK(cudaEventRecord(p->ev_end[cs], s));
+        p->n_timed++;
+    }
+    return LAPH_OK;
+}
+
+// Scale and site-blocked copy of the timeslices of chunk ci, one launch pair
+// per run of consecutive timeslices of one instance.
+static int launch_chunk_prep(laph_plan *p, char *ws, size_t ci, cudaStream_t s)
+{
+    unsigned *maxbits = (unsigned *)(ws + p->off_maxbits);
+    const laph_plan::Chunk &c = p->chunks[ci];
+    for (int u = c.unit0; u < c.unit0 + c.n_units;) {
+        const int n = p->h_units[u].inst, t0 = p->h_units[u].t;
+        int nt = 1;
+        while (u + nt < c.unit0 + c.n_units && p->h_units[u + nt].inst == n && p->h_units[u + nt].t == t0 + nt) nt++;
+        cudaError_t e = laph::launch_scale_max_range(p->d_inst, n, t0, nt, p->phi_elems[n] / p->h_T[n], maxbits, s);
+        if (e == cudaSuccess) e = laph::launch_blockify_range(p->d_inst, n, p->h_inst[n], t0, nt, maxbits, s);
+        if (e != cudaSuccess) return cuda_fail(e, "scale/blockify");
+        u += nt;
+    }
+    return LAPH_OK;
+}
+
 static int launch_batch(laph_plan *p, void *workspace, cudaStream_t s)
 {
     cudaError_t e;
@@ -501,34 +569,10 @@ static int launch_batch(laph_plan *p, void *workspace, cudaStream_t s)
             e = laph::launch_blockify(p->d_inst, n, p->h_inst[n], maxbits, s);
             if (e != cudaSuccess) return cuda_fail(e, "blockify");
         }
-        laph::TcConfig cfg;
-        cfg.elem = (p->mode == LAPH_MODE_TC_BF16X3 || p->mode == LAPH_MODE_TC_BF16) ? 1 : 0;
-        cfg.terms = (p->mode == LAPH_MODE_TC_F16X3 || p->mode == LAPH_MODE_TC_BF16X3) ? 3 : 1;
-        cfg.chunk_sites = p->chunk_sites;
-        cfg.grid = p->grid;
-        cfg.max_staged = p->max_staged;
-        cfg.debug_stall = (p->flags & LAPH_PLAN_DEBUG_STALL) ? 1 : 0;
-        uint8_t *psi = (uint8_t *)(ws + p->off_psi);
-        unsigned *counters = (unsigned *)(ws + p->off_counter);
+        const laph::TcConfig cfg = tc_config(p);
         for (size_t ci = 0; ci < p->chunks.size(); ci++) {
-            const laph_plan::Chunk &c = p->chunks[ci];
-            const int ps = (int)(p->n_ptimed % laph_plan::RING), cs = (int)(p->n_timed % laph_plan::RING);
-            if (timing) CK(cudaEventRecord(p->pv_begin[ps], s));
-            e = laph::launch_psi(p->d_inst, p->d_units + c.unit0, c.n_units, c.n_jobs, maxbits, cfg.elem, psi, s);
-            if (e != cudaSuccess) return cuda_fail(e, "psi");
-            if (timing) {
-                CK(cudaEventRecord(p->pv_end[ps], s));
-                p->n_ptimed++;
-                CK(cudaEventRecord(p->ev_begin[cs], s));
-            }
-            e = laph::launch_tc(p->d_inst, p->d_tiles + c.tile0, c.n_tiles, maxbits, psi, counters + ci, cfg, p->d_status,
-                                s);
-            if (e == cudaErrorNotSupported) return LAPH_ERR_UNSUPPORTED;
-            if (e != cudaSuccess) return cuda_fail(e, "tc contraction");
-            if (timing) {
-                CK(cudaEventRecord(p->ev_end[cs], s));
-                p->n_timed++;
-            }
+            const int rc = launch_tc_chunk(p, ws, ci, cfg, s);
+            if (rc != LAPH_OK) return rc;
         }
     } else {
         laph::SimtConfig cfg;
@@ -626,7 +670,7 @@ int laph_plan_host_workspace_size(const laph_plan *plan, size_t *bytes)
 int laph_plan_execute_host(laph_plan *plan, const void *const *phi_host, void *const *out_B_host,
                            void *const *out_M_host, void *workspace, void *stream)
 {
-    if (!plan || !phi_host || !workspace || ((uintptr_t)workspace) % 256) return plan ? LAPH_ERR_ARG : LAPH_ERR_ARG;
+    if (!plan || !phi_host || !workspace || ((uintptr_t)workspace) % 256) return LAPH_ERR_ARG;
     const bool needB = !(plan->flags & LAPH_PLAN_SKIP_B), needM = !(plan->flags & LAPH_PLAN_SKIP_M);
     if ((needB && !out_B_host) || (needM && !out_M_host)) return LAPH_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -642,20 +686,78 @@ int laph_plan_execute_host(laph_plan *plan, const void *const *phi_host, void *c
         off += ((plan->outB_elems[n] * sizeof(double2) + 255) / 256) * 256;
         dM[n] = ws + off;
         off += ((plan->outM_elems[n] * sizeof(double2) + 255) / 256) * 256;
-        CK(cudaMemcpyAsync((void *)dphi[n], phi_host[n], plan->phi_elems[n] * sizeof(float2), cudaMemcpyHostToDevice, s));
     }
-    CK(cudaGetLastError());
     cudaError_t e = laph::launch_set_pointers(plan->d_inst, 0, plan->n_inst, dphi.data(), needB ? dB.data() : nullptr,
                                               needM ? dM.data() : nullptr, ws, s);
     if (e != cudaSuccess) return cuda_fail(e, "set_pointers");
-    int rc = launch_batch(plan, ws, s);
-    if (rc != LAPH_OK) return rc;
-    for (int n = 0; n < plan->n_inst; n++) {
-        if (needB)
-            CK(cudaMemcpyAsync(out_B_host[n], dB[n], plan->outB_elems[n] * sizeof(double2), cudaMemcpyDeviceToHost, s));
-        if (needM)
-            CK(cudaMemcpyAsync(out_M_host[n], dM[n], plan->outM_elems[n] * sizeof(double2), cudaMemcpyDeviceToHost, s));
+
+    if (!is_tc_mode(plan->mode)) {
+        for (int n = 0; n < plan->n_inst; n++)
+            CK(cudaMemcpyAsync((void *)dphi[n], phi_host[n], plan->phi_elems[n] * sizeof(float2), cudaMemcpyHostToDevice,
+                               s));
+        int rc = launch_batch(plan, ws, s);
+        if (rc != LAPH_OK) return rc;
+        for (int n = 0; n < plan->n_inst; n++) {
+            if (needB)
+                CK(cudaMemcpyAsync(out_B_host[n], dB[n], plan->outB_elems[n] * sizeof(double2), cudaMemcpyDeviceToHost, s));
+            if (needM)
+                CK(cudaMemcpyAsync(out_M_host[n], dM[n], plan->outM_elems[n] * sizeof(double2), cudaMemcpyDeviceToHost, s));
+        }
+        CK(cudaStreamSynchronize(s));
+        return LAPH_OK;
     }
+
+    // tensor-core path, chunk by chunk: the inputs of chunk c are copied in on
+    // one stream while chunk c-1 computes, and its outputs are copied out on a
+    // second stream while chunk c+1 computes
+    const size_t nc = plan->chunks.size();
+    if (!plan->h2d) {
+        CK(cudaStreamCreateWithFlags(&plan->h2d, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&plan->d2h, cudaStreamNonBlocking));
+    }
+    while (plan->ev_in.size() < nc) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        CK(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
+        plan->ev_in.push_back(a);
+        plan->ev_out.push_back(b);
+    }
+    CK(cudaMemsetAsync(ws, 0, plan->ws_zero_bytes, s));
+    // the copy streams start after everything already queued on `stream`
+    CK(cudaEventRecord(plan->ev_out[0], s));
+    CK(cudaStreamWaitEvent(plan->h2d, plan->ev_out[0], 0));
+    CK(cudaStreamWaitEvent(plan->d2h, plan->ev_out[0], 0));
+    const laph::TcConfig cfg = tc_config(plan);
+    for (size_t ci = 0; ci < nc; ci++) {
+        const laph_plan::Chunk &c = plan->chunks[ci];
+        for (int u = c.unit0; u < c.unit0 + c.n_units; u++) {
+            const int n = plan->h_units[u].inst, t = plan->h_units[u].t;
+            const size_t bytes = plan->phi_elems[n] / plan->h_T[n] * sizeof(float2);
+            CK(cudaMemcpyAsync((char *)dphi[n] + t * bytes, (const char *)phi_host[n] + t * bytes, bytes,
+                               cudaMemcpyHostToDevice, plan->h2d));
+        }
+        CK(cudaEventRecord(plan->ev_in[ci], plan->h2d));
+        CK(cudaStreamWaitEvent(s, plan->ev_in[ci], 0));
+        int rc = launch_chunk_prep(plan, ws, ci, s);
+        if (rc == LAPH_OK) rc = launch_tc_chunk(plan, ws, ci, cfg, s);
+        if (rc != LAPH_OK) return rc;
+        CK(cudaEventRecord(plan->ev_out[ci], s));
+        CK(cudaStreamWaitEvent(plan->d2h, plan->ev_out[ci], 0));
+        for (int u = c.unit0; u < c.unit0 + c.n_units; u++) {
+            const int n = plan->h_units[u].inst, t = plan->h_units[u].t;
+            if (needB) {
+                const size_t bytes = plan->outB_elems[n] / plan->h_T[n] * sizeof(double2);
+                CK(cudaMemcpyAsync((char *)out_B_host[n] + t * bytes, (char *)dB[n] + t * bytes, bytes,
+                                   cudaMemcpyDeviceToHost, plan->d2h));
+            }
+            if (needM) {
+                const size_t bytes = plan->outM_elems[n] / plan->h_T[n] * sizeof(double2);
+                CK(cudaMemcpyAsync((char *)out_M_host[n] + t * bytes, (char *)dM[n] + t * bytes, bytes,
+                                   cudaMemcpyDeviceToHost, plan->d2h));
+            }
+        }
+    }
+    CK(cudaStreamSynchronize(plan->d2h));
     CK(cudaStreamSynchronize(s));
     return LAPH_OK;
 }

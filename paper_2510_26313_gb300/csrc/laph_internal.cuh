@@ -123,6 +123,11 @@ cudaError_t launch_diquarks(const float2 *phi, int L, int T, int N, float2 *out,
 cudaError_t launch_dense_fill(const double2 *packed, int T, int N, int P, double2 *dense, cudaStream_t s);
 cudaError_t launch_blockify(const InstDev *d_inst, int inst, const InstDev &h, const unsigned *d_maxbits,
                             cudaStream_t s);
+// The same for the timeslices [t0, t0 + nt) of one instance.
+cudaError_t launch_scale_max_range(const InstDev *d_inst, int inst, int t0, int nt, long long elems_per_ts,
+                                   unsigned *d_maxbits, cudaStream_t s);
+cudaError_t launch_blockify_range(const InstDev *d_inst, int inst, const InstDev &h, int t0, int nt,
+                                  const unsigned *d_maxbits, cudaStream_t s);
 
 // laph_simt.cu
 struct SimtConfig {

@@ -85,10 +85,10 @@ cudaError_t launch_set_pointers(InstDev *d_inst, int first, int count, const voi
 // Largest |re|, |im| of phi per timeslice, as FP32 bits (non-negative floats
 // order like their bit patterns).  The tensor-core kernel turns it into an
 // exact power-of-two rescale before splitting into hi/lo halves.
-__global__ void scale_max_kernel(const InstDev *__restrict__ d_inst, int inst, unsigned *__restrict__ maxbits)
+__global__ void scale_max_kernel(const InstDev *__restrict__ d_inst, int inst, int t0, unsigned *__restrict__ maxbits)
 {
     const InstDev &I = d_inst[inst];
-    const int t = blockIdx.y;
+    const int t = t0 + blockIdx.y;
     const long long n = (long long)I.N * I.V * 3;
     const float2 *base = I.phi + (long long)t * n;
     float m = 0.f;
@@ -116,23 +116,37 @@ cudaError_t launch_scale_max(const InstDev *d_inst, int n_inst, const int *h_ts_
         if (blocks > 256) blocks = 256;
         if (blocks < 1) blocks = 1;
         dim3 g((unsigned)blocks, (unsigned)h_T[n]);
-        scale_max_kernel<<<g, 256, 0, s>>>(d_inst, n, d_maxbits);
+        scale_max_kernel<<<g, 256, 0, s>>>(d_inst, n, 0, d_maxbits);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
+cudaError_t launch_scale_max_range(const InstDev *d_inst, int inst, int t0, int nt, long long elems_per_ts,
+                                   unsigned *d_maxbits, cudaStream_t s)
+{
+    long long blocks = (elems_per_ts + 256 * 8 - 1) / (256 * 8);
+    if (blocks > 256) blocks = 256;
+    if (blocks < 1) blocks = 1;
+    dim3 g((unsigned)blocks, (unsigned)nt);
+    scale_max_kernel<<<g, 256, 0, s>>>(d_inst, inst, t0, d_maxbits);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- site blocks
 // Scaled, site-blocked copy of phi for the tensor-core path:
 // phi_blk[t][b][n][e] = 2^s_t phi[t][n][8b + e/3][e%3] for e < 24 (zero past V),
 // e = 24, 25 padding.  Memory bound: one read of phi, one write of the copy.
-__global__ void blockify_kernel(const InstDev *__restrict__ d_inst, int inst, const unsigned *__restrict__ maxbits)
+__global__ void blockify_kernel(const InstDev *__restrict__ d_inst, int inst, int t0, int nt,
+                                const unsigned *__restrict__ maxbits)
 {
     const InstDev &I = d_inst[inst];
-    const long long total = (long long)I.T * I.nblk * I.N * TC_SLOT;
+    const long long per_t = (long long)I.nblk * I.N * TC_SLOT;
+    const long long total = (long long)(t0 + nt) * per_t;
     const long long V = I.V;
-    for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < total; o += (long long)gridDim.x * blockDim.x) {
+    for (long long o = (long long)t0 * per_t + (long long)blockIdx.x * blockDim.x + threadIdx.x; o < total;
+         o += (long long)gridDim.x * blockDim.x) {
         const long long chunk = o / TC_SLOT;
         const int e = (int)(o - chunk * TC_SLOT);
         const int n = (int)(chunk % I.N);
@@ -152,10 +166,17 @@ __global__ void blockify_kernel(const InstDev *__restrict__ d_inst, int inst, co
 
 cudaError_t launch_blockify(const InstDev *d_inst, int inst, const InstDev &h, const unsigned *d_maxbits, cudaStream_t s)
 {
-    const long long n = (long long)h.T * h.nblk * h.N * TC_SLOT;
+    return launch_blockify_range(d_inst, inst, h, 0, h.T, d_maxbits, s);
+}
+
+cudaError_t launch_blockify_range(const InstDev *d_inst, int inst, const InstDev &h, int t0, int nt,
+                                  const unsigned *d_maxbits, cudaStream_t s)
+{
+    const long long n = (long long)nt * h.nblk * h.N * TC_SLOT;
     long long blocks = (n + 255) / 256;
     if (blocks > 152 * 64) blocks = 152 * 64;
-    blockify_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_inst, inst, d_maxbits);
+    if (blocks < 1) blocks = 1;
+    blockify_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_inst, inst, t0, nt, d_maxbits);
     return cudaGetLastError();
 }
 

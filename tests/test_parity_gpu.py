@@ -180,18 +180,20 @@ def test_plan_execute_is_capturable_in_a_cuda_graph(laph):
 
 
 def test_execute_host_buffers(laph):
+    """Host inputs and outputs; the tensor-core path pipelines copies and compute chunk by chunk."""
     import torch
-    L, T, N = 5, 2, 9
+    L, T, N = 5, 3, 9
     mom = synth.momentum_shell(1)
     phi_h = synth.random_phi(L, N, T=T, instance=61)
-    plan = laph.Plan([(L, T, N, mom)], mode=SPLIT_MODES[0])
-    ws = torch.empty(plan.host_workspace_size(), dtype=torch.uint8, device="cuda")
-    Bh = np.zeros((T, len(mom), N * (N - 1) * (N - 2) // 6), dtype=np.complex128)
-    Mh = np.zeros((T, len(mom), N, N), dtype=np.complex128)
-    plan.execute_host([phi_h], [Bh], [Mh], ws)
     rB, rM = _oracle(phi_h, L, mom)
-    assert rel_frob(Bh, rB) <= 1e-5 and rel_frob(Mh, rM) <= 1e-5
-    plan.close()
+    for mode, flags in [("fp32", 0), ("f16x3", 0), ("f16x3", laph.PLAN_CHUNK_PER_TIMESLICE)]:
+        plan = laph.Plan([(L, T, N, mom)], mode=mode, flags=flags)
+        ws = torch.empty(plan.host_workspace_size(), dtype=torch.uint8, device="cuda")
+        Bh = np.zeros((T, len(mom), N * (N - 1) * (N - 2) // 6), dtype=np.complex128)
+        Mh = np.zeros((T, len(mom), N, N), dtype=np.complex128)
+        plan.execute_host([phi_h], [Bh], [Mh], ws)
+        assert rel_frob(Bh, rB) <= 1e-5 and rel_frob(Mh, rM) <= 1e-5
+        plan.close()
 
 
 def test_invariances_at_size(laph):
