@@ -17,7 +17,10 @@
 // the number of additions; the accumulator is drained every `chunk_stages`
 // K stages into a second tensor-memory region of FP32 running sums kept by
 // CUDA cores with round-to-nearest, and at the end of a tile the sums are
-// scaled back and written to the complex128 output in FP64.
+// scaled back and written to the complex128 output in FP64.  At chunk
+// boundaries the MMAs of the two column halves of the accumulator are issued
+// and committed separately, so that the drain of one half overlaps the MMAs
+// of the other.
 //
 // Tile: 128 rows x 96 complex columns (UMMA M = 128, N = 192).  A K stage is
 // one site block: TC_BS = 8 sites = 24 complex = 48 real K entries, three
@@ -40,7 +43,8 @@
 //         formed at once.  Within a group, two warps per TMEM lane quadrant:
 //         warp half h forms the 12 K entries of sites 4h..4h+3 of its row
 //         (diquark or conj(phi)), splits them and tcgen05.st's them;
-//   16-19 epilogue: drains ACC into SUM, writes the output at tile end;
+//   16-19 epilogue: drains ACC into SUM, one column half at a time, writes
+//         the output at tile end;
 //   20    loader: claims the next tile, then the stage ring's bulk copies;
 //   21    TMEM allocation and single-thread MMA issue.
 // Every wait on an mbarrier is bounded; on expiry the CTA records
@@ -88,7 +92,7 @@ struct Shared {
     uint64_t tfull[TRING], tempty[TRING];
     int tile_ring[TRING];
     uint64_t a_full[2], a_empty[2];
-    uint64_t acc_full, acc_empty;
+    uint64_t acc_full[2], acc_empty[2];   // per column half of the accumulator
     uint64_t done;
     uint32_t tmem_base;
     int abort;
@@ -437,8 +441,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
             mbar_init(&S->a_full[s], N_AGROUP);
             mbar_init(&S->a_empty[s], 1);
         }
-        mbar_init(&S->acc_full, 1);
-        mbar_init(&S->acc_empty, 4);
+        for (int h = 0; h < 2; h++) {
+            mbar_init(&S->acc_full[h], 1);
+            mbar_init(&S->acc_empty[h], 4);
+        }
         mbar_init(&S->done, 1);
         S->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -559,7 +565,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
         const int quad = warp & 3;
         const int r = quad * 32 + lane;
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
-        uint32_t gc = 0;
+        uint32_t gc = 0, gc1 = 0;   // drains done of the low / high column half
         bool ok = true;
         Ring rt{0, 0};
         while (ok) {
@@ -582,28 +588,35 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
             const int s = scale_exp(kp.maxbits[I.ts_base + td.t]);
             const double fac = meson ? pow2d(-2 * s) : pow2d(-3 * s);
             const int n_ch = (I.nblk + kp.chunk_stages - 1) / kp.chunk_stages;
-            for (int ch = 0; ch < n_ch; ch++, gc++) {
-                if (!warp_wait(c, &S->acc_full, gc & 1u)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                for (int b = 0; b * 16 < n_real; b++) {
-                    uint32_t va[16], vs[16];
-                    tmem_ld16(tmem + lane_base + ACC_COL + 16u * b, va);
-                    if (ch > 0) tmem_ld16(tmem + lane_base + SUM_COL + 16u * b, vs);
-                    tmem_wait_ld();
-                    if (ch > 0) {
-#pragma unroll
-                        for (int e = 0; e < 16; e++)
-                            va[e] = __float_as_uint(__uint_as_float(va[e]) + __uint_as_float(vs[e]));
+            const int n_lo = n_real >= 32 ? ((n_real / 2 + 15) & ~15) : n_real;
+            for (int ch = 0; ch < n_ch && ok; ch++) {
+                for (int h = 0; h < 2; h++) {
+                    const int c0 = h ? n_lo : 0, c1 = h ? n_real : n_lo;
+                    if (c1 <= c0) continue;
+                    uint32_t &g = h ? gc1 : gc;
+                    if (!warp_wait(c, &S->acc_full[h], g & 1u)) {
+                        ok = false;
+                        break;
                     }
-                    tmem_st16(tmem + lane_base + SUM_COL + 16u * b, va);
+                    tc_fence_after();
+                    for (int b = c0 / 16; b * 16 < c1; b++) {
+                        uint32_t va[16], vs[16];
+                        tmem_ld16(tmem + lane_base + ACC_COL + 16u * b, va);
+                        if (ch > 0) tmem_ld16(tmem + lane_base + SUM_COL + 16u * b, vs);
+                        tmem_wait_ld();
+                        if (ch > 0) {
+#pragma unroll
+                            for (int e = 0; e < 16; e++)
+                                va[e] = __float_as_uint(__uint_as_float(va[e]) + __uint_as_float(vs[e]));
+                        }
+                        tmem_st16(tmem + lane_base + SUM_COL + 16u * b, va);
+                    }
+                    tmem_wait_st();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&S->acc_empty[h]);
+                    g++;
                 }
-                tmem_wait_st();
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&S->acc_empty);
             }
             if (!ok) break;
             // tile done: FP32 sums -> FP64 output, scale undone
@@ -636,7 +649,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
     } else {
         // ---------------------------------------------------------- MMA issue
         Ring rs{0, 0}, ra{0, 0};
-        uint32_t gc = 0;
+        uint32_t gc = 0, gc1 = 0;   // chunks of the low / high column half
         bool issued = false, ok = true;
         Ring rt{0, 0};
         while (ok) {
@@ -650,47 +663,73 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
             const int n_real = 2 * ((td.ncols + 7) & ~7) - 2 * td.cskip;
             const uint32_t idesc = idesc_f16(n_real, ELEM);
             const uint64_t bskip = (uint64_t)(td.cskip * 64) >> 4;
+            // column halves [0, n_lo) and [n_lo, n_real) of the accumulator
+            const int n_lo = n_real >= 32 ? ((n_real / 2 + 15) & ~15) : n_real;
+            const int nh = n_real > n_lo ? 2 : 1;
+            const uint32_t idesc_h[2] = {idesc_f16(n_lo, ELEM), nh == 2 ? idesc_f16(n_real - n_lo, ELEM) : 0u};
             int cs = 0;   // stage within the current accumulation chunk
             for (int st = 0; st < nst; st++) {
                 const bool chunk_start = cs == 0;
                 const bool chunk_end = cs + 1 == kp.chunk_stages || st + 1 == nst;
-                if (chunk_start && !warp_wait(c, &S->acc_empty, (gc & 1u) ^ 1u)) {
-                    ok = false;
-                    break;
-                }
                 if (!warp_wait(c, &S->a_full[ra.slot], ra.phase) || !warp_wait(c, &S->full[rs.slot], rs.phase)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                if (lane == 0) {
-                    const uint32_t a_hi = tmem + A_COL + (uint32_t)ra.slot * A_SLOT_COLS, a_lo = a_hi + A_LO;
-                    // descriptor start addresses advance one atom column (in units of 16 bytes) per k-step
-                    const uint64_t dhi = desc_sw32(smem_u32(smem + rs.slot * kp.stage_bytes)) + bskip;
-                    const uint64_t dlo = dhi + (uint64_t)(B_BYTES >> 4);
-                    const uint32_t d = tmem + ACC_COL;
+                const uint32_t a_hi = tmem + A_COL + (uint32_t)ra.slot * A_SLOT_COLS, a_lo = a_hi + A_LO;
+                // descriptor start addresses advance one atom column (in units of 16 bytes) per k-step
+                const uint64_t dhi = desc_sw32(smem_u32(smem + rs.slot * kp.stage_bytes)) + bskip;
+                const uint64_t dlo = dhi + (uint64_t)(B_BYTES >> 4);
+                if (!chunk_start && !chunk_end) {
+                    if (lane == 0) {
 #pragma unroll
-                    for (int ks = 0; ks < KSTEPS; ks++) {
-                        const uint32_t acc = (chunk_start && ks == 0) ? 0u : 1u;
-                        const uint64_t koff = (uint64_t)ks * (ATOM_COL_BYTES >> 4);
-                        mma_ts(d, a_hi + 8 * ks, dhi + koff, idesc, acc);
-                        if (TERMS == 3) {
-                            mma_ts(d, a_hi + 8 * ks, dlo + koff, idesc, 1u);
-                            mma_ts(d, a_lo + 8 * ks, dhi + koff, idesc, 1u);
+                        for (int ks = 0; ks < KSTEPS; ks++) {
+                            const uint64_t koff = (uint64_t)ks * (ATOM_COL_BYTES >> 4);
+                            mma_ts(tmem + ACC_COL, a_hi + 8 * ks, dhi + koff, idesc, 1u);
+                            if (TERMS == 3) {
+                                mma_ts(tmem + ACC_COL, a_hi + 8 * ks, dlo + koff, idesc, 1u);
+                                mma_ts(tmem + ACC_COL, a_lo + 8 * ks, dhi + koff, idesc, 1u);
+                            }
                         }
                     }
+                } else {
+                    for (int h = 0; h < nh && ok; h++) {
+                        uint32_t &g = h ? gc1 : gc;
+                        if (chunk_start) {
+                            if (!warp_wait(c, &S->acc_empty[h], (g & 1u) ^ 1u)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                        }
+                        if (lane == 0) {
+                            // half h: accumulator columns and B rows from h * n_lo (32 bytes per row per atom column)
+                            const uint32_t d = tmem + ACC_COL + (uint32_t)(h * n_lo);
+                            const uint64_t hoff = (uint64_t)(h * n_lo * 32) >> 4;
+#pragma unroll
+                            for (int ks = 0; ks < KSTEPS; ks++) {
+                                const uint32_t acc = (chunk_start && ks == 0) ? 0u : 1u;
+                                const uint64_t koff = (uint64_t)ks * (ATOM_COL_BYTES >> 4) + hoff;
+                                mma_ts(d, a_hi + 8 * ks, dhi + koff, idesc_h[h], acc);
+                                if (TERMS == 3) {
+                                    mma_ts(d, a_hi + 8 * ks, dlo + koff, idesc_h[h], 1u);
+                                    mma_ts(d, a_lo + 8 * ks, dhi + koff, idesc_h[h], 1u);
+                                }
+                            }
+                            if (chunk_end) mma_commit(&S->acc_full[h]);
+                        }
+                        __syncwarp();
+                        if (chunk_end) g++;
+                    }
+                    if (!ok) break;
+                }
+                if (lane == 0) {
                     mma_commit(&S->a_empty[ra.slot]);
                     mma_commit(&S->empty[rs.slot]);
-                    if (chunk_end) mma_commit(&S->acc_full);
                     issued = true;
                 }
                 __syncwarp();
-                if (chunk_end) {
-                    gc++;
-                    cs = 0;
-                } else {
-                    cs++;
-                }
+                cs = chunk_end ? 0 : cs + 1;
                 rs.next(NS);
                 ra.next(2);
             }
