@@ -138,29 +138,26 @@ cudaError_t launch_scale_max_range(const InstDev *d_inst, int inst, int t0, int 
 // Scaled, site-blocked copy of phi for the tensor-core path:
 // phi_blk[t][b][n][e] = 2^s_t phi[t][n][8b + e/3][e%3] for e < 24 (zero past V),
 // e = 24, 25 padding.  Memory bound: one read of phi, one write of the copy.
-__global__ void blockify_kernel(const InstDev *__restrict__ d_inst, int inst, int t0, int nt,
-                                const unsigned *__restrict__ maxbits)
+// Block (b, t) writes the N slots of site block b (contiguous) and reads the
+// 24 complex entries of each vector for those sites (contiguous too).
+__global__ void __launch_bounds__(256) blockify_kernel(const InstDev *__restrict__ d_inst, int inst, int t0,
+                                                       const unsigned *__restrict__ maxbits)
 {
     const InstDev &I = d_inst[inst];
-    const long long per_t = (long long)I.nblk * I.N * TC_SLOT;
-    const long long total = (long long)(t0 + nt) * per_t;
+    const int b = blockIdx.x, t = t0 + blockIdx.y, N = I.N;
     const long long V = I.V;
-    for (long long o = (long long)t0 * per_t + (long long)blockIdx.x * blockDim.x + threadIdx.x; o < total;
-         o += (long long)gridDim.x * blockDim.x) {
-        const long long chunk = o / TC_SLOT;
-        const int e = (int)(o - chunk * TC_SLOT);
-        const int n = (int)(chunk % I.N);
-        const long long tb = chunk / I.N;
-        const int b = (int)(tb % I.nblk);
-        const int t = (int)(tb / I.nblk);
-        const long long x = (long long)TC_BS * b + e / 3;
+    const float sc = __int_as_float((127 + scale_exp(maxbits[I.ts_base + t])) << 23);
+    const float2 *src = I.phi + (long long)t * N * V * 3 + (long long)TC_BS * b * 3;
+    float2 *dst = I.phi_blk + ((long long)t * I.nblk + b) * N * TC_SLOT;
+    const int nvalid = (int)(V - (long long)TC_BS * b < TC_BS ? V - (long long)TC_BS * b : TC_BS) * 3;
+    for (int idx = threadIdx.x; idx < N * TC_SLOT; idx += blockDim.x) {
+        const int n = idx / TC_SLOT, e = idx - n * TC_SLOT;
         float2 v = make_float2(0.f, 0.f);
-        if (e < 3 * TC_BS && x < V) {
-            const float sc = __int_as_float((127 + scale_exp(maxbits[I.ts_base + t])) << 23);
-            const float2 f = __ldg(I.phi + (((long long)t * I.N + n) * V + x) * 3 + e % 3);
+        if (e < nvalid) {
+            const float2 f = __ldg(src + (long long)n * V * 3 + e);
             v = make_float2(f.x * sc, f.y * sc);
         }
-        I.phi_blk[o] = v;
+        dst[idx] = v;
     }
 }
 
@@ -172,12 +169,14 @@ cudaError_t launch_blockify(const InstDev *d_inst, int inst, const InstDev &h, c
 cudaError_t launch_blockify_range(const InstDev *d_inst, int inst, const InstDev &h, int t0, int nt,
                                   const unsigned *d_maxbits, cudaStream_t s)
 {
-    const long long n = (long long)nt * h.nblk * h.N * TC_SLOT;
-    long long blocks = (n + 255) / 256;
-    if (blocks > 152 * 64) blocks = 152 * 64;
-    if (blocks < 1) blocks = 1;
-    blockify_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_inst, inst, t0, nt, d_maxbits);
-    return cudaGetLastError();
+    for (int tb = 0; tb < nt; tb += 65535) {
+        const int n = nt - tb < 65535 ? nt - tb : 65535;
+        dim3 g((unsigned)h.nblk, (unsigned)n);
+        blockify_kernel<<<g, 256, 0, s>>>(d_inst, inst, t0 + tb, d_maxbits);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // ---------------------------------------------------------------- K-b
