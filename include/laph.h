@@ -83,7 +83,7 @@ extern "C" {
 /* ---- plan flags ------------------------------------------------------ */
 #define LAPH_PLAN_SKIP_B 0x1u   /* do not compute baryon blocks (out_B may be NULL) */
 #define LAPH_PLAN_SKIP_M 0x2u   /* do not compute meson blocks (out_M may be NULL) */
-#define LAPH_PLAN_AUTOTUNE 0x4u /* pick kernel parameters by timing at creation */
+#define LAPH_PLAN_AUTOTUNE 0x4u /* pick the tensor-core schedule by timing candidates at creation */
 /* Record CUDA events around every contraction-kernel launch (see
  * laph_plan_kernel_times). */
 #define LAPH_PLAN_TIMING 0x8u
@@ -160,8 +160,8 @@ LAPH_API int laph_meson_blocks(const void *phi, int L, int T, int N, const int32
 /* Validates the instances (L >= 1; N >= 3 unless LAPH_PLAN_SKIP_B, N >= 1;
  * N <= 3 L^3; 1 <= n_mom; |n| components within +-2^20), copies the
  * momenta, builds the phase tables and the tile table on the current device
- * and picks kernel parameters (LAPH_PLAN_AUTOTUNE times candidates on an
- * internal stream).  *plan is set only on success. */
+ * and picks the schedule (LAPH_PLAN_AUTOTUNE times candidates on an internal
+ * stream, see laph_plan_schedule).  *plan is set only on success. */
 LAPH_API int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned flags, laph_plan **plan);
 
 /* Bytes of device workspace laph_plan_execute needs (256-byte aligned). */
@@ -210,6 +210,23 @@ LAPH_API int laph_plan_operand_times(laph_plan *plan, int n, float *ms);
  * processes the batch's timeslices in chunks whose B-operand images fit its
  * workspace (at most 24 GiB), one launch per chunk. */
 LAPH_API int laph_plan_contraction_launches(const laph_plan *plan, int *n);
+
+/* Schedule of the tensor-core path.
+ *   timeslices_per_chunk: timeslices per chunk of B-operand images (0: chunks
+ *                         filled by bytes, for batches of several instances);
+ *   tile_order:           0 = column tiles outer within a timeslice (the CTAs
+ *                         that share a B stage image run together), 1 = row
+ *                         tiles outer;
+ *   n_chunks:             chunks (contraction launches) per execute.
+ * Without LAPH_PLAN_AUTOTUNE the chunk size minimises partly filled waves of
+ * persistent CTAs and the order is 0.  With it, plan creation times the
+ * candidates (both orders x {that chunk size, the largest chunk within the
+ * 24 GiB cap}) on seeded synthetic inputs of the plan's shapes, allocating
+ * inputs, outputs and a workspace for the duration, and keeps the fastest;
+ * *n_candidates and candidate_ms (room for 8) report their times.  Any
+ * pointer may be NULL. */
+LAPH_API int laph_plan_schedule(const laph_plan *plan, int64_t *timeslices_per_chunk, int *tile_order, int *n_chunks,
+                               int *n_candidates, float *candidate_ms);
 
 /* Number of kernels of this library one laph_plan_execute launches. */
 LAPH_API int laph_plan_launches_per_execute(const laph_plan *plan, int *n);

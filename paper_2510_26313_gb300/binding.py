@@ -79,6 +79,8 @@ def lib() -> ctypes.CDLL:
             "laph_plan_operand_times": (i32, [vp, i32, ctypes.POINTER(ctypes.c_float)]),
             "laph_plan_contraction_launches": (i32, [vp, ctypes.POINTER(i32)]),
             "laph_plan_launches_per_execute": (i32, [vp, ctypes.POINTER(i32)]),
+            "laph_plan_schedule": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                         ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]),
             "laph_plan_destroy": (i32, [vp]),
             "laph_blocks_noalloc": (i32, [vp, i32, i32, i32, ip32, i32, vp, vp, vp]),
         }
@@ -262,6 +264,16 @@ class Plan:
         v = ctypes.c_int()
         _check(lib().laph_plan_contraction_launches(self._h, ctypes.byref(v)), "laph_plan_contraction_launches")
         return int(v.value)
+
+    def schedule(self) -> dict:
+        """Tensor-core schedule: timeslices per chunk (0: filled by bytes), tile order, chunks,
+        and the autotuner's candidate timings (ms) when PLAN_AUTOTUNE was given."""
+        pc, order, nc, ncand = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ms = (ctypes.c_float * 8)()
+        _check(lib().laph_plan_schedule(self._h, ctypes.byref(pc), ctypes.byref(order), ctypes.byref(nc),
+                                        ctypes.byref(ncand), ms), "laph_plan_schedule")
+        return {"timeslices_per_chunk": int(pc.value), "tile_order": int(order.value), "n_chunks": int(nc.value),
+                "candidate_ms": [float(ms[k]) for k in range(ncand.value)]}
 
     def launches_per_execute(self) -> int:
         v = ctypes.c_int()

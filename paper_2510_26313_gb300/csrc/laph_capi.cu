@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <string>
 #include <vector>
@@ -81,6 +82,13 @@ struct laph_plan {
         long long tile0, n_tiles;
     };
     std::vector<Chunk> chunks;
+    // schedule of the tensor-core path: timeslices per chunk (0: chunks filled by
+    // bytes) and tile order within a timeslice (0: column tiles outer, 1: row
+    // tiles outer); with LAPH_PLAN_AUTOTUNE the candidates' timings
+    long long sched_per_chunk = 0;
+    int sched_order = 0;
+    bool tuned = false;
+    std::vector<float> tune_ms;
     size_t off_psi = 0;
     // LAPH_PLAN_TIMING: ring of event pairs around the contraction launches
     static constexpr int RING = 256;
@@ -174,6 +182,10 @@ static void free_plan(laph_plan *p)
     for (cudaEvent_t e : p->pv_end) cudaEventDestroy(e);
     delete p;
 }
+
+static int autotune_time(laph_plan *p, const std::vector<std::pair<long long, int>> &cand,
+                         const std::function<void(long long, int)> &emit, const std::function<cudaError_t()> &upload,
+                         size_t *best);
 
 static int tc_supported(int device)
 {
@@ -376,76 +388,126 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
             return (long long)p->h_inst[a].n_st * (long long)ones[a].size() >
                    (long long)p->h_inst[b].n_st * (long long)ones[b].size();
         });
-    size_t psi_max = 0;
-    laph_plan::Chunk cur{0, 0, 0, 0, 0};
-    size_t cur_bytes = 0;
-    for (int n : order) {
-        const InstDev &d = p->h_inst[n];
-        const std::vector<TileDev> &one = ones[n];
-        for (int t = 0; t < d.T; t++) {
-            if (tc) {
-                const bool full = per_chunk > 0 ? cur.n_units >= per_chunk : cur_bytes + unit_bytes[n] > psi_target;
-                if (cur.n_units > 0 && full) {
-                    p->chunks.push_back(cur);
-                    psi_max = std::max(psi_max, cur_bytes);
-                    cur = laph_plan::Chunk{(int)units.size(), 0, 0, (long long)tiles.size(), 0};
-                    cur_bytes = 0;
-                }
-                units.push_back(laph::PsiUnit{n, t, (long long)cur_bytes, cur.n_jobs});
-                cur.n_units++;
-                cur.n_jobs += (long long)d.n_ct * ((d.n_st + laph::TC_PSI_GROUP - 1) / laph::TC_PSI_GROUP);
-            }
-            for (TileDev u : one) {
-                u.t = t;
-                if (tc) u.psi_off += (long long)cur_bytes;
-                tiles.push_back(u);
-            }
-            if (tc) {
-                cur.n_tiles += (long long)one.size();
-                cur_bytes += unit_bytes[n];
-            }
-        }
-    }
-    if (tc && cur.n_units > 0) {
-        p->chunks.push_back(cur);
-        psi_max = std::max(psi_max, cur_bytes);
-    }
-    p->n_tiles = (long long)tiles.size();
     if (tc && p->max_staged > laph::TC_MAX_STAGED) {
         free_plan(p);
         return LAPH_ERR_UNSUPPORTED;
     }
-    if (p->n_tiles > 0) {
-        PCK(cudaMalloc((void **)&p->d_tiles, sizeof(TileDev) * tiles.size()));
-        PCK(cudaMemcpy(p->d_tiles, tiles.data(), sizeof(TileDev) * tiles.size(), cudaMemcpyHostToDevice));
-    }
-    p->h_units = units;
-    if (!units.empty()) {
-        PCK(cudaMalloc((void **)&p->d_units, sizeof(laph::PsiUnit) * units.size()));
-        PCK(cudaMemcpy(p->d_units, units.data(), sizeof(laph::PsiUnit) * units.size(), cudaMemcpyHostToDevice));
-    }
-
-    // ---- workspace layout (tensor-core modes only): per-timeslice max |phi|
-    // bits and one tile counter per chunk (both cleared by every execute), the
-    // site-blocked copies of phi, then the B-operand images of one chunk.
-    if (tc) {
-        p->grid = sms;
-        p->off_maxbits = 0;
-        p->off_counter = ((sizeof(unsigned) * p->total_ts + 255) / 256) * 256;
-        size_t off = p->off_counter + ((sizeof(unsigned) * p->chunks.size() + 255) / 256) * 256;
-        p->ws_zero_bytes = off;
-        for (int n = 0; n < n_inst; n++) {
-            InstDev &d = p->h_inst[n];
-            d.blk_off = (long long)off;
-            off += (((size_t)d.T * d.nblk * d.N * laph::TC_SLOT * sizeof(float2) + 255) / 256) * 256;
+    size_t psi_max = 0;
+    // tile, unit and chunk tables for a schedule (pc timeslices per chunk, or
+    // chunks filled up to psi_target bytes when pc is 0)
+    std::function<void(long long, int)> emit = [&](long long pc, int tile_order) {
+        tiles.clear();
+        units.clear();
+        p->chunks.clear();
+        psi_max = 0;
+        laph_plan::Chunk cur{0, 0, 0, 0, 0};
+        size_t cur_bytes = 0;
+        for (int n : order) {
+            const InstDev &d = p->h_inst[n];
+            std::vector<TileDev> one = ones[n];
+            if (tile_order == 1)
+                std::stable_sort(one.begin(), one.end(), [](const TileDev &x, const TileDev &y) {
+                    return x.row0 != y.row0 ? x.row0 < y.row0 : x.col0 < y.col0;
+                });
+            for (int t = 0; t < d.T; t++) {
+                if (tc) {
+                    const bool full = pc > 0 ? cur.n_units >= pc : cur_bytes + unit_bytes[n] > psi_target;
+                    if (cur.n_units > 0 && full) {
+                        p->chunks.push_back(cur);
+                        psi_max = std::max(psi_max, cur_bytes);
+                        cur = laph_plan::Chunk{(int)units.size(), 0, 0, (long long)tiles.size(), 0};
+                        cur_bytes = 0;
+                    }
+                    units.push_back(laph::PsiUnit{n, t, (long long)cur_bytes, cur.n_jobs});
+                    cur.n_units++;
+                    cur.n_jobs += (long long)d.n_ct * ((d.n_st + laph::TC_PSI_GROUP - 1) / laph::TC_PSI_GROUP);
+                }
+                for (TileDev u : one) {
+                    u.t = t;
+                    if (tc) u.psi_off += (long long)cur_bytes;
+                    tiles.push_back(u);
+                }
+                if (tc) {
+                    cur.n_tiles += (long long)one.size();
+                    cur_bytes += unit_bytes[n];
+                }
+            }
         }
-        p->off_psi = off;
-        off += ((psi_max + 255) / 256) * 256;
-        p->ws_bytes = off;
-        PCK(cudaMemcpy(p->d_inst, p->h_inst.data(), sizeof(InstDev) * n_inst, cudaMemcpyHostToDevice));
-    } else {
-        p->grid = 0;
-        p->ws_bytes = 0;
+        if (tc && cur.n_units > 0) {
+            p->chunks.push_back(cur);
+            psi_max = std::max(psi_max, cur_bytes);
+        }
+        p->n_tiles = (long long)tiles.size();
+        p->h_units = units;
+        p->sched_per_chunk = pc;
+        p->sched_order = tile_order;
+    };
+    // device copies of the tables and the workspace layout (tensor-core modes:
+    // per-timeslice max |phi| bits and one tile counter per chunk, both cleared
+    // by every execute, the site-blocked copies of phi, then the B-operand
+    // images of one chunk)
+    std::function<cudaError_t()> upload = [&]() -> cudaError_t {
+        cudaError_t er = cudaSuccess;
+        cudaFree(p->d_tiles);
+        cudaFree(p->d_units);
+        p->d_tiles = nullptr;
+        p->d_units = nullptr;
+        if (!tiles.empty()) {
+            if ((er = cudaMalloc((void **)&p->d_tiles, sizeof(TileDev) * tiles.size())) != cudaSuccess) return er;
+            er = cudaMemcpy(p->d_tiles, tiles.data(), sizeof(TileDev) * tiles.size(), cudaMemcpyHostToDevice);
+            if (er != cudaSuccess) return er;
+        }
+        if (!units.empty()) {
+            if ((er = cudaMalloc((void **)&p->d_units, sizeof(laph::PsiUnit) * units.size())) != cudaSuccess) return er;
+            er = cudaMemcpy(p->d_units, units.data(), sizeof(laph::PsiUnit) * units.size(), cudaMemcpyHostToDevice);
+            if (er != cudaSuccess) return er;
+        }
+        if (tc) {
+            p->grid = sms;
+            p->off_maxbits = 0;
+            p->off_counter = ((sizeof(unsigned) * p->total_ts + 255) / 256) * 256;
+            size_t off = p->off_counter + ((sizeof(unsigned) * p->chunks.size() + 255) / 256) * 256;
+            p->ws_zero_bytes = off;
+            for (int n = 0; n < n_inst; n++) {
+                InstDev &d = p->h_inst[n];
+                d.blk_off = (long long)off;
+                off += (((size_t)d.T * d.nblk * d.N * laph::TC_SLOT * sizeof(float2) + 255) / 256) * 256;
+            }
+            p->off_psi = off;
+            off += ((psi_max + 255) / 256) * 256;
+            p->ws_bytes = off;
+            er = cudaMemcpy(p->d_inst, p->h_inst.data(), sizeof(InstDev) * n_inst, cudaMemcpyHostToDevice);
+        } else {
+            p->grid = 0;
+            p->ws_bytes = 0;
+        }
+        return er;
+    };
+    emit(per_chunk, 0);
+    PCK(upload());
+    if (tc && (flags & LAPH_PLAN_AUTOTUNE)) {
+        // candidates: both tile orders x {the wave-model chunk size, the largest
+        // chunk within the cap} (one instance), each timed on seeded synthetic
+        // inputs of the plan's shapes; the fastest is kept
+        std::vector<std::pair<long long, int>> cand;
+        std::vector<long long> pcs{per_chunk};
+        if (n_inst == 1 && per_chunk > 0 && !(flags & LAPH_PLAN_CHUNK_PER_TIMESLICE)) {
+            const long long U = p->h_inst[0].T;
+            const long long n_max =
+                std::max(1LL, std::min(U, (long long)(PSI_CAP_BYTES / std::max<size_t>(unit_bytes[0], 1))));
+            if (n_max != per_chunk) pcs.push_back(n_max);
+        }
+        for (long long pc : pcs)
+            for (int o = 0; o < 2; o++) cand.push_back({pc, o});
+        size_t best = 0;
+        const int rc_t = autotune_time(p, cand, emit, upload, &best);
+        if (rc_t != LAPH_OK) {
+            free_plan(p);
+            return rc_t;
+        }
+        emit(cand[best].first, cand[best].second);
+        PCK(upload());
+        p->tuned = true;
     }
     if (flags & LAPH_PLAN_TIMING) {
         p->ev_begin.resize(laph_plan::RING, nullptr);
@@ -599,6 +661,86 @@ static int ring_times(const std::vector<cudaEvent_t> &b, const std::vector<cudaE
         CK(cudaEventSynchronize(e[slot]));
         CK(cudaEventElapsedTime(&ms[q], b[slot], e[slot]));
     }
+    return LAPH_OK;
+}
+
+// Times every candidate schedule: seeded synthetic inputs of the plan's
+// shapes, a workspace of the candidate's size, one warm-up execute and one
+// timed execute on an internal stream.  *best = the fastest candidate.
+static int autotune_time(laph_plan *p, const std::vector<std::pair<long long, int>> &cand,
+                         const std::function<void(long long, int)> &emit, const std::function<cudaError_t()> &upload,
+                         size_t *best)
+{
+    const bool needB = !(p->flags & LAPH_PLAN_SKIP_B), needM = !(p->flags & LAPH_PLAN_SKIP_M);
+    std::vector<void *> phi(p->n_inst, nullptr), ob(p->n_inst, nullptr), om(p->n_inst, nullptr);
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    void *ws = nullptr;
+    int rc = LAPH_OK;
+    cudaError_t e = cudaSuccess;
+#define TCK(call)                            \
+    do {                                     \
+        if ((e = (call)) != cudaSuccess) {   \
+            rc = cuda_fail(e, #call);        \
+            goto done;                       \
+        }                                    \
+    } while (0)
+    TCK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    TCK(cudaEventCreate(&e0));
+    TCK(cudaEventCreate(&e1));
+    for (int n = 0; n < p->n_inst; n++) {
+        TCK(cudaMalloc(&phi[n], p->phi_elems[n] * sizeof(float2)));
+        TCK(laph::launch_fill_pattern((float2 *)phi[n], p->phi_elems[n], 1000u + (unsigned)n, st));
+        if (needB) TCK(cudaMalloc(&ob[n], std::max<long long>(p->outB_elems[n], 1) * sizeof(double2)));
+        if (needM) TCK(cudaMalloc(&om[n], std::max<long long>(p->outM_elems[n], 1) * sizeof(double2)));
+    }
+    p->tune_ms.clear();
+    for (size_t k = 0; k < cand.size(); k++) {
+        emit(cand[k].first, cand[k].second);
+        TCK(upload());
+        TCK(cudaMalloc(&ws, std::max<size_t>(p->ws_bytes, 256)));
+        TCK(laph::launch_set_pointers(p->d_inst, 0, p->n_inst, phi.data(), needB ? ob.data() : nullptr,
+                                      needM ? om.data() : nullptr, ws, st));
+        if ((rc = launch_batch(p, ws, st)) != LAPH_OK) goto done;
+        TCK(cudaEventRecord(e0, st));
+        if ((rc = launch_batch(p, ws, st)) != LAPH_OK) goto done;
+        TCK(cudaEventRecord(e1, st));
+        TCK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        TCK(cudaEventElapsedTime(&ms, e0, e1));
+        p->tune_ms.push_back(ms);
+        TCK(cudaFree(ws));
+        ws = nullptr;
+    }
+    *best = 0;
+    for (size_t k = 1; k < cand.size(); k++)
+        if (p->tune_ms[k] < p->tune_ms[*best]) *best = k;
+    TCK(cudaMemsetAsync(p->d_status, 0, sizeof(int), st));
+    TCK(cudaStreamSynchronize(st));
+done:
+#undef TCK
+    cudaFree(ws);
+    for (int n = 0; n < p->n_inst; n++) {
+        cudaFree(phi[n]);
+        cudaFree(ob[n]);
+        cudaFree(om[n]);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    return rc;
+}
+
+int laph_plan_schedule(const laph_plan *plan, int64_t *timeslices_per_chunk, int *tile_order, int *n_chunks,
+                       int *n_candidates, float *candidate_ms)
+{
+    if (!plan) return LAPH_ERR_ARG;
+    if (timeslices_per_chunk) *timeslices_per_chunk = plan->sched_per_chunk;
+    if (tile_order) *tile_order = plan->sched_order;
+    if (n_chunks) *n_chunks = (int)plan->chunks.size();
+    if (n_candidates) *n_candidates = (int)plan->tune_ms.size();
+    if (candidate_ms)
+        for (size_t k = 0; k < plan->tune_ms.size(); k++) candidate_ms[k] = plan->tune_ms[k];
     return LAPH_OK;
 }
 

@@ -120,6 +120,8 @@ __host__ __device__ inline int scale_exp(unsigned maxbits)
 cudaError_t launch_scale_max(const InstDev *d_inst, int n_inst, const int *h_ts_base, const int *h_T,
                              const long long *h_elems, unsigned *d_maxbits, cudaStream_t s);
 cudaError_t launch_diquarks(const float2 *phi, int L, int T, int N, float2 *out, cudaStream_t s);
+// Seeded pseudo-random complex entries in [-1, 1) (inputs the library makes itself).
+cudaError_t launch_fill_pattern(float2 *out, long long n, unsigned seed, cudaStream_t s);
 cudaError_t launch_dense_fill(const double2 *packed, int T, int N, int P, double2 *dense, cudaStream_t s);
 cudaError_t launch_blockify(const InstDev *d_inst, int inst, const InstDev &h, const unsigned *d_maxbits,
                             cudaStream_t s);

@@ -81,6 +81,32 @@ cudaError_t launch_set_pointers(InstDev *d_inst, int first, int count, const voi
     return cudaSuccess;
 }
 
+// ---------------------------------------------------------------- synthetic
+// Seeded pseudo-random complex entries in [-1, 1) (a 32-bit integer hash of
+// the index and seed), for inputs that the library makes itself (autotuning).
+__global__ void fill_pattern_kernel(float2 *__restrict__ out, long long n, unsigned seed)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        unsigned h = (unsigned)i * 2654435761u ^ (unsigned)(i >> 32) * 40503u ^ seed * 2246822519u;
+        h ^= h >> 15;
+        h *= 2246822519u;
+        h ^= h >> 13;
+        h *= 3266489917u;
+        h ^= h >> 16;
+        const float a = (float)(h & 0xffffu) * (1.f / 32768.f) - 1.f, b = (float)(h >> 16) * (1.f / 32768.f) - 1.f;
+        out[i] = make_float2(a, b);
+    }
+}
+
+cudaError_t launch_fill_pattern(float2 *out, long long n, unsigned seed, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    fill_pattern_kernel<<<(unsigned)blocks, 256, 0, s>>>(out, n, seed);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- scale
 // Largest |re|, |im| of phi per timeslice, as FP32 bits (non-negative floats
 // order like their bit patterns).  The tensor-core kernel turns it into an

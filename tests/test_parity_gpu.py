@@ -303,3 +303,24 @@ def test_large_streamed_shape_sampled_parity(laph):
     gM = Ms[0][0].cpu().numpy()[:, sub][:, :, sub]
     assert rel_frob(gM, rM) <= 1e-5
     plan.close()
+
+
+def test_autotuned_plan_matches_oracle(laph):
+    """PLAN_AUTOTUNE times the candidate schedules at creation and keeps the fastest; the
+    chosen schedule gives the same blocks."""
+    import torch
+    L, T, N = 6, 3, 20
+    mom = synth.momentum_shell(1)
+    plan = laph.Plan([(L, T, N, mom)], mode="f16x3", flags=laph.PLAN_AUTOTUNE)
+    sch = plan.schedule()
+    assert len(sch["candidate_ms"]) >= 2 and all(ms > 0 for ms in sch["candidate_ms"])
+    assert sch["tile_order"] in (0, 1) and sch["n_chunks"] == plan.contraction_launches()
+    phi_h = synth.random_phi(L, N, T=T, instance=95)
+    Bs, Ms = plan.alloc_outputs()
+    ws = plan.alloc_workspace()
+    plan.execute([torch.from_numpy(phi_h).cuda()], Bs, Ms, ws)
+    torch.cuda.synchronize()
+    assert plan.device_status() == laph.LAPH_OK
+    rB, rM = _oracle(phi_h, L, mom)
+    assert rel_frob(Bs[0].cpu().numpy(), rB) <= 1e-5 and rel_frob(Ms[0].cpu().numpy(), rM) <= 1e-5
+    plan.close()
