@@ -361,13 +361,12 @@ __device__ __forceinline__ int next_tile(const Ctx c, Ring &rt, bool &ok)
 // ------------------------------------------------------------ A producer
 
 // The 12 K entries of sites 4h..4h+3 of one row, from the block slots of
-// phi_i (pu) and phi_j (pv), split and written to tensor memory: hi at
-// columns ta..ta+11, lo at ta + A_LO.  kind: 2 diquark, 1 meson
-// (conj(phi_i)), 0 no row (zeros).
+// phi_i (pu) and phi_j (pv), split into hi and lo words.  kind: 2 diquark,
+// 1 meson (conj(phi_i)), 0 no row (zeros).
 template <int ELEM>
-__device__ __forceinline__ void a_quarter(int kind, const uint8_t *pu, const uint8_t *pv, uint32_t ta)
+__device__ __forceinline__ void a_quarter(int kind, const uint8_t *pu, const uint8_t *pv, uint32_t (&hi)[12],
+                                          uint32_t (&lo)[12])
 {
-    uint32_t hi[12], lo[12];
 #pragma unroll
     for (int m = 0; m < 2; m++) {
         // two sites = 6 entries = three 16-byte loads per vector
@@ -393,6 +392,11 @@ __device__ __forceinline__ void a_quarter(int kind, const uint8_t *pu, const uin
             split2<ELEM>(d.x, d.y, hi[6 * m + e], lo[6 * m + e]);
         }
     }
+}
+
+// hi words to columns ta..ta+11, lo words to ta + A_LO ..
+__device__ __forceinline__ void a_store(uint32_t ta, const uint32_t (&hi)[12], const uint32_t (&lo)[12])
+{
 #pragma unroll
     for (int q = 0; q < 3; q++) {
         tmem_st4(ta + 4 * q, hi[4 * q], hi[4 * q + 1], hi[4 * q + 2], hi[4 * q + 3]);
@@ -538,13 +542,21 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
             uint32_t ph = (Gs / (uint32_t)NS) & 1u;  // stage ring phase
             uint32_t pa = (Gs >> 1) & 1u;            // A slot phase: uses of slot grp so far
             for (; st < nst; st += 2) {
-                if (!warp_wait(c, &S->a_empty[grp], pa ^ 1u) || !warp_wait(c, &S->full[s], ph)) {
+                // the entries are formed as soon as the stage has landed; only
+                // the stores into the A slot wait for the MMAs reading it
+                if (!warp_wait(c, &S->full[s], ph)) {
+                    ok = false;
+                    break;
+                }
+                const uint8_t *buf = smem + s * kp.stage_bytes;
+                uint32_t hi[12], lo[12];
+                a_quarter<ELEM>(kind, buf + off_u, buf + off_v, hi, lo);
+                if (!warp_wait(c, &S->a_empty[grp], pa ^ 1u)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint8_t *buf = smem + s * kp.stage_bytes;
-                a_quarter<ELEM>(kind, buf + off_u, buf + off_v, ta0);
+                a_store(ta0, hi, lo);
                 tmem_wait_st();
                 tc_fence_before();
                 __syncwarp();
