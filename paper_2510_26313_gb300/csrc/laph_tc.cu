@@ -91,7 +91,7 @@ struct Shared {
     uint64_t full[MAX_NS], empty[MAX_NS];
     uint64_t tfull[TRING], tempty[TRING];
     int tile_ring[TRING];
-    uint64_t a_full[2], a_empty[2];
+    uint64_t a_full[2];
     uint64_t acc_full[2], acc_empty[2];   // per column half of the accumulator
     uint64_t done;
     uint32_t tmem_base;
@@ -443,7 +443,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
         }
         for (int s = 0; s < 2; s++) {
             mbar_init(&S->a_full[s], N_AGROUP);
-            mbar_init(&S->a_empty[s], 1);
         }
         for (int h = 0; h < 2; h++) {
             mbar_init(&S->acc_full[h], 1);
@@ -540,7 +539,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
             const uint32_t Gs = G + st;
             int s = (int)(Gs % (uint32_t)NS);
             uint32_t ph = (Gs / (uint32_t)NS) & 1u;  // stage ring phase
-            uint32_t pa = (Gs >> 1) & 1u;            // A slot phase: uses of slot grp so far
+            // A slot grp is free once stage Gs - 2, its previous user, has
+            // completed: the stage's commit to empty[(Gs - 2) mod NS].  Before
+            // the first use the parity wait passes on the fresh barrier.
+            const uint32_t Gp = Gs + (uint32_t)NS - 2u;
+            int s2 = (int)(Gp % (uint32_t)NS);
+            uint32_t ph2 = ((Gp / (uint32_t)NS) & 1u) ^ 1u;
             for (; st < nst; st += 2) {
                 // the entries are formed as soon as the stage has landed; only
                 // the stores into the A slot wait for the MMAs reading it
@@ -551,7 +555,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
                 const uint8_t *buf = smem + s * kp.stage_bytes;
                 uint32_t hi[12], lo[12];
                 a_quarter<ELEM>(kind, buf + off_u, buf + off_v, hi, lo);
-                if (!warp_wait(c, &S->a_empty[grp], pa ^ 1u)) {
+                if (!warp_wait(c, &S->empty[s2], ph2)) {
                     ok = false;
                     break;
                 }
@@ -563,11 +567,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
                 const bool skip = kp.debug_stall && !stalled && blockIdx.x == 0 && warp == 0;
                 if (skip) stalled = true;
                 if (lane == 0 && !skip) mbar_arrive(&S->a_full[grp]);
-                pa ^= 1u;
                 s += 2;
                 if (s >= NS) {
                     s -= NS;
                     ph ^= 1u;
+                }
+                s2 += 2;
+                if (s2 >= NS) {
+                    s2 -= NS;
+                    ph2 ^= 1u;
                 }
             }
             G += (uint32_t)nst;
@@ -736,7 +744,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
                     if (!ok) break;
                 }
                 if (lane == 0) {
-                    mma_commit(&S->a_empty[ra.slot]);
+                    // one commit frees the stage buffer (loader) and the A slot (producers)
                     mma_commit(&S->empty[rs.slot]);
                     issued = true;
                 }
