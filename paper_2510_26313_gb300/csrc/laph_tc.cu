@@ -691,7 +691,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
             for (int st = 0; st < nst; st++) {
                 const bool chunk_start = cs == 0;
                 const bool chunk_end = cs + 1 == kp.chunk_stages || st + 1 == nst;
-                if (!warp_wait(c, &S->a_full[ra.slot], ra.phase) || !warp_wait(c, &S->full[rs.slot], rs.phase)) {
+                // Every producer warp of the stage waited for the stage's data
+                // (full[rs.slot]) before its release-arrive on a_full, so the
+                // acquire of a_full also orders the MMAs after the bulk copies;
+                // the MMA warp waits on one barrier per stage.
+                if (!warp_wait(c, &S->a_full[ra.slot], ra.phase)) {
                     ok = false;
                     break;
                 }
