@@ -38,6 +38,12 @@
  *   mom  [P][3]         int32 (n_x, n_y, n_z)
  *   B    [P][C(N,3)]    packed
  *   M    [P][N][N]
+ *
+ * General fields (three different sets of N colour vectors phi, psi, chi,
+ * e.g. stochastic-LapH quark sinks; same paper passage):
+ *
+ *   B3[p][i][j][k] = sum_x ph_p(x) sum_{a,b,c} eps_abc phi_i^a(x) psi_j^b(x) chi_k^c(x)   (dense, no symmetry)
+ *   M2[p][i][j]    = sum_x ph_p(x) sum_a conj(phi_i^a(x)) psi_j^a(x)
  */
 #include <math.h>
 #include <stdint.h>
@@ -319,4 +325,140 @@ void oracle_baryon_dense(const double *packed, int N, int P, double *dense)
                     dense[o] = sign * packed[2 * (p * T3 + idx)];
                     dense[o + 1] = sign * packed[2 * (p * T3 + idx) + 1];
                 }
+}
+
+/* eps_abc f1_i^a(x) f2_j^b(x) f3_k^c(x) for three different fields, summed over the six permutations. */
+static cplx eps_site_fields(const double *f1, const double *f2, const double *f3, int64_t V, int i, int j, int k,
+                            int64_t x)
+{
+    cplx s = {0.0, 0.0};
+    for (int q = 0; q < 6; q++) {
+        cplx t = cmul(cmul(phi_at(f1, V, i, x, EPS_PERM[q][0]), phi_at(f2, V, j, x, EPS_PERM[q][1])),
+                      phi_at(f3, V, k, x, EPS_PERM[q][2]));
+        s.re += EPS_SIGN[q] * t.re;
+        s.im += EPS_SIGN[q] * t.im;
+    }
+    return s;
+}
+
+/*
+ * Three-field triplets for a list of index triples: out[n][P] complex =
+ * B3[p][ijk[n][0], ijk[n][1], ijk[n][2]] with field f1 = phi at index i,
+ * f2 = psi at j, f3 = chi at k.  Returns 0, or -1 on allocation failure /
+ * bad index.
+ */
+int oracle_triplet_triples(const double *f1, const double *f2, const double *f3, int L, int N, const int32_t *mom,
+                           int P, int64_t n_trip, const int32_t *ijk, double *out)
+{
+    int64_t V = (int64_t)L * L * L;
+    for (int64_t t = 0; t < 3 * n_trip; t++)
+        if (ijk[t] < 0 || ijk[t] >= N) return -1;
+    cplx *phT = phase_site_major(L, mom, P);
+    if (!phT) return -1;
+    int failed = 0;
+#pragma omp parallel
+    {
+        cplx *acc = (cplx *)malloc(sizeof(cplx) * (size_t)P);
+        if (!acc) {
+#pragma omp atomic write
+            failed = 1;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t t = 0; t < n_trip; t++) {
+            if (!acc) continue;
+            int i = ijk[3 * t], j = ijk[3 * t + 1], k = ijk[3 * t + 2];
+            for (int p = 0; p < P; p++) acc[p].re = acc[p].im = 0.0;
+            for (int64_t x = 0; x < V; x++) {
+                cplx e = eps_site_fields(f1, f2, f3, V, i, j, k, x);
+                const cplx *ph = phT + x * P;
+                for (int p = 0; p < P; p++) {
+                    cplx u = cmul(ph[p], e);
+                    acc[p].re += u.re;
+                    acc[p].im += u.im;
+                }
+            }
+            for (int p = 0; p < P; p++) {
+                out[2 * (t * P + p)] = acc[p].re;
+                out[2 * (t * P + p) + 1] = acc[p].im;
+            }
+        }
+        free(acc);
+    }
+    free(phT);
+    return failed ? -1 : 0;
+}
+
+/* Dense three-field triplets: out[P][N][N][N] complex, element [p][i][j][k]. */
+int oracle_triplet_blocks(const double *f1, const double *f2, const double *f3, int L, int N, const int32_t *mom,
+                          int P, double *out)
+{
+    int64_t n3 = (int64_t)N * N * N;
+    if (n3 == 0) return 0;
+    int32_t *ijk = (int32_t *)malloc(sizeof(int32_t) * (size_t)(3 * n3));
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)(2 * n3 * P));
+    if (!ijk || !tmp) {
+        free(ijk);
+        free(tmp);
+        return -1;
+    }
+    for (int64_t e = 0; e < n3; e++) {
+        ijk[3 * e] = (int32_t)(e / ((int64_t)N * N));
+        ijk[3 * e + 1] = (int32_t)((e / N) % N);
+        ijk[3 * e + 2] = (int32_t)(e % N);
+    }
+    int rc = oracle_triplet_triples(f1, f2, f3, L, N, mom, P, n3, ijk, tmp);
+    if (rc == 0)
+        for (int64_t e = 0; e < n3; e++)
+            for (int p = 0; p < P; p++) {
+                out[2 * (p * n3 + e)] = tmp[2 * (e * P + p)];
+                out[2 * (p * n3 + e) + 1] = tmp[2 * (e * P + p) + 1];
+            }
+    free(ijk);
+    free(tmp);
+    return rc;
+}
+
+/* Two-field doublets: out[P][N][N] complex, M2[p][i][j] = sum_x ph_p(x) sum_a conj(f1_i^a) f2_j^a. */
+int oracle_doublet_blocks(const double *f1, const double *f2, int L, int N, const int32_t *mom, int P, double *out)
+{
+    int64_t V = (int64_t)L * L * L;
+    cplx *phT = phase_site_major(L, mom, P);
+    if (!phT) return -1;
+    int failed = 0;
+#pragma omp parallel
+    {
+        cplx *acc = (cplx *)malloc(sizeof(cplx) * (size_t)P);
+        if (!acc) {
+#pragma omp atomic write
+            failed = 1;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t ij = 0; ij < (int64_t)N * N; ij++) {
+            if (!acc) continue;
+            int i = (int)(ij / N), j = (int)(ij % N);
+            for (int p = 0; p < P; p++) acc[p].re = acc[p].im = 0.0;
+            for (int64_t x = 0; x < V; x++) {
+                cplx s = {0.0, 0.0};
+                for (int a = 0; a < 3; a++) {
+                    cplx u = cmul(cconj(phi_at(f1, V, i, x, a)), phi_at(f2, V, j, x, a));
+                    s.re += u.re;
+                    s.im += u.im;
+                }
+                const cplx *ph = phT + x * P;
+                for (int p = 0; p < P; p++) {
+                    cplx u = cmul(ph[p], s);
+                    acc[p].re += u.re;
+                    acc[p].im += u.im;
+                }
+            }
+            for (int p = 0; p < P; p++) {
+                int64_t o = 2 * ((p * (int64_t)N + i) * N + j);   /* [p][i][j] */
+                out[o] = acc[p].re;
+                out[o + 1] = acc[p].im;
+            }
+        }
+        free(acc);
+    }
+    free(phT);
+    return failed ? -1 : 0;
 }

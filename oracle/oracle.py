@@ -12,6 +12,12 @@ from the LapH eigenvectors):
     B[p][i,j,k] = sum_x exp(-2 pi i ((n_p.x) mod L)/L) eps_abc phi_i^a phi_j^b phi_k^c
     M[p][i][j]  = sum_x exp(-2 pi i ((n_p.x) mod L)/L) conj(phi_i^a) phi_j^a
 
+and the same contractions of three (two) different sets of vectors, e.g.
+stochastic-LapH quark sinks (same passage):
+
+    B3[p][i][j][k] = sum_x ph_p(x) eps_abc phi_i^a psi_j^b chi_k^c   (dense)
+    M2[p][i][j]    = sum_x ph_p(x) conj(phi_i^a) psi_j^a
+
 in double precision with plain loops (see ``laph_oracle.c``).
 """
 from __future__ import annotations
@@ -67,6 +73,13 @@ def _load():
             lib.oracle_baryon_dense.restype = None
             lib.oracle_diquarks.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp]
             lib.oracle_diquarks.restype = None
+            lib.oracle_triplet_triples.argtypes = [dp, dp, dp, ctypes.c_int, ctypes.c_int, ip, ctypes.c_int,
+                                                   ctypes.c_int64, ip, dp]
+            lib.oracle_triplet_triples.restype = ctypes.c_int
+            lib.oracle_triplet_blocks.argtypes = [dp, dp, dp, ctypes.c_int, ctypes.c_int, ip, ctypes.c_int, dp]
+            lib.oracle_triplet_blocks.restype = ctypes.c_int
+            lib.oracle_doublet_blocks.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ip, ctypes.c_int, dp]
+            lib.oracle_doublet_blocks.restype = ctypes.c_int
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -155,4 +168,50 @@ def baryon_dense(packed: np.ndarray, N: int) -> np.ndarray:
     P = packed.shape[0]
     out = np.empty((P, N, N, N), dtype=np.complex128)
     _load().oracle_baryon_dense(_dptr(packed), N, P, _dptr(out))
+    return out
+
+
+def _prep_fields(fields, L: int, momenta):
+    out = []
+    for f in fields:
+        f, mom = _prep(f, L, momenta)
+        out.append(f)
+    if any(f.shape != out[0].shape for f in out):
+        raise ValueError("the fields must have the same shape [N][L^3][3]")
+    return out, mom
+
+
+def triplet_blocks(phi: np.ndarray, psi: np.ndarray, chi: np.ndarray, L: int, momenta) -> np.ndarray:
+    """Dense three-field triplets, complex128 [P][N][N][N]: [p][i][j][k] = sum_x ph eps phi_i psi_j chi_k."""
+    (phi, psi, chi), mom = _prep_fields((phi, psi, chi), L, momenta)
+    N = phi.shape[0]
+    out = np.zeros((mom.shape[0], N, N, N), dtype=np.complex128)
+    rc = _load().oracle_triplet_blocks(_dptr(phi), _dptr(psi), _dptr(chi), L, N, _iptr(mom), mom.shape[0],
+                                       _dptr(out))
+    if rc != 0:
+        raise RuntimeError("oracle_triplet_blocks failed")
+    return out
+
+
+def triplet_triples(phi: np.ndarray, psi: np.ndarray, chi: np.ndarray, L: int, momenta, ijk) -> np.ndarray:
+    """Three-field triplets for a list of (i, j, k): complex128 [n][P]."""
+    (phi, psi, chi), mom = _prep_fields((phi, psi, chi), L, momenta)
+    ijk = np.ascontiguousarray(np.asarray(ijk, dtype=np.int32).reshape(-1, 3))
+    out = np.zeros((ijk.shape[0], mom.shape[0]), dtype=np.complex128)
+    if ijk.shape[0]:
+        rc = _load().oracle_triplet_triples(_dptr(phi), _dptr(psi), _dptr(chi), L, phi.shape[0], _iptr(mom),
+                                            mom.shape[0], ijk.shape[0], _iptr(ijk), _dptr(out))
+        if rc != 0:
+            raise RuntimeError("oracle_triplet_triples failed (bad index or allocation)")
+    return out
+
+
+def doublet_blocks(phi: np.ndarray, psi: np.ndarray, L: int, momenta) -> np.ndarray:
+    """Two-field doublets, complex128 [P][N][N]: [p][i][j] = sum_x ph conj(phi_i) . psi_j."""
+    (phi, psi), mom = _prep_fields((phi, psi), L, momenta)
+    N = phi.shape[0]
+    out = np.zeros((mom.shape[0], N, N), dtype=np.complex128)
+    rc = _load().oracle_doublet_blocks(_dptr(phi), _dptr(psi), L, N, _iptr(mom), mom.shape[0], _dptr(out))
+    if rc != 0:
+        raise RuntimeError("oracle_doublet_blocks failed")
     return out

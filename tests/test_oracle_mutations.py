@@ -2,8 +2,10 @@
 
 Each case copies ``oracle/laph_oracle.c``, plants one plausible mistake
 (wrong epsilon sign, missing or misplaced conjugation, wrong phase sign,
-transposed site axes, swapped packing, transposed meson output), builds it
-and runs the pin tests against it: they must fail.
+transposed site axes, swapped packing, transposed meson output; for the
+general-field routines: fields bound to the wrong index, a colour index
+swapped, a conjugation on the wrong field, transposed or misindexed
+outputs), builds it and runs the pin tests against it: they must fail.
 """
 import os
 import subprocess
@@ -26,6 +28,15 @@ MUTATIONS = {
                      "ijk[3 * idx] = j;\n                ijk[3 * idx + 1] = i;"),
     "meson_transpose": ("out[2 * ((p * (int64_t)N + i) * N + j)] = acc[p].re;",
                         "out[2 * ((p * (int64_t)N + j) * N + i)] = acc[p].re;"),
+    # three-field triplets and two-field doublets
+    "fields_swapped": ("cmul(cmul(phi_at(f1, V, i, x, EPS_PERM[q][0]), phi_at(f2, V, j, x, EPS_PERM[q][1])),",
+                       "cmul(cmul(phi_at(f2, V, i, x, EPS_PERM[q][0]), phi_at(f1, V, j, x, EPS_PERM[q][1])),"),
+    "fields_colour_swap": ("phi_at(f3, V, k, x, EPS_PERM[q][2]));", "phi_at(f3, V, k, x, EPS_PERM[q][1]));"),
+    "doublet_conj_second": ("cmul(cconj(phi_at(f1, V, i, x, a)), phi_at(f2, V, j, x, a))",
+                            "cmul(phi_at(f1, V, i, x, a), cconj(phi_at(f2, V, j, x, a)))"),
+    "doublet_transpose": ("int64_t o = 2 * ((p * (int64_t)N + i) * N + j);",
+                          "int64_t o = 2 * ((p * (int64_t)N + j) * N + i);"),
+    "triplet_dense_index": ("ijk[3 * e + 2] = (int32_t)(e % N);", "ijk[3 * e + 2] = (int32_t)((e / N) % N);"),
 }
 
 
@@ -41,6 +52,7 @@ def test_pins_fail_on_planted_mistake(name, tmp_path):
                     str(mutated), "-lm"], check=True)
     env = dict(os.environ, LAPH_ORACLE_LIB=str(lib), OMP_NUM_THREADS="2")
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_fields_pins.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins did not catch mutation {name}:\n{r.stdout[-2000:]}"
