@@ -93,6 +93,17 @@ extern "C" {
 /* Test hook: every (instance, timeslice) becomes its own chunk of the
  * tensor-core path, so that small batches exercise the chunked execution. */
 #define LAPH_PLAN_CHUNK_PER_TIMESLICE 0x20000u
+/* Instances of several fields (stochastic-LapH quark sinks; same passage of
+ * the paper: doublets and triplets of colour vectors for the sources and
+ * sinks), run with laph_plan_execute_fields.  Together with exactly one of:
+ *   LAPH_PLAN_SKIP_M  three-field triplets, dense, no symmetry:
+ *       B3[t][p][i][j][k] = sum_x ph_p(x) eps_abc phi_i^a(x) psi_j^b(x) chi_k^c(x)
+ *       out_B: device complex128 [T][P][N][N][N];
+ *   LAPH_PLAN_SKIP_B  two-field doublets:
+ *       M2[t][p][i][j] = sum_x ph_p(x) sum_a conj(phi_i^a(x)) psi_j^a(x)
+ *       out_M: device complex128 [T][P][N][N].
+ * Tensor-core modes only (LAPH_ERR_UNSUPPORTED otherwise); N >= 1. */
+#define LAPH_PLAN_FIELDS 0x40000u
 
 /* One independent problem of a (possibly ragged) batch. */
 typedef struct {
@@ -156,6 +167,17 @@ LAPH_API int laph_baryon_blocks(const void *phi, int L, int T, int N, const int3
 LAPH_API int laph_meson_blocks(const void *phi, int L, int T, int N, const int32_t *momenta, int n_mom, void *out,
                       int mode, void *stream);
 
+/* Three-field triplets of one instance (LAPH_PLAN_FIELDS | LAPH_PLAN_SKIP_M):
+ * out = B3, device complex128 [T][P][N][N][N]; phi, psi, chi device
+ * complex64 [T][N][L^3][3].  Same behaviour as laph_baryon_blocks. */
+LAPH_API int laph_triplet_blocks(const void *phi, const void *psi, const void *chi, int L, int T, int N,
+                                 const int32_t *momenta, int n_mom, void *out, int mode, void *stream);
+
+/* Two-field doublets of one instance (LAPH_PLAN_FIELDS | LAPH_PLAN_SKIP_B):
+ * out = M2, device complex128 [T][P][N][N]. */
+LAPH_API int laph_doublet_blocks(const void *phi, const void *psi, int L, int T, int N, const int32_t *momenta,
+                                 int n_mom, void *out, int mode, void *stream);
+
 /* ---- plan API (ragged batches, capture-safe execution) ----------------- */
 /* Validates the instances (L >= 1; N >= 3 unless LAPH_PLAN_SKIP_B, N >= 1;
  * N <= 3 L^3; 1 <= n_mom; |n| components within +-2^20), copies the
@@ -174,6 +196,16 @@ LAPH_API int laph_plan_workspace_size(const laph_plan *plan, size_t *bytes);
  * workspace_size > 0. */
 LAPH_API int laph_plan_execute(laph_plan *plan, const void *const *phi, void *const *out_B, void *const *out_M,
                       void *workspace, void *stream);
+
+/* Runs a LAPH_PLAN_FIELDS plan on `stream`.  fields holds the device
+ * complex64 [T][N][L^3][3] fields of every instance, three per instance
+ * (phi, psi, chi) for triplets, two (phi, psi) for doublets, each 8-byte
+ * aligned; out[n] is instance n's B3 or M2 (16-byte aligned).  Same
+ * behaviour as laph_plan_execute (no allocation, capture-safe).
+ * LAPH_ERR_ARG for a plan without LAPH_PLAN_FIELDS, null or misaligned
+ * pointers. */
+LAPH_API int laph_plan_execute_fields(laph_plan *plan, const void *const *fields, void *const *out, void *workspace,
+                                      void *stream);
 
 /* Same batch with HOST buffers: phi_host[n] (complex64, pinned or pageable)
  * is copied in, computed, and out_B_host[n]/out_M_host[n] (complex128) are

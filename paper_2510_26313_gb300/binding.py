@@ -30,6 +30,7 @@ PLAN_AUTOTUNE = 0x4
 PLAN_TIMING = 0x8
 PLAN_DEBUG_STALL = 0x10000
 PLAN_CHUNK_PER_TIMESLICE = 0x20000
+PLAN_FIELDS = 0x40000
 
 _lib = None
 
@@ -66,6 +67,9 @@ def lib() -> ctypes.CDLL:
             "laph_baryon_dense": (i32, [vp, i32, i32, i32, vp, vp]),
             "laph_baryon_blocks": (i32, [vp, i32, i32, i32, ip32, i32, vp, i32, vp]),
             "laph_meson_blocks": (i32, [vp, i32, i32, i32, ip32, i32, vp, i32, vp]),
+            "laph_triplet_blocks": (i32, [vp, vp, vp, i32, i32, i32, ip32, i32, vp, i32, vp]),
+            "laph_doublet_blocks": (i32, [vp, vp, i32, i32, i32, ip32, i32, vp, i32, vp]),
+            "laph_plan_execute_fields": (i32, [vp, vpp, vpp, vp, vp]),
             "laph_plan_create": (i32, [ctypes.POINTER(laph_instance), i32, i32, ctypes.c_uint, ctypes.POINTER(vp)]),
             "laph_plan_workspace_size": (i32, [vp, ctypes.POINTER(sz)]),
             "laph_plan_execute": (i32, [vp, vpp, vpp, vpp, vp, vp]),
@@ -187,6 +191,42 @@ def meson_blocks(phi, L: int, momenta, mode="f16x3", out=None, stream=None):
     return out
 
 
+def _check_fields(fields, L):
+    T, N = _check_phi(fields[0], L)
+    for f in fields[1:]:
+        if tuple(f.shape) != tuple(fields[0].shape) or f.device != fields[0].device:
+            raise ValueError("the fields must have the same shape and device")
+        _check_phi(f, L)
+    return T, N
+
+
+def triplet_blocks(phi, psi, chi, L: int, momenta, mode="f16x3", out=None, stream=None):
+    """Three-field triplets complex128 [T][P][N][N][N], dense (one-shot; blocking)."""
+    import torch
+    T, N = _check_fields((phi, psi, chi), L)
+    mom = _momenta(momenta)
+    if out is None:
+        out = torch.empty((T, mom.shape[0], N, N, N), dtype=torch.complex128, device=phi.device)
+    rc = lib().laph_triplet_blocks(_ptr(phi), _ptr(psi), _ptr(chi), L, T, N,
+                                   mom.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), mom.shape[0], _ptr(out),
+                                   _mode(mode), _stream(stream))
+    _check(rc, "laph_triplet_blocks")
+    return out
+
+
+def doublet_blocks(phi, psi, L: int, momenta, mode="f16x3", out=None, stream=None):
+    """Two-field doublets complex128 [T][P][N][N] (one-shot; blocking)."""
+    import torch
+    T, N = _check_fields((phi, psi), L)
+    mom = _momenta(momenta)
+    if out is None:
+        out = torch.empty((T, mom.shape[0], N, N), dtype=torch.complex128, device=phi.device)
+    rc = lib().laph_doublet_blocks(_ptr(phi), _ptr(psi), L, T, N, mom.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   mom.shape[0], _ptr(out), _mode(mode), _stream(stream))
+    _check(rc, "laph_doublet_blocks")
+    return out
+
+
 def blocks_noalloc(phi, L: int, momenta, out_B, out_M, stream=None):
     """FP32 B and/or M into caller-owned outputs with no device allocation.
 
@@ -292,8 +332,9 @@ class Plan:
         Bs, Ms = [], []
         for (L, T, N, m) in self.instances:
             P = m.shape[0]
+            shapeB = (T, P, N, N, N) if self.flags & PLAN_FIELDS else (T, P, N * (N - 1) * (N - 2) // 6)
             Bs.append(None if self.flags & PLAN_SKIP_B else
-                      torch.empty((T, P, N * (N - 1) * (N - 2) // 6), dtype=torch.complex128, device=device or "cuda"))
+                      torch.empty(shapeB, dtype=torch.complex128, device=device or "cuda"))
             Ms.append(None if self.flags & PLAN_SKIP_M else
                       torch.empty((T, P, N, N), dtype=torch.complex128, device=device or "cuda"))
         return Bs, Ms
@@ -313,6 +354,18 @@ class Plan:
         ma = self._ptr_array(Ms) if Ms is not None else None
         ws = ctypes.c_void_p(workspace.data_ptr()) if workspace is not None else ctypes.c_void_p()
         _check(lib().laph_plan_execute(self._h, pa, ba, ma, ws, _stream(stream)), "laph_plan_execute")
+
+    def execute_fields(self, fields, outs, workspace, stream=None):
+        """LAPH_PLAN_FIELDS plans: fields[n] = (phi, psi, chi) for triplets, (phi, psi) for
+        doublets; outs[n] the instance's B3 or M2."""
+        flat = []
+        for (L, T, N, _), fs in zip(self.instances, fields):
+            _check_fields(tuple(fs), L)
+            flat.extend(fs)
+        fa = self._ptr_array(flat)
+        oa = self._ptr_array(outs)
+        ws = ctypes.c_void_p(workspace.data_ptr()) if workspace is not None else ctypes.c_void_p()
+        _check(lib().laph_plan_execute_fields(self._h, fa, oa, ws, _stream(stream)), "laph_plan_execute_fields")
 
     def execute_host(self, phis_host, Bs_host, Ms_host, workspace, stream=None):
         """Host (numpy / pinned torch CPU) inputs and outputs; blocking."""

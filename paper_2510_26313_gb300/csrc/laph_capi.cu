@@ -201,12 +201,17 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
     if (mode < 0 || mode >= LAPH_NUM_MODES) return LAPH_ERR_ARG;
     const bool skipB = flags & LAPH_PLAN_SKIP_B, skipM = flags & LAPH_PLAN_SKIP_M;
     if (skipB && skipM) return LAPH_ERR_ARG;
+    // several fields: triplets (skip M) or doublets (skip B), tensor-core modes only
+    const bool fields = flags & LAPH_PLAN_FIELDS;
+    const int kind = !fields ? laph::INST_BLOCKS : (skipM ? laph::INST_TRIPLETS : laph::INST_DOUBLETS);
+    if (fields && !(skipB || skipM)) return LAPH_ERR_ARG;
+    if (fields && !is_tc_mode(mode)) return LAPH_ERR_UNSUPPORTED;
     for (int n = 0; n < n_inst; n++) {
         const laph_instance &I = inst[n];
         if (I.L < 1 || I.L > MAX_L || I.T < 1 || I.N < 1 || I.N > MAX_N || I.n_mom < 1 || I.n_mom > MAX_P ||
             !I.momenta)
             return LAPH_ERR_ARG;
-        if (!skipB && I.N < 3) return LAPH_ERR_ARG;
+        if (!skipB && !fields && I.N < 3) return LAPH_ERR_ARG;
         if ((long long)I.N > 3LL * I.L * I.L * I.L) return LAPH_ERR_ARG;
         for (int q = 0; q < 3 * I.n_mom; q++)
             if (I.momenta[q] > MAX_MOM || I.momenta[q] < -MAX_MOM) return LAPH_ERR_ARG;
@@ -243,8 +248,11 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
         d.blk_off = -1;
         d.nblk = (int)((d.V + laph::TC_BS - 1) / laph::TC_BS);
         d.n_trip = laph::binom3(I.N);
+        d.kind = kind;
+        d.n_fields = kind == laph::INST_TRIPLETS ? 3 : (kind == laph::INST_DOUBLETS ? 2 : 1);
+        d.blkv_off = -1;
         d.mes_rows = skipM ? 0 : I.N;
-        d.pair_rows = skipB ? 0 : (int)laph::binom2(I.N);
+        d.pair_rows = skipB ? 0 : (kind == laph::INST_TRIPLETS ? I.N * I.N : (int)laph::binom2(I.N));
         d.rows = d.mes_rows + d.pair_rows;
         d.cols = I.N * I.n_mom;
         d.n_ct = (d.cols + laph::TC_TC - 1) / laph::TC_TC;
@@ -255,7 +263,9 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
         ts += I.T;
         p->h_inst.push_back(d);
         p->phi_elems.push_back((long long)I.T * I.N * d.V * 3);
-        p->outB_elems.push_back(skipB ? 0 : (long long)I.T * I.n_mom * d.n_trip);
+        p->outB_elems.push_back(skipB ? 0
+                                      : (long long)I.T * I.n_mom *
+                                            (kind == laph::INST_TRIPLETS ? (long long)I.N * I.N * I.N : d.n_trip));
         p->outM_elems.push_back(skipM ? 0 : (long long)I.T * I.n_mom * I.N * I.N);
         phase_off[n] = phase_total;
         phase_total += (long long)I.n_mom * d.Vs;
@@ -317,20 +327,29 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
         for (int col0 = 0; col0 < d.cols; col0 += TC) {
             const int nc = std::min(TC, d.cols - col0);
             const int kmin = col0 / d.P, kmax = (col0 + nc - 1) / d.P;
+            const bool trip = d.kind == laph::INST_TRIPLETS;
             for (int row0 = 0; row0 < d.rows; row0 += TR) {
+                // baryon blocks: rows of pairs i < j need only columns k > j
                 int jmin = -1;
-                if (row0 >= d.mes_rows) {
+                if (row0 >= d.mes_rows && !trip) {
                     int i, j;
                     laph::pair_of(row0 - d.mes_rows, i, j);
                     jmin = j;
                 }
                 if (jmin >= 0 && kmax <= jmin) continue;
-                // contiguous range of vectors used by the rows of this tile
-                int v_lo = d.N, v_hi = -1;
+                // contiguous range of vectors used by the rows of this tile (for
+                // triplets: of phi_u, and [w_lo, w_hi] of phi_v)
+                int v_lo = d.N, v_hi = -1, w_lo = d.N, w_hi = -1;
                 for (int g = row0; g < std::min(row0 + TR, d.rows); g++) {
                     if (g < d.mes_rows) {
                         v_lo = std::min(v_lo, g);
                         v_hi = std::max(v_hi, g);
+                    } else if (trip) {
+                        const int q = g - d.mes_rows, i = q / d.N, j = q - i * d.N;
+                        v_lo = std::min(v_lo, i);
+                        v_hi = std::max(v_hi, i);
+                        w_lo = std::min(w_lo, j);
+                        w_hi = std::max(w_hi, j);
                     } else {
                         int i, j;
                         laph::pair_of(g - d.mes_rows, i, j);
@@ -339,14 +358,16 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
                     }
                 }
                 const int nv = v_hi - v_lo + 1;
-                p->max_staged = std::max(p->max_staged, tc ? nv : nv + (kmax - kmin + 1));
+                const int nw = trip ? w_hi - w_lo + 1 : 0;
+                if (!trip) w_lo = 0;
+                p->max_staged = std::max(p->max_staged, tc ? nv + nw : nv + (kmax - kmin + 1));
                 const long long psi_ct = (long long)(col0 / TC) * d.n_st * laph::TC_STAGE_BYTES;
                 int cskip = 0;
                 if (tc && jmin >= 0) {
                     const int lead = std::max(0, std::min(nc, (jmin + 1) * d.P - col0));
                     cskip = (lead / 8) * 8;
                 }
-                one.push_back(TileDev{n, 0, row0, col0, v_lo, nv, kmin, kmax - kmin + 1, nc, cskip, psi_ct});
+                one.push_back(TileDev{n, 0, row0, col0, v_lo, nv, w_lo, nw, kmin, kmax - kmin + 1, nc, cskip, psi_ct});
             }
         }
         p->max_P = std::max(p->max_P, d.P);
@@ -470,8 +491,13 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
             p->ws_zero_bytes = off;
             for (int n = 0; n < n_inst; n++) {
                 InstDev &d = p->h_inst[n];
+                const size_t blk_bytes = (((size_t)d.T * d.nblk * d.N * laph::TC_SLOT * sizeof(float2) + 255) / 256) * 256;
                 d.blk_off = (long long)off;
-                off += (((size_t)d.T * d.nblk * d.N * laph::TC_SLOT * sizeof(float2) + 255) / 256) * 256;
+                off += blk_bytes;
+                if (d.kind == laph::INST_TRIPLETS) {
+                    d.blkv_off = (long long)off;
+                    off += blk_bytes;
+                }
             }
             p->off_psi = off;
             off += ((psi_max + 255) / 256) * 256;
@@ -606,7 +632,8 @@ static int launch_chunk_prep(laph_plan *p, char *ws, size_t ci, cudaStream_t s)
         const int n = p->h_units[u].inst, t0 = p->h_units[u].t;
         int nt = 1;
         while (u + nt < c.unit0 + c.n_units && p->h_units[u + nt].inst == n && p->h_units[u + nt].t == t0 + nt) nt++;
-        cudaError_t e = laph::launch_scale_max_range(p->d_inst, n, t0, nt, p->phi_elems[n] / p->h_T[n], maxbits, s);
+        cudaError_t e = laph::launch_scale_max_range(p->d_inst, n, t0, nt, p->phi_elems[n] / p->h_T[n], maxbits, s,
+                                                     p->h_inst[n].n_fields);
         if (e == cudaSuccess) e = laph::launch_blockify_range(p->d_inst, n, p->h_inst[n], t0, nt, maxbits, s);
         if (e != cudaSuccess) return cuda_fail(e, "scale/blockify");
         u += nt;
@@ -624,8 +651,13 @@ static int launch_batch(laph_plan *p, void *workspace, cudaStream_t s)
         unsigned *maxbits = (unsigned *)(ws + p->off_maxbits);
         CK(cudaMemsetAsync(ws, 0, p->ws_zero_bytes, s));
         std::vector<long long> elems(p->n_inst);
-        for (int n = 0; n < p->n_inst; n++) elems[n] = p->phi_elems[n] / p->h_T[n];
-        e = laph::launch_scale_max(p->d_inst, p->n_inst, p->h_ts_base.data(), p->h_T.data(), elems.data(), maxbits, s);
+        std::vector<int> nf(p->n_inst);
+        for (int n = 0; n < p->n_inst; n++) {
+            elems[n] = p->phi_elems[n] / p->h_T[n];
+            nf[n] = p->h_inst[n].n_fields;
+        }
+        e = laph::launch_scale_max(p->d_inst, p->n_inst, p->h_ts_base.data(), p->h_T.data(), elems.data(), maxbits, s,
+                                   nf.data());
         if (e != cudaSuccess) return cuda_fail(e, "scale_max");
         for (int n = 0; n < p->n_inst; n++) {
             e = laph::launch_blockify(p->d_inst, n, p->h_inst[n], maxbits, s);
@@ -778,7 +810,7 @@ int laph_plan_launches_per_execute(const laph_plan *plan, int *n)
 int laph_plan_execute(laph_plan *plan, const void *const *phi, void *const *out_B, void *const *out_M,
                       void *workspace, void *stream)
 {
-    if (!plan || !phi) return LAPH_ERR_ARG;
+    if (!plan || !phi || (plan->flags & LAPH_PLAN_FIELDS)) return LAPH_ERR_ARG;
     const bool needB = !(plan->flags & LAPH_PLAN_SKIP_B), needM = !(plan->flags & LAPH_PLAN_SKIP_M);
     if ((needB && !out_B) || (needM && !out_M)) return LAPH_ERR_ARG;
     for (int n = 0; n < plan->n_inst; n++) {
@@ -792,6 +824,27 @@ int laph_plan_execute(laph_plan *plan, const void *const *phi, void *const *out_
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = laph::launch_set_pointers(plan->d_inst, 0, plan->n_inst, phi, needB ? out_B : nullptr,
                                               needM ? out_M : nullptr, workspace, s);
+    if (e != cudaSuccess) return cuda_fail(e, "set_pointers");
+    return launch_batch(plan, workspace, s);
+}
+
+int laph_plan_execute_fields(laph_plan *plan, const void *const *fields, void *const *out, void *workspace,
+                             void *stream)
+{
+    if (!plan || !fields || !out || !(plan->flags & LAPH_PLAN_FIELDS)) return LAPH_ERR_ARG;
+    const bool trip = plan->flags & LAPH_PLAN_SKIP_M;
+    const int nf = trip ? 3 : 2;
+    for (int n = 0; n < plan->n_inst; n++) {
+        for (int f = 0; f < nf; f++)
+            if (!fields[nf * n + f] || ((uintptr_t)fields[nf * n + f]) % 8) return LAPH_ERR_ARG;
+        if (!out[n] || ((uintptr_t)out[n]) % 16) return LAPH_ERR_ARG;
+    }
+    int cur = 0;
+    CK(cudaGetDevice(&cur));
+    if (cur != plan->device) return LAPH_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = laph::launch_set_pointers(plan->d_inst, 0, plan->n_inst, nullptr, trip ? out : nullptr,
+                                              trip ? nullptr : out, workspace, s, fields, nf);
     if (e != cudaSuccess) return cuda_fail(e, "set_pointers");
     return launch_batch(plan, workspace, s);
 }
@@ -813,6 +866,7 @@ int laph_plan_execute_host(laph_plan *plan, const void *const *phi_host, void *c
                            void *const *out_M_host, void *workspace, void *stream)
 {
     if (!plan || !phi_host || !workspace || ((uintptr_t)workspace) % 256) return LAPH_ERR_ARG;
+    if (plan->flags & LAPH_PLAN_FIELDS) return LAPH_ERR_UNSUPPORTED;
     const bool needB = !(plan->flags & LAPH_PLAN_SKIP_B), needM = !(plan->flags & LAPH_PLAN_SKIP_M);
     if ((needB && !out_B_host) || (needM && !out_M_host)) return LAPH_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -963,6 +1017,50 @@ int laph_meson_blocks(const void *phi, int L, int T, int N, const int32_t *momen
                       void *stream)
 {
     return one_shot(phi, L, T, N, momenta, n_mom, out, mode, stream, false);
+}
+
+// Triplets (three fields) or doublets (two fields) of one instance.
+static int one_shot_fields(const void *const *fields, int L, int T, int N, const int32_t *momenta, int n_mom,
+                           void *out, int mode, void *stream, bool triplets)
+{
+    if (!out) return LAPH_ERR_ARG;
+    laph_instance inst = {L, T, N, n_mom, momenta};
+    laph_plan *plan = nullptr;
+    int rc = laph_plan_create(&inst, 1, mode, LAPH_PLAN_FIELDS | (triplets ? LAPH_PLAN_SKIP_M : LAPH_PLAN_SKIP_B),
+                              &plan);
+    if (rc != LAPH_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    void *ws = nullptr;
+    if (plan->ws_bytes) {
+        cudaError_t e = cudaMallocAsync(&ws, plan->ws_bytes, s);
+        if (e != cudaSuccess) {
+            laph_plan_destroy(plan);
+            return cuda_fail(e, "cudaMallocAsync");
+        }
+    }
+    void *o = out;
+    rc = laph_plan_execute_fields(plan, fields, &o, ws, stream);
+    if (ws) cudaFreeAsync(ws, s);
+    int dev = LAPH_OK;
+    int rc2 = laph_get_device_status(plan, stream, &dev);  // synchronises the stream
+    laph_plan_destroy(plan);
+    if (rc != LAPH_OK) return rc;
+    if (rc2 != LAPH_OK) return rc2;
+    return dev;
+}
+
+int laph_triplet_blocks(const void *phi, const void *psi, const void *chi, int L, int T, int N,
+                        const int32_t *momenta, int n_mom, void *out, int mode, void *stream)
+{
+    const void *f[3] = {phi, psi, chi};
+    return one_shot_fields(f, L, T, N, momenta, n_mom, out, mode, stream, true);
+}
+
+int laph_doublet_blocks(const void *phi, const void *psi, int L, int T, int N, const int32_t *momenta, int n_mom,
+                        void *out, int mode, void *stream)
+{
+    const void *f[2] = {phi, psi};
+    return one_shot_fields(f, L, T, N, momenta, n_mom, out, mode, stream, false);
 }
 
 }  // extern "C"

@@ -11,20 +11,34 @@ namespace laph {
 constexpr int STATUS_TIMEOUT = 1;
 constexpr int STATUS_CHECK = 2;
 
+// Kinds of instance.  INST_BLOCKS: the LapH meson and baryon blocks of one
+// set of vectors phi (B packed over i<j<k).  INST_TRIPLETS: three-field
+// triplets B3[p][i][j][k] = sum_x ph eps phi_i psi_j chi_k, dense.
+// INST_DOUBLETS: two-field doublets M2[p][i][j] = sum_x ph conj(phi_i) psi_j.
+constexpr int INST_BLOCKS = 0;
+constexpr int INST_TRIPLETS = 1;
+constexpr int INST_DOUBLETS = 2;
+
 // One instance of a batch, as the kernels see it.  Row space of the
-// contraction: rows [0, mes_rows) are meson rows (vector i = row), rows
-// [mes_rows, mes_rows + pair_rows) are diquark rows, pair q = row - mes_rows
-// in colex order q = C(j,2) + i.  Column space: col = k * P + p.
+// contraction: rows [0, mes_rows) are meson rows (vector i = row, A operand
+// conj(phi_u_i)), rows [mes_rows, mes_rows + pair_rows) are diquark rows
+// (A operand phi_u_i x phi_v_j): pair q = row - mes_rows in colex order
+// q = C(j,2) + i for INST_BLOCKS, q = i * N + j for INST_TRIPLETS.  Column
+// space: col = k * P + p, B operand ph_p * phi_k (phi is the column field).
 struct InstDev {
-    const float2 *phi;       // [T][N][V][3]
+    const float2 *phi;       // [T][N][V][3] column field (phi; chi for triplets, psi for doublets)
+    const float2 *phi_u;     // [T][N][V][3] first row field (phi)
+    const float2 *phi_v;     // [T][N][V][3] second row field (phi; psi for triplets)
     double2 *outB;           // [T][P][C(N,3)]
     double2 *outM;           // [T][P][N][N]
     const float2 *phase;     // [P][Vs], FP32 rounding of the FP64 phase
-    float2 *phi_blk;         // tensor-core path: scaled, site-blocked copy of phi in the workspace
+    float2 *phi_blk;         // tensor-core path: scaled, site-blocked copy of phi_u in the workspace
+    float2 *blk_v;           // the same for phi_v (triplets only)
     long long V;
     long long Vs;            // V rounded up to even: row stride of `phase`
     long long n_trip;        // C(N,3)
     long long blk_off;       // byte offset of phi_blk in the workspace (-1: none)
+    long long blkv_off;      // byte offset of blk_v in the workspace (-1: none)
     int L, T, N, P;
     int mes_rows;            // N, or 0 when mesons are skipped
     int pair_rows;           // C(N,2), or 0 when baryons are skipped
@@ -34,6 +48,8 @@ struct InstDev {
     int nblk;                // site blocks: ceil(V / TC_BS)
     int n_ct;                // column tiles of the tensor-core path: ceil(cols / TC_TC)
     int n_st;                // K stages of the tensor-core path: one per site block (= nblk)
+    int kind;                // INST_BLOCKS, INST_TRIPLETS or INST_DOUBLETS
+    int n_fields;            // distinct input fields: 1, 3 (triplets) or 2 (doublets)
     int pad_;
 };
 
@@ -46,11 +62,14 @@ constexpr int TC_SLOT = 3 * TC_BS + 2;        // complex entries per (block, vec
 
 // One unit of work: a (row tile, column tile) of one timeslice.  v_lo and nv
 // give the contiguous range of vector indices the tile's rows use (the
-// tensor-core path stages exactly these vectors in shared memory); psi_off is
-// the byte offset of the tile's B operand stages in the Psi buffer.
+// tensor-core path stages exactly these vectors in shared memory; for
+// triplets these are phi_u vectors, and [w_lo, w_lo + nw) of phi_v follow
+// them); psi_off is the byte offset of the tile's B operand stages in the
+// Psi buffer.
 struct TileDev {
     int inst, t, row0, col0;
     int v_lo, nv;        // vectors used by the rows: [v_lo, v_lo + nv)
+    int w_lo, nw;        // triplets: phi_v vectors used by the rows (nw = 0 otherwise)
     int k_lo, nk;        // vectors used by the columns: [k_lo, k_lo + nk)
     int ncols;           // valid columns of the tile
     int cskip;           // leading columns no row of the tile needs (multiple of 8; tensor-core path)
@@ -106,8 +125,12 @@ __device__ __forceinline__ float2 cross_c(const float2 *u, const float2 *v, int 
 // laph_prep.cu
 cudaError_t launch_phase_table(int L, const int32_t *d_mom, int P, double2 *out64, float2 *out32,
                                cudaStream_t s);
+// fields: null (every instance has one field, phi[n]), else n_fields entries
+// per instance in the order (phi, psi, chi) for triplets, (phi, psi) for
+// doublets; phi may then be null.
 cudaError_t launch_set_pointers(InstDev *d_inst, int first, int count, const void *const *phi,
-                                void *const *outB, void *const *outM, void *workspace, cudaStream_t s);
+                                void *const *outB, void *const *outM, void *workspace, cudaStream_t s,
+                                const void *const *fields = nullptr, int n_fields = 1);
 // Power-of-two exponent s with max|phi| * 2^s in [0.5, 1), from the FP32 bits of max|phi|.
 __host__ __device__ inline int scale_exp(unsigned maxbits)
 {
@@ -117,17 +140,20 @@ __host__ __device__ inline int scale_exp(unsigned maxbits)
     int s = 126 - E;
     return s > 100 ? 100 : (s < -100 ? -100 : s);
 }
+// Max |field entry| per timeslice over all of an instance's fields (h_nfields[n] of them).
 cudaError_t launch_scale_max(const InstDev *d_inst, int n_inst, const int *h_ts_base, const int *h_T,
-                             const long long *h_elems, unsigned *d_maxbits, cudaStream_t s);
+                             const long long *h_elems, unsigned *d_maxbits, cudaStream_t s,
+                             const int *h_nfields = nullptr);
 cudaError_t launch_diquarks(const float2 *phi, int L, int T, int N, float2 *out, cudaStream_t s);
 // Seeded pseudo-random complex entries in [-1, 1) (inputs the library makes itself).
 cudaError_t launch_fill_pattern(float2 *out, long long n, unsigned seed, cudaStream_t s);
 cudaError_t launch_dense_fill(const double2 *packed, int T, int N, int P, double2 *dense, cudaStream_t s);
+// Site-blocked copies of phi_u (and, for triplets, phi_v).
 cudaError_t launch_blockify(const InstDev *d_inst, int inst, const InstDev &h, const unsigned *d_maxbits,
                             cudaStream_t s);
 // The same for the timeslices [t0, t0 + nt) of one instance.
 cudaError_t launch_scale_max_range(const InstDev *d_inst, int inst, int t0, int nt, long long elems_per_ts,
-                                   unsigned *d_maxbits, cudaStream_t s);
+                                   unsigned *d_maxbits, cudaStream_t s, int n_fields = 1);
 cudaError_t launch_blockify_range(const InstDev *d_inst, int inst, const InstDev &h, int t0, int nt,
                                   const unsigned *d_maxbits, cudaStream_t s);
 

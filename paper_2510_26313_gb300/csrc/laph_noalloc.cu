@@ -119,7 +119,7 @@ __global__ void noalloc_setup_kernel(NoallocSetup su, InstDev *d_inst, int32_t *
             const int kmax = (col0 + nc - 1) / d.P;
             if (jmin >= 0 && kmax <= jmin) continue;
             for (int t = 0; t < d.T; t++) {
-                TileDev u{0, t, row0, col0, 0, 0, 0, 0, nc, 0, 0};
+                TileDev u{0, t, row0, col0, 0, 0, 0, 0, 0, 0, nc, 0, 0};
                 d_tiles[(long long)t * su.tiles_per_ts + k] = u;
             }
             k++;
@@ -152,6 +152,9 @@ extern "C" int laph_blocks_noalloc(const void *phi, int L, int T, int N, const i
     memset(&su, 0, sizeof(su));
     InstDev &d = su.inst;
     d.phi = (const float2 *)phi;
+    d.phi_u = d.phi_v = d.phi;
+    d.blkv_off = -1;
+    d.n_fields = 1;
     d.outB = (double2 *)out_B;
     d.outM = (double2 *)out_M;
     d.L = L;

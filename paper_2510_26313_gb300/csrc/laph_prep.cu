@@ -44,7 +44,9 @@ constexpr int PTR_BATCH = 64;
 struct PtrBatch {
     int first, count;
     char *ws;
-    const void *phi[PTR_BATCH];
+    const void *phi[PTR_BATCH];    // column field
+    const void *phi_u[PTR_BATCH];  // first row field
+    const void *phi_v[PTR_BATCH];  // second row field
     void *outB[PTR_BATCH];
     void *outM[PTR_BATCH];
 };
@@ -55,14 +57,18 @@ __global__ void set_pointers_kernel(InstDev *d_inst, PtrBatch b)
     if (n < b.count) {
         InstDev &I = d_inst[b.first + n];
         I.phi = (const float2 *)b.phi[n];
+        I.phi_u = (const float2 *)b.phi_u[n];
+        I.phi_v = (const float2 *)b.phi_v[n];
         I.outB = (double2 *)b.outB[n];
         I.outM = (double2 *)b.outM[n];
         I.phi_blk = (I.blk_off >= 0 && b.ws) ? (float2 *)(b.ws + I.blk_off) : nullptr;
+        I.blk_v = (I.blkv_off >= 0 && b.ws) ? (float2 *)(b.ws + I.blkv_off) : I.phi_blk;
     }
 }
 
 cudaError_t launch_set_pointers(InstDev *d_inst, int first, int count, const void *const *phi, void *const *outB,
-                                void *const *outM, void *workspace, cudaStream_t s)
+                                void *const *outM, void *workspace, cudaStream_t s, const void *const *fields,
+                                int n_fields)
 {
     for (int base = 0; base < count; base += PTR_BATCH) {
         PtrBatch b;
@@ -70,7 +76,16 @@ cudaError_t launch_set_pointers(InstDev *d_inst, int first, int count, const voi
         b.first = first + base;
         b.count = count - base < PTR_BATCH ? count - base : PTR_BATCH;
         for (int n = 0; n < b.count; n++) {
-            b.phi[n] = phi[base + n];
+            if (!fields) {
+                b.phi[n] = b.phi_u[n] = b.phi_v[n] = phi[base + n];
+            } else if (n_fields == 3) {   // triplets: rows phi x psi, columns chi
+                b.phi_u[n] = fields[3 * (base + n)];
+                b.phi_v[n] = fields[3 * (base + n) + 1];
+                b.phi[n] = fields[3 * (base + n) + 2];
+            } else {                      // doublets: rows conj(phi), columns psi
+                b.phi_u[n] = b.phi_v[n] = fields[2 * (base + n)];
+                b.phi[n] = fields[2 * (base + n) + 1];
+            }
             b.outB[n] = outB ? outB[base + n] : nullptr;
             b.outM[n] = outM ? outM[base + n] : nullptr;
         }
@@ -116,7 +131,9 @@ __global__ void scale_max_kernel(const InstDev *__restrict__ d_inst, int inst, i
     const InstDev &I = d_inst[inst];
     const int t = t0 + blockIdx.y;
     const long long n = (long long)I.N * I.V * 3;
-    const float2 *base = I.phi + (long long)t * n;
+    // field blockIdx.z: the column field, then the row fields of a multi-field instance
+    const float2 *f = blockIdx.z == 0 ? I.phi : (blockIdx.z == 1 ? I.phi_u : I.phi_v);
+    const float2 *base = f + (long long)t * n;
     float m = 0.f;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         float2 v = __ldg(base + e);
@@ -134,14 +151,14 @@ __global__ void scale_max_kernel(const InstDev *__restrict__ d_inst, int inst, i
 }
 
 cudaError_t launch_scale_max(const InstDev *d_inst, int n_inst, const int *h_ts_base, const int *h_T,
-                             const long long *h_elems, unsigned *d_maxbits, cudaStream_t s)
+                             const long long *h_elems, unsigned *d_maxbits, cudaStream_t s, const int *h_nfields)
 {
     (void)h_ts_base;
     for (int n = 0; n < n_inst; n++) {
         long long blocks = (h_elems[n] + 256 * 8 - 1) / (256 * 8);
         if (blocks > 256) blocks = 256;
         if (blocks < 1) blocks = 1;
-        dim3 g((unsigned)blocks, (unsigned)h_T[n]);
+        dim3 g((unsigned)blocks, (unsigned)h_T[n], (unsigned)(h_nfields ? h_nfields[n] : 1));
         scale_max_kernel<<<g, 256, 0, s>>>(d_inst, n, 0, d_maxbits);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -150,22 +167,24 @@ cudaError_t launch_scale_max(const InstDev *d_inst, int n_inst, const int *h_ts_
 }
 
 cudaError_t launch_scale_max_range(const InstDev *d_inst, int inst, int t0, int nt, long long elems_per_ts,
-                                   unsigned *d_maxbits, cudaStream_t s)
+                                   unsigned *d_maxbits, cudaStream_t s, int n_fields)
 {
     long long blocks = (elems_per_ts + 256 * 8 - 1) / (256 * 8);
     if (blocks > 256) blocks = 256;
     if (blocks < 1) blocks = 1;
-    dim3 g((unsigned)blocks, (unsigned)nt);
+    dim3 g((unsigned)blocks, (unsigned)nt, (unsigned)n_fields);
     scale_max_kernel<<<g, 256, 0, s>>>(d_inst, inst, t0, d_maxbits);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- site blocks
-// Scaled, site-blocked copy of phi for the tensor-core path:
-// phi_blk[t][b][n][e] = 2^s_t phi[t][n][8b + e/3][e%3] for e < 24 (zero past V),
-// e = 24, 25 padding.  Memory bound: one read of phi, one write of the copy.
-// Block (b, t) writes the N slots of site block b (contiguous) and reads the
-// 24 complex entries of each vector for those sites (contiguous too).
+// Scaled, site-blocked copy of a row field for the tensor-core path:
+// blk[t][b][n][e] = 2^s_t f[t][n][8b + e/3][e%3] for e < 24 (zero past V),
+// e = 24, 25 padding, with (f, blk) = (phi_u, phi_blk) for blockIdx.z = 0 and
+// (phi_v, blk_v) for blockIdx.z = 1 (triplets).  Memory bound: one read of
+// the field, one write of the copy.  Block (b, t) writes the N slots of site
+// block b (contiguous) and reads the 24 complex entries of each vector for
+// those sites (contiguous too).
 __global__ void __launch_bounds__(256) blockify_kernel(const InstDev *__restrict__ d_inst, int inst, int t0,
                                                        const unsigned *__restrict__ maxbits)
 {
@@ -173,8 +192,8 @@ __global__ void __launch_bounds__(256) blockify_kernel(const InstDev *__restrict
     const int b = blockIdx.x, t = t0 + blockIdx.y, N = I.N;
     const long long V = I.V;
     const float sc = __int_as_float((127 + scale_exp(maxbits[I.ts_base + t])) << 23);
-    const float2 *src = I.phi + (long long)t * N * V * 3 + (long long)TC_BS * b * 3;
-    float2 *dst = I.phi_blk + ((long long)t * I.nblk + b) * N * TC_SLOT;
+    const float2 *src = (blockIdx.z ? I.phi_v : I.phi_u) + (long long)t * N * V * 3 + (long long)TC_BS * b * 3;
+    float2 *dst = (blockIdx.z ? I.blk_v : I.phi_blk) + ((long long)t * I.nblk + b) * N * TC_SLOT;
     const int nvalid = (int)(V - (long long)TC_BS * b < TC_BS ? V - (long long)TC_BS * b : TC_BS) * 3;
     for (int idx = threadIdx.x; idx < N * TC_SLOT; idx += blockDim.x) {
         const int n = idx / TC_SLOT, e = idx - n * TC_SLOT;
@@ -197,7 +216,7 @@ cudaError_t launch_blockify_range(const InstDev *d_inst, int inst, const InstDev
 {
     for (int tb = 0; tb < nt; tb += 65535) {
         const int n = nt - tb < 65535 ? nt - tb : 65535;
-        dim3 g((unsigned)h.nblk, (unsigned)n);
+        dim3 g((unsigned)h.nblk, (unsigned)n, h.kind == INST_TRIPLETS ? 2u : 1u);
         blockify_kernel<<<g, 256, 0, s>>>(d_inst, inst, t0 + tb, d_maxbits);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -481,9 +481,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
             const TileDev td = kp.tiles[tile];
             const InstDev &I = kp.insts[td.inst];
             const int nst = I.nblk;
-            const uint32_t bytesA = td.nv * SLOT_BYTES;
+            // row vectors: [v_lo, v_lo + nv) of phi_u, then (triplets) [w_lo, w_lo + nw) of phi_v
+            const uint32_t bytesA = td.nv * SLOT_BYTES, bytesW = td.nw * SLOT_BYTES;
             const uint8_t *bsrc = kp.psi + td.psi_off;
             const float2 *asrc = I.phi_blk + ((long long)td.t * nst * I.N + td.v_lo) * TC_SLOT;
+            const float2 *wsrc = I.blk_v + ((long long)td.t * nst * I.N + td.w_lo) * TC_SLOT;
             const long long astep = (long long)I.N * TC_SLOT;
             for (int st = 0; st < nst; st++) {
                 if (!warp_wait(c, &S->empty[rs.slot], rs.phase ^ 1u)) {
@@ -492,9 +494,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
                 }
                 if (lane == 0) {
                     uint8_t *buf = smem + rs.slot * kp.stage_bytes;
-                    mbar_arrive_expect_tx(&S->full[rs.slot], BIMG_BYTES + bytesA);
+                    mbar_arrive_expect_tx(&S->full[rs.slot], BIMG_BYTES + bytesA + bytesW);
                     bulk_g2s(buf, bsrc + (long long)st * BIMG_BYTES, BIMG_BYTES, &S->full[rs.slot]);
                     bulk_g2s(buf + BIMG_BYTES, asrc + st * astep, bytesA, &S->full[rs.slot]);
+                    if (bytesW) bulk_g2s(buf + BIMG_BYTES + bytesA, wsrc + st * astep, bytesW, &S->full[rs.slot]);
                 }
                 __syncwarp();
                 rs.next(NS);
@@ -522,16 +525,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
             const int nst = I.nblk;
             const int gr = td.row0 + r;
             int kind = 0, vi = 0, vj = 0;
+            const bool trip = I.kind == INST_TRIPLETS;
             if (gr < I.rows) {
                 if (gr < I.mes_rows) {
                     kind = 1;
                     vi = gr;
                 } else {
                     kind = 2;
-                    pair_of(gr - I.mes_rows, vi, vj);
+                    const int q = gr - I.mes_rows;
+                    if (trip) {
+                        vi = q / I.N;
+                        vj = q - vi * I.N;
+                    } else {
+                        pair_of(q, vi, vj);
+                    }
                 }
             }
-            const int si = kind ? vi - td.v_lo : 0, sj = kind == 2 ? vj - td.v_lo : 0;
+            // staged slots: phi_u vector vi, and phi_v vector vj (the same staged
+            // vectors unless triplets, whose phi_v slots follow the nv phi_u slots)
+            const int si = kind ? vi - td.v_lo : 0;
+            const int sj = kind == 2 ? (trip ? td.nv + vj - td.w_lo : vj - td.v_lo) : 0;
             const int off_u = BIMG_BYTES + si * SLOT_BYTES + half * HALF_BYTES;
             const int off_v = BIMG_BYTES + sj * SLOT_BYTES + half * HALF_BYTES;
             // this group's stages: global index Gs = G + st with parity grp
@@ -598,12 +611,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
             const int gr = td.row0 + r;
             const bool rvalid = gr < I.rows;
             const bool meson = gr < I.mes_rows;
-            int pj = 0;
+            const bool trip = I.kind == INST_TRIPLETS;
+            int pi_ = 0, pj = 0;
             long long q = 0;
             if (rvalid && !meson) {
-                int pi_;
                 q = gr - I.mes_rows;
-                pair_of(q, pi_, pj);
+                if (trip) {
+                    pi_ = (int)(q / I.N);
+                    pj = (int)(q - (long long)pi_ * I.N);
+                } else {
+                    pair_of(q, pi_, pj);
+                }
             }
             const int s = scale_exp(kp.maxbits[I.ts_base + td.t]);
             const double fac = meson ? pow2d(-2 * s) : pow2d(-3 * s);
@@ -657,6 +675,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
                     double2 *dst;
                     if (meson) {
                         dst = outM + ((tP + p) * N + gr) * N + k;
+                    } else if (trip) {
+                        dst = outB + (((tP + p) * N + pi_) * N + pj) * N + k;   // dense [t][p][i][j][k]
                     } else {
                         if (k <= pj) continue;
                         dst = outB + (tP + p) * n_trip + binom3(k) + q;

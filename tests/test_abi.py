@@ -24,7 +24,8 @@ def declared_functions():
 
 def test_header_declares_the_boundary():
     names = declared_functions()
-    for must in ["laph_baryon_blocks", "laph_meson_blocks", "laph_plan_create", "laph_plan_execute",
+    for must in ["laph_baryon_blocks", "laph_meson_blocks", "laph_triplet_blocks", "laph_doublet_blocks",
+                 "laph_plan_execute_fields", "laph_plan_create", "laph_plan_execute",
                  "laph_plan_workspace_size", "laph_plan_destroy", "laph_phase_table", "laph_diquarks",
                  "laph_baryon_dense", "laph_get_device_status", "laph_triple_index", "laph_status_string"]:
         assert must in names
@@ -77,6 +78,11 @@ def test_plan_create_rejects_bad_arguments_before_touching_cuda(lib):
     arr = (binding.laph_instance * 1)(binding.laph_instance(4, 1, 8, 1, big))
     assert lib.laph_plan_create(arr, 1, 0, 0, ctypes.byref(h)) == binding.LAPH_ERR_ARG          # |n| too large
     assert lib.laph_plan_create(None, 1, 0, 0, ctypes.byref(h)) == binding.LAPH_ERR_ARG
+    # several fields: needs exactly one of the skip flags, and a tensor-core mode
+    arr = (binding.laph_instance * 1)(binding.laph_instance(4, 1, 2, 1, mom))
+    assert lib.laph_plan_create(arr, 1, 1, binding.PLAN_FIELDS, ctypes.byref(h)) == binding.LAPH_ERR_ARG
+    assert lib.laph_plan_create(arr, 1, 0, binding.PLAN_FIELDS | binding.PLAN_SKIP_M,
+                                ctypes.byref(h)) == binding.LAPH_ERR_UNSUPPORTED                 # FP32 SIMT
 
 
 def test_entry_points_reject_null_pointers(lib):
@@ -88,6 +94,9 @@ def test_entry_points_reject_null_pointers(lib):
     assert lib.laph_baryon_dense(None, 1, 8, 1, None, None) == binding.LAPH_ERR_ARG
     assert lib.laph_phase_table(0, mom, 1, None, None) == binding.LAPH_ERR_ARG
     assert lib.laph_plan_destroy(None) == binding.LAPH_ERR_ARG
+    assert lib.laph_triplet_blocks(None, None, None, 4, 1, 8, mom, 1, None, 1, None) == binding.LAPH_ERR_ARG
+    assert lib.laph_doublet_blocks(None, None, 4, 1, 8, mom, 1, None, 1, None) == binding.LAPH_ERR_ARG
+    assert lib.laph_plan_execute_fields(None, None, None, None, None) == binding.LAPH_ERR_ARG
 
 
 def test_product_path_does_not_reference_the_oracle():
