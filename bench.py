@@ -197,6 +197,101 @@ def run_reference(args):
     return 0
 
 
+def triplet_flops_per_timeslice(L, N, P):
+    """Algorithmic flops of the dense three-field triplets: 3V complex MACs per output entry."""
+    return 8.0 * 3 * L ** 3 * N ** 3 * P
+
+
+def measure_triplets(laph, L, T, N, mom, mode, steps, warmup, n_sample=0, timed_oracle=False):
+    """Three-field triplets B3 (dense) through a LAPH_PLAN_FIELDS plan: device time per step, contraction
+    kernel time, and (n_sample > 0) the relative error of sampled (i, j, k) of timeslice 0 against the
+    oracle, with the oracle's own rate when timed_oracle."""
+    import torch
+    P = mom.shape[0]
+    V = L ** 3
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(synth.SEED_BASE + 7)
+    fields = []
+    for _ in range(3):
+        z = torch.randn((T, N, V, 3, 2), generator=gen, device="cuda", dtype=torch.float32)
+        fields.append(torch.view_as_complex(z).contiguous() / math.sqrt(3 * V))
+    plan = laph.Plan([(L, T, N, mom)], mode=mode, flags=laph.PLAN_FIELDS | laph.PLAN_SKIP_M | laph.PLAN_TIMING)
+    Bs, _ = plan.alloc_outputs()
+    ws = plan.alloc_workspace()
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        plan.execute_fields([fields], Bs, ws, stream=stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        plan.execute_fields([fields], Bs, ws, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    status = plan.device_status()
+    ms = e0.elapsed_time(e1) / steps
+    n_con = plan.contraction_launches()
+    k_ms = sum(plan.kernel_times(steps * n_con)) / steps
+    o_ms = sum(plan.operand_times(steps * n_con)) / steps
+    flops = T * triplet_flops_per_timeslice(L, N, P)
+    out = {"ms_per_step": ms, "kernel_ms": k_ms, "operand_ms": o_ms, "flops_per_step": flops,
+           "value": flops / (ms / 1e3) / 1e12, "kernel_tflops": flops / (k_ms / 1e3) / 1e12,
+           "launches": plan.launches_per_execute() * steps, "device_status": status}
+    if n_sample:
+        from oracle import oracle as O
+        rng = np.random.default_rng(5)
+        ijk = rng.integers(0, N, size=(n_sample, 3))
+        f0 = [f[0].cpu().numpy() for f in fields]
+        t0 = time.perf_counter()
+        ref = O.triplet_triples(f0[0], f0[1], f0[2], L, mom, ijk)
+        dt = time.perf_counter() - t0
+        got = Bs[0][0][:, ijk[:, 0], ijk[:, 1], ijk[:, 2]].cpu().numpy().T
+        out["rel_err"] = {"B3": rel_frob(got, ref), "sample": f"{n_sample} random (i,j,k) x {P} momenta, timeslice 0"}
+        if timed_oracle:
+            out["cpu_baseline"] = {"value": 8.0 * 3 * V * n_sample * P / dt / 1e12, "unit": "TFLOP/s",
+                                   "cores": O.num_threads(), "kind": "oracle",
+                                   "sample": f"{n_sample} random (i,j,k) triples x {P} momenta of timeslice 0 "
+                                             f"({dt:.1f} s)"}
+    plan.close()
+    del Bs, ws, fields
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_triplets(args):
+    """--workload triplets: three-field triplets (the next row of the hot path: stochastic-LapH quark
+    sinks, no antisymmetry) at L=32, T=8, N=64, P=19."""
+    import torch
+    from paper_2510_26313_gb300 import binding as laph
+    torch.cuda.set_device(0)
+    L, T, N = 32, 8, 64
+    mom = synth.momentum_shell(2)
+    clocks = ClockSampler(0)
+    clocks.start()
+    r = measure_triplets(laph, L, T, N, mom, args.mode, args.steps, args.warmup,
+                         n_sample=0 if args.no_cpu_baseline else 150000, timed_oracle=not args.no_cpu_baseline)
+    clk = clocks.stop()
+    peaks, _ = measured_peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    line = {
+        "metric": "three-field triplet complex TFLOP/s at L=32,N=64,Np=19 (dense N^3)", "value": r["value"],
+        "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": f"{args.mode}->f32/f64",
+        "data": "synthetic (seeded complex Gaussian fields phi, psi, chi)",
+        "config": {"workload": f"L={L},T={T},N={N},P={mom.shape[0]} (triplets)", "L": L, "T": T, "N": N,
+                   "P": int(mom.shape[0]), "mode": args.mode},
+        "roofline": {"bound": "tensor", "achieved": r["kernel_tflops"], "peak": peak, "unit": "TFLOP/s",
+                     "frac": r["kernel_tflops"] / peak, "traffic": None,
+                     "note": "achieved counts algorithmic flops; the 3-term split executes 3x that"},
+        "cpu_baseline": r.get("cpu_baseline"), "e2e": None, "gpu_launches": r["launches"], "clocks": clk,
+        "rel_err": r.get("rel_err"), "kernel_ms": r["kernel_ms"], "operand_ms": r["operand_ms"],
+        "device_status": r["device_status"],
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ragged(args):
     """--workload ragged: 200 ragged instances (L in {16,24,32}, N in [24,96], P in {1,7,19,33},
     T in 1..8) in one plan; the same instances as 200 separate plans for comparison."""
@@ -281,7 +376,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="f16x3")
-    ap.add_argument("--workload", default="metric", choices=sorted(WORKLOADS) + ["ragged"])
+    ap.add_argument("--workload", default="metric", choices=sorted(WORKLOADS) + ["ragged", "triplets"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -292,6 +387,8 @@ def main():
         return run_reference(args)
     if args.workload == "ragged":
         return run_ragged(args)
+    if args.workload == "triplets":
+        return run_triplets(args)
 
     import torch
     import torch.distributed as dist
@@ -411,6 +508,13 @@ def main():
                                   "frac": df_bytes / (df_ms / 1e3) / 1e9 / hbm},
         }
         del D, dense
+        # the next row of the path: three-field triplets at the workload's shape, 4 timeslices
+        if args.mode in ("f16x3", "bf16x3"):
+            tr = measure_triplets(laph, L, min(4, T), N, mom, args.mode, 2, 1,
+                                  n_sample=0 if args.no_cpu_baseline else 24)
+            aux["triplets"] = {"timeslices": min(4, T), "ms": tr["ms_per_step"], "kernel_ms": tr["kernel_ms"],
+                               "value": tr["value"], "kernel_tflops": tr["kernel_tflops"], "unit": "TFLOP/s",
+                               "rel_err": tr.get("rel_err"), "device_status": tr["device_status"]}
 
     # ---- accuracy and CPU baseline on timeslice 0 (rank 0 only)
     rel = None
