@@ -418,8 +418,16 @@ int oracle_triplet_blocks(const double *f1, const double *f2, const double *f3, 
     return rc;
 }
 
-/* Two-field doublets: out[P][N][N] complex, M2[p][i][j] = sum_x ph_p(x) sum_a conj(f1_i^a) f2_j^a. */
-int oracle_doublet_blocks(const double *f1, const double *f2, int L, int N, const int32_t *mom, int P, double *out)
+/*
+ * Projection of one set of colour vectors onto another (paper, section
+ * "Innovations", subsection "Eigenvector Projection": inner products of the
+ * solution vectors with the LapH eigenvectors), with a momentum phase:
+ * out[P][N1][N2] complex, out[p][i][j] = sum_x ph_p(x) sum_a conj(f1_i^a(x)) f2_j^a(x),
+ * f1 [N1][V][3], f2 [N2][V][3].  With the single momentum n = 0 this is the
+ * plain inner product <f1_i, f2_j>.
+ */
+int oracle_projection(const double *f1, const double *f2, int L, int N1, int N2, const int32_t *mom, int P,
+                      double *out)
 {
     int64_t V = (int64_t)L * L * L;
     cplx *phT = phase_site_major(L, mom, P);
@@ -433,9 +441,9 @@ int oracle_doublet_blocks(const double *f1, const double *f2, int L, int N, cons
             failed = 1;
         }
 #pragma omp for schedule(dynamic, 1)
-        for (int64_t ij = 0; ij < (int64_t)N * N; ij++) {
+        for (int64_t ij = 0; ij < (int64_t)N1 * N2; ij++) {
             if (!acc) continue;
-            int i = (int)(ij / N), j = (int)(ij % N);
+            int i = (int)(ij / N2), j = (int)(ij % N2);
             for (int p = 0; p < P; p++) acc[p].re = acc[p].im = 0.0;
             for (int64_t x = 0; x < V; x++) {
                 cplx s = {0.0, 0.0};
@@ -452,7 +460,7 @@ int oracle_doublet_blocks(const double *f1, const double *f2, int L, int N, cons
                 }
             }
             for (int p = 0; p < P; p++) {
-                int64_t o = 2 * ((p * (int64_t)N + i) * N + j);   /* [p][i][j] */
+                int64_t o = 2 * ((p * (int64_t)N1 + i) * N2 + j);   /* [p][i][j] */
                 out[o] = acc[p].re;
                 out[o + 1] = acc[p].im;
             }
@@ -461,4 +469,11 @@ int oracle_doublet_blocks(const double *f1, const double *f2, int L, int N, cons
     }
     free(phT);
     return failed ? -1 : 0;
+}
+
+/* Two-field doublets: out[P][N][N] complex, M2[p][i][j] = sum_x ph_p(x) sum_a conj(f1_i^a) f2_j^a
+ * (the projection of N vectors onto N vectors). */
+int oracle_doublet_blocks(const double *f1, const double *f2, int L, int N, const int32_t *mom, int P, double *out)
+{
+    return oracle_projection(f1, f2, L, N, N, mom, P, out);
 }

@@ -12,8 +12,9 @@ from the LapH eigenvectors):
     B[p][i,j,k] = sum_x exp(-2 pi i ((n_p.x) mod L)/L) eps_abc phi_i^a phi_j^b phi_k^c
     M[p][i][j]  = sum_x exp(-2 pi i ((n_p.x) mod L)/L) conj(phi_i^a) phi_j^a
 
-and the same contractions of three (two) different sets of vectors, e.g.
-stochastic-LapH quark sinks (same passage):
+the same contractions of three (two) different sets of vectors, e.g.
+stochastic-LapH quark sinks (same passage), and the projection of one set of
+vectors onto another (subsection "Eigenvector Projection"):
 
     B3[p][i][j][k] = sum_x ph_p(x) eps_abc phi_i^a psi_j^b chi_k^c   (dense)
     M2[p][i][j]    = sum_x ph_p(x) conj(phi_i^a) psi_j^a
@@ -80,6 +81,8 @@ def _load():
             lib.oracle_triplet_blocks.restype = ctypes.c_int
             lib.oracle_doublet_blocks.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ip, ctypes.c_int, dp]
             lib.oracle_doublet_blocks.restype = ctypes.c_int
+            lib.oracle_projection.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ctypes.c_int, dp]
+            lib.oracle_projection.restype = ctypes.c_int
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -214,4 +217,17 @@ def doublet_blocks(phi: np.ndarray, psi: np.ndarray, L: int, momenta) -> np.ndar
     rc = _load().oracle_doublet_blocks(_dptr(phi), _dptr(psi), L, N, _iptr(mom), mom.shape[0], _dptr(out))
     if rc != 0:
         raise RuntimeError("oracle_doublet_blocks failed")
+    return out
+
+
+def projection(v: np.ndarray, s: np.ndarray, L: int, momenta=((0, 0, 0),)) -> np.ndarray:
+    """Projection of the vectors s onto the vectors v, complex128 [P][Nv][Ns]:
+    [p][i][j] = sum_x ph_p(x) sum_a conj(v_i^a) s_j^a (n = 0: the inner products <v_i, s_j>)."""
+    v, mom = _prep(v, L, momenta)
+    s, _ = _prep(s, L, momenta)
+    Nv, Ns = v.shape[0], s.shape[0]
+    out = np.zeros((mom.shape[0], Nv, Ns), dtype=np.complex128)
+    rc = _load().oracle_projection(_dptr(v), _dptr(s), L, Nv, Ns, _iptr(mom), mom.shape[0], _dptr(out))
+    if rc != 0:
+        raise RuntimeError("oracle_projection failed")
     return out

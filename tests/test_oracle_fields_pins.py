@@ -1,7 +1,9 @@
-"""Pins for the oracle's three-field triplets and two-field doublets.
+"""Pins for the oracle's three-field triplets, two-field doublets and projection.
 
     B3[p][i][j][k] = sum_x ph_p(x) eps_abc phi_i^a(x) psi_j^b(x) chi_k^c(x)   (dense, no symmetry)
     M2[p][i][j]    = sum_x ph_p(x) sum_a conj(phi_i^a(x)) psi_j^a(x)
+    Pr[p][i][j]    = the same with Nv vectors v and Ns vectors s (subsection
+                     "Eigenvector Projection": at n = 0 the inner products <v_i, s_j>)
 
 The same contractions as the LapH baryon/meson blocks, of different sets of
 colour vectors (e.g. stochastic-LapH quark sinks; paper, section
@@ -169,3 +171,34 @@ def test_triples_form_matches_dense_form():
     got = O.triplet_triples(phi, psi, chi, L, MOMS, ijk)
     for n, (i, j, k) in enumerate(ijk):
         np.testing.assert_allclose(got[n], B[:, i, j, k], rtol=0, atol=0)
+
+
+# ----------------------------------------------------------------- projection
+
+@pytest.mark.parametrize("L,Nv,Ns", [(2, 3, 7), (3, 6, 2)])
+def test_projection_matches_numpy_einsum(L, Nv, Ns):
+    rng = np.random.default_rng(110 + L)
+    V = L ** 3
+    v = rng.standard_normal((Nv, V, 3)) + 1j * rng.standard_normal((Nv, V, 3))
+    s = rng.standard_normal((Ns, V, 3)) + 1j * rng.standard_normal((Ns, V, 3))
+    ph = np_phase(L, MOMS)
+    got = O.projection(v, s, L, MOMS)
+    np.testing.assert_allclose(got, np.einsum("px,ixa,jxa->pij", ph, v.conj(), s), rtol=1e-12, atol=1e-12)
+    # the plain inner products at n = 0
+    np.testing.assert_allclose(O.projection(v, s, L)[0], np.einsum("ixa,jxa->ij", v.conj(), s), rtol=1e-12,
+                               atol=1e-12)
+
+
+def test_projection_recovers_the_coefficients_of_an_orthonormal_expansion():
+    """s_j = sum_i C_ij v_i with orthonormal v  =>  <v_i, s_j> = C_ij (closed form)."""
+    L, Nv, Ns = 4, 10, 6
+    v = synth.random_phi(L, Nv, T=1, instance=3)[0].astype(np.complex128)
+    rng = np.random.default_rng(7)
+    C = rng.standard_normal((Nv, Ns)) + 1j * rng.standard_normal((Nv, Ns))
+    s = np.einsum("ij,ixa->jxa", C, v)
+    got = O.projection(v, s, L)[0]
+    np.testing.assert_allclose(got, C, atol=1e-5 * np.abs(C).max())   # v is orthonormal to the complex64 cast
+    # and a vector orthogonal to every v_i projects to zero
+    w = rng.standard_normal((1, L ** 3, 3)) + 1j * rng.standard_normal((1, L ** 3, 3))
+    w -= np.einsum("i,ixa->xa", np.einsum("ixa,xa->i", v.conj(), w[0]), v)[None]
+    assert np.abs(O.projection(v, w, L)).max() < 1e-5 * np.linalg.norm(w)

@@ -34,8 +34,9 @@ MUTATIONS = {
     "fields_colour_swap": ("phi_at(f3, V, k, x, EPS_PERM[q][2]));", "phi_at(f3, V, k, x, EPS_PERM[q][1]));"),
     "doublet_conj_second": ("cmul(cconj(phi_at(f1, V, i, x, a)), phi_at(f2, V, j, x, a))",
                             "cmul(phi_at(f1, V, i, x, a), cconj(phi_at(f2, V, j, x, a)))"),
-    "doublet_transpose": ("int64_t o = 2 * ((p * (int64_t)N + i) * N + j);",
-                          "int64_t o = 2 * ((p * (int64_t)N + j) * N + i);"),
+    "doublet_transpose": ("int64_t o = 2 * ((p * (int64_t)N1 + i) * N2 + j);",
+                          "int64_t o = 2 * ((p * (int64_t)N1 + j) * N2 + i);"),
+    "projection_counts": ("int i = (int)(ij / N2), j = (int)(ij % N2);", "int i = (int)(ij / N1), j = (int)(ij % N1);"),
     "triplet_dense_index": ("ijk[3 * e + 2] = (int32_t)(e % N);", "ijk[3 * e + 2] = (int32_t)((e / N) % N);"),
 }
 
