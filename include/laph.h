@@ -112,6 +112,9 @@ typedef struct {
     int N;                  /* colour vectors per timeslice */
     int n_mom;              /* number of momenta P */
     const int32_t *momenta; /* host [n_mom][3]; copied at plan creation */
+    int n_col;              /* doublet plans (LAPH_PLAN_FIELDS | LAPH_PLAN_SKIP_B): vectors of the second
+                               field psi, which may differ from N (projections); 0 means N.  Must be 0 (or N)
+                               for every other plan. */
 } laph_instance;
 
 typedef struct laph_plan laph_plan;
@@ -177,6 +180,18 @@ LAPH_API int laph_triplet_blocks(const void *phi, const void *psi, const void *c
  * out = M2, device complex128 [T][P][N][N]. */
 LAPH_API int laph_doublet_blocks(const void *phi, const void *psi, int L, int T, int N, const int32_t *momenta,
                                  int n_mom, void *out, int mode, void *stream);
+
+/* Projection of Ns vectors s onto Nv vectors v (paper, section "Innovations",
+ * subsection "Eigenvector Projection": inner products of solution vectors
+ * with the LapH eigenvectors), with momentum phases:
+ *   out[t][p][i][j] = sum_x ph_p(x) sum_a conj(v_i^a(x)) s_j^a(x),
+ * the inner products <v_i, s_j> for the single momentum n = 0.
+ * v: device complex64 [T][Nv][L^3][3]; s: device complex64 [T][Ns][L^3][3];
+ * out: device complex128 [T][P][Nv][Ns].  A doublet plan with n_col = Ns;
+ * same behaviour as laph_baryon_blocks.  LAPH_ERR_ARG for Nv < 1, Ns < 1,
+ * Nv > 3 L^3 and the conditions of laph_plan_create. */
+LAPH_API int laph_projection(const void *v, const void *s, int L, int T, int Nv, int Ns, const int32_t *momenta,
+                             int n_mom, void *out, int mode, void *stream);
 
 /* ---- plan API (ragged batches, capture-safe execution) ----------------- */
 /* Validates the instances (L >= 1; N >= 3 unless LAPH_PLAN_SKIP_B, N >= 1;

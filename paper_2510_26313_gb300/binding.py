@@ -44,7 +44,7 @@ class LaphError(RuntimeError):
 
 class laph_instance(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("T", ctypes.c_int), ("N", ctypes.c_int), ("n_mom", ctypes.c_int),
-                ("momenta", ctypes.POINTER(ctypes.c_int32))]
+                ("momenta", ctypes.POINTER(ctypes.c_int32)), ("n_col", ctypes.c_int)]
 
 
 def lib() -> ctypes.CDLL:
@@ -70,6 +70,7 @@ def lib() -> ctypes.CDLL:
             "laph_triplet_blocks": (i32, [vp, vp, vp, i32, i32, i32, ip32, i32, vp, i32, vp]),
             "laph_doublet_blocks": (i32, [vp, vp, i32, i32, i32, ip32, i32, vp, i32, vp]),
             "laph_plan_execute_fields": (i32, [vp, vpp, vpp, vp, vp]),
+            "laph_projection": (i32, [vp, vp, i32, i32, i32, i32, ip32, i32, vp, i32, vp]),
             "laph_plan_create": (i32, [ctypes.POINTER(laph_instance), i32, i32, ctypes.c_uint, ctypes.POINTER(vp)]),
             "laph_plan_workspace_size": (i32, [vp, ctypes.POINTER(sz)]),
             "laph_plan_execute": (i32, [vp, vpp, vpp, vpp, vp, vp]),
@@ -191,12 +192,12 @@ def meson_blocks(phi, L: int, momenta, mode="f16x3", out=None, stream=None):
     return out
 
 
-def _check_fields(fields, L):
+def _check_fields(fields, L, same_n=True):
     T, N = _check_phi(fields[0], L)
     for f in fields[1:]:
-        if tuple(f.shape) != tuple(fields[0].shape) or f.device != fields[0].device:
+        Tf, Nf = _check_phi(f, L)
+        if Tf != T or f.device != fields[0].device or (same_n and Nf != N):
             raise ValueError("the fields must have the same shape and device")
-        _check_phi(f, L)
     return T, N
 
 
@@ -227,6 +228,23 @@ def doublet_blocks(phi, psi, L: int, momenta, mode="f16x3", out=None, stream=Non
     return out
 
 
+def projection(v, s, L: int, momenta=((0, 0, 0),), mode="f16x3", out=None, stream=None):
+    """Projection of the vectors s onto the vectors v, complex128 [T][P][Nv][Ns]:
+    sum_x ph_p(x) conj(v_i) . s_j (the inner products <v_i, s_j> at n = 0); one-shot, blocking."""
+    import torch
+    T, Nv = _check_phi(v, L)
+    Ts, Ns = _check_phi(s, L)
+    if Ts != T or s.device != v.device:
+        raise ValueError("v and s must have the same timeslices and device")
+    mom = _momenta(momenta)
+    if out is None:
+        out = torch.empty((T, mom.shape[0], Nv, Ns), dtype=torch.complex128, device=v.device)
+    rc = lib().laph_projection(_ptr(v), _ptr(s), L, T, Nv, Ns, mom.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                               mom.shape[0], _ptr(out), _mode(mode), _stream(stream))
+    _check(rc, "laph_projection")
+    return out
+
+
 def blocks_noalloc(phi, L: int, momenta, out_B, out_M, stream=None):
     """FP32 B and/or M into caller-owned outputs with no device allocation.
 
@@ -251,12 +269,16 @@ class Plan:
     """
 
     def __init__(self, instances, mode="f16x3", flags: int = 0, chunk_sites: int = 0):
-        self._moms = [_momenta(m) for (_, _, _, m) in instances]
+        # (L, T, N, momenta) or, for doublet plans of two vector counts, (L, T, N, momenta, n_col)
+        self._moms = [_momenta(inst[3]) for inst in instances]
+        self.n_col = [int(inst[4]) if len(inst) > 4 else 0 for inst in instances]
         arr = (laph_instance * len(instances))()
-        for n, (L, T, N, _) in enumerate(instances):
+        for n, inst in enumerate(instances):
+            L, T, N = inst[0], inst[1], inst[2]
             m = self._moms[n]
-            arr[n] = laph_instance(L, T, N, m.shape[0], m.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
-        self.instances = [(int(L), int(T), int(N), self._moms[n]) for n, (L, T, N, _) in enumerate(instances)]
+            arr[n] = laph_instance(L, T, N, m.shape[0], m.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   self.n_col[n])
+        self.instances = [(int(inst[0]), int(inst[1]), int(inst[2]), self._moms[n]) for n, inst in enumerate(instances)]
         self.flags = flags
         self.mode = _mode(mode)
         h = ctypes.c_void_p()
@@ -335,8 +357,9 @@ class Plan:
             shapeB = (T, P, N, N, N) if self.flags & PLAN_FIELDS else (T, P, N * (N - 1) * (N - 2) // 6)
             Bs.append(None if self.flags & PLAN_SKIP_B else
                       torch.empty(shapeB, dtype=torch.complex128, device=device or "cuda"))
+            Nc = self.n_col[len(Ms)] or N
             Ms.append(None if self.flags & PLAN_SKIP_M else
-                      torch.empty((T, P, N, N), dtype=torch.complex128, device=device or "cuda"))
+                      torch.empty((T, P, N, Nc), dtype=torch.complex128, device=device or "cuda"))
         return Bs, Ms
 
     @staticmethod
@@ -360,7 +383,7 @@ class Plan:
         doublets; outs[n] the instance's B3 or M2."""
         flat = []
         for (L, T, N, _), fs in zip(self.instances, fields):
-            _check_fields(tuple(fs), L)
+            _check_fields(tuple(fs), L, same_n=not (self.flags & PLAN_SKIP_B))
             flat.extend(fs)
         fa = self._ptr_array(flat)
         oa = self._ptr_array(outs)

@@ -212,6 +212,9 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
             !I.momenta)
             return LAPH_ERR_ARG;
         if (!skipB && !fields && I.N < 3) return LAPH_ERR_ARG;
+        // a second vector count only for doublets
+        if (I.n_col < 0 || I.n_col > MAX_N || (I.n_col && I.n_col != I.N && kind != laph::INST_DOUBLETS))
+            return LAPH_ERR_ARG;
         if ((long long)I.N > 3LL * I.L * I.L * I.L) return LAPH_ERR_ARG;
         for (int q = 0; q < 3 * I.n_mom; q++)
             if (I.momenta[q] > MAX_MOM || I.momenta[q] < -MAX_MOM) return LAPH_ERR_ARG;
@@ -254,7 +257,8 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
         d.mes_rows = skipM ? 0 : I.N;
         d.pair_rows = skipB ? 0 : (kind == laph::INST_TRIPLETS ? I.N * I.N : (int)laph::binom2(I.N));
         d.rows = d.mes_rows + d.pair_rows;
-        d.cols = I.N * I.n_mom;
+        d.Nc = (kind == laph::INST_DOUBLETS && I.n_col) ? I.n_col : I.N;
+        d.cols = d.Nc * I.n_mom;
         d.n_ct = (d.cols + laph::TC_TC - 1) / laph::TC_TC;
         d.n_st = (int)((3 * d.V + laph::TC_KSTAGE - 1) / laph::TC_KSTAGE);
         d.ts_base = ts;
@@ -262,11 +266,11 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
         p->h_T.push_back(I.T);
         ts += I.T;
         p->h_inst.push_back(d);
-        p->phi_elems.push_back((long long)I.T * I.N * d.V * 3);
+        p->phi_elems.push_back((long long)I.T * std::max(I.N, d.Nc) * d.V * 3);   // the larger field
         p->outB_elems.push_back(skipB ? 0
                                       : (long long)I.T * I.n_mom *
                                             (kind == laph::INST_TRIPLETS ? (long long)I.N * I.N * I.N : d.n_trip));
-        p->outM_elems.push_back(skipM ? 0 : (long long)I.T * I.n_mom * I.N * I.N);
+        p->outM_elems.push_back(skipM ? 0 : (long long)I.T * I.n_mom * I.N * d.Nc);
         phase_off[n] = phase_total;
         phase_total += (long long)I.n_mom * d.Vs;
     }
@@ -1041,6 +1045,35 @@ static int one_shot_fields(const void *const *fields, int L, int T, int N, const
     void *o = out;
     rc = laph_plan_execute_fields(plan, fields, &o, ws, stream);
     if (ws) cudaFreeAsync(ws, s);
+    int dev = LAPH_OK;
+    int rc2 = laph_get_device_status(plan, stream, &dev);  // synchronises the stream
+    laph_plan_destroy(plan);
+    if (rc != LAPH_OK) return rc;
+    if (rc2 != LAPH_OK) return rc2;
+    return dev;
+}
+
+int laph_projection(const void *v, const void *s, int L, int T, int Nv, int Ns, const int32_t *momenta, int n_mom,
+                    void *out, int mode, void *stream)
+{
+    if (!out || Ns < 1) return LAPH_ERR_ARG;
+    laph_instance inst = {L, T, Nv, n_mom, momenta, Ns};
+    laph_plan *plan = nullptr;
+    int rc = laph_plan_create(&inst, 1, mode, LAPH_PLAN_FIELDS | LAPH_PLAN_SKIP_B, &plan);
+    if (rc != LAPH_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    void *ws = nullptr;
+    if (plan->ws_bytes) {
+        cudaError_t e = cudaMallocAsync(&ws, plan->ws_bytes, st);
+        if (e != cudaSuccess) {
+            laph_plan_destroy(plan);
+            return cuda_fail(e, "cudaMallocAsync");
+        }
+    }
+    const void *f[2] = {v, s};
+    void *o = out;
+    rc = laph_plan_execute_fields(plan, f, &o, ws, stream);
+    if (ws) cudaFreeAsync(ws, st);
     int dev = LAPH_OK;
     int rc2 = laph_get_device_status(plan, stream, &dev);  // synchronises the stream
     laph_plan_destroy(plan);

@@ -24,7 +24,8 @@ constexpr int INST_DOUBLETS = 2;
 // conj(phi_u_i)), rows [mes_rows, mes_rows + pair_rows) are diquark rows
 // (A operand phi_u_i x phi_v_j): pair q = row - mes_rows in colex order
 // q = C(j,2) + i for INST_BLOCKS, q = i * N + j for INST_TRIPLETS.  Column
-// space: col = k * P + p, B operand ph_p * phi_k (phi is the column field).
+// space: col = k * P + p, k < Nc, B operand ph_p * phi_k (phi is the column
+// field, of Nc vectors; the row fields have N).
 struct InstDev {
     const float2 *phi;       // [T][N][V][3] column field (phi; chi for triplets, psi for doublets)
     const float2 *phi_u;     // [T][N][V][3] first row field (phi)
@@ -50,7 +51,7 @@ struct InstDev {
     int n_st;                // K stages of the tensor-core path: one per site block (= nblk)
     int kind;                // INST_BLOCKS, INST_TRIPLETS or INST_DOUBLETS
     int n_fields;            // distinct input fields: 1, 3 (triplets) or 2 (doublets)
-    int pad_;
+    int Nc;                  // vectors of the column field (N, except doublets of two vector counts)
 };
 
 // Site-blocked layout of the tensor-core path.  phi_blk[t][b][n][TC_SLOT]:

@@ -155,6 +155,7 @@ extern "C" int laph_blocks_noalloc(const void *phi, int L, int T, int N, const i
     d.phi_u = d.phi_v = d.phi;
     d.blkv_off = -1;
     d.n_fields = 1;
+    d.Nc = N;
     d.outB = (double2 *)out_B;
     d.outM = (double2 *)out_M;
     d.L = L;

@@ -130,8 +130,8 @@ __global__ void scale_max_kernel(const InstDev *__restrict__ d_inst, int inst, i
 {
     const InstDev &I = d_inst[inst];
     const int t = t0 + blockIdx.y;
-    const long long n = (long long)I.N * I.V * 3;
-    // field blockIdx.z: the column field, then the row fields of a multi-field instance
+    // field blockIdx.z: the column field (Nc vectors), then the row fields (N) of a multi-field instance
+    const long long n = (long long)(blockIdx.z == 0 ? I.Nc : I.N) * I.V * 3;
     const float2 *f = blockIdx.z == 0 ? I.phi : (blockIdx.z == 1 ? I.phi_u : I.phi_v);
     const float2 *base = f + (long long)t * n;
     float m = 0.f;

@@ -674,7 +674,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
                     const int k = col / P, p = col - k * P;
                     double2 *dst;
                     if (meson) {
-                        dst = outM + ((tP + p) * N + gr) * N + k;
+                        dst = outM + ((tP + p) * N + gr) * I.Nc + k;   // [t][p][i][k], k < Nc
                     } else if (trip) {
                         dst = outB + (((tP + p) * N + pi_) * N + pj) * N + k;   // dense [t][p][i][j][k]
                     } else {
@@ -837,7 +837,7 @@ __global__ void __launch_bounds__(192) psi_kernel(const InstDev *__restrict__ in
             p = col0 + cu - k * I.P;
         }
         const float2 *ph = I.phase + (long long)p * I.Vs;
-        const float2 *phk = I.phi + ((long long)un.t * I.N + k) * V * 3;
+        const float2 *phk = I.phi + ((long long)un.t * I.Nc + k) * V * 3;
         uint8_t *img = psi + un.psi_off + ((long long)ct * n_st + st0) * BIMG_BYTES;
         const int n0 = 2 * cu, n1 = n0 + 1;
         const uint32_t o0 = sw32(n0, j), o1 = sw32(n1, j);

@@ -25,7 +25,7 @@ def declared_functions():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ["laph_baryon_blocks", "laph_meson_blocks", "laph_triplet_blocks", "laph_doublet_blocks",
-                 "laph_plan_execute_fields", "laph_plan_create", "laph_plan_execute",
+                 "laph_plan_execute_fields", "laph_projection", "laph_plan_create", "laph_plan_execute",
                  "laph_plan_workspace_size", "laph_plan_destroy", "laph_phase_table", "laph_diquarks",
                  "laph_baryon_dense", "laph_get_device_status", "laph_triple_index", "laph_status_string"]:
         assert must in names
@@ -83,6 +83,11 @@ def test_plan_create_rejects_bad_arguments_before_touching_cuda(lib):
     assert lib.laph_plan_create(arr, 1, 1, binding.PLAN_FIELDS, ctypes.byref(h)) == binding.LAPH_ERR_ARG
     assert lib.laph_plan_create(arr, 1, 0, binding.PLAN_FIELDS | binding.PLAN_SKIP_M,
                                 ctypes.byref(h)) == binding.LAPH_ERR_UNSUPPORTED                 # FP32 SIMT
+    # a second vector count only for doublet plans, and not negative
+    for flags, n_col in [(0, 9), (binding.PLAN_FIELDS | binding.PLAN_SKIP_M, 9),
+                         (binding.PLAN_FIELDS | binding.PLAN_SKIP_B, -1)]:
+        arr = (binding.laph_instance * 1)(binding.laph_instance(4, 1, 8, 1, mom, n_col))
+        assert lib.laph_plan_create(arr, 1, 1, flags, ctypes.byref(h)) == binding.LAPH_ERR_ARG
 
 
 def test_entry_points_reject_null_pointers(lib):
@@ -97,6 +102,8 @@ def test_entry_points_reject_null_pointers(lib):
     assert lib.laph_triplet_blocks(None, None, None, 4, 1, 8, mom, 1, None, 1, None) == binding.LAPH_ERR_ARG
     assert lib.laph_doublet_blocks(None, None, 4, 1, 8, mom, 1, None, 1, None) == binding.LAPH_ERR_ARG
     assert lib.laph_plan_execute_fields(None, None, None, None, None) == binding.LAPH_ERR_ARG
+    assert lib.laph_projection(None, None, 4, 1, 8, 5, mom, 1, None, 1, None) == binding.LAPH_ERR_ARG
+    assert lib.laph_projection(None, None, 4, 1, 8, 0, mom, 1, ctypes.c_void_p(16), 1, None) == binding.LAPH_ERR_ARG
 
 
 def test_product_path_does_not_reference_the_oracle():

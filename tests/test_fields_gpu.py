@@ -1,7 +1,8 @@
-"""GPU parity of the three-field triplets and two-field doublets against the FP64 oracle.
+"""GPU parity of the three-field triplets, two-field doublets and projection against the FP64 oracle.
 
     B3[t][p][i][j][k] = sum_x ph_p(x) eps_abc phi_i^a psi_j^b chi_k^c   (dense)
     M2[t][p][i][j]    = sum_x ph_p(x) conj(phi_i^a) psi_j^a
+    Pr[t][p][i][j]    = the same with Nv vectors v and Ns vectors s (inner products at n = 0)
 
 Element-by-element relative Frobenius error per output and worst per-(t, p)
 slice, bounded by 1e-5 for the split-precision tensor-core modes, at shapes
@@ -141,3 +142,41 @@ def test_triplets_at_L32_N64_P19_sampled_parity(laph):
         assert rel_frob(got, ref) <= 1e-5
     M = laph.doublet_blocks(*[torch.from_numpy(f).cuda() for f in fs[:2]], L, mom)
     assert rel_frob(M[0].cpu().numpy(), O.doublet_blocks(fs[0][0], fs[1][0], L, mom)) <= 1e-5
+
+
+# ------------------------------------------------------------ projection
+
+PROJ_CASES = [
+    # (L, T, Nv, Ns, momenta, instance)
+    (4, 2, 10, 37, np.zeros((1, 3), dtype=np.int32), 1),          # plain inner products
+    (5, 1, 130, 20, synth.momentum_shell(1), 2),                   # Nv > 128: two row tiles
+    (6, 1, 3, 200, np.zeros((1, 3), dtype=np.int32), 3),           # Ns = 200: three column tiles, ragged
+]
+
+
+@pytest.mark.parametrize("mode", SPLIT_TC)
+@pytest.mark.parametrize("case", range(len(PROJ_CASES)))
+def test_projection_matches_oracle(laph, mode, case):
+    import torch
+    L, T, Nv, Ns, mom, inst = PROJ_CASES[case]
+    v = synth.random_phi(L, Nv, T=T, instance=inst)
+    s = synth.random_phi(L, Ns, T=T, instance=50 + inst)
+    got = laph.projection(torch.from_numpy(v).cuda(), torch.from_numpy(s).cuda(), L, mom, mode=mode).cpu().numpy()
+    ref = np.stack([O.projection(v[t], s[t], L, mom) for t in range(T)])
+    e = rel_frob(got, ref)
+    print(f"mode={mode} L={L} Nv={Nv} Ns={Ns} P={len(mom)}: rel {e:.2e}")
+    assert got.shape == (T, len(mom), Nv, Ns)
+    assert e <= 1e-5
+    assert worst_slice(got, ref, 2) <= 4e-5
+
+
+def test_projection_recovers_expansion_coefficients_at_size(laph):
+    """s_j = sum_i C_ij v_i with orthonormal v (L=16, 96 vectors): <v_i, s_j> = C_ij."""
+    import torch
+    L, Nv, Ns = 16, 96, 160
+    v = synth.random_phi(L, Nv, T=1, instance=5)
+    rng = np.random.default_rng(9)
+    C = (rng.standard_normal((Nv, Ns)) + 1j * rng.standard_normal((Nv, Ns))).astype(np.complex64)
+    s = np.einsum("ij,ixa->jxa", C, v[0]).astype(np.complex64)[None]
+    got = laph.projection(torch.from_numpy(v).cuda(), torch.from_numpy(np.ascontiguousarray(s)).cuda(), L)
+    assert rel_frob(got[0, 0].cpu().numpy(), C) <= 1e-5
