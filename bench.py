@@ -292,6 +292,76 @@ def run_triplets(args):
     return 0
 
 
+def run_projection(args):
+    """--workload projection: the projection of solution vectors onto LapH eigenvectors (the inner
+    products <v_i, s_j> per timeslice, n = 0) at L=32, T=16, Nv=128 eigenvectors, Ns=512 columns."""
+    import torch
+    from paper_2510_26313_gb300 import binding as laph
+    from oracle import oracle as O
+    torch.cuda.set_device(0)
+    L, T, Nv, Ns = 32, 16, 128, 512
+    V = L ** 3
+    mom = np.zeros((1, 3), dtype=np.int32)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(synth.SEED_BASE + 11)
+    fields = []
+    for n in (Nv, Ns):
+        z = torch.randn((T, n, V, 3, 2), generator=gen, device="cuda", dtype=torch.float32)
+        fields.append(torch.view_as_complex(z).contiguous() / math.sqrt(3 * V))
+    plan = laph.Plan([(L, T, Nv, mom, Ns)], mode=args.mode,
+                     flags=laph.PLAN_FIELDS | laph.PLAN_SKIP_B | laph.PLAN_TIMING)
+    _, Ms = plan.alloc_outputs()
+    ws = plan.alloc_workspace()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        plan.execute_fields([fields], Ms, ws, stream=stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.execute_fields([fields], Ms, ws, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    n_con = plan.contraction_launches()
+    k_ms = sum(plan.kernel_times(args.steps * n_con)) / args.steps
+    o_ms = sum(plan.operand_times(args.steps * n_con)) / args.steps
+    flops = 8.0 * 3 * V * Nv * Ns * T
+    in_bytes = (Nv + Ns) * T * V * 3 * 8
+    rel = cpu = None
+    if not args.no_cpu_baseline:
+        v0, s0 = fields[0][0].cpu().numpy(), fields[1][0].cpu().numpy()
+        t0 = time.perf_counter()
+        ref = O.projection(v0, s0, L, mom)
+        dt = time.perf_counter() - t0
+        rel = {"P": rel_frob(Ms[0][0].cpu().numpy(), ref), "timeslice": 0}
+        cpu = {"value": 8.0 * 3 * V * Nv * Ns / dt / 1e12, "unit": "TFLOP/s", "cores": O.num_threads(), "kind": "oracle",
+               "sample": f"timeslice 0: all {Nv} x {Ns} inner products ({dt:.1f} s)"}
+    peaks, _ = measured_peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    line = {
+        "metric": "eigenvector projection complex TFLOP/s at L=32, Nv=128 x Ns=512 (n = 0)",
+        "value": flops / (ms / 1e3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": f"{args.mode}->f32/f64", "data": "synthetic (seeded complex Gaussian v and s)",
+        "config": {"workload": f"L={L},T={T},Nv={Nv},Ns={Ns},P=1 (projection)", "L": L, "T": T, "Nv": Nv, "Ns": Ns,
+                   "mode": args.mode},
+        "roofline": {"bound": "tensor", "achieved": flops / (k_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                     "frac": flops / (k_ms / 1e3) / 1e12 / peak, "traffic": None,
+                     "note": "achieved counts algorithmic flops; the 3-term split executes 3x that",
+                     "input_gbs": in_bytes / (ms / 1e3) / 1e9, "hbm_peak": hbm},
+        "cpu_baseline": cpu, "e2e": None, "gpu_launches": plan.launches_per_execute() * args.steps, "clocks": clk,
+        "rel_err": rel, "kernel_ms": k_ms, "operand_ms": o_ms, "device_status": plan.device_status(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ragged(args):
     """--workload ragged: 200 ragged instances (L in {16,24,32}, N in [24,96], P in {1,7,19,33},
     T in 1..8) in one plan; the same instances as 200 separate plans for comparison."""
@@ -376,7 +446,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="f16x3")
-    ap.add_argument("--workload", default="metric", choices=sorted(WORKLOADS) + ["ragged", "triplets"])
+    ap.add_argument("--workload", default="metric", choices=sorted(WORKLOADS) + ["ragged", "triplets", "projection"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -389,6 +459,8 @@ def main():
         return run_ragged(args)
     if args.workload == "triplets":
         return run_triplets(args)
+    if args.workload == "projection":
+        return run_projection(args)
 
     import torch
     import torch.distributed as dist

@@ -88,7 +88,10 @@ static_assert(A_LO + KSTAGE <= A_SLOT_COLS && SUM_COL + 192 <= A_COL && A_COL + 
               "tensor memory budget");
 
 struct Shared {
-    uint64_t full[MAX_NS], empty[MAX_NS];
+    // full: data of stage k landed, barrier k mod 2 NS (every barrier serves
+    // one A-producer group only, even when NS is odd); empty: stage k's MMAs
+    // done, barrier k mod NS (the stage buffer)
+    uint64_t full[2 * MAX_NS], empty[MAX_NS];
     uint64_t tfull[TRING], tempty[TRING];
     int tile_ring[TRING];
     uint64_t a_full[2];
@@ -435,6 +438,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; s++) {
             mbar_init(&S->full[s], 1);
+            mbar_init(&S->full[NS + s], 1);
             mbar_init(&S->empty[s], 1);
         }
         for (int s = 0; s < TRING; s++) {
@@ -463,7 +467,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
 
     if (warp == WARP_LOAD) {
         // ---------------------------------------------------------- loader
-        Ring rs{0, 0}, rt{0, 0};
+        Ring rs{0, 0}, rf{0, 0}, rt{0, 0};   // stage buffer, data barrier, tile ring
         uint32_t n_issued = 0;   // stages whose copies were issued
         bool ok = true;
         while (ok) {
@@ -494,20 +498,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
                 }
                 if (lane == 0) {
                     uint8_t *buf = smem + rs.slot * kp.stage_bytes;
-                    mbar_arrive_expect_tx(&S->full[rs.slot], BIMG_BYTES + bytesA + bytesW);
-                    bulk_g2s(buf, bsrc + (long long)st * BIMG_BYTES, BIMG_BYTES, &S->full[rs.slot]);
-                    bulk_g2s(buf + BIMG_BYTES, asrc + st * astep, bytesA, &S->full[rs.slot]);
-                    if (bytesW) bulk_g2s(buf + BIMG_BYTES + bytesA, wsrc + st * astep, bytesW, &S->full[rs.slot]);
+                    uint64_t *fb = &S->full[rf.slot];
+                    mbar_arrive_expect_tx(fb, BIMG_BYTES + bytesA + bytesW);
+                    bulk_g2s(buf, bsrc + (long long)st * BIMG_BYTES, BIMG_BYTES, fb);
+                    bulk_g2s(buf + BIMG_BYTES, asrc + st * astep, bytesA, fb);
+                    if (bytesW) bulk_g2s(buf + BIMG_BYTES + bytesA, wsrc + st * astep, bytesW, fb);
                 }
                 __syncwarp();
                 rs.next(NS);
+                rf.next(2 * NS);
                 n_issued++;
             }
         }
         // the copies of the last NS issued stages may still be in flight (after
         // an abort nobody consumed them): wait until they have landed
         for (uint32_t k = n_issued > (uint32_t)NS ? n_issued - NS : 0; k < n_issued; k++)
-            drain_wait(S, kp.status, lane, &S->full[k % NS], (k / NS) & 1u);
+            drain_wait(S, kp.status, lane, &S->full[k % (2 * NS)], (k / (2 * NS)) & 1u);
     } else if (warp < N_AWARPS) {
         // ---------------------------------------------------------- A producers
         const int quad = warp & 3, half = (warp >> 2) & 1, grp = warp >> 3;
@@ -550,8 +556,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
             // this group's stages: global index Gs = G + st with parity grp
             int st = (grp - (int)(G & 1u)) & 1;
             const uint32_t Gs = G + st;
-            int s = (int)(Gs % (uint32_t)NS);
-            uint32_t ph = (Gs / (uint32_t)NS) & 1u;  // stage ring phase
+            int s = (int)(Gs % (uint32_t)NS);        // stage buffer
+            int sf = (int)(Gs % (uint32_t)(2 * NS)); // its data barrier: used by this group only,
+            uint32_t ph = (Gs / (uint32_t)(2 * NS)) & 1u;  // one phase per use, in order
             // A slot grp is free once stage Gs - 2, its previous user, has
             // completed: the stage's commit to empty[(Gs - 2) mod NS].  Before
             // the first use the parity wait passes on the fresh barrier.
@@ -561,7 +568,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
             for (; st < nst; st += 2) {
                 // the entries are formed as soon as the stage has landed; only
                 // the stores into the A slot wait for the MMAs reading it
-                if (!warp_wait(c, &S->full[s], ph)) {
+                if (!warp_wait(c, &S->full[sf], ph)) {
                     ok = false;
                     break;
                 }
@@ -581,8 +588,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
                 if (skip) stalled = true;
                 if (lane == 0 && !skip) mbar_arrive(&S->a_full[grp]);
                 s += 2;
-                if (s >= NS) {
-                    s -= NS;
+                if (s >= NS) s -= NS;
+                sf += 2;
+                if (sf >= 2 * NS) {
+                    sf -= 2 * NS;
                     ph ^= 1u;
                 }
                 s2 += 2;
@@ -712,7 +721,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
                 const bool chunk_start = cs == 0;
                 const bool chunk_end = cs + 1 == kp.chunk_stages || st + 1 == nst;
                 // Every producer warp of the stage waited for the stage's data
-                // (full[rs.slot]) before its release-arrive on a_full, so the
+                // (its full barrier) before its release-arrive on a_full, so the
                 // acquire of a_full also orders the MMAs after the bulk copies;
                 // the MMA warp waits on one barrier per stage.
                 if (!warp_wait(c, &S->a_full[ra.slot], ra.phase)) {

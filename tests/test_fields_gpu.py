@@ -180,3 +180,29 @@ def test_projection_recovers_expansion_coefficients_at_size(laph):
     s = np.einsum("ij,ixa->jxa", C, v[0]).astype(np.complex64)[None]
     got = laph.projection(torch.from_numpy(v).cuda(), torch.from_numpy(np.ascontiguousarray(s)).cuda(), L)
     assert rel_frob(got[0, 0].cpu().numpy(), C) <= 1e-5
+
+
+def test_odd_stage_ring_over_long_tiles_and_repeated_executes(laph):
+    """128 staged vectors per tile leave room for only 3 stage buffers, so the two A-producer groups take turns on
+    each buffer; long tiles (L=32, 4096 stages) and back-to-back executes exercise the barrier phases of that
+    ring.  Sampled inner products of every execute against the oracle."""
+    import torch
+    L, T, Nv, Ns = 32, 4, 128, 512
+    v = synth.random_phi(L, Nv, T=T, instance=31)
+    s = synth.random_phi(L, Ns, T=T, instance=32)
+    mom = np.zeros((1, 3), dtype=np.int32)
+    plan = laph.Plan([(L, T, Nv, mom, Ns)], mode="f16x3", flags=laph.PLAN_FIELDS | laph.PLAN_SKIP_B)
+    _, Ms = plan.alloc_outputs()
+    ws = plan.alloc_workspace()
+    vd, sd = torch.from_numpy(v).cuda(), torch.from_numpy(s).cuda()
+    rows, cols = np.arange(0, Nv, 17), np.arange(3, Ns, 61)
+    for t in (0, T - 1):
+        ref = O.projection(v[t][rows], s[t][cols], L, mom)[0]
+        for _ in range(3):
+            Ms[0].zero_()
+            plan.execute_fields([[vd, sd]], Ms, ws)
+            torch.cuda.synchronize()
+            assert plan.device_status() == laph.LAPH_OK
+            got = Ms[0][t, 0].cpu().numpy()[np.ix_(rows, cols)]
+            assert rel_frob(got, ref) <= 1e-5
+    plan.close()
