@@ -477,3 +477,49 @@ int oracle_doublet_blocks(const double *f1, const double *f2, int L, int N, cons
 {
     return oracle_projection(f1, f2, L, N, N, mom, P, out);
 }
+
+/*
+ * The 3-d gauge-covariant Laplacian of one timeslice, whose lowest
+ * eigenvectors are the LapH vectors (paper, section "Innovations",
+ * subsection "Scalable Lanczos Eigensolver"):
+ *
+ *   (-Delta f)(x) = sum_mu [ 2 f(x) - U_mu(x) f(x + mu) - U_mu(x - mu)^dagger f(x - mu) ]
+ *
+ * over the three spatial directions mu, periodic.  U [3][V][3][3] complex
+ * (row-major colour matrices), f and out [nvec][V][3] complex.
+ */
+void oracle_laplacian(const double *U, const double *f, int L, int nvec, double *out)
+{
+    int64_t V = (int64_t)L * L * L;
+#pragma omp parallel for schedule(static)
+    for (int64_t nx = 0; nx < (int64_t)nvec * V; nx++) {
+        int64_t n = nx / V, x = nx % V;
+        int64_t c[3] = {x % L, (x / L) % L, x / ((int64_t)L * L)};
+        const int64_t stride[3] = {1, L, (int64_t)L * L};
+        cplx acc[3];
+        for (int a = 0; a < 3; a++) {
+            cplx v = phi_at(f, V, (int)n, x, a);
+            acc[a].re = 6.0 * v.re;
+            acc[a].im = 6.0 * v.im;
+        }
+        for (int mu = 0; mu < 3; mu++) {
+            int64_t up = x + (c[mu] == L - 1 ? -(int64_t)(L - 1) * stride[mu] : stride[mu]);
+            int64_t dn = x - (c[mu] == 0 ? -(int64_t)(L - 1) * stride[mu] : stride[mu]);
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) {
+                    /* U_mu(x)_{ab} f_b(x + mu) */
+                    const double *u = U + 2 * (((mu * V + x) * 3 + a) * 3 + b);
+                    cplx uf = cmul((cplx){u[0], u[1]}, phi_at(f, V, (int)n, up, b));
+                    /* (U_mu(x - mu)^dagger)_{ab} f_b(x - mu) = conj(U_mu(x - mu)_{ba}) f_b(x - mu) */
+                    const double *w = U + 2 * (((mu * V + dn) * 3 + b) * 3 + a);
+                    cplx wf = cmul(cconj((cplx){w[0], w[1]}), phi_at(f, V, (int)n, dn, b));
+                    acc[a].re -= uf.re + wf.re;
+                    acc[a].im -= uf.im + wf.im;
+                }
+        }
+        for (int a = 0; a < 3; a++) {
+            out[2 * ((n * V + x) * 3 + a)] = acc[a].re;
+            out[2 * ((n * V + x) * 3 + a) + 1] = acc[a].im;
+        }
+    }
+}

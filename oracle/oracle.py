@@ -13,8 +13,10 @@ from the LapH eigenvectors):
     M[p][i][j]  = sum_x exp(-2 pi i ((n_p.x) mod L)/L) conj(phi_i^a) phi_j^a
 
 the same contractions of three (two) different sets of vectors, e.g.
-stochastic-LapH quark sinks (same passage), and the projection of one set of
-vectors onto another (subsection "Eigenvector Projection"):
+stochastic-LapH quark sinks (same passage), the projection of one set of
+vectors onto another (subsection "Eigenvector Projection"), and the 3-d
+gauge-covariant Laplacian whose lowest eigenvectors are the LapH vectors
+(subsection "Scalable Lanczos Eigensolver"):
 
     B3[p][i][j][k] = sum_x ph_p(x) eps_abc phi_i^a psi_j^b chi_k^c   (dense)
     M2[p][i][j]    = sum_x ph_p(x) conj(phi_i^a) psi_j^a
@@ -83,6 +85,8 @@ def _load():
             lib.oracle_doublet_blocks.restype = ctypes.c_int
             lib.oracle_projection.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ctypes.c_int, dp]
             lib.oracle_projection.restype = ctypes.c_int
+            lib.oracle_laplacian.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, dp]
+            lib.oracle_laplacian.restype = None
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -231,3 +235,30 @@ def projection(v: np.ndarray, s: np.ndarray, L: int, momenta=((0, 0, 0),)) -> np
     if rc != 0:
         raise RuntimeError("oracle_projection failed")
     return out
+
+
+def laplacian(U: np.ndarray, f: np.ndarray, L: int) -> np.ndarray:
+    """(-Delta f) for one timeslice: U complex [3][L^3][3][3], f complex [nvec][L^3][3] (or [L^3][3])."""
+    U = np.ascontiguousarray(U, dtype=np.complex128)
+    single = f.ndim == 2
+    f = np.ascontiguousarray(f[None] if single else f, dtype=np.complex128)
+    V = L ** 3
+    if U.shape != (3, V, 3, 3) or f.shape[1:] != (V, 3):
+        raise ValueError("U must be [3][L^3][3][3] and f [nvec][L^3][3]")
+    out = np.empty_like(f)
+    _load().oracle_laplacian(_dptr(U), _dptr(f), L, f.shape[0], _dptr(out))
+    return out[0] if single else out
+
+
+def laplacian_matrix(U: np.ndarray, L: int) -> np.ndarray:
+    """Dense (3V x 3V) matrix of -Delta (small L only): the oracle applied to every unit vector."""
+    V = L ** 3
+    eye = np.eye(3 * V, dtype=np.complex128).reshape(3 * V, V, 3)
+    return laplacian(U, eye, L).reshape(3 * V, 3 * V).T
+
+
+def lowest_eigenpairs(U: np.ndarray, L: int, n: int):
+    """The n smallest eigenvalues (ascending) and eigenvectors complex128 [n][L^3][3] of -Delta
+    (small L only): numpy's Hermitian eigensolver on the dense matrix."""
+    w, v = np.linalg.eigh(laplacian_matrix(U, L))
+    return w[:n], v[:, :n].T.reshape(n, L ** 3, 3)

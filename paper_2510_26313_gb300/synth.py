@@ -6,7 +6,8 @@ and is shared by the CUDA path's tests/benchmark and by the oracle's tests.
 
 The paper's gauge ensembles (64^3 x 192 and 96^3 x 192, section
 "Performance Measurement Method") and the LapH eigenvectors computed on them
-are not available, so the vectors are stand-ins with the same shapes:
+are not available, so the vectors (and, for the Laplacian eigensolver, the
+gauge links) are stand-ins with the same shapes:
 complex Gaussian entries (re, im ~ N(0,1), numpy PCG64), orthonormalised over
 the combined (site, colour) index in FP64 -- the result equals Gram-Schmidt
 applied in vector order -- and cast to complex64.  Layout: [T][N][L^3][3],
@@ -127,3 +128,38 @@ def plane_wave_phi(L: int, qs, us) -> np.ndarray:
     ang = 2.0 * np.pi * (xc @ qs.T) / L  # [V][N]
     wave = np.exp(1j * ang).T / np.sqrt(V)  # [N][V]
     return wave[:, :, None] * us[:, None, :]
+
+
+def random_su3(n: int, rng: np.random.Generator) -> np.ndarray:
+    """n seeded SU(3) matrices, complex128 [n][3][3]: QR of a complex Gaussian (phases of R's diagonal
+    removed, which makes Q Haar-distributed in U(3)), then divided by a cube root of the determinant."""
+    z = rng.standard_normal((n, 3, 3)) + 1j * rng.standard_normal((n, 3, 3))
+    q, r = np.linalg.qr(z)
+    d = np.diagonal(r, axis1=1, axis2=2)
+    q = q * (d / np.abs(d))[:, None, :]
+    det = np.linalg.det(q)
+    return q / (det ** (1.0 / 3.0))[:, None, None]
+
+
+def random_links(L: int, T: int = 1, instance: int = 0, eps: float | None = None) -> np.ndarray:
+    """Seeded gauge links complex64 [T][3][L^3][3][3]: U_mu(x) for the three spatial directions mu.
+
+    eps None: independent Haar-like SU(3) links (a maximally rough field).  eps > 0: links
+    exp(i eps H) built from the polar part of 1 + i eps H for Hermitian Gaussian H, i.e. a field close
+    to the identity, smoother like a smeared gauge field.
+    """
+    V = L ** 3
+    out = np.empty((T, 3, V, 3, 3), dtype=np.complex64)
+    for t in range(T):
+        rng = np.random.default_rng(seed_for(1000 + instance, t))
+        if eps is None:
+            out[t] = random_su3(3 * V, rng).reshape(3, V, 3, 3)
+        else:
+            h = rng.standard_normal((3 * V, 3, 3)) + 1j * rng.standard_normal((3 * V, 3, 3))
+            h = 0.5 * (h + np.conj(np.transpose(h, (0, 2, 1))))
+            m = np.eye(3)[None] + 1j * eps * h
+            u, _, vh = np.linalg.svd(m)
+            q = u @ vh
+            det = np.linalg.det(q)
+            out[t] = (q / (det ** (1.0 / 3.0))[:, None, None]).reshape(3, V, 3, 3)
+    return out

@@ -5,7 +5,9 @@ Each case copies ``oracle/laph_oracle.c``, plants one plausible mistake
 transposed site axes, swapped packing, transposed meson output; for the
 general-field routines: fields bound to the wrong index, a colour index
 swapped, a conjugation on the wrong field, transposed or misindexed
-outputs), builds it and runs the pin tests against it: they must fail.
+outputs; for the Laplacian: a dropped dagger, the backward link at the
+wrong site, a wrong diagonal, a wrong periodic wrap), builds it and runs the
+pin tests against it: they must fail.
 """
 import os
 import subprocess
@@ -37,6 +39,14 @@ MUTATIONS = {
     "doublet_transpose": ("int64_t o = 2 * ((p * (int64_t)N1 + i) * N2 + j);",
                           "int64_t o = 2 * ((p * (int64_t)N1 + j) * N2 + i);"),
     "projection_counts": ("int i = (int)(ij / N2), j = (int)(ij % N2);", "int i = (int)(ij / N1), j = (int)(ij % N1);"),
+    # covariant Laplacian
+    "laplacian_no_dagger": ("cplx wf = cmul(cconj((cplx){w[0], w[1]}), phi_at(f, V, (int)n, dn, b));",
+                            "cplx wf = cmul((cplx){w[0], w[1]}, phi_at(f, V, (int)n, dn, b));"),
+    "laplacian_backward_link_site": ("const double *w = U + 2 * (((mu * V + dn) * 3 + b) * 3 + a);",
+                                     "const double *w = U + 2 * (((mu * V + x) * 3 + b) * 3 + a);"),
+    "laplacian_diagonal": ("acc[a].re = 6.0 * v.re;", "acc[a].re = 4.0 * v.re;"),
+    "laplacian_wrap": ("int64_t up = x + (c[mu] == L - 1 ? -(int64_t)(L - 1) * stride[mu] : stride[mu]);",
+                       "int64_t up = x + (c[mu] == L - 1 ? 0 : stride[mu]);"),
     "triplet_dense_index": ("ijk[3 * e + 2] = (int32_t)(e % N);", "ijk[3 * e + 2] = (int32_t)((e / N) % N);"),
 }
 
@@ -54,6 +64,7 @@ def test_pins_fail_on_planted_mistake(name, tmp_path):
     env = dict(os.environ, LAPH_ORACLE_LIB=str(lib), OMP_NUM_THREADS="2")
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_fields_pins.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_fields_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_laplacian_pins.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins did not catch mutation {name}:\n{r.stdout[-2000:]}"
