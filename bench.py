@@ -362,6 +362,123 @@ def run_projection(args):
     return 0
 
 
+LANCZOS = dict(L=32, T=64, n_ev=64, m=160, degree=40, lo=0.95, eps=0.6)
+
+
+def laplacian_bytes_per_site(with_z: bool) -> int:
+    """Algorithmic bytes of one application of -Delta (or one Chebyshev step) per site and vector: the six links
+    touching the site counted once each (3 x 72 B), the input vector, the output and, for a Chebyshev step, the
+    vector y_{k-1} (24 B each)."""
+    return 3 * 72 + 24 + 24 + (24 if with_z else 0)
+
+
+def run_lanczos(args):
+    """--workload lanczos: the LapH eigenvectors, the 64 lowest eigenpairs of the 3-d gauge-covariant Laplacian
+    on every timeslice of an L=32, T=64 lattice (batched Lanczos, 160 Krylov steps on a degree-40 Chebyshev
+    filter), smoothed synthetic links."""
+    import torch
+    from paper_2510_26313_gb300 import binding as laph
+    from oracle import oracle as O
+    torch.cuda.set_device(0)
+    c = LANCZOS
+    L, T, n_ev, m, d, lo = c["L"], c["T"], c["n_ev"], c["m"], c["degree"], c["lo"]
+    V = L ** 3
+    U = synth.random_links_device(L, T, c["eps"], synth.SEED_BASE + 21)
+    evecs = torch.empty((T, n_ev, V, 3), dtype=torch.complex64, device="cuda")
+    ws = torch.empty(laph.lanczos_workspace_size(L, T, n_ev, m, d, lo), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        laph.lanczos(U, L, n_ev, m, cheb_degree=d, cheb_lo=lo, out=evecs, workspace=ws, stream=stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    stats = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        st = {}
+        _, ev, res = laph.lanczos(U, L, n_ev, m, cheb_degree=d, cheb_lo=lo, out=evecs, workspace=ws, stream=stream,
+                                  stats=st)
+        stats.append(st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    apply_ms = sum(s["apply_ms"] for s in stats) / args.steps
+    orth_ms = sum(s["orth_ms"] for s in stats) / args.steps
+    n_apply = stats[0]["apply_launches"]
+    # algorithmic bytes: Laplacian launches (the first step of each filter without y_{k-1})
+    per_iter = laplacian_bytes_per_site(False) + (d - 1) * laplacian_bytes_per_site(True)
+    apply_bytes = m * per_iter * V * T
+    # orthogonalisation of step j: two passes over the j + 1 basis vectors, each reading them once for the
+    # inner products (with w) and once for the update (reading and writing w; the second update also sums |w|^2)
+    K8 = 3 * V * 8
+    orth_bytes = sum(2 * ((j + 2) + (j + 3)) for j in range(m)) * K8 * T
+    peaks, src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    apply_gbs = apply_bytes / (apply_ms / 1e3) / 1e9
+    orth_gbs = orth_bytes / (orth_ms / 1e3) / 1e9
+    dominant = "apply" if apply_ms >= orth_ms else "orth"
+    ach = apply_gbs if dominant == "apply" else orth_gbs
+    e2e = None
+    if not args.no_e2e:
+        # through the public API with host buffers: links copied in from pinned memory, eigenvectors and
+        # eigenvalues copied back, every step
+        U_host = U.cpu().pin_memory()
+        out_host = torch.empty((T, n_ev, V, 3), dtype=torch.complex64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            Ud = U_host.to("cuda", non_blocking=True)
+            laph.lanczos(Ud, L, n_ev, m, cheb_degree=d, cheb_lo=lo, out=evecs, workspace=ws, stream=stream)
+            out_host.copy_(evecs, non_blocking=True)
+            torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.e2e_steps
+        e2e = {"value": T / dt, "unit": "timeslices/s", "h2d_bytes_per_step": U_host.numel() * 8,
+               "d2h_bytes_per_step": out_host.numel() * 8 + T * n_ev * 16}
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle has no iterative eigensolver at this size (its reference is a dense Hermitian solve): time its
+        # FP64 Laplacian stencil on timeslice 0 and scale to the m (d) operator applications of one solve,
+        # leaving out the orthogonalisation (in the CPU's favour)
+        U0 = U[0].cpu().numpy()
+        f = evecs[0, :8].cpu().numpy()
+        t0 = time.perf_counter()
+        reps = 0
+        while time.perf_counter() - t0 < 10.0:
+            O.laplacian(U0, f, L)
+            reps += 1
+        per_apply = (time.perf_counter() - t0) / (reps * f.shape[0])
+        cpu = {"value": 1.0 / (per_apply * m * d), "unit": "timeslices/s", "cores": O.num_threads(), "kind": "oracle",
+               "sample": f"{reps} x 8 applications of the oracle's FP64 Laplacian on timeslice 0, scaled to the "
+                         f"{m * d} applications of one solve (orthogonalisation not counted)"}
+    line = {
+        "metric": f"LapH eigenvectors: timeslices/s for the {n_ev} lowest eigenpairs of the 3-d Laplacian at L={L}",
+        "value": T / (ms / 1e3), "unit": "timeslices/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 vectors, f64 inner products",
+        "data": f"synthetic smoothed SU(3) links (polar part of 1 + i {c['eps']} H, H Hermitian Gaussian)",
+        "config": {"workload": f"L={L},T={T},n_ev={n_ev} (lanczos: m={m}, Chebyshev degree {d}, lo={lo})",
+                   "L": L, "T": T, "n_ev": n_ev, "n_krylov": m, "cheb_degree": d, "cheb_lo": lo,
+                   "l2": f"inputs larger than L2: links {U.numel() * 8 / 1e9:.2f} GB, basis "
+                         f"{T * (m + 1) * 3 * V * 8 / 1e9:.1f} GB"},
+        "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                     "traffic": None, "kernel": "laplacian (Chebyshev steps)" if dominant == "apply" else
+                     "orthogonalisation (dots + update)", "peak_source": src},
+        "phases": {"apply_ms": apply_ms, "apply_gbs": apply_gbs, "apply_launches": n_apply,
+                   "orth_ms": orth_ms, "orth_gbs": orth_gbs,
+                   "setup_ms": sum(s["setup_ms"] for s in stats) / args.steps,
+                   "ritz_ms": sum(s["ritz_ms"] for s in stats) / args.steps,
+                   "other_ms": ms - apply_ms - orth_ms},
+        "convergence": {"max_resid": float(res.max()), "median_resid": float(np.median(res)),
+                        "ev_min": float(ev.min()), "ev_max": float(ev.max())},
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(sum(s["launches"] for s in stats)), "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ragged(args):
     """--workload ragged: 200 ragged instances (L in {16,24,32}, N in [24,96], P in {1,7,19,33},
     T in 1..8) in one plan; the same instances as 200 separate plans for comparison."""
@@ -446,7 +563,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="f16x3")
-    ap.add_argument("--workload", default="metric", choices=sorted(WORKLOADS) + ["ragged", "triplets", "projection"])
+    ap.add_argument("--workload", default="metric", choices=sorted(WORKLOADS) + ["ragged", "triplets", "projection", "lanczos"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -461,6 +578,8 @@ def main():
         return run_triplets(args)
     if args.workload == "projection":
         return run_projection(args)
+    if args.workload == "lanczos":
+        return run_lanczos(args)
 
     import torch
     import torch.distributed as dist

@@ -193,6 +193,67 @@ LAPH_API int laph_doublet_blocks(const void *phi, const void *psi, int L, int T,
 LAPH_API int laph_projection(const void *v, const void *s, int L, int T, int Nv, int Ns, const int32_t *momenta,
                              int n_mom, void *out, int mode, void *stream);
 
+/* ---- LapH eigenvectors: the 3-d gauge-covariant Laplacian and a batched
+ * Lanczos eigensolver (paper, section "Innovations", subsection "Scalable
+ * Lanczos Eigensolver"; the timeslices are independent problems) ---------- */
+/*   (-Delta f)(x) = sum_mu [ 2 f(x) - U_mu(x) f(x + mu) - U_mu(x - mu)^dagger f(x - mu) ]
+ * over the three spatial directions, periodic.  U: device complex64
+ * [T][3][L^3][3][3] (row-major SU(3) colour matrices per direction and site);
+ * f, out: device complex64 [T][nvec][L^3][3].  Asynchronous on `stream`, no
+ * allocation.  LAPH_ERR_ARG for L < 2, T < 1, nvec < 1, null or misaligned
+ * pointers. */
+LAPH_API int laph_laplacian(const void *U, const void *f, void *out, int L, int T, int nvec, void *stream);
+
+typedef struct {
+    int n_krylov;     /* Lanczos steps m, n_ev <= m <= min(4096, 3 L^3) */
+    int cheb_degree;  /* 0: Lanczos on -Delta; d > 0: on the Chebyshev filter T_d((-Delta - c) / e),
+                         which maps [cheb_lo, 12] onto [-1, 1] and magnifies the eigenvalues below cheb_lo */
+    double cheb_lo;   /* 0 < cheb_lo < 12 when cheb_degree > 0: above the wanted eigenvalues */
+    uint32_t seed;    /* start vectors (0: a fixed default) */
+} laph_lanczos_params;
+
+/* Where the time of one laph_lanczos call goes, from CUDA events recorded on
+ * its stream: the whole call; the setup (workspace, start vectors); the
+ * applications of -Delta (or of the filter); the orthogonalisation with the
+ * norm of each new basis vector (including its read-back to the host); the
+ * Ritz vectors, Rayleigh quotients and residuals.  Launches of this
+ * library's kernels, of which the Laplacian launches (each over all T
+ * timeslices, one vector each). */
+typedef struct {
+    double total_ms;
+    double setup_ms;
+    double apply_ms;
+    double orth_ms;
+    double ritz_ms;
+    int64_t launches;
+    int64_t apply_launches;
+} laph_lanczos_stats;
+
+/* Bytes of device workspace laph_lanczos needs (about 8 T 3 L^3 (n_krylov +
+ * n_ev + 5) bytes: the basis, the Ritz vectors, scratch vectors). */
+LAPH_API int laph_lanczos_workspace_size(int L, int T, int n_ev, const laph_lanczos_params *params, size_t *bytes);
+
+/* The n_ev lowest eigenpairs of -Delta on every timeslice: Lanczos with full
+ * reorthogonalisation (FP32 vectors, FP64 inner products) on -Delta or its
+ * Chebyshev filter, Ritz vectors, then Rayleigh quotients and residuals with
+ * -Delta.  evecs: device complex64 [T][n_ev][L^3][3], unit norm; evals, resid:
+ * HOST double [T][n_ev], ascending eigenvalues and |(-Delta) v - lambda v|
+ * (resid may be NULL); stats (may be NULL) receives the timings above.
+ * workspace: device memory of laph_lanczos_workspace_size bytes, 256-byte
+ * aligned (workspace_bytes its size), or NULL to have the call allocate it on
+ * `stream` and free it before returning.  Synchronises the stream once per
+ * Krylov step and blocks until done.  LAPH_ERR_ARG for bad parameters,
+ * LAPH_ERR_WORKSPACE for a workspace too small or misaligned. */
+LAPH_API int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_params *params, void *evecs,
+                          double *evals, double *resid, void *workspace, size_t workspace_bytes,
+                          laph_lanczos_stats *stats, void *stream);
+
+/* Host utility: eigenvalues (ascending, in d) and orthonormal eigenvectors
+ * (z, n x n row-major, column k for d[k]) of the symmetric tridiagonal matrix
+ * with diagonal d[0..n) and off-diagonal e[0..n-1); implicit-shift QL.  No
+ * GPU involved.  LAPH_ERR_ARG for bad arguments or no convergence. */
+LAPH_API int laph_tridiag_eigen(int n, double *d, const double *e, double *z);
+
 /* ---- plan API (ragged batches, capture-safe execution) ----------------- */
 /* Validates the instances (L >= 1; N >= 3 unless LAPH_PLAN_SKIP_B, N >= 1;
  * N <= 3 L^3; 1 <= n_mom; |n| components within +-2^20), copies the

@@ -47,6 +47,17 @@ class laph_instance(ctypes.Structure):
                 ("momenta", ctypes.POINTER(ctypes.c_int32)), ("n_col", ctypes.c_int)]
 
 
+class laph_lanczos_params(ctypes.Structure):
+    _fields_ = [("n_krylov", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("cheb_lo", ctypes.c_double),
+                ("seed", ctypes.c_uint32)]
+
+
+class laph_lanczos_stats(ctypes.Structure):
+    _fields_ = [("total_ms", ctypes.c_double), ("setup_ms", ctypes.c_double), ("apply_ms", ctypes.c_double),
+                ("orth_ms", ctypes.c_double), ("ritz_ms", ctypes.c_double), ("launches", ctypes.c_int64),
+                ("apply_launches", ctypes.c_int64)]
+
+
 def lib() -> ctypes.CDLL:
     """The loaded CUDA library; raises if it has not been built."""
     global _lib
@@ -88,6 +99,14 @@ def lib() -> ctypes.CDLL:
                                          ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]),
             "laph_plan_destroy": (i32, [vp]),
             "laph_blocks_noalloc": (i32, [vp, i32, i32, i32, ip32, i32, vp, vp, vp]),
+            "laph_laplacian": (i32, [vp, vp, vp, i32, i32, i32, vp]),
+            "laph_lanczos": (i32, [vp, i32, i32, i32, ctypes.POINTER(laph_lanczos_params), vp,
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp, sz,
+                                   ctypes.POINTER(laph_lanczos_stats), vp]),
+            "laph_lanczos_workspace_size": (i32, [i32, i32, i32, ctypes.POINTER(laph_lanczos_params),
+                                                  ctypes.POINTER(sz)]),
+            "laph_tridiag_eigen": (i32, [i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -243,6 +262,80 @@ def projection(v, s, L: int, momenta=((0, 0, 0),), mode="f16x3", out=None, strea
                                mom.shape[0], _ptr(out), _mode(mode), _stream(stream))
     _check(rc, "laph_projection")
     return out
+
+
+def _check_links(U, L):
+    import torch
+    if U.dtype != torch.complex64 or not U.is_cuda or not U.is_contiguous():
+        raise ValueError("U must be a contiguous complex64 CUDA tensor [T][3][L^3][3][3]")
+    if U.dim() != 5 or tuple(U.shape[1:]) != (3, L ** 3, 3, 3):
+        raise ValueError(f"U must have shape [T][3][{L ** 3}][3][3], got {tuple(U.shape)}")
+    return U.shape[0]
+
+
+def laplacian(U, f, L: int, out=None, stream=None):
+    """(-Delta) f on every timeslice, complex64 [T][nvec][L^3][3] (asynchronous on `stream`)."""
+    import torch
+    T = _check_links(U, L)
+    Tf, nvec = _check_phi(f, L)
+    if Tf != T or f.device != U.device:
+        raise ValueError("f and U must have the same timeslices and device")
+    if out is None:
+        out = torch.empty_like(f)
+    rc = lib().laph_laplacian(_ptr(U), _ptr(f), _ptr(out), L, T, nvec, _stream(stream))
+    _check(rc, "laph_laplacian")
+    return out
+
+
+def lanczos_workspace_size(L: int, T: int, n_ev: int, n_krylov: int, cheb_degree: int = 0,
+                           cheb_lo: float = 0.0) -> int:
+    p = laph_lanczos_params(n_krylov, cheb_degree, cheb_lo, 0)
+    n = ctypes.c_size_t()
+    _check(lib().laph_lanczos_workspace_size(L, T, n_ev, ctypes.byref(p), ctypes.byref(n)),
+           "laph_lanczos_workspace_size")
+    return n.value
+
+
+def lanczos(U, L: int, n_ev: int, n_krylov: int, cheb_degree: int = 0, cheb_lo: float = 0.0, seed: int = 0,
+            out=None, workspace=None, stream=None, stats=None):
+    """The n_ev lowest eigenpairs of -Delta per timeslice (blocking).
+
+    Returns (evecs complex64 [T][n_ev][L^3][3] on the device, evals float64 [T][n_ev] and
+    residual norms float64 [T][n_ev] as numpy arrays).  workspace: a uint8 CUDA tensor of
+    lanczos_workspace_size bytes (None: the call allocates its own).  stats: a dict that receives
+    the call's event-timed breakdown (total_ms, setup_ms, apply_ms, orth_ms, ritz_ms, launches,
+    apply_launches)."""
+    import torch
+    T = _check_links(U, L)
+    if out is None:
+        out = torch.empty((T, n_ev, L ** 3, 3), dtype=torch.complex64, device=U.device)
+    p = laph_lanczos_params(n_krylov, cheb_degree, cheb_lo, seed)
+    ws = ctypes.c_void_p(workspace.data_ptr()) if workspace is not None else None
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    ev = np.zeros((T, n_ev), dtype=np.float64)
+    rs = np.zeros((T, n_ev), dtype=np.float64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    st = laph_lanczos_stats()
+    rc = lib().laph_lanczos(_ptr(U), L, T, n_ev, ctypes.byref(p), _ptr(out), ev.ctypes.data_as(dp),
+                            rs.ctypes.data_as(dp), ws, ws_bytes, ctypes.byref(st) if stats is not None else None,
+                            _stream(stream))
+    _check(rc, "laph_lanczos")
+    if stats is not None:
+        stats.update({k: getattr(st, k) for k, _ in laph_lanczos_stats._fields_})
+    return out, ev, rs
+
+
+def tridiag_eigen(d, e):
+    """Host QL solver: eigenvalues (ascending) and eigenvectors (columns) of a symmetric tridiagonal matrix."""
+    d = np.array(d, dtype=np.float64)
+    e = np.ascontiguousarray(np.asarray(e, dtype=np.float64))
+    n = d.shape[0]
+    z = np.zeros((n, n), dtype=np.float64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = lib().laph_tridiag_eigen(n, d.ctypes.data_as(dp), e.ctypes.data_as(dp) if n > 1 else None,
+                                  z.ctypes.data_as(dp))
+    _check(rc, "laph_tridiag_eigen")
+    return d, z
 
 
 def blocks_noalloc(phi, L: int, momenta, out_B, out_M, stream=None):

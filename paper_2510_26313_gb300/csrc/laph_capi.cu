@@ -19,6 +19,10 @@
 using laph::InstDev;
 using laph::TileDev;
 
+namespace laph {
+int record_cuda_error(cudaError_t e, const char *where);
+}
+
 namespace {
 
 thread_local char g_last_cuda[256] = "";
@@ -28,6 +32,13 @@ int cuda_fail(cudaError_t e, const char *where)
     snprintf(g_last_cuda, sizeof(g_last_cuda), "%s: %s", where, cudaGetErrorString(e));
     return LAPH_ERR_CUDA;
 }
+
+}  // namespace
+
+// the same record for the other translation units
+int laph::record_cuda_error(cudaError_t e, const char *where) { return cuda_fail(e, where); }
+
+namespace {
 
 #define CK(call)                                         \
     do {                                                 \

@@ -123,6 +123,9 @@ __device__ __forceinline__ float2 cross_c(const float2 *u, const float2 *v, int 
 
 // ---- host-side launchers (defined in the .cu files) ----------------------
 
+// laph_capi.cu: records a CUDA error for laph_last_cuda_error, returns LAPH_ERR_CUDA
+int record_cuda_error(cudaError_t e, const char *where);
+
 // laph_prep.cu
 cudaError_t launch_phase_table(int L, const int32_t *d_mom, int P, double2 *out64, float2 *out32,
                                cudaStream_t s);

@@ -1,0 +1,786 @@
+// The 3-d gauge-covariant Laplacian of every timeslice and a batched Lanczos
+// eigensolver for its lowest eigenpairs, the LapH eigenvectors (paper,
+// section "Innovations", subsection "Scalable Lanczos Eigensolver": the
+// timeslices are independent problems, solved side by side, with no
+// communication between them).
+//
+//   (-Delta f)(x) = sum_mu [ 2 f(x) - U_mu(x) f(x + mu) - U_mu(x - mu)^dagger f(x - mu) ]
+//
+// Layouts (complex interleaved): links U [T][3][V][3][3] complex64 (row-major
+// colour matrices), vectors [T][n][V][3] complex64, site x = x0 + L x1 + L^2 x2.
+//
+// Lanczos with full reorthogonalisation, batched over timeslices: every
+// iteration applies the operator to the newest basis vector of every
+// timeslice, removes its components along the whole basis twice ("twice is
+// enough"), and normalises.  The operator is -Delta itself or the Chebyshev
+// filter T_d((-Delta - c) / e), which maps the unwanted part of the spectrum,
+// [lo, 12], onto [-1, 1] and magnifies the lowest eigenvalues.  The Ritz
+// vectors of the wanted end are formed from the basis, and their eigenvalues
+// and residuals are Rayleigh quotients with -Delta.  Vectors are FP32,
+// inner products FP64.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <initializer_list>
+#include <thread>
+#include <vector>
+
+#include "laph.h"
+#include "laph_internal.cuh"
+
+namespace laph {
+namespace {
+
+constexpr int LAP_THREADS = 256;
+
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 acc)   // acc + a b
+{
+    return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y)));
+}
+
+__device__ __forceinline__ float2 cfma_conj(float2 a, float2 b, float2 acc)   // acc + conj(a) b
+{
+    return make_float2(fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(-a.y, b.x, acc.y)));
+}
+
+// out = a (-Delta in) + b in + c z for the vectors of blockIdx.z of timeslice
+// blockIdx.y; one thread per site.  in/z/out: [T][nvec][V][3] with the given
+// per-timeslice strides (in elements of float2); z may be null (c ignored).
+__global__ void __launch_bounds__(LAP_THREADS) lap_kernel(const float2 *__restrict__ U, const float2 *__restrict__ in,
+                                                          const float2 *__restrict__ z, float2 *__restrict__ out,
+                                                          int L, long long ts_in, long long ts_z, long long ts_out,
+                                                          float a, float b, float c)
+{
+    const long long V = (long long)L * L * L;
+    const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= V) return;
+    const int t = blockIdx.y, n = blockIdx.z;
+    const float2 *f = in + t * ts_in + n * V * 3;
+    const float2 *Ut = U + (long long)t * 3 * V * 9;
+    const int c0 = (int)(x % L), c1 = (int)((x / L) % L), c2 = (int)(x / ((long long)L * L));
+    const int cc[3] = {c0, c1, c2};
+    const long long stride[3] = {1, L, (long long)L * L};
+    float2 fx[3], acc[3];
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+        fx[q] = f[3 * x + q];
+        acc[q] = make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int mu = 0; mu < 3; mu++) {
+        const long long up = x + (cc[mu] == L - 1 ? -(long long)(L - 1) * stride[mu] : stride[mu]);
+        const long long dn = x - (cc[mu] == 0 ? -(long long)(L - 1) * stride[mu] : stride[mu]);
+        const float2 *uf = Ut + (mu * V + x) * 9;     // U_mu(x)
+        const float2 *ub = Ut + (mu * V + dn) * 9;    // U_mu(x - mu)
+        float2 fu[3], fd[3];
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            fu[q] = f[3 * up + q];
+            fd[q] = f[3 * dn + q];
+        }
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                acc[r] = cfma(__ldg(uf + 3 * r + q), fu[q], acc[r]);          // U_mu(x)_{rq} f_q(x + mu)
+                acc[r] = cfma_conj(__ldg(ub + 3 * q + r), fd[q], acc[r]);     // conj(U_mu(x - mu)_{qr}) f_q(x - mu)
+            }
+    }
+    float2 *o = out + t * ts_out + n * V * 3 + 3 * x;
+    const float2 *zz = z ? z + t * ts_z + n * V * 3 + 3 * x : nullptr;
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+        // -Delta f = 6 f(x) - (hops)
+        float2 lap = make_float2(6.f * fx[q].x - acc[q].x, 6.f * fx[q].y - acc[q].y);
+        float2 r = make_float2(a * lap.x + b * fx[q].x, a * lap.y + b * fx[q].y);
+        if (zz) {
+            r.x += c * zz[q].x;
+            r.y += c * zz[q].y;
+        }
+        o[q] = r;
+    }
+}
+
+// Block reduction of a double into thread 0.
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    v = 0.0;
+    if (threadIdx.x < (blockDim.x >> 5)) v = sh[threadIdx.x];
+    if (w == 0)
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Gram-Schmidt inner products, dots[t][j] += <basis[t][j], w[t]> over this
+// block's elements, j < nj.  Each thread holds DOT_EPT elements of w in
+// registers; per row the products are summed in FP32 within the thread and
+// the warp (shuffles), the warps' partials in FP64 and across blocks with
+// FP64 atomics.  GB300's FP64 rate is a small fraction of its FP32 rate, so no
+// FP64 arithmetic runs per element.
+constexpr int DOT_EPT = 8;      // elements of w per thread
+constexpr int DOT_JC = 32;      // rows between flushes of the warp partials
+constexpr int DOT_RG = 4;       // rows whose loads are issued together
+__global__ void __launch_bounds__(LAP_THREADS) dots_kernel(const float2 *__restrict__ basis, long long ts_basis,
+                                                           const float2 *__restrict__ w, long long ts_w, long long K,
+                                                           int nj, double2 *__restrict__ dots, int dots_stride)
+{
+    __shared__ float2 part[LAP_THREADS / 32][DOT_JC];
+    const int t = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long e0 = (long long)blockIdx.x * LAP_THREADS * DOT_EPT + threadIdx.x;
+    const float2 *B = basis + t * ts_basis;
+    float2 wv[DOT_EPT];
+#pragma unroll
+    for (int q = 0; q < DOT_EPT; q++) {
+        const long long e = e0 + (long long)q * LAP_THREADS;
+        wv[q] = e < K ? w[t * ts_w + e] : make_float2(0.f, 0.f);
+    }
+    for (int j0 = 0; j0 < nj; j0 += DOT_JC) {
+        const int jn = min(DOT_JC, nj - j0);
+        for (int jj = 0; jj < jn; jj += DOT_RG) {
+            float2 b[DOT_RG][DOT_EPT];
+#pragma unroll
+            for (int r = 0; r < DOT_RG; r++)
+#pragma unroll
+                for (int q = 0; q < DOT_EPT; q++) {
+                    const long long e = e0 + (long long)q * LAP_THREADS;
+                    b[r][q] = (jj + r < jn && e < K) ? B[(long long)(j0 + jj + r) * K + e] : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+            for (int r = 0; r < DOT_RG; r++) {
+                float re = 0.f, im = 0.f;
+#pragma unroll
+                for (int q = 0; q < DOT_EPT; q++) {
+                    re = fmaf(b[r][q].x, wv[q].x, fmaf(b[r][q].y, wv[q].y, re));
+                    im = fmaf(b[r][q].x, wv[q].y, fmaf(-b[r][q].y, wv[q].x, im));
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    re += __shfl_xor_sync(0xffffffffu, re, o);
+                    im += __shfl_xor_sync(0xffffffffu, im, o);
+                }
+                if (lane == 0 && jj + r < jn) part[warp][jj + r] = make_float2(re, im);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < jn) {
+            double re = 0.0, im = 0.0;
+#pragma unroll
+            for (int q = 0; q < LAP_THREADS / 32; q++) {
+                re += part[q][threadIdx.x].x;
+                im += part[q][threadIdx.x].y;
+            }
+            atomicAdd(&dots[t * dots_stride + j0 + threadIdx.x].x, re);
+            atomicAdd(&dots[t * dots_stride + j0 + threadIdx.x].y, im);
+        }
+        __syncthreads();
+    }
+}
+
+// Gram-Schmidt update, w[t] -= sum_j coef[t][j] basis[t][j] for j < nj, with
+// the coefficients rounded to FP32 in shared memory (dynamic, nj float2) and
+// FP32 multiply-adds; UPD_EPT elements per thread, the loads of UPD_RG rows
+// issued together.  norm (may be null): norm[t] += |w[t]|^2 of the result.
+constexpr int UPD_EPT = 4;
+constexpr int UPD_RG = 4;
+__global__ void __launch_bounds__(LAP_THREADS) update_kernel(const float2 *__restrict__ basis, long long ts_basis,
+                                                             float2 *__restrict__ w, long long ts_w, long long K, int nj,
+                                                             const double2 *__restrict__ coef, int coef_stride,
+                                                             double *__restrict__ norm)
+{
+    extern __shared__ float2 cs[];
+    __shared__ float npart[LAP_THREADS / 32];
+    const int t = blockIdx.y;
+    for (int i = threadIdx.x; i < nj; i += LAP_THREADS) {
+        const double2 c = coef[t * coef_stride + i];
+        cs[i] = make_float2((float)c.x, (float)c.y);
+    }
+    __syncthreads();
+    const long long e0 = (long long)blockIdx.x * LAP_THREADS * UPD_EPT + threadIdx.x;
+    const float2 *B = basis + t * ts_basis;
+    float2 acc[UPD_EPT];
+#pragma unroll
+    for (int q = 0; q < UPD_EPT; q++) acc[q] = make_float2(0.f, 0.f);
+    for (int j = 0; j < nj; j += UPD_RG) {
+        float2 b[UPD_RG][UPD_EPT];
+#pragma unroll
+        for (int r = 0; r < UPD_RG; r++)
+#pragma unroll
+            for (int q = 0; q < UPD_EPT; q++) {
+                const long long e = e0 + (long long)q * LAP_THREADS;
+                b[r][q] = (j + r < nj && e < K) ? B[(long long)(j + r) * K + e] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+        for (int r = 0; r < UPD_RG; r++) {
+            const float2 c = j + r < nj ? cs[j + r] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < UPD_EPT; q++) acc[q] = cfma(c, b[r][q], acc[q]);
+        }
+    }
+    float nrm = 0.f;
+#pragma unroll
+    for (int q = 0; q < UPD_EPT; q++) {
+        const long long e = e0 + (long long)q * LAP_THREADS;
+        if (e < K) {
+            float2 &x = w[t * ts_w + e];
+            const float2 v = make_float2(x.x - acc[q].x, x.y - acc[q].y);
+            x = v;
+            nrm = fmaf(v.x, v.x, fmaf(v.y, v.y, nrm));
+        }
+    }
+    if (norm) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+        if ((threadIdx.x & 31) == 0) npart[threadIdx.x >> 5] = nrm;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sum = 0.0;
+            for (int q = 0; q < LAP_THREADS / 32; q++) sum += npart[q];
+            atomicAdd(&norm[t], sum);
+        }
+    }
+}
+
+// out[t] = w[t] * scale[t] (scale from the host, FP64).
+__global__ void scale_kernel(const float2 *__restrict__ w, long long ts_w, float2 *__restrict__ out, long long ts_out,
+                             long long K, const double *__restrict__ scale)
+{
+    const int t = blockIdx.y;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= K) return;
+    const float s = (float)scale[t];
+    const float2 v = w[t * ts_w + e];
+    out[t * ts_out + e] = make_float2(v.x * s, v.y * s);
+}
+
+// X[t][r] = sum_j S[t][j][r] basis[t][j] for r < nr (S real, [T][m][nr]); each
+// thread one element and RT outputs, the S column block staged in shared memory.
+constexpr int RT = 16;
+__global__ void __launch_bounds__(LAP_THREADS) ritz_kernel(const float2 *__restrict__ basis, long long ts_basis,
+                                                           long long K, int m, const double *__restrict__ S, int nr,
+                                                           float2 *__restrict__ X, long long ts_X)
+{
+    __shared__ float Ss[64][RT];
+    const int t = blockIdx.y, r0 = blockIdx.z * RT;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    float2 acc[RT];
+#pragma unroll
+    for (int r = 0; r < RT; r++) acc[r] = make_float2(0.f, 0.f);
+    for (int j0 = 0; j0 < m; j0 += 64) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 64 * RT; i += blockDim.x) {
+            const int jj = j0 + i / RT, rr = r0 + i % RT;
+            Ss[i / RT][i % RT] = (jj < m && rr < nr) ? (float)S[((long long)t * m + jj) * nr + rr] : 0.f;
+        }
+        __syncthreads();
+        if (e < K) {
+            const int jn = min(64, m - j0);
+            for (int jj = 0; jj < jn; jj++) {
+                const float2 b = basis[t * ts_basis + (long long)(j0 + jj) * K + e];
+#pragma unroll
+                for (int r = 0; r < RT; r++) {
+                    acc[r].x = fmaf(Ss[jj][r], b.x, acc[r].x);
+                    acc[r].y = fmaf(Ss[jj][r], b.y, acc[r].y);
+                }
+            }
+        }
+    }
+    if (e >= K) return;
+#pragma unroll
+    for (int r = 0; r < RT; r++)
+        if (r0 + r < nr) X[t * ts_X + (long long)(r0 + r) * K + e] = acc[r];
+}
+
+// Per (timeslice, vector) sums over the elements: xy = <x, y>, xx = <x, x>
+// (mode 0), or rr = |y - lam x|^2 (mode 1, lam per vector).
+__global__ void __launch_bounds__(LAP_THREADS) rayleigh_kernel(const float2 *__restrict__ X, const float2 *__restrict__ Y,
+                                                               long long ts, long long K, int mode,
+                                                               const double *__restrict__ lam, int nr,
+                                                               double *__restrict__ out)
+{
+    __shared__ double sh[LAP_THREADS / 32];
+    const int t = blockIdx.y, r = blockIdx.z;
+    const float2 *x = X + t * ts + (long long)r * K, *y = Y + t * ts + (long long)r * K;
+    double s0 = 0.0, s1 = 0.0;
+    const double l = mode ? lam[t * nr + r] : 0.0;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < K; e += (long long)gridDim.x * blockDim.x) {
+        const float2 a = x[e], b = y[e];
+        if (mode == 0) {
+            s0 += (double)a.x * b.x + (double)a.y * b.y;
+            s1 += (double)a.x * a.x + (double)a.y * a.y;
+        } else {
+            const double dx = b.x - l * a.x, dy = b.y - l * a.y;
+            s0 += dx * dx + dy * dy;
+        }
+    }
+    s0 = block_sum(s0, sh);
+    s1 = block_sum(s1, sh);
+    if (threadIdx.x == 0) {
+        atomicAdd(&out[2 * (t * nr + r)], s0);
+        atomicAdd(&out[2 * (t * nr + r) + 1], s1);
+    }
+}
+
+// out[t][r] = X[t][perm[t][r]] * scale[t][r] (vectors of K elements).
+__global__ void gather_kernel(const float2 *__restrict__ X, long long ts_X, const int *__restrict__ perm,
+                              const double *__restrict__ scale, int nr, float2 *__restrict__ out, long long ts_out,
+                              long long K)
+{
+    const int t = blockIdx.y, r = blockIdx.z;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= K) return;
+    const float sc = (float)scale[t * nr + r];
+    const float2 v = X[t * ts_X + (long long)perm[t * nr + r] * K + e];
+    out[t * ts_out + (long long)r * K + e] = make_float2(v.x * sc, v.y * sc);
+}
+
+}  // namespace
+
+// Eigenvalues d (ascending) and orthonormal eigenvectors z (column k of the n x n
+// row-major z belongs to d[k]) of the symmetric tridiagonal matrix with diagonal
+// d[0..n) and off-diagonal e[0..n-1), by the QL algorithm with implicit Wilkinson
+// shifts (Givens rotations chased up from the bottom of each unreduced block).
+// Returns 0, or -1 when an eigenvalue needs more than 60 sweeps.
+int tridiag_eigen(int n, double *d, const double *e_in, double *z)
+{
+    std::vector<double> e(n, 0.0);
+    for (int i = 0; i + 1 < n; i++) e[i] = e_in[i];
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) z[i * n + j] = i == j ? 1.0 : 0.0;
+    for (int l = 0; l < n; l++) {
+        int iter = 0;
+        while (true) {
+            int m = l;
+            for (; m + 1 < n; m++) {
+                const double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
+                if (std::fabs(e[m]) <= 1e-16 * dd) break;
+            }
+            if (m == l) break;
+            if (++iter > 60) return -1;
+            // shift from the leading 2 x 2 of the block
+            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+            double r = std::hypot(g, 1.0);
+            g = d[m] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
+            double s = 1.0, c = 1.0, p = 0.0;
+            int i = m - 1;
+            for (; i >= l; i--) {
+                double f = s * e[i], b = c * e[i];
+                r = std::hypot(f, g);
+                e[i + 1] = r;
+                if (r == 0.0) {
+                    d[i + 1] -= p;
+                    e[m] = 0.0;
+                    break;
+                }
+                s = f / r;
+                c = g / r;
+                g = d[i + 1] - p;
+                r = (d[i] - g) * s + 2.0 * c * b;
+                p = s * r;
+                d[i + 1] = g + p;
+                g = c * r - b;
+                for (int k = 0; k < n; k++) {
+                    const double zk1 = z[k * n + i + 1], zk = z[k * n + i];
+                    z[k * n + i + 1] = s * zk + c * zk1;
+                    z[k * n + i] = c * zk - s * zk1;
+                }
+            }
+            if (r == 0.0 && i >= l) continue;
+            d[l] -= p;
+            e[l] = g;
+            e[m] = 0.0;
+        }
+    }
+    // ascending order
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; i++) idx[i] = i;
+    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return d[a] < d[b]; });
+    std::vector<double> d2(n), z2((size_t)n * n);
+    for (int k = 0; k < n; k++) {
+        d2[k] = d[idx[k]];
+        for (int i = 0; i < n; i++) z2[(size_t)i * n + k] = z[(size_t)i * n + idx[k]];
+    }
+    std::memcpy(d, d2.data(), sizeof(double) * n);
+    std::memcpy(z, z2.data(), sizeof(double) * n * n);
+    return 0;
+}
+
+cudaError_t launch_laplacian(const float2 *U, const float2 *in, const float2 *z, float2 *out, int L, int T, int nvec,
+                             long long ts_in, long long ts_z, long long ts_out, float a, float b, float c, cudaStream_t s)
+{
+    const long long V = (long long)L * L * L;
+    if (T > 65535 || nvec > 65535) return cudaErrorInvalidValue;
+    dim3 g((unsigned)((V + LAP_THREADS - 1) / LAP_THREADS), (unsigned)T, (unsigned)nvec);
+    lap_kernel<<<g, LAP_THREADS, 0, s>>>(U, in, z, out, L, ts_in, ts_z, ts_out, a, b, c);
+    return cudaGetLastError();
+}
+
+}  // namespace laph
+
+using namespace laph;
+
+#define LCK(call)                                                   \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) {                                    \
+            rc = laph::record_cuda_error(e_, #call);                \
+            goto done;                                              \
+        }                                                           \
+    } while (0)
+
+extern "C" {
+
+int laph_laplacian(const void *U, const void *f, void *out, int L, int T, int nvec, void *stream)
+{
+    if (!U || !f || !out || L < 2 || L > 1024 || T < 1 || T > 65535 || nvec < 1 || nvec > 65535) return LAPH_ERR_ARG;
+    if (((uintptr_t)U | (uintptr_t)f | (uintptr_t)out) % 8) return LAPH_ERR_ARG;
+    const long long V = (long long)L * L * L;
+    cudaError_t e = launch_laplacian((const float2 *)U, (const float2 *)f, nullptr, (float2 *)out, L, T, nvec,
+                                     (long long)nvec * V * 3, 0, (long long)nvec * V * 3, 1.f, 0.f, 0.f,
+                                     (cudaStream_t)stream);
+    return e == cudaSuccess ? LAPH_OK : laph::record_cuda_error(e, "laplacian");
+}
+
+int laph_tridiag_eigen(int n, double *d, const double *e, double *z)
+{
+    if (n < 1 || !d || (!e && n > 1) || !z) return LAPH_ERR_ARG;
+    return laph::tridiag_eigen(n, d, e, z) == 0 ? LAPH_OK : LAPH_ERR_ARG;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Device workspace of one solve, offsets 256-byte aligned.  The basis holds
+// m + 1 vectors of every timeslice; after the Ritz vectors have been formed it
+// is reused for (-Delta) applied to them.
+struct LzLayout {
+    size_t basis, w, ya, yb, yc, X, dots, dscale, dnorm, dS, dred, dlam, dperm, total;
+};
+
+LzLayout lz_layout(long long K, int T, int m, int nr)
+{
+    LzLayout l{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) / 256 * 256;
+        return o;
+    };
+    l.basis = take(sizeof(float2) * (size_t)K * (m + 1) * T);
+    l.w = take(sizeof(float2) * (size_t)K * T);
+    l.ya = take(sizeof(float2) * (size_t)K * T);
+    l.yb = take(sizeof(float2) * (size_t)K * T);
+    l.yc = take(sizeof(float2) * (size_t)K * T);
+    l.X = take(sizeof(float2) * (size_t)K * nr * T);
+    l.dots = take(sizeof(double2) * (size_t)(m + 1) * T);
+    l.dscale = take(sizeof(double) * T);
+    l.dnorm = take(sizeof(double) * T);
+    l.dS = take(sizeof(double) * (size_t)T * m * nr);
+    l.dred = take(sizeof(double) * 2 * (size_t)T * nr);
+    l.dlam = take(sizeof(double) * (size_t)T * nr);
+    l.dperm = take(sizeof(int) * (size_t)T * nr);
+    l.total = off;
+    return l;
+}
+
+int lz_check(int L, int T, int n_ev, const laph_lanczos_params *prm)
+{
+    if (!prm || L < 2 || L > 1024 || T < 1 || T > 65535 || n_ev < 1) return LAPH_ERR_ARG;
+    const long long K = 3LL * L * L * L;
+    const int m = prm->n_krylov;
+    if (m < n_ev || m > 4096 || (long long)m > K || prm->cheb_degree < 0 || prm->cheb_degree > 10000) return LAPH_ERR_ARG;
+    if (prm->cheb_degree > 0 && !(prm->cheb_lo > 0.0 && prm->cheb_lo < 12.0)) return LAPH_ERR_ARG;
+    return LAPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int laph_lanczos_workspace_size(int L, int T, int n_ev, const laph_lanczos_params *prm, size_t *bytes)
+{
+    if (!bytes) return LAPH_ERR_ARG;
+    const int rc = lz_check(L, T, n_ev, prm);
+    if (rc != LAPH_OK) return rc;
+    *bytes = lz_layout(3LL * L * L * L, T, prm->n_krylov, n_ev).total;
+    return LAPH_OK;
+}
+
+int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_params *prm, void *evecs, double *evals,
+                 double *resid, void *workspace, size_t workspace_bytes, laph_lanczos_stats *stats, void *stream)
+{
+    if (!U || !evecs || !evals) return LAPH_ERR_ARG;
+    int rc = lz_check(L, T, n_ev, prm);
+    if (rc != LAPH_OK) return rc;
+    if (((uintptr_t)U | (uintptr_t)evecs) % 8) return LAPH_ERR_ARG;
+    const long long V = (long long)L * L * L, K = 3 * V;
+    const int m = prm->n_krylov, nr = n_ev, d = prm->cheb_degree;
+    const LzLayout lay = lz_layout(K, T, m, nr);
+    if (workspace && (workspace_bytes < lay.total || (uintptr_t)workspace % 256)) return LAPH_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const float2 *Ud = (const float2 *)U;
+    char *ws = (char *)workspace, *owned = nullptr;
+    cudaEvent_t ev[7] = {};   // call start, loop start, iteration (apply, orth, end), loop end, call end
+    laph_lanczos_stats st = {};
+    const long long ts_b = (long long)(m + 1) * K;   // basis of one timeslice
+    std::vector<double> alpha((size_t)T * m, 0.0), beta((size_t)T * m, 0.0), h_dots(2 * (size_t)T * (m + 1)),
+        h_norm(T), h_scale(T), h_S((size_t)T * m * nr, 0.0), h_red(2 * (size_t)T * nr);
+    const unsigned blocks_e = (unsigned)((K + LAP_THREADS - 1) / LAP_THREADS);
+    const unsigned blocks_dot = (unsigned)((K + LAP_THREADS * DOT_EPT - 1) / (LAP_THREADS * DOT_EPT));
+    const unsigned blocks_upd = (unsigned)((K + LAP_THREADS * UPD_EPT - 1) / (LAP_THREADS * UPD_EPT));
+    const double cheb_c = 0.5 * (12.0 + prm->cheb_lo), cheb_e = 0.5 * (12.0 - prm->cheb_lo);
+    float2 *basis, *w, *ya, *yb, *yc, *X, *Y;
+    double2 *dots;
+    double *dscale, *dnorm, *dS, *dred, *dlam;
+    int *dperm;
+
+    if (stats) {
+        for (auto &e : ev) LCK(cudaEventCreate(&e));
+        LCK(cudaEventRecord(ev[0], s));
+    }
+    if (!ws) {
+        LCK(cudaMallocAsync((void **)&owned, lay.total, s));
+        ws = owned;
+    }
+    basis = (float2 *)(ws + lay.basis);
+    w = (float2 *)(ws + lay.w);
+    ya = (float2 *)(ws + lay.ya);
+    yb = (float2 *)(ws + lay.yb);
+    yc = (float2 *)(ws + lay.yc);
+    X = (float2 *)(ws + lay.X);
+    Y = basis;
+    dots = (double2 *)(ws + lay.dots);
+    dscale = (double *)(ws + lay.dscale);
+    dnorm = (double *)(ws + lay.dnorm);
+    dS = (double *)(ws + lay.dS);
+    dred = (double *)(ws + lay.dred);
+    dlam = (double *)(ws + lay.dlam);
+    dperm = (int *)(ws + lay.dperm);
+
+    {
+        // the operator on the newest basis vector v (of every timeslice) -> w
+        auto apply = [&](const float2 *v) -> cudaError_t {
+            const int n_apply = d == 0 ? 1 : d;
+            st.launches += n_apply;
+            st.apply_launches += n_apply;
+            if (d == 0) return launch_laplacian(Ud, v, nullptr, w, L, T, 1, ts_b, 0, K, 1.f, 0.f, 0.f, s);
+            // Chebyshev recurrence in B = (A - c) / e:
+            //   y_0 = v, y_1 = B v, y_{k+1} = 2 B y_k - y_{k-1}, result y_d in w;
+            // three scratch vectors rotate, so no step writes an operand it reads.
+            float2 *y1 = d == 1 ? w : ya;
+            cudaError_t e = launch_laplacian(Ud, v, nullptr, y1, L, T, 1, ts_b, 0, K, (float)(1.0 / cheb_e),
+                                             (float)(-cheb_c / cheb_e), 0.f, s);
+            const float2 *prev = v;
+            long long ts_prev = ts_b;
+            float2 *cur = y1;
+            for (int k = 2; k <= d && e == cudaSuccess; k++) {
+                float2 *dst = k == d ? w : (cur != ya && prev != ya ? ya : (cur != yb && prev != yb ? yb : yc));
+                e = launch_laplacian(Ud, cur, prev, dst, L, T, 1, K, ts_prev, K, (float)(2.0 / cheb_e),
+                                     (float)(-2.0 * cheb_c / cheb_e), -1.f, s);
+                prev = cur;
+                ts_prev = K;
+                cur = dst;
+            }
+            return e;
+        };
+        // removes from w its components along basis vectors [0, nj), twice
+        // ("twice is enough"); the first pass's coefficients land in h_dots,
+        // |w|^2 of the result in h_norm.  Synchronises the stream.
+        auto orthogonalise = [&](int nj) -> cudaError_t {
+            cudaError_t e = cudaSuccess;
+            for (int pass = 0; pass < 2 && e == cudaSuccess; pass++) {
+                e = cudaMemsetAsync(dots, 0, sizeof(double2) * (m + 1) * T, s);
+                if (e == cudaSuccess && pass == 1) e = cudaMemsetAsync(dnorm, 0, sizeof(double) * T, s);
+                if (e != cudaSuccess) break;
+                dots_kernel<<<dim3(blocks_dot, T), LAP_THREADS, 0, s>>>(basis, ts_b, w, K, K, nj, dots, m + 1);
+                update_kernel<<<dim3(blocks_upd, T), LAP_THREADS, sizeof(float2) * nj, s>>>(
+                    basis, ts_b, w, K, K, nj, dots, m + 1, pass == 1 ? dnorm : nullptr);
+                e = cudaGetLastError();
+                st.launches += 2;
+                if (e == cudaSuccess && pass == 0)
+                    e = cudaMemcpyAsync(h_dots.data(), dots, sizeof(double2) * (m + 1) * T, cudaMemcpyDeviceToHost, s);
+            }
+            if (e == cudaSuccess) e = cudaMemcpyAsync(h_norm.data(), dnorm, sizeof(double) * T, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            return e;
+        };
+        // |w|^2 of every timeslice into h_norm (the inner-product kernel with w as its one basis row)
+        auto norm_w = [&]() -> cudaError_t {
+            cudaError_t e = cudaMemsetAsync(dots, 0, sizeof(double2) * T, s);
+            if (e == cudaSuccess) {
+                dots_kernel<<<dim3(blocks_dot, T), LAP_THREADS, 0, s>>>(w, K, w, K, K, 1, dots, 1);
+                e = cudaGetLastError();
+                st.launches++;
+            }
+            std::vector<double> tmp(2 * (size_t)T);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(tmp.data(), dots, sizeof(double2) * T, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            for (int t = 0; t < T; t++) h_norm[t] = tmp[2 * t];
+            return e;
+        };
+        // basis vector j = w * h_scale
+        auto store = [&](int j) -> cudaError_t {
+            cudaError_t e = cudaMemcpyAsync(dscale, h_scale.data(), sizeof(double) * T, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) return e;
+            scale_kernel<<<dim3(blocks_e, T), LAP_THREADS, 0, s>>>(w, K, basis + (long long)j * K, ts_b, K, dscale);
+            st.launches++;
+            return cudaGetLastError();
+        };
+
+        // start vectors: seeded pattern, normalised
+        LCK(laph::launch_fill_pattern(w, K * T, prm->seed ? prm->seed : 12345u, s));
+        st.launches++;
+        LCK(norm_w());
+        for (int t = 0; t < T; t++) h_scale[t] = 1.0 / std::sqrt(std::max(h_norm[t], 1e-300));
+        LCK(store(0));
+        if (stats) LCK(cudaEventRecord(ev[1], s));
+        for (int j = 0; j < m; j++) {
+            if (stats) LCK(cudaEventRecord(ev[2], s));
+            LCK(apply(basis + (long long)j * K));
+            if (stats) LCK(cudaEventRecord(ev[3], s));
+            LCK(orthogonalise(j + 1));
+            if (stats) {
+                float a = 0.f, o = 0.f;
+                LCK(cudaEventRecord(ev[4], s));
+                LCK(cudaEventSynchronize(ev[4]));
+                LCK(cudaEventElapsedTime(&a, ev[2], ev[3]));
+                LCK(cudaEventElapsedTime(&o, ev[3], ev[4]));
+                st.apply_ms += a;
+                st.orth_ms += o;
+            }
+            bool broke = false;
+            for (int t = 0; t < T; t++) {
+                const double a = h_dots[2 * ((size_t)t * (m + 1) + j)], b = std::sqrt(std::max(h_norm[t], 0.0));
+                alpha[(size_t)t * m + j] = a;
+                beta[(size_t)t * m + j] = b;
+                h_scale[t] = b > 1e-30 ? 1.0 / b : 0.0;
+                if (b < 1e-6 * std::max(1.0, std::fabs(a))) broke = true;
+            }
+            if (j + 1 == m) break;
+            if (broke) {
+                // an invariant subspace: the timeslices concerned continue from a
+                // fresh vector orthogonal to their basis, with a zero coupling
+                LCK(laph::launch_fill_pattern(ya, K * T, 777u + (unsigned)j, s));
+                st.launches++;
+                for (int t = 0; t < T; t++) {
+                    const double a = alpha[(size_t)t * m + j];
+                    if (beta[(size_t)t * m + j] < 1e-6 * std::max(1.0, std::fabs(a))) {
+                        LCK(cudaMemcpyAsync(w + (long long)t * K, ya + (long long)t * K, sizeof(float2) * K,
+                                            cudaMemcpyDeviceToDevice, s));
+                        beta[(size_t)t * m + j] = 0.0;
+                    }
+                }
+                const std::vector<double> keep = h_dots;
+                LCK(orthogonalise(j + 1));
+                h_dots = keep;
+                for (int t = 0; t < T; t++) h_scale[t] = 1.0 / std::sqrt(std::max(h_norm[t], 1e-300));
+            }
+            LCK(store(j + 1));
+        }
+        if (stats) LCK(cudaEventRecord(ev[5], s));
+        // Ritz pairs of the tridiagonal matrices; the wanted end: the smallest
+        // eigenvalues of -Delta, the largest of the filter (times (-1)^d: T_d
+        // grows with sign (-1)^d below the damped interval)
+        {
+            // the timeslices' tridiagonal problems are independent: host threads share them
+            const double sgn = (d % 2) ? -1.0 : 1.0;
+            const int n_thr = (int)std::max(1u, std::min<unsigned>((unsigned)T, std::min(32u, std::thread::hardware_concurrency())));
+            std::vector<int> failed(n_thr, 0);
+            auto work = [&](int id) {
+                std::vector<double> dd(m), ee(m), z((size_t)m * m);
+                for (int t = id; t < T; t += n_thr) {
+                    for (int i = 0; i < m; i++) dd[i] = alpha[(size_t)t * m + i];
+                    for (int i = 0; i + 1 < m; i++) ee[i] = beta[(size_t)t * m + i];
+                    if (laph::tridiag_eigen(m, dd.data(), ee.data(), z.data()) != 0) {
+                        failed[id] = 1;
+                        return;
+                    }
+                    for (int r = 0; r < nr; r++) {
+                        const int k = (d > 0 && sgn > 0) ? m - 1 - r : r;
+                        for (int i = 0; i < m; i++) h_S[((size_t)t * m + i) * nr + r] = z[(size_t)i * m + k];
+                    }
+                }
+            };
+            std::vector<std::thread> pool;
+            for (int id = 1; id < n_thr; id++) pool.emplace_back(work, id);
+            work(0);
+            for (auto &th : pool) th.join();
+            for (int f : failed)
+                if (f) {
+                    rc = LAPH_ERR_ARG;
+                    goto done;
+                }
+        }
+        LCK(cudaMemcpyAsync(dS, h_S.data(), sizeof(double) * T * m * nr, cudaMemcpyHostToDevice, s));
+        ritz_kernel<<<dim3(blocks_e, T, (nr + RT - 1) / RT), LAP_THREADS, 0, s>>>(basis, ts_b, K, m, dS, nr, X,
+                                                                                   K * nr);
+        LCK(cudaGetLastError());
+        // Rayleigh quotients and residuals with -Delta (Y reuses the basis)
+        LCK(launch_laplacian(Ud, X, nullptr, Y, L, T, nr, K * nr, 0, K * nr, 1.f, 0.f, 0.f, s));
+        LCK(cudaMemsetAsync(dred, 0, sizeof(double) * 2 * T * nr, s));
+        st.launches += 5;   // Ritz vectors, -Delta on them, two Rayleigh passes, gather
+        {
+            const unsigned rb = std::min<unsigned>(blocks_e, 64u);
+            rayleigh_kernel<<<dim3(rb, T, nr), LAP_THREADS, 0, s>>>(X, Y, K * nr, K, 0, nullptr, nr, dred);
+            LCK(cudaGetLastError());
+            LCK(cudaMemcpyAsync(h_red.data(), dred, sizeof(double) * 2 * T * nr, cudaMemcpyDeviceToHost, s));
+            LCK(cudaStreamSynchronize(s));
+            std::vector<double> lam((size_t)T * nr), xx((size_t)T * nr);
+            for (size_t i = 0; i < (size_t)T * nr; i++) {
+                xx[i] = h_red[2 * i + 1];
+                lam[i] = h_red[2 * i] / std::max(xx[i], 1e-300);
+            }
+            LCK(cudaMemcpyAsync(dlam, lam.data(), sizeof(double) * T * nr, cudaMemcpyHostToDevice, s));
+            LCK(cudaMemsetAsync(dred, 0, sizeof(double) * 2 * T * nr, s));
+            rayleigh_kernel<<<dim3(rb, T, nr), LAP_THREADS, 0, s>>>(X, Y, K * nr, K, 1, dlam, nr, dred);
+            LCK(cudaGetLastError());
+            LCK(cudaMemcpyAsync(h_red.data(), dred, sizeof(double) * 2 * T * nr, cudaMemcpyDeviceToHost, s));
+            LCK(cudaStreamSynchronize(s));
+            // ascending eigenvalues per timeslice; the vectors leave with unit norm
+            std::vector<int> perm((size_t)T * nr);
+            std::vector<double> inv_norm((size_t)T * nr);
+            for (int t = 0; t < T; t++) {
+                int *pt = perm.data() + (size_t)t * nr;
+                for (int r = 0; r < nr; r++) pt[r] = r;
+                std::sort(pt, pt + nr, [&](int a, int b) { return lam[(size_t)t * nr + a] < lam[(size_t)t * nr + b]; });
+                for (int r = 0; r < nr; r++) {
+                    const size_t src = (size_t)t * nr + pt[r];
+                    evals[(size_t)t * nr + r] = lam[src];
+                    inv_norm[(size_t)t * nr + r] = 1.0 / std::sqrt(std::max(xx[src], 1e-300));
+                    if (resid) resid[(size_t)t * nr + r] = std::sqrt(std::max(h_red[2 * src], 0.0) / std::max(xx[src], 1e-300));
+                }
+            }
+            LCK(cudaMemcpyAsync(dperm, perm.data(), sizeof(int) * T * nr, cudaMemcpyHostToDevice, s));
+            LCK(cudaMemcpyAsync(dred, inv_norm.data(), sizeof(double) * T * nr, cudaMemcpyHostToDevice, s));
+            gather_kernel<<<dim3(blocks_e, T, nr), LAP_THREADS, 0, s>>>(X, K * nr, dperm, dred, nr, (float2 *)evecs,
+                                                                        K * nr, K);
+            LCK(cudaGetLastError());
+            if (stats) {
+                float tot = 0.f, setup = 0.f, ritz = 0.f;
+                LCK(cudaEventRecord(ev[6], s));
+                LCK(cudaEventSynchronize(ev[6]));
+                LCK(cudaEventElapsedTime(&tot, ev[0], ev[6]));
+                LCK(cudaEventElapsedTime(&setup, ev[0], ev[1]));
+                LCK(cudaEventElapsedTime(&ritz, ev[5], ev[6]));
+                st.total_ms = tot;
+                st.setup_ms = setup;
+                st.ritz_ms = ritz;
+                *stats = st;
+            }
+            LCK(cudaStreamSynchronize(s));
+        }
+    }
+done:
+    for (auto &e : ev)
+        if (e) cudaEventDestroy(e);
+    if (owned) cudaFreeAsync(owned, s);
+    cudaStreamSynchronize(s);
+    return rc;
+}
+
+}  // extern "C"

@@ -163,3 +163,30 @@ def random_links(L: int, T: int = 1, instance: int = 0, eps: float | None = None
             det = np.linalg.det(q)
             out[t] = (q / (det ** (1.0 / 3.0))[:, None, None]).reshape(3, V, 3, 3)
     return out
+
+
+def random_links_device(L: int, T: int, eps: float, seed: int, device="cuda"):
+    """Smoothed links of the same distribution as random_links(eps=eps), drawn on the device with torch's
+    generator (other numbers than the numpy path, for large benchmark inputs).  The polar factor of
+    M = 1 + i eps H (H Hermitian Gaussian) is unique, so it is computed by the Newton-Schulz iteration
+    X <- X (3 - X^dagger X) / 2 from X = M / |M|_F (singular values in (0, 1], converging to 1), using batched
+    3 x 3 products only; then divided by a cube root of its determinant.  complex64 [T][3][L^3][3][3]."""
+    import torch
+    V = L ** 3
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    out = torch.empty((T, 3, V, 3, 3), dtype=torch.complex64, device=device)
+    eye = torch.eye(3, dtype=torch.complex128, device=device)
+    for t in range(T):
+        h = torch.view_as_complex(torch.randn((3 * V, 3, 3, 2), generator=g, device=device, dtype=torch.float64))
+        h = 0.5 * (h + h.conj().transpose(1, 2))
+        x = eye + 1j * eps * h
+        x = x / torch.linalg.vector_norm(x, dim=(1, 2))[:, None, None]
+        for _ in range(40):
+            x = 0.5 * x @ (3.0 * eye - x.conj().transpose(1, 2) @ x)
+        a, b, c = x[:, 0], x[:, 1], x[:, 2]
+        det = (a[:, 0] * (b[:, 1] * c[:, 2] - b[:, 2] * c[:, 1]) - a[:, 1] * (b[:, 0] * c[:, 2] - b[:, 2] * c[:, 0])
+               + a[:, 2] * (b[:, 0] * c[:, 1] - b[:, 1] * c[:, 0]))
+        x = x * torch.exp(-1j * torch.angle(det) / 3.0)[:, None, None]
+        out[t] = x.reshape(3, V, 3, 3).to(torch.complex64)
+    return out

@@ -27,7 +27,8 @@ def test_header_declares_the_boundary():
     for must in ["laph_baryon_blocks", "laph_meson_blocks", "laph_triplet_blocks", "laph_doublet_blocks",
                  "laph_plan_execute_fields", "laph_projection", "laph_plan_create", "laph_plan_execute",
                  "laph_plan_workspace_size", "laph_plan_destroy", "laph_phase_table", "laph_diquarks",
-                 "laph_baryon_dense", "laph_get_device_status", "laph_triple_index", "laph_status_string"]:
+                 "laph_baryon_dense", "laph_get_device_status", "laph_triple_index", "laph_status_string",
+                 "laph_laplacian", "laph_lanczos", "laph_tridiag_eigen"]:
         assert must in names
 
 
@@ -104,6 +105,55 @@ def test_entry_points_reject_null_pointers(lib):
     assert lib.laph_plan_execute_fields(None, None, None, None, None) == binding.LAPH_ERR_ARG
     assert lib.laph_projection(None, None, 4, 1, 8, 5, mom, 1, None, 1, None) == binding.LAPH_ERR_ARG
     assert lib.laph_projection(None, None, 4, 1, 8, 0, mom, 1, ctypes.c_void_p(16), 1, None) == binding.LAPH_ERR_ARG
+    fake = ctypes.c_void_p(256)
+    assert lib.laph_laplacian(None, fake, fake, 4, 1, 1, None) == binding.LAPH_ERR_ARG
+    assert lib.laph_laplacian(fake, fake, fake, 1, 1, 1, None) == binding.LAPH_ERR_ARG          # L < 2
+    assert lib.laph_laplacian(fake, fake, ctypes.c_void_p(260), 4, 1, 1, None) == binding.LAPH_ERR_ARG   # misaligned
+    ev = (ctypes.c_double * 64)()
+    ok = binding.laph_lanczos_params(40, 0, 0.0, 0)
+    assert lib.laph_lanczos(None, 4, 1, 8, ctypes.byref(ok), fake, ev, None, None, 0, None, None) == binding.LAPH_ERR_ARG
+    for bad in [binding.laph_lanczos_params(4, 0, 0.0, 0),        # m < n_ev
+                binding.laph_lanczos_params(200, 0, 0.0, 0),      # m > 3 L^3 = 192
+                binding.laph_lanczos_params(40, 8, 0.0, 0),       # filter without a bound
+                binding.laph_lanczos_params(40, 8, 12.5, 0),      # bound above the spectrum
+                binding.laph_lanczos_params(40, -1, 1.0, 0)]:
+        assert lib.laph_lanczos(fake, 4, 1, 8, ctypes.byref(bad), fake, ev, None, None, 0, None, None) == binding.LAPH_ERR_ARG
+        n = ctypes.c_size_t(0)
+        assert lib.laph_lanczos_workspace_size(4, 1, 8, ctypes.byref(bad), ctypes.byref(n)) == binding.LAPH_ERR_ARG
+    assert lib.laph_tridiag_eigen(0, None, None, None) == binding.LAPH_ERR_ARG
+    # workspace: the size query needs no GPU; a workspace too small or misaligned is refused before any launch
+    assert binding.lanczos_workspace_size(32, 64, 64, 160, 40, 0.95) >= 8 * 64 * 3 * 32 ** 3 * (160 + 1 + 64)
+    assert lib.laph_lanczos(fake, 4, 1, 8, ctypes.byref(ok), fake, ev, None, fake, 1024, None,
+                            None) == binding.LAPH_ERR_WORKSPACE
+    assert lib.laph_lanczos(fake, 4, 1, 8, ctypes.byref(ok), fake, ev, None, ctypes.c_void_p(264), 1 << 30, None,
+                            None) == binding.LAPH_ERR_WORKSPACE
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 17, 150])
+def test_tridiagonal_eigensolver_against_numpy(lib, n):
+    """The host QL solver behind the Lanczos Ritz values: eigenvalues against numpy's dense solver, eigenvectors
+    through the eigen-equation and orthonormality, on random matrices with some zero couplings (split blocks)."""
+    import numpy as np
+    from paper_2510_26313_gb300 import binding
+    rng = np.random.default_rng(n)
+    d = rng.standard_normal(n)
+    e = rng.standard_normal(max(n - 1, 0))
+    e[5::11] = 0.0
+    Tm = np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+    w, z = binding.tridiag_eigen(d, e)
+    np.testing.assert_allclose(w, np.linalg.eigvalsh(Tm), atol=1e-12 * max(1.0, np.abs(w).max()))
+    np.testing.assert_allclose(Tm @ z, z * w, atol=1e-12 * max(1.0, np.abs(w).max()))
+    np.testing.assert_allclose(z.T @ z, np.eye(n), atol=1e-12)
+
+
+def test_tridiagonal_eigensolver_on_the_free_chain():
+    """-1, 2, -1 chain of n sites (open ends): eigenvalues 2 - 2 cos(pi k / (n + 1)), k = 1..n."""
+    import numpy as np
+    from paper_2510_26313_gb300 import binding
+    ensure_built()
+    n = 64
+    w, _ = binding.tridiag_eigen(np.full(n, 2.0), np.full(n - 1, -1.0))
+    np.testing.assert_allclose(w, 2 - 2 * np.cos(np.pi * np.arange(1, n + 1) / (n + 1)), atol=1e-13)
 
 
 def test_product_path_does_not_reference_the_oracle():

@@ -1,0 +1,164 @@
+"""GPU parity of the 3-d gauge-covariant Laplacian and of the batched Lanczos eigensolver against the FP64 oracle
+(paper, section "Innovations", subsection "Scalable Lanczos Eigensolver").
+
+- The Laplacian: element by element against the oracle's stencil, on rough (Haar) and smooth links, at lattice
+  sizes from L = 2 (both neighbours of a site coincide) to L = 32 (the size of the L=32, T=64 workload).
+- Lanczos: eigenvalues against the oracle's dense Hermitian eigensolver where the dense matrix is small
+  (L <= 8), eigenvectors through their overlap with the oracle's, independence of the timeslices of a batch,
+  and at L = 16 / 32 the properties that hold at any size (orthonormal vectors, small residuals recomputed in
+  FP64 by the oracle's stencil, agreement of two runs from different start vectors).
+
+Tolerances.  The vectors are FP32 and the inner products FP64: the operator applied in FP32 carries a relative
+error of a few 1e-7 of |(-Delta)| <= 12, so a Rayleigh quotient of a converged vector is good to about 1e-5 in
+absolute terms; eigenvalues are compared at 5e-5, residuals bounded at 1e-3 (relative to the spectral radius).
+"""
+import numpy as np
+import pytest
+
+from helpers import ensure_built, rel_frob
+from oracle import oracle as O
+from paper_2510_26313_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def laph():
+    ensure_built()
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2510_26313_gb300 import binding
+    return binding
+
+
+def oracle_lap(U, f, L):
+    return np.stack([O.laplacian(U[t], f[t], L) for t in range(U.shape[0])])
+
+
+@pytest.mark.parametrize("L,T,nvec,eps", [(2, 1, 2, None), (3, 2, 3, None), (5, 2, 1, 0.3), (8, 3, 2, None),
+                                          (7, 1, 4, 0.1)])
+def test_laplacian_matches_oracle(laph, L, T, nvec, eps):
+    import torch
+    U = synth.random_links(L, T, instance=L + 10 * T, eps=eps)
+    f = synth.random_phi(L, nvec, T=T, instance=3 * L)
+    got = laph.laplacian(torch.from_numpy(U).cuda(), torch.from_numpy(f).cuda(), L).cpu().numpy()
+    ref = oracle_lap(U, f, L)
+    e = rel_frob(got, ref)
+    print(f"L={L} T={T} nvec={nvec} eps={eps}: rel {e:.2e}")
+    assert e <= 1e-6
+
+
+@pytest.mark.parametrize("L", [16, 32])
+def test_laplacian_at_size_matches_oracle(laph, L):
+    import torch
+    U = synth.random_links(L, 2, instance=5, eps=0.2)
+    f = synth.random_phi(L, 1, T=2, instance=6)
+    got = laph.laplacian(torch.from_numpy(U).cuda(), torch.from_numpy(f).cuda(), L).cpu().numpy()
+    assert rel_frob(got, oracle_lap(U, f, L)) <= 1e-6
+
+
+def test_laplacian_free_field_plane_wave(laph):
+    """U = 1: a plane wave is an eigenvector with eigenvalue sum_mu 4 sin^2(pi k_mu / L)."""
+    import torch
+    L = 12
+    V = L ** 3
+    U = np.broadcast_to(np.eye(3, dtype=np.complex64), (1, 3, V, 3, 3)).copy()
+    x = np.arange(V)
+    c = np.stack([x % L, (x // L) % L, x // (L * L)], axis=1)
+    k = np.array([1, 5, 11])
+    f = (np.exp(2j * np.pi * (c @ k) / L)[:, None] * np.array([1.0, -0.5j, 0.25])[None, :]).astype(np.complex64)
+    got = laph.laplacian(torch.from_numpy(U).cuda(), torch.from_numpy(f[None, None].copy()).cuda(), L)
+    lam = sum(4 * np.sin(np.pi * kk / L) ** 2 for kk in k)
+    np.testing.assert_allclose(got[0, 0].cpu().numpy(), lam * f, atol=2e-6)
+
+
+def check_against_dense(U, L, n_ev, ev, vecs, resid, tol_ev=5e-5):
+    for t in range(U.shape[0]):
+        w, v = O.lowest_eigenpairs(U[t], L, n_ev + 1)
+        err = np.abs(ev[t] - w[:n_ev]).max()
+        print(f"t={t}: max |dlambda| {err:.2e}, max resid {resid[t].max():.2e}")
+        assert err <= tol_ev
+        assert resid[t].max() <= 1e-3
+        # eigenvectors: overlap with the oracle's, for eigenvalues separated from their neighbours
+        for r in range(n_ev):
+            gap = min(abs(w[r] - w[r - 1]) if r > 0 else np.inf, abs(w[r + 1] - w[r]))
+            if gap > 1e-2:
+                ov = abs(np.vdot(v[r].ravel(), vecs[t, r].ravel().astype(np.complex128)))
+                assert ov >= 1 - 1e-4, (t, r, ov)
+
+
+@pytest.mark.parametrize("L,T,n_ev", [(3, 2, 8), (4, 1, 12)])
+def test_lanczos_on_the_whole_space_matches_the_dense_solver(laph, L, T, n_ev):
+    """n_krylov = 3 L^3: the Krylov space is the whole space, every eigenvalue is found."""
+    import torch
+    U = synth.random_links(L, T, instance=L, eps=None)
+    vecs, ev, res = laph.lanczos(torch.from_numpy(U).cuda(), L, n_ev, 3 * L ** 3)
+    check_against_dense(U, L, n_ev, ev, vecs.cpu().numpy(), res)
+
+
+@pytest.mark.parametrize("degree", [0, 7, 8])
+def test_lanczos_with_and_without_the_chebyshev_filter_at_L8(laph, degree):
+    """Smoothed links (eps = 0.6), 24 eigenpairs from a Krylov space of 60 (filtered) or 400 vectors.  The filter
+    bound 1.45 lies in the gap above the 26th eigenvalue of timeslice 0 (1.448 < 1.45 < 1.454); an odd degree
+    makes the wanted end the most negative one."""
+    import torch
+    L, T, n_ev = 8, 1, 24
+    U = synth.random_links(L, T, instance=8, eps=0.6)
+    m = 400 if degree == 0 else 60
+    vecs, ev, res = laph.lanczos(torch.from_numpy(U).cuda(), L, n_ev, m, cheb_degree=degree, cheb_lo=1.45)
+    check_against_dense(U, L, n_ev, ev, vecs.cpu().numpy(), res)
+
+
+def test_lanczos_breakdown_on_the_degenerate_free_field(laph):
+    """U = 1 at L = 3: eigenvalues 0 (x3), 3 (x18), 6 (x36), 9 (x24).  A Krylov space of one start vector holds
+    one vector per eigenspace, so the iteration breaks down and continues from fresh vectors; with 3 L^3 steps
+    every eigenvector is found."""
+    import torch
+    L = 3
+    V = L ** 3
+    U = np.broadcast_to(np.eye(3, dtype=np.complex64), (2, 3, V, 3, 3)).copy()
+    vecs, ev, res = laph.lanczos(torch.from_numpy(U).cuda(), L, 24, 3 * V)
+    ref = np.array([0.0] * 3 + [3.0] * 18 + [6.0] * 3)
+    np.testing.assert_allclose(ev, np.broadcast_to(ref, ev.shape), atol=5e-5)
+    assert res.max() <= 1e-3
+    v = vecs.cpu().numpy().astype(np.complex128).reshape(2, 24, -1)
+    for t in range(2):
+        np.testing.assert_allclose(v[t].conj() @ v[t].T, np.eye(24), atol=1e-4)
+
+
+def test_lanczos_timeslices_are_independent(laph):
+    """A timeslice solved inside a batch gives the eigenvalues it gives alone."""
+    import torch
+    L, T, n_ev = 6, 3, 10
+    U = synth.random_links(L, T, instance=61, eps=0.25)
+    _, ev, _ = laph.lanczos(torch.from_numpy(U).cuda(), L, n_ev, 90, cheb_degree=6, cheb_lo=1.5)
+    _, ev1, _ = laph.lanczos(torch.from_numpy(U[1:2].copy()).cuda(), L, n_ev, 90, cheb_degree=6, cheb_lo=1.5)
+    np.testing.assert_allclose(ev[1], ev1[0], atol=5e-5)
+    for t in range(T):
+        np.testing.assert_allclose(ev[t], O.lowest_eigenpairs(U[t], L, n_ev)[0], atol=5e-5)
+
+
+@pytest.mark.parametrize("L,n_ev,m,d,lo", [(16, 16, 96, 20, 1.05), (32, 64, 160, 40, 0.95)])
+def test_lanczos_at_size_properties(laph, L, n_ev, m, d, lo):
+    """Large lattices (no dense oracle), smoothed links (eps = 0.6): unit, mutually orthogonal vectors; residuals
+    recomputed in FP64 by the oracle's stencil agree with the reported ones and are small; a second start vector
+    gives the same eigenvalues.  L = 32 with 64 eigenpairs is the shape of the L=32, T=64, N=64 workload."""
+    import torch
+    T = 2
+    U = synth.random_links(L, T, instance=L, eps=0.6)
+    Ud = torch.from_numpy(U).cuda()
+    vecs, ev, res = laph.lanczos(Ud, L, n_ev, m, cheb_degree=d, cheb_lo=lo, seed=1)
+    _, ev2, _ = laph.lanczos(Ud, L, n_ev, m, cheb_degree=d, cheb_lo=lo, seed=2)
+    v = vecs.cpu().numpy().astype(np.complex128)
+    print(f"L={L}: ev {ev[0][:4]} ... {ev[0][-1]:.4f}; max resid {res.max():.2e}; run diff {np.abs(ev - ev2).max():.2e}")
+    assert np.all(np.diff(ev, axis=1) >= -1e-9)
+    np.testing.assert_allclose(ev, ev2, atol=5e-5)
+    for t in range(T):
+        G = v[t].reshape(n_ev, -1).conj() @ v[t].reshape(n_ev, -1).T
+        assert np.abs(G - np.eye(n_ev)).max() <= 1e-4
+        Av = O.laplacian(U[t], v[t], L)
+        for r in range(0, n_ev, 5):
+            rr = np.linalg.norm(Av[r] - ev[t, r] * v[t, r])
+            assert rr <= 1e-3 * 12
+            assert abs(rr - res[t, r]) <= 1e-4 + 0.05 * rr
+            assert abs(np.vdot(v[t, r], Av[r]).real - ev[t, r]) <= 2e-5
