@@ -210,6 +210,8 @@ typedef struct {
                          which maps [cheb_lo, 12] onto [-1, 1] and magnifies the eigenvalues below cheb_lo */
     double cheb_lo;   /* 0 < cheb_lo < 12 when cheb_degree > 0: above the wanted eigenvalues */
     uint32_t seed;    /* start vectors (0: a fixed default) */
+    int ts_group;     /* timeslices whose filter steps run back to back, so that their links and vectors stay
+                         in L2 across the steps (0: as many as fit in a third of the L2); d > 0 only */
 } laph_lanczos_params;
 
 /* Where the time of one laph_lanczos call goes, from CUDA events recorded on
@@ -230,7 +232,8 @@ typedef struct {
 } laph_lanczos_stats;
 
 /* Bytes of device workspace laph_lanczos needs (about 8 T 3 L^3 (n_krylov +
- * n_ev + 5) bytes: the basis, the Ritz vectors, scratch vectors). */
+ * n_ev + 15) bytes: the basis, the Ritz vectors, scratch vectors and a copy
+ * of the links in the solver's layout). */
 LAPH_API int laph_lanczos_workspace_size(int L, int T, int n_ev, const laph_lanczos_params *params, size_t *bytes);
 
 /* The n_ev lowest eigenpairs of -Delta on every timeslice: Lanczos with full

@@ -101,6 +101,78 @@ __global__ void __launch_bounds__(LAP_THREADS) lap_kernel(const float2 *__restri
     }
 }
 
+// The solver's own layouts, with every warp access 32 consecutive float2:
+// links Us [T][3][9][V] (direction, row-major colour entry, site) and vectors
+// [3][V] per vector (colour, site).  The transpose of the links runs once per
+// solve.
+__global__ void links_soa_kernel(const float2 *__restrict__ U, float2 *__restrict__ Us, long long V)
+{
+    const int t = blockIdx.y;
+    const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= V) return;
+    const float2 *u = U + (long long)t * 27 * V;
+    float2 *o = Us + (long long)t * 27 * V;
+#pragma unroll
+    for (int mu = 0; mu < 3; mu++)
+#pragma unroll
+        for (int rc = 0; rc < 9; rc++) o[(mu * 9 + rc) * V + x] = u[(mu * V + x) * 9 + rc];
+}
+
+// lap_kernel in the solver's layouts: out = a (-Delta in) + b in + c z.
+__global__ void __launch_bounds__(LAP_THREADS) lap_soa_kernel(const float2 *__restrict__ Us,
+                                                              const float2 *__restrict__ in,
+                                                              const float2 *__restrict__ z, float2 *__restrict__ out,
+                                                              int L, long long ts_in, long long ts_z, long long ts_out,
+                                                              float a, float b, float c)
+{
+    const long long V = (long long)L * L * L;
+    const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= V) return;
+    const int t = blockIdx.y, n = blockIdx.z;
+    const float2 *f = in + t * ts_in + n * V * 3;
+    const float2 *Ut = Us + (long long)t * 27 * V;
+    const int c0 = (int)(x % L), c1 = (int)((x / L) % L), c2 = (int)(x / ((long long)L * L));
+    const int cc[3] = {c0, c1, c2};
+    const long long stride[3] = {1, L, (long long)L * L};
+    float2 fx[3], acc[3];
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+        fx[q] = f[q * V + x];
+        acc[q] = make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int mu = 0; mu < 3; mu++) {
+        const long long up = x + (cc[mu] == L - 1 ? -(long long)(L - 1) * stride[mu] : stride[mu]);
+        const long long dn = x - (cc[mu] == 0 ? -(long long)(L - 1) * stride[mu] : stride[mu]);
+        const float2 *um = Ut + (long long)mu * 9 * V;
+        float2 fu[3], fd[3];
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            fu[q] = f[q * V + up];
+            fd[q] = f[q * V + dn];
+        }
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                acc[r] = cfma(__ldg(um + (3 * r + q) * V + x), fu[q], acc[r]);          // U_mu(x)_{rq} f_q(x + mu)
+                acc[r] = cfma_conj(__ldg(um + (3 * q + r) * V + dn), fd[q], acc[r]);    // conj(U_mu(x - mu)_{qr}) f_q(x - mu)
+            }
+    }
+    float2 *o = out + t * ts_out + n * V * 3;
+    const float2 *zz = z ? z + t * ts_z + n * V * 3 : nullptr;
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+        const float2 lap = make_float2(6.f * fx[q].x - acc[q].x, 6.f * fx[q].y - acc[q].y);
+        float2 r = make_float2(a * lap.x + b * fx[q].x, a * lap.y + b * fx[q].y);
+        if (zz) {
+            r.x += c * zz[q * V + x].x;
+            r.y += c * zz[q * V + x].y;
+        }
+        o[q * V + x] = r;
+    }
+}
+
 // Block reduction of a double into thread 0.
 __device__ __forceinline__ double block_sum(double v, double *sh)
 {
@@ -246,15 +318,18 @@ __global__ void __launch_bounds__(LAP_THREADS) update_kernel(const float2 *__res
 }
 
 // out[t] = w[t] * scale[t] (scale from the host, FP64).
+// copy: a second destination (may be null), [T][K].
 __global__ void scale_kernel(const float2 *__restrict__ w, long long ts_w, float2 *__restrict__ out, long long ts_out,
-                             long long K, const double *__restrict__ scale)
+                             long long K, const double *__restrict__ scale, float2 *__restrict__ copy)
 {
     const int t = blockIdx.y;
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= K) return;
     const float s = (float)scale[t];
     const float2 v = w[t * ts_w + e];
-    out[t * ts_out + e] = make_float2(v.x * s, v.y * s);
+    const float2 r = make_float2(v.x * s, v.y * s);
+    out[t * ts_out + e] = r;
+    if (copy) copy[t * K + e] = r;
 }
 
 // X[t][r] = sum_j S[t][j][r] basis[t][j] for r < nr (S real, [T][m][nr]); each
@@ -325,17 +400,20 @@ __global__ void __launch_bounds__(LAP_THREADS) rayleigh_kernel(const float2 *__r
     }
 }
 
-// out[t][r] = X[t][perm[t][r]] * scale[t][r] (vectors of K elements).
+// out[t][r] = X[t][perm[t][r]] * scale[t][r], from the solver's vector
+// layout [3][V] to the caller's [V][3].
 __global__ void gather_kernel(const float2 *__restrict__ X, long long ts_X, const int *__restrict__ perm,
                               const double *__restrict__ scale, int nr, float2 *__restrict__ out, long long ts_out,
-                              long long K)
+                              long long V)
 {
     const int t = blockIdx.y, r = blockIdx.z;
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= K) return;
+    if (e >= 3 * V) return;
+    const long long x = e / 3;
+    const int q = (int)(e - 3 * x);
     const float sc = (float)scale[t * nr + r];
-    const float2 v = X[t * ts_X + (long long)perm[t * nr + r] * K + e];
-    out[t * ts_out + (long long)r * K + e] = make_float2(v.x * sc, v.y * sc);
+    const float2 v = X[t * ts_X + (long long)perm[t * nr + r] * 3 * V + q * V + x];
+    out[t * ts_out + (long long)r * 3 * V + e] = make_float2(v.x * sc, v.y * sc);
 }
 
 }  // namespace
@@ -419,6 +497,16 @@ cudaError_t launch_laplacian(const float2 *U, const float2 *in, const float2 *z,
     return cudaGetLastError();
 }
 
+cudaError_t launch_lap_soa(const float2 *Us, const float2 *in, const float2 *z, float2 *out, int L, int T, int nvec,
+                           long long ts_in, long long ts_z, long long ts_out, float a, float b, float c, cudaStream_t s)
+{
+    const long long V = (long long)L * L * L;
+    if (T > 65535 || nvec > 65535) return cudaErrorInvalidValue;
+    dim3 g((unsigned)((V + LAP_THREADS - 1) / LAP_THREADS), (unsigned)T, (unsigned)nvec);
+    lap_soa_kernel<<<g, LAP_THREADS, 0, s>>>(Us, in, z, out, L, ts_in, ts_z, ts_out, a, b, c);
+    return cudaGetLastError();
+}
+
 }  // namespace laph
 
 using namespace laph;
@@ -459,7 +547,7 @@ namespace {
 // m + 1 vectors of every timeslice; after the Ritz vectors have been formed it
 // is reused for (-Delta) applied to them.
 struct LzLayout {
-    size_t basis, w, ya, yb, yc, X, dots, dscale, dnorm, dS, dred, dlam, dperm, total;
+    size_t Us, basis, w, ya, yb, yc, vin, X, dots, dscale, dnorm, dS, dred, dlam, dperm, total;
 };
 
 LzLayout lz_layout(long long K, int T, int m, int nr)
@@ -471,11 +559,13 @@ LzLayout lz_layout(long long K, int T, int m, int nr)
         off += (bytes + 255) / 256 * 256;
         return o;
     };
+    l.Us = take(sizeof(float2) * (size_t)9 * K * T);
     l.basis = take(sizeof(float2) * (size_t)K * (m + 1) * T);
     l.w = take(sizeof(float2) * (size_t)K * T);
     l.ya = take(sizeof(float2) * (size_t)K * T);
     l.yb = take(sizeof(float2) * (size_t)K * T);
     l.yc = take(sizeof(float2) * (size_t)K * T);
+    l.vin = take(sizeof(float2) * (size_t)K * T);
     l.X = take(sizeof(float2) * (size_t)K * nr * T);
     l.dots = take(sizeof(double2) * (size_t)(m + 1) * T);
     l.dscale = take(sizeof(double) * T);
@@ -495,6 +585,7 @@ int lz_check(int L, int T, int n_ev, const laph_lanczos_params *prm)
     const int m = prm->n_krylov;
     if (m < n_ev || m > 4096 || (long long)m > K || prm->cheb_degree < 0 || prm->cheb_degree > 10000) return LAPH_ERR_ARG;
     if (prm->cheb_degree > 0 && !(prm->cheb_lo > 0.0 && prm->cheb_lo < 12.0)) return LAPH_ERR_ARG;
+    if (prm->ts_group < 0) return LAPH_ERR_ARG;
     return LAPH_OK;
 }
 
@@ -523,9 +614,11 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
     const LzLayout lay = lz_layout(K, T, m, nr);
     if (workspace && (workspace_bytes < lay.total || (uintptr_t)workspace % 256)) return LAPH_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
-    const float2 *Ud = (const float2 *)U;
     char *ws = (char *)workspace, *owned = nullptr;
     cudaEvent_t ev[7] = {};   // call start, loop start, iteration (apply, orth, end), loop end, call end
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t filter = nullptr;
     laph_lanczos_stats st = {};
     const long long ts_b = (long long)(m + 1) * K;   // basis of one timeslice
     std::vector<double> alpha((size_t)T * m, 0.0), beta((size_t)T * m, 0.0), h_dots(2 * (size_t)T * (m + 1)),
@@ -534,7 +627,22 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
     const unsigned blocks_dot = (unsigned)((K + LAP_THREADS * DOT_EPT - 1) / (LAP_THREADS * DOT_EPT));
     const unsigned blocks_upd = (unsigned)((K + LAP_THREADS * UPD_EPT - 1) / (LAP_THREADS * UPD_EPT));
     const double cheb_c = 0.5 * (12.0 + prm->cheb_lo), cheb_e = 0.5 * (12.0 - prm->cheb_lo);
-    float2 *basis, *w, *ya, *yb, *yc, *X, *Y;
+    // filter steps run group by group of timeslices, so that a group's links
+    // and the five vectors the recurrence touches, 8 (27 + 15) V bytes per
+    // timeslice, stay in L2 across its d steps: groups filling about 70% of the
+    // L2 (measured at L = 32, T = 64 on GB300: 8 timeslices, 88 MB, take 0.71x
+    // the time of one group of all 64; 16 timeslices overflow it)
+    int tg = prm->ts_group;
+    if (tg == 0) {
+        int dev = 0, l2 = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess &&
+            l2 > 0)
+            tg = (int)std::max<long long>(1, (long long)(0.7 * l2) / (8 * 42 * V));
+        else
+            tg = 1;
+    }
+    tg = std::min(tg, T);
+    float2 *Ud, *basis, *w, *ya, *yb, *yc, *vin, *X, *Y;
     double2 *dots;
     double *dscale, *dnorm, *dS, *dred, *dlam;
     int *dperm;
@@ -547,11 +655,13 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
         LCK(cudaMallocAsync((void **)&owned, lay.total, s));
         ws = owned;
     }
+    Ud = (float2 *)(ws + lay.Us);
     basis = (float2 *)(ws + lay.basis);
     w = (float2 *)(ws + lay.w);
     ya = (float2 *)(ws + lay.ya);
     yb = (float2 *)(ws + lay.yb);
     yc = (float2 *)(ws + lay.yc);
+    vin = (float2 *)(ws + lay.vin);
     X = (float2 *)(ws + lay.X);
     Y = basis;
     dots = (double2 *)(ws + lay.dots);
@@ -564,29 +674,49 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
 
     {
         // the operator on the newest basis vector v (of every timeslice) -> w
-        auto apply = [&](const float2 *v) -> cudaError_t {
-            const int n_apply = d == 0 ? 1 : d;
-            st.launches += n_apply;
-            st.apply_launches += n_apply;
-            if (d == 0) return launch_laplacian(Ud, v, nullptr, w, L, T, 1, ts_b, 0, K, 1.f, 0.f, 0.f, s);
-            // Chebyshev recurrence in B = (A - c) / e:
-            //   y_0 = v, y_1 = B v, y_{k+1} = 2 B y_k - y_{k-1}, result y_d in w;
-            // three scratch vectors rotate, so no step writes an operand it reads.
-            float2 *y1 = d == 1 ? w : ya;
-            cudaError_t e = launch_laplacian(Ud, v, nullptr, y1, L, T, 1, ts_b, 0, K, (float)(1.0 / cheb_e),
-                                             (float)(-cheb_c / cheb_e), 0.f, s);
-            const float2 *prev = v;
-            long long ts_prev = ts_b;
-            float2 *cur = y1;
-            for (int k = 2; k <= d && e == cudaSuccess; k++) {
-                float2 *dst = k == d ? w : (cur != ya && prev != ya ? ya : (cur != yb && prev != yb ? yb : yc));
-                e = launch_laplacian(Ud, cur, prev, dst, L, T, 1, K, ts_prev, K, (float)(2.0 / cheb_e),
-                                     (float)(-2.0 * cheb_c / cheb_e), -1.f, s);
-                prev = cur;
-                ts_prev = K;
-                cur = dst;
+        // The Chebyshev filter of the vectors in vin (stride K) into w on stream
+        // cs.  Recurrence in B = (A - c) / e:
+        //   y_0 = v, y_1 = B v, y_{k+1} = 2 B y_k - y_{k-1}, result y_d in w;
+        // three scratch vectors rotate, so no step writes an operand it reads.
+        // All d steps of a group of timeslices run before the next group's.
+        auto filter_launches = [&](cudaStream_t cs) -> cudaError_t {
+            cudaError_t e = cudaSuccess;
+            const float2 *v = vin;
+            const long long ts_v = K;
+            for (int t0 = 0; t0 < T && e == cudaSuccess; t0 += tg) {
+                const int nt = std::min(tg, T - t0);
+                const float2 *Ug = Ud + (long long)t0 * 27 * V;
+                auto at = [&](const float2 *base, long long ts) { return base + (long long)t0 * ts; };
+                float2 *y1 = d == 1 ? w : ya;
+                e = launch_lap_soa(Ug, at(v, ts_v), nullptr, (float2 *)at(y1, K), L, nt, 1, ts_v, 0, K,
+                                     (float)(1.0 / cheb_e), (float)(-cheb_c / cheb_e), 0.f, cs);
+                const float2 *prev = v;
+                long long ts_prev = ts_v;
+                float2 *cur = y1;
+                for (int k = 2; k <= d && e == cudaSuccess; k++) {
+                    float2 *dst = k == d ? w : (cur != ya && prev != ya ? ya : (cur != yb && prev != yb ? yb : yc));
+                    e = launch_lap_soa(Ug, at(cur, K), at(prev, ts_prev), (float2 *)at(dst, K), L, nt, 1, K, ts_prev,
+                                         K, (float)(2.0 / cheb_e), (float)(-2.0 * cheb_c / cheb_e), -1.f, cs);
+                    prev = cur;
+                    ts_prev = K;
+                    cur = dst;
+                }
             }
             return e;
+        };
+        const int n_filter = d * ((T + tg - 1) / tg);
+        // the operator on the newest basis vector v (of every timeslice) -> w; for
+        // the filter v is also in vin, and its launches replay as one CUDA graph
+        auto apply = [&](const float2 *v) -> cudaError_t {
+            if (d == 0) {
+                st.launches++;
+                st.apply_launches++;
+                return launch_lap_soa(Ud, v, nullptr, w, L, T, 1, ts_b, 0, K, 1.f, 0.f, 0.f, s);
+            }
+            st.launches += n_filter;
+            st.apply_launches += n_filter;
+            if (filter) return cudaGraphLaunch(filter, s);
+            return filter_launches(s);
         };
         // removes from w its components along basis vectors [0, nj), twice
         // ("twice is enough"); the first pass's coefficients land in h_dots,
@@ -627,11 +757,28 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
         auto store = [&](int j) -> cudaError_t {
             cudaError_t e = cudaMemcpyAsync(dscale, h_scale.data(), sizeof(double) * T, cudaMemcpyHostToDevice, s);
             if (e != cudaSuccess) return e;
-            scale_kernel<<<dim3(blocks_e, T), LAP_THREADS, 0, s>>>(w, K, basis + (long long)j * K, ts_b, K, dscale);
+            scale_kernel<<<dim3(blocks_e, T), LAP_THREADS, 0, s>>>(w, K, basis + (long long)j * K, ts_b, K, dscale,
+                                                                   d > 0 ? vin : nullptr);
             st.launches++;
             return cudaGetLastError();
         };
 
+        // the links in the solver's layout
+        links_soa_kernel<<<dim3((unsigned)((V + LAP_THREADS - 1) / LAP_THREADS), T), LAP_THREADS, 0, s>>>(
+            (const float2 *)U, Ud, V);
+        LCK(cudaGetLastError());
+        st.launches++;
+        // capture the filter once (on a stream of its own: the caller's may be
+        // the legacy default stream, which cannot capture)
+        if (d > 0 && n_filter > 1) {
+            LCK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+            LCK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+            const cudaError_t e1 = filter_launches(cap);
+            const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+            LCK(e1);
+            LCK(e2);
+            LCK(cudaGraphInstantiate(&filter, graph, 0));
+        }
         // start vectors: seeded pattern, normalised
         LCK(laph::launch_fill_pattern(w, K * T, prm->seed ? prm->seed : 12345u, s));
         st.launches++;
@@ -721,7 +868,7 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
                                                                                    K * nr);
         LCK(cudaGetLastError());
         // Rayleigh quotients and residuals with -Delta (Y reuses the basis)
-        LCK(launch_laplacian(Ud, X, nullptr, Y, L, T, nr, K * nr, 0, K * nr, 1.f, 0.f, 0.f, s));
+        LCK(launch_lap_soa(Ud, X, nullptr, Y, L, T, nr, K * nr, 0, K * nr, 1.f, 0.f, 0.f, s));
         LCK(cudaMemsetAsync(dred, 0, sizeof(double) * 2 * T * nr, s));
         st.launches += 5;   // Ritz vectors, -Delta on them, two Rayleigh passes, gather
         {
@@ -758,7 +905,7 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
             LCK(cudaMemcpyAsync(dperm, perm.data(), sizeof(int) * T * nr, cudaMemcpyHostToDevice, s));
             LCK(cudaMemcpyAsync(dred, inv_norm.data(), sizeof(double) * T * nr, cudaMemcpyHostToDevice, s));
             gather_kernel<<<dim3(blocks_e, T, nr), LAP_THREADS, 0, s>>>(X, K * nr, dperm, dred, nr, (float2 *)evecs,
-                                                                        K * nr, K);
+                                                                        K * nr, V);
             LCK(cudaGetLastError());
             if (stats) {
                 float tot = 0.f, setup = 0.f, ritz = 0.f;
@@ -778,6 +925,9 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
 done:
     for (auto &e : ev)
         if (e) cudaEventDestroy(e);
+    if (filter) cudaGraphExecDestroy(filter);
+    if (graph) cudaGraphDestroy(graph);
+    if (cap) cudaStreamDestroy(cap);
     if (owned) cudaFreeAsync(owned, s);
     cudaStreamSynchronize(s);
     return rc;
