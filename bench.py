@@ -362,7 +362,12 @@ def run_projection(args):
     return 0
 
 
-LANCZOS = dict(L=32, T=64, n_ev=64, m=160, degree=40, lo=0.95, eps=0.6)
+LANCZOS = {
+    # the LapH eigenvectors of the L=32, T=64, N=64 workload
+    "lanczos": dict(L=32, T=64, n_ev=64, m=160, degree=40, lo=0.95, eps=0.6),
+    # a small case of the same kernels for profiler captures (one group of 8 timeslices)
+    "lanczos-small": dict(L=32, T=8, n_ev=16, m=24, degree=8, lo=0.95, eps=0.6),
+}
 
 
 def laplacian_bytes_per_site(with_z: bool) -> int:
@@ -380,7 +385,7 @@ def run_lanczos(args):
     from paper_2510_26313_gb300 import binding as laph
     from oracle import oracle as O
     torch.cuda.set_device(0)
-    c = LANCZOS
+    c = LANCZOS[args.workload]
     L, T, n_ev, m, d, lo = c["L"], c["T"], c["n_ev"], c["m"], c["degree"], c["lo"]
     V = L ** 3
     U = synth.random_links_device(L, T, c["eps"], synth.SEED_BASE + 21)
@@ -563,7 +568,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="f16x3")
-    ap.add_argument("--workload", default="metric", choices=sorted(WORKLOADS) + ["ragged", "triplets", "projection", "lanczos"])
+    ap.add_argument("--workload", default="metric", choices=sorted(WORKLOADS) + ["ragged", "triplets", "projection"] + sorted(LANCZOS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -578,7 +583,7 @@ def main():
         return run_triplets(args)
     if args.workload == "projection":
         return run_projection(args)
-    if args.workload == "lanczos":
+    if args.workload in LANCZOS:
         return run_lanczos(args)
 
     import torch

@@ -211,7 +211,8 @@ typedef struct {
     double cheb_lo;   /* 0 < cheb_lo < 12 when cheb_degree > 0: above the wanted eigenvalues */
     uint32_t seed;    /* start vectors (0: a fixed default) */
     int ts_group;     /* timeslices whose filter steps run back to back, so that their links and vectors stay
-                         in L2 across the steps (0: as many as fit in a third of the L2); d > 0 only */
+                         in L2 across the steps (0: as many as fill about 70% of the L2); d > 0 only */
+    int pdl;          /* 1: filter steps launched as programmatic dependents of their predecessors */
 } laph_lanczos_params;
 
 /* Where the time of one laph_lanczos call goes, from CUDA events recorded on
@@ -245,7 +246,8 @@ LAPH_API int laph_lanczos_workspace_size(int L, int T, int n_ev, const laph_lanc
  * workspace: device memory of laph_lanczos_workspace_size bytes, 256-byte
  * aligned (workspace_bytes its size), or NULL to have the call allocate it on
  * `stream` and free it before returning.  Synchronises the stream once per
- * Krylov step and blocks until done.  LAPH_ERR_ARG for bad parameters,
+ * Krylov step and blocks until done.  LAPH_ERR_ARG for bad parameters
+ * (2 <= L <= 512, n_ev <= n_krylov, the bounds on n_krylov and the filter above),
  * LAPH_ERR_WORKSPACE for a workspace too small or misaligned. */
 LAPH_API int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_params *params, void *evecs,
                           double *evals, double *resid, void *workspace, size_t workspace_bytes,

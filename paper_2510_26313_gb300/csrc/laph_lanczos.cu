@@ -119,21 +119,29 @@ __global__ void links_soa_kernel(const float2 *__restrict__ U, float2 *__restric
 }
 
 // lap_kernel in the solver's layouts: out = a (-Delta in) + b in + c z.
-__global__ void __launch_bounds__(LAP_THREADS) lap_soa_kernel(const float2 *__restrict__ Us,
+// Launched as a programmatic dependent of the previous step (a filter step
+// reads its predecessors' outputs and overwrites the vector read two steps
+// back): it lets the next grid be scheduled at once and waits for the full
+// completion of the previous grid before its first access to vectors.
+__global__ void __launch_bounds__(LAP_THREADS, 4) lap_soa_kernel(const float2 *__restrict__ Us,
                                                               const float2 *__restrict__ in,
                                                               const float2 *__restrict__ z, float2 *__restrict__ out,
                                                               int L, long long ts_in, long long ts_z, long long ts_out,
                                                               float a, float b, float c)
 {
-    const long long V = (long long)L * L * L;
-    const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    // offsets within a timeslice are 32-bit (L <= 512: 9 V < 2^31); two
+    // 32-bit divisions give the coordinates
+    const unsigned uL = (unsigned)L, V = uL * uL * uL;
+    const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= V) return;
     const int t = blockIdx.y, n = blockIdx.z;
-    const float2 *f = in + t * ts_in + n * V * 3;
+    const float2 *f = in + t * ts_in + (long long)n * V * 3;
     const float2 *Ut = Us + (long long)t * 27 * V;
-    const int c0 = (int)(x % L), c1 = (int)((x / L) % L), c2 = (int)(x / ((long long)L * L));
-    const int cc[3] = {c0, c1, c2};
-    const long long stride[3] = {1, L, (long long)L * L};
+    const unsigned q1 = x / uL, c0 = x - q1 * uL, c2 = q1 / uL, c1 = q1 - c2 * uL;
+    const unsigned cc[3] = {c0, c1, c2};
+    const unsigned stride[3] = {1u, uL, uL * uL};
     float2 fx[3], acc[3];
 #pragma unroll
     for (int q = 0; q < 3; q++) {
@@ -142,25 +150,31 @@ __global__ void __launch_bounds__(LAP_THREADS) lap_soa_kernel(const float2 *__re
     }
 #pragma unroll
     for (int mu = 0; mu < 3; mu++) {
-        const long long up = x + (cc[mu] == L - 1 ? -(long long)(L - 1) * stride[mu] : stride[mu]);
-        const long long dn = x - (cc[mu] == 0 ? -(long long)(L - 1) * stride[mu] : stride[mu]);
+        const unsigned up = cc[mu] == uL - 1 ? x - (uL - 1) * stride[mu] : x + stride[mu];
+        const unsigned dn = cc[mu] == 0 ? x + (uL - 1) * stride[mu] : x - stride[mu];
         const float2 *um = Ut + (long long)mu * 9 * V;
-        float2 fu[3], fd[3];
+        // all 24 loads of this direction issued before its multiply-adds
+        float2 fu[3], fd[3], uf[9], ub[9];
 #pragma unroll
         for (int q = 0; q < 3; q++) {
             fu[q] = f[q * V + up];
             fd[q] = f[q * V + dn];
         }
 #pragma unroll
+        for (int k = 0; k < 9; k++) {
+            uf[k] = __ldg(um + k * V + x);
+            ub[k] = __ldg(um + k * V + dn);
+        }
+#pragma unroll
         for (int r = 0; r < 3; r++)
 #pragma unroll
             for (int q = 0; q < 3; q++) {
-                acc[r] = cfma(__ldg(um + (3 * r + q) * V + x), fu[q], acc[r]);          // U_mu(x)_{rq} f_q(x + mu)
-                acc[r] = cfma_conj(__ldg(um + (3 * q + r) * V + dn), fd[q], acc[r]);    // conj(U_mu(x - mu)_{qr}) f_q(x - mu)
+                acc[r] = cfma(uf[3 * r + q], fu[q], acc[r]);          // U_mu(x)_{rq} f_q(x + mu)
+                acc[r] = cfma_conj(ub[3 * q + r], fd[q], acc[r]);     // conj(U_mu(x - mu)_{qr}) f_q(x - mu)
             }
     }
-    float2 *o = out + t * ts_out + n * V * 3;
-    const float2 *zz = z ? z + t * ts_z + n * V * 3 : nullptr;
+    float2 *o = out + t * ts_out + (long long)n * V * 3;
+    const float2 *zz = z ? z + t * ts_z + (long long)n * V * 3 : nullptr;
 #pragma unroll
     for (int q = 0; q < 3; q++) {
         const float2 lap = make_float2(6.f * fx[q].x - acc[q].x, 6.f * fx[q].y - acc[q].y);
@@ -498,13 +512,21 @@ cudaError_t launch_laplacian(const float2 *U, const float2 *in, const float2 *z,
 }
 
 cudaError_t launch_lap_soa(const float2 *Us, const float2 *in, const float2 *z, float2 *out, int L, int T, int nvec,
-                           long long ts_in, long long ts_z, long long ts_out, float a, float b, float c, cudaStream_t s)
+                           long long ts_in, long long ts_z, long long ts_out, float a, float b, float c, cudaStream_t s,
+                           bool pdl = false)
 {
     const long long V = (long long)L * L * L;
     if (T > 65535 || nvec > 65535) return cudaErrorInvalidValue;
-    dim3 g((unsigned)((V + LAP_THREADS - 1) / LAP_THREADS), (unsigned)T, (unsigned)nvec);
-    lap_soa_kernel<<<g, LAP_THREADS, 0, s>>>(Us, in, z, out, L, ts_in, ts_z, ts_out, a, b, c);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((V + LAP_THREADS - 1) / LAP_THREADS), (unsigned)T, (unsigned)nvec);
+    cfg.blockDim = dim3(LAP_THREADS);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, lap_soa_kernel, Us, in, z, out, L, ts_in, ts_z, ts_out, a, b, c);
 }
 
 }  // namespace laph
@@ -580,7 +602,7 @@ LzLayout lz_layout(long long K, int T, int m, int nr)
 
 int lz_check(int L, int T, int n_ev, const laph_lanczos_params *prm)
 {
-    if (!prm || L < 2 || L > 1024 || T < 1 || T > 65535 || n_ev < 1) return LAPH_ERR_ARG;
+    if (!prm || L < 2 || L > 512 || T < 1 || T > 65535 || n_ev < 1) return LAPH_ERR_ARG;
     const long long K = 3LL * L * L * L;
     const int m = prm->n_krylov;
     if (m < n_ev || m > 4096 || (long long)m > K || prm->cheb_degree < 0 || prm->cheb_degree > 10000) return LAPH_ERR_ARG;
@@ -642,6 +664,7 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
             tg = 1;
     }
     tg = std::min(tg, T);
+    const bool pdl = prm->pdl != 0;
     float2 *Ud, *basis, *w, *ya, *yb, *yc, *vin, *X, *Y;
     double2 *dots;
     double *dscale, *dnorm, *dS, *dred, *dlam;
@@ -689,14 +712,14 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
                 auto at = [&](const float2 *base, long long ts) { return base + (long long)t0 * ts; };
                 float2 *y1 = d == 1 ? w : ya;
                 e = launch_lap_soa(Ug, at(v, ts_v), nullptr, (float2 *)at(y1, K), L, nt, 1, ts_v, 0, K,
-                                     (float)(1.0 / cheb_e), (float)(-cheb_c / cheb_e), 0.f, cs);
+                                     (float)(1.0 / cheb_e), (float)(-cheb_c / cheb_e), 0.f, cs, pdl && t0 > 0);
                 const float2 *prev = v;
                 long long ts_prev = ts_v;
                 float2 *cur = y1;
                 for (int k = 2; k <= d && e == cudaSuccess; k++) {
                     float2 *dst = k == d ? w : (cur != ya && prev != ya ? ya : (cur != yb && prev != yb ? yb : yc));
                     e = launch_lap_soa(Ug, at(cur, K), at(prev, ts_prev), (float2 *)at(dst, K), L, nt, 1, K, ts_prev,
-                                         K, (float)(2.0 / cheb_e), (float)(-2.0 * cheb_c / cheb_e), -1.f, cs);
+                                         K, (float)(2.0 / cheb_e), (float)(-2.0 * cheb_c / cheb_e), -1.f, cs, pdl);
                     prev = cur;
                     ts_prev = K;
                     cur = dst;
