@@ -370,11 +370,17 @@ LANCZOS = {
 }
 
 
-def laplacian_bytes_per_site(with_z: bool) -> int:
-    """Algorithmic bytes of one application of -Delta (or one Chebyshev step) per site and vector: the six links
-    touching the site counted once each (3 x 72 B), the input vector, the output and, for a Chebyshev step, the
-    vector y_{k-1} (24 B each)."""
-    return 3 * 72 + 24 + 24 + (24 if with_z else 0)
+# DRAM bytes (read + write) of one lap_soa_kernel launch on a group of 8 timeslices at L=32 with links read as three
+# rows, from the ncu capture summarised in profiles/lap_soa_kernel_L32_T8_group8_full.md (warm L2, the launch shape of
+# every filter launch of the L=32, T=64 workload); to be retaken whenever the kernel changes
+LAP_SOA_TRAFFIC = 10.7e6
+
+
+def laplacian_bytes_per_site(with_z: bool, link_rows: int = 3) -> int:
+    """Algorithmic bytes of one application of -Delta (or one Chebyshev step) per site and vector: the three links
+    leaving the site counted once each (3 x 72 B, or 3 x 48 B when read as two rows), the input vector, the output
+    and, for a Chebyshev step, the vector y_{k-1} (24 B each)."""
+    return 3 * 24 * link_rows + 24 + 24 + (24 if with_z else 0)
 
 
 def run_lanczos(args):
@@ -413,8 +419,10 @@ def run_lanczos(args):
     apply_ms = sum(s["apply_ms"] for s in stats) / args.steps
     orth_ms = sum(s["orth_ms"] for s in stats) / args.steps
     n_apply = stats[0]["apply_launches"]
+    rows = 2 if stats[0]["links_two_rows"] else 3
+    tg = stats[0]["ts_group"]
     # algorithmic bytes: Laplacian launches (the first step of each filter without y_{k-1})
-    per_iter = laplacian_bytes_per_site(False) + (d - 1) * laplacian_bytes_per_site(True)
+    per_iter = laplacian_bytes_per_site(False, rows) + (d - 1) * laplacian_bytes_per_site(True, rows)
     apply_bytes = m * per_iter * V * T
     # orthogonalisation of step j: two passes over the j + 1 basis vectors, each reading them once for the
     # inner products (with w) and once for the update (reading and writing w; the second update also sums |w|^2)
@@ -432,10 +440,11 @@ def run_lanczos(args):
         # eigenvalues copied back, every step
         U_host = U.cpu().pin_memory()
         out_host = torch.empty((T, n_ev, V, 3), dtype=torch.complex64).pin_memory()
+        Ud = torch.empty_like(U)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            Ud = U_host.to("cuda", non_blocking=True)
+            Ud.copy_(U_host, non_blocking=True)
             laph.lanczos(Ud, L, n_ev, m, cheb_degree=d, cheb_lo=lo, out=evecs, workspace=ws, stream=stream)
             out_host.copy_(evecs, non_blocking=True)
             torch.cuda.synchronize()
@@ -466,11 +475,18 @@ def run_lanczos(args):
         "data": f"synthetic smoothed SU(3) links (polar part of 1 + i {c['eps']} H, H Hermitian Gaussian)",
         "config": {"workload": f"L={L},T={T},n_ev={n_ev} (lanczos: m={m}, Chebyshev degree {d}, lo={lo})",
                    "L": L, "T": T, "n_ev": n_ev, "n_krylov": m, "cheb_degree": d, "cheb_lo": lo,
+                   "ts_group": tg, "link_rows": rows,
                    "l2": f"inputs larger than L2: links {U.numel() * 8 / 1e9:.2f} GB, basis "
                          f"{T * (m + 1) * 3 * V * 8 / 1e9:.1f} GB"},
         "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                     "traffic": None, "kernel": "laplacian (Chebyshev steps)" if dominant == "apply" else
-                     "orthogonalisation (dots + update)", "peak_source": src},
+                     "traffic": LAP_SOA_TRAFFIC if (dominant == "apply" and (L, tg, rows) == (32, 8, 3)) else None,
+                     "kernel": "lap_soa_kernel (Chebyshev steps)" if dominant == "apply" else
+                     "dots_kernel + update_kernel (orthogonalisation)", "peak_source": src,
+                     "bytes_per_launch": apply_bytes / n_apply if dominant == "apply" else None,
+                     "note": (f"the filter runs in groups of {tg} timeslices whose links and vectors stay in L2 "
+                              f"across its {d} steps, so its algorithmic bytes are mostly served from L2 and the "
+                              "fraction of the HBM copy peak can exceed 1") if dominant == "apply" and tg < T else
+                             None},
         "phases": {"apply_ms": apply_ms, "apply_gbs": apply_gbs, "apply_launches": n_apply,
                    "orth_ms": orth_ms, "orth_gbs": orth_gbs,
                    "setup_ms": sum(s["setup_ms"] for s in stats) / args.steps,

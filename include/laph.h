@@ -213,6 +213,9 @@ typedef struct {
     int ts_group;     /* timeslices whose filter steps run back to back, so that their links and vectors stay
                          in L2 across the steps (0: as many as fill about 70% of the L2); d > 0 only */
     int pdl;          /* 1: filter steps launched as programmatic dependents of their predecessors */
+    int link_rows;    /* 2: read SU(3) links as their first two rows, the third rebuilt (used only if every
+                         link is SU(3) to FP32 accuracy); 3: all three rows; 0: two rows unless the filter
+                         groups fit in L2 */
 } laph_lanczos_params;
 
 /* Where the time of one laph_lanczos call goes, from CUDA events recorded on
@@ -230,6 +233,10 @@ typedef struct {
     double ritz_ms;
     int64_t launches;
     int64_t apply_launches;
+    int links_two_rows; /* 1: the solver read its copy of the links as two rows (requested or chosen,
+                           and every link SU(3) to FP32 accuracy: third row within 2e-6 of
+                           conj(row0 x row1)) */
+    int ts_group;       /* timeslices per filter group used (T without a filter) */
 } laph_lanczos_stats;
 
 /* Bytes of device workspace laph_lanczos needs (about 8 T 3 L^3 (n_krylov +

@@ -49,13 +49,14 @@ class laph_instance(ctypes.Structure):
 
 class laph_lanczos_params(ctypes.Structure):
     _fields_ = [("n_krylov", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("cheb_lo", ctypes.c_double),
-                ("seed", ctypes.c_uint32), ("ts_group", ctypes.c_int), ("pdl", ctypes.c_int)]
+                ("seed", ctypes.c_uint32), ("ts_group", ctypes.c_int), ("pdl", ctypes.c_int),
+                ("link_rows", ctypes.c_int)]
 
 
 class laph_lanczos_stats(ctypes.Structure):
     _fields_ = [("total_ms", ctypes.c_double), ("setup_ms", ctypes.c_double), ("apply_ms", ctypes.c_double),
                 ("orth_ms", ctypes.c_double), ("ritz_ms", ctypes.c_double), ("launches", ctypes.c_int64),
-                ("apply_launches", ctypes.c_int64)]
+                ("apply_launches", ctypes.c_int64), ("links_two_rows", ctypes.c_int), ("ts_group", ctypes.c_int)]
 
 
 def lib() -> ctypes.CDLL:
@@ -297,7 +298,8 @@ def lanczos_workspace_size(L: int, T: int, n_ev: int, n_krylov: int, cheb_degree
 
 
 def lanczos(U, L: int, n_ev: int, n_krylov: int, cheb_degree: int = 0, cheb_lo: float = 0.0, seed: int = 0,
-            out=None, workspace=None, stream=None, stats=None, ts_group: int = 0, pdl: bool = False):
+            out=None, workspace=None, stream=None, stats=None, ts_group: int = 0, pdl: bool = False,
+            link_rows: int = 0):
     """The n_ev lowest eigenpairs of -Delta per timeslice (blocking).
 
     Returns (evecs complex64 [T][n_ev][L^3][3] on the device, evals float64 [T][n_ev] and
@@ -309,7 +311,7 @@ def lanczos(U, L: int, n_ev: int, n_krylov: int, cheb_degree: int = 0, cheb_lo: 
     T = _check_links(U, L)
     if out is None:
         out = torch.empty((T, n_ev, L ** 3, 3), dtype=torch.complex64, device=U.device)
-    p = laph_lanczos_params(n_krylov, cheb_degree, cheb_lo, seed, ts_group, int(pdl))
+    p = laph_lanczos_params(n_krylov, cheb_degree, cheb_lo, seed, ts_group, int(pdl), link_rows)
     ws = ctypes.c_void_p(workspace.data_ptr()) if workspace is not None else None
     ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     ev = np.zeros((T, n_ev), dtype=np.float64)

@@ -101,21 +101,54 @@ __global__ void __launch_bounds__(LAP_THREADS) lap_kernel(const float2 *__restri
     }
 }
 
+// The third row of an SU(3) matrix from its first two: row2 = conj(row0 x row1)
+// (its rows are orthonormal and its determinant, row2 . (row0 x row1), is 1).
+__device__ __forceinline__ void su3_third_row(float2 *u)
+{
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+        const float2 a = u[k1], b = u[3 + k2], c = u[k2], e = u[3 + k1];
+        // (a b - c e)^*
+        const float re = a.x * b.x - a.y * b.y - (c.x * e.x - c.y * e.y);
+        const float im = a.x * b.y + a.y * b.x - (c.x * e.y + c.y * e.x);
+        u[6 + k] = make_float2(re, -im);
+    }
+}
+
 // The solver's own layouts, with every warp access 32 consecutive float2:
 // links Us [T][3][9][V] (direction, row-major colour entry, site) and vectors
 // [3][V] per vector (colour, site).  The transpose of the links runs once per
-// solve.
-__global__ void links_soa_kernel(const float2 *__restrict__ U, float2 *__restrict__ Us, long long V)
+// solve; it sets *bad when a link's third row differs from the one rebuilt
+// from its first two by more than tol (the links are not SU(3) to FP32
+// accuracy), in which case the stencil reads all three rows.
+constexpr float SU3_TOL = 2e-6f;
+__global__ void links_soa_kernel(const float2 *__restrict__ U, float2 *__restrict__ Us, unsigned V,
+                                 int *__restrict__ bad)
 {
     const int t = blockIdx.y;
-    const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= V) return;
-    const float2 *u = U + (long long)t * 27 * V;
-    float2 *o = Us + (long long)t * 27 * V;
+    const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
+    bool off = false;
+    if (x < V) {
+        const float2 *u = U + (long long)t * 27 * V;
+        float2 *o = Us + (long long)t * 27 * V;
 #pragma unroll
-    for (int mu = 0; mu < 3; mu++)
+        for (int mu = 0; mu < 3; mu++) {
+            float2 m[9];
 #pragma unroll
-        for (int rc = 0; rc < 9; rc++) o[(mu * 9 + rc) * V + x] = u[(mu * V + x) * 9 + rc];
+            for (int rc = 0; rc < 9; rc++) {
+                m[rc] = u[((long long)mu * V + x) * 9 + rc];
+                o[((long long)mu * 9 + rc) * V + x] = m[rc];
+            }
+            float2 r[9];
+#pragma unroll
+            for (int k = 0; k < 6; k++) r[k] = m[k];
+            su3_third_row(r);
+#pragma unroll
+            for (int k = 6; k < 9; k++) off |= !(fabsf(r[k].x - m[k].x) <= SU3_TOL && fabsf(r[k].y - m[k].y) <= SU3_TOL);
+        }
+    }
+    if (__ballot_sync(0xffffffffu, off) && (threadIdx.x & 31) == 0) atomicOr(bad, 1);
 }
 
 // lap_kernel in the solver's layouts: out = a (-Delta in) + b in + c z.
@@ -123,6 +156,8 @@ __global__ void links_soa_kernel(const float2 *__restrict__ U, float2 *__restric
 // reads its predecessors' outputs and overwrites the vector read two steps
 // back): it lets the next grid be scheduled at once and waits for the full
 // completion of the previous grid before its first access to vectors.
+// R12: the links are SU(3) and only their first two rows are read.
+template <bool R12>
 __global__ void __launch_bounds__(LAP_THREADS, 4) lap_soa_kernel(const float2 *__restrict__ Us,
                                                               const float2 *__restrict__ in,
                                                               const float2 *__restrict__ z, float2 *__restrict__ out,
@@ -161,9 +196,13 @@ __global__ void __launch_bounds__(LAP_THREADS, 4) lap_soa_kernel(const float2 *_
             fd[q] = f[q * V + dn];
         }
 #pragma unroll
-        for (int k = 0; k < 9; k++) {
+        for (int k = 0; k < (R12 ? 6 : 9); k++) {
             uf[k] = __ldg(um + k * V + x);
             ub[k] = __ldg(um + k * V + dn);
+        }
+        if (R12) {
+            su3_third_row(uf);
+            su3_third_row(ub);
         }
 #pragma unroll
         for (int r = 0; r < 3; r++)
@@ -513,7 +552,7 @@ cudaError_t launch_laplacian(const float2 *U, const float2 *in, const float2 *z,
 
 cudaError_t launch_lap_soa(const float2 *Us, const float2 *in, const float2 *z, float2 *out, int L, int T, int nvec,
                            long long ts_in, long long ts_z, long long ts_out, float a, float b, float c, cudaStream_t s,
-                           bool pdl = false)
+                           bool r12, bool pdl = false)
 {
     const long long V = (long long)L * L * L;
     if (T > 65535 || nvec > 65535) return cudaErrorInvalidValue;
@@ -526,7 +565,8 @@ cudaError_t launch_lap_soa(const float2 *Us, const float2 *in, const float2 *z, 
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, lap_soa_kernel, Us, in, z, out, L, ts_in, ts_z, ts_out, a, b, c);
+    return r12 ? cudaLaunchKernelEx(&cfg, lap_soa_kernel<true>, Us, in, z, out, L, ts_in, ts_z, ts_out, a, b, c)
+               : cudaLaunchKernelEx(&cfg, lap_soa_kernel<false>, Us, in, z, out, L, ts_in, ts_z, ts_out, a, b, c);
 }
 
 }  // namespace laph
@@ -569,7 +609,7 @@ namespace {
 // m + 1 vectors of every timeslice; after the Ritz vectors have been formed it
 // is reused for (-Delta) applied to them.
 struct LzLayout {
-    size_t Us, basis, w, ya, yb, yc, vin, X, dots, dscale, dnorm, dS, dred, dlam, dperm, total;
+    size_t Us, basis, w, ya, yb, yc, vin, X, dots, dscale, dnorm, dS, dred, dlam, dperm, dflag, total;
 };
 
 LzLayout lz_layout(long long K, int T, int m, int nr)
@@ -596,6 +636,7 @@ LzLayout lz_layout(long long K, int T, int m, int nr)
     l.dred = take(sizeof(double) * 2 * (size_t)T * nr);
     l.dlam = take(sizeof(double) * (size_t)T * nr);
     l.dperm = take(sizeof(int) * (size_t)T * nr);
+    l.dflag = take(sizeof(int));
     l.total = off;
     return l;
 }
@@ -608,6 +649,7 @@ int lz_check(int L, int T, int n_ev, const laph_lanczos_params *prm)
     if (m < n_ev || m > 4096 || (long long)m > K || prm->cheb_degree < 0 || prm->cheb_degree > 10000) return LAPH_ERR_ARG;
     if (prm->cheb_degree > 0 && !(prm->cheb_lo > 0.0 && prm->cheb_lo < 12.0)) return LAPH_ERR_ARG;
     if (prm->ts_group < 0) return LAPH_ERR_ARG;
+    if (prm->link_rows != 0 && prm->link_rows != 2 && prm->link_rows != 3) return LAPH_ERR_ARG;
     return LAPH_OK;
 }
 
@@ -654,17 +696,21 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
     // timeslice, stay in L2 across its d steps: groups filling about 70% of the
     // L2 (measured at L = 32, T = 64 on GB300: 8 timeslices, 88 MB, take 0.71x
     // the time of one group of all 64; 16 timeslices overflow it)
-    int tg = prm->ts_group;
-    if (tg == 0) {
-        int dev = 0, l2 = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess &&
-            l2 > 0)
-            tg = (int)std::max<long long>(1, (long long)(0.7 * l2) / (8 * 42 * V));
-        else
-            tg = 1;
-    }
+    int tg = prm->ts_group, dev = 0, l2 = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
+        l2 = 0;
+    if (tg == 0) tg = (int)std::max<long long>(1, (long long)(0.7 * l2) / (8 * 42 * V));
     tg = std::min(tg, T);
+    // SU(3) links can be read as two rows (the third rebuilt), 144 instead of
+    // 216 bytes per site: a gain where the stencil streams them from HBM
+    // (measured at L = 32, T = 64 on GB300: 0.83x the filter time), a loss
+    // where a filter group's links stay in L2 (1.04x).  Automatic choice: two
+    // rows unless the filter runs in groups that fit in L2.
+    const bool group_in_l2 = d > 0 && (double)tg * 8 * 42 * V <= 0.7 * l2;
+    st.ts_group = d > 0 ? tg : T;
+    const bool want_r12 = prm->link_rows == 2 || (prm->link_rows == 0 && !group_in_l2);
     const bool pdl = prm->pdl != 0;
+    bool r12 = false;
     float2 *Ud, *basis, *w, *ya, *yb, *yc, *vin, *X, *Y;
     double2 *dots;
     double *dscale, *dnorm, *dS, *dred, *dlam;
@@ -712,14 +758,14 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
                 auto at = [&](const float2 *base, long long ts) { return base + (long long)t0 * ts; };
                 float2 *y1 = d == 1 ? w : ya;
                 e = launch_lap_soa(Ug, at(v, ts_v), nullptr, (float2 *)at(y1, K), L, nt, 1, ts_v, 0, K,
-                                     (float)(1.0 / cheb_e), (float)(-cheb_c / cheb_e), 0.f, cs, pdl && t0 > 0);
+                                     (float)(1.0 / cheb_e), (float)(-cheb_c / cheb_e), 0.f, cs, r12, pdl && t0 > 0);
                 const float2 *prev = v;
                 long long ts_prev = ts_v;
                 float2 *cur = y1;
                 for (int k = 2; k <= d && e == cudaSuccess; k++) {
                     float2 *dst = k == d ? w : (cur != ya && prev != ya ? ya : (cur != yb && prev != yb ? yb : yc));
                     e = launch_lap_soa(Ug, at(cur, K), at(prev, ts_prev), (float2 *)at(dst, K), L, nt, 1, K, ts_prev,
-                                         K, (float)(2.0 / cheb_e), (float)(-2.0 * cheb_c / cheb_e), -1.f, cs, pdl);
+                                         K, (float)(2.0 / cheb_e), (float)(-2.0 * cheb_c / cheb_e), -1.f, cs, r12, pdl);
                     prev = cur;
                     ts_prev = K;
                     cur = dst;
@@ -734,7 +780,7 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
             if (d == 0) {
                 st.launches++;
                 st.apply_launches++;
-                return launch_lap_soa(Ud, v, nullptr, w, L, T, 1, ts_b, 0, K, 1.f, 0.f, 0.f, s);
+                return launch_lap_soa(Ud, v, nullptr, w, L, T, 1, ts_b, 0, K, 1.f, 0.f, 0.f, s, r12);
             }
             st.launches += n_filter;
             st.apply_launches += n_filter;
@@ -786,11 +832,19 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
             return cudaGetLastError();
         };
 
-        // the links in the solver's layout
-        links_soa_kernel<<<dim3((unsigned)((V + LAP_THREADS - 1) / LAP_THREADS), T), LAP_THREADS, 0, s>>>(
-            (const float2 *)U, Ud, V);
-        LCK(cudaGetLastError());
-        st.launches++;
+        // the links in the solver's layout; two rows suffice when they are SU(3)
+        {
+            int *dflag = (int *)(ws + lay.dflag), h_flag = 0;
+            LCK(cudaMemsetAsync(dflag, 0, sizeof(int), s));
+            links_soa_kernel<<<dim3((unsigned)((V + LAP_THREADS - 1) / LAP_THREADS), T), LAP_THREADS, 0, s>>>(
+                (const float2 *)U, Ud, (unsigned)V, dflag);
+            LCK(cudaGetLastError());
+            st.launches++;
+            LCK(cudaMemcpyAsync(&h_flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+            LCK(cudaStreamSynchronize(s));
+            r12 = want_r12 && h_flag == 0;
+            st.links_two_rows = r12 ? 1 : 0;
+        }
         // capture the filter once (on a stream of its own: the caller's may be
         // the legacy default stream, which cannot capture)
         if (d > 0 && n_filter > 1) {
@@ -891,7 +945,7 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
                                                                                    K * nr);
         LCK(cudaGetLastError());
         // Rayleigh quotients and residuals with -Delta (Y reuses the basis)
-        LCK(launch_lap_soa(Ud, X, nullptr, Y, L, T, nr, K * nr, 0, K * nr, 1.f, 0.f, 0.f, s));
+        LCK(launch_lap_soa(Ud, X, nullptr, Y, L, T, nr, K * nr, 0, K * nr, 1.f, 0.f, 0.f, s, r12));
         LCK(cudaMemsetAsync(dred, 0, sizeof(double) * 2 * T * nr, s));
         st.launches += 5;   // Ritz vectors, -Delta on them, two Rayleigh passes, gather
         {

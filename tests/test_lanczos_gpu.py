@@ -96,8 +96,8 @@ def test_lanczos_on_the_whole_space_matches_the_dense_solver(laph, L, T, n_ev):
     check_against_dense(U, L, n_ev, ev, vecs.cpu().numpy(), res)
 
 
-@pytest.mark.parametrize("degree", [0, 7, 8])
-def test_lanczos_with_and_without_the_chebyshev_filter_at_L8(laph, degree):
+@pytest.mark.parametrize("degree,link_rows", [(0, 0), (7, 0), (8, 0), (8, 2), (8, 3)])
+def test_lanczos_with_and_without_the_chebyshev_filter_at_L8(laph, degree, link_rows):
     """Smoothed links (eps = 0.6), 24 eigenpairs from a Krylov space of 60 (filtered) or 400 vectors.  The filter
     bound 1.45 lies in the gap above the 26th eigenvalue of timeslice 0 (1.448 < 1.45 < 1.454); an odd degree
     makes the wanted end the most negative one."""
@@ -105,7 +105,10 @@ def test_lanczos_with_and_without_the_chebyshev_filter_at_L8(laph, degree):
     L, T, n_ev = 8, 1, 24
     U = synth.random_links(L, T, instance=8, eps=0.6)
     m = 400 if degree == 0 else 60
-    vecs, ev, res = laph.lanczos(torch.from_numpy(U).cuda(), L, n_ev, m, cheb_degree=degree, cheb_lo=1.45)
+    st = {}
+    vecs, ev, res = laph.lanczos(torch.from_numpy(U).cuda(), L, n_ev, m, cheb_degree=degree, cheb_lo=1.45,
+                                 link_rows=link_rows, stats=st)
+    assert st["links_two_rows"] == (link_rows == 2 or (link_rows == 0 and degree == 0))
     check_against_dense(U, L, n_ev, ev, vecs.cpu().numpy(), res)
 
 
@@ -148,7 +151,8 @@ def test_lanczos_at_size_properties(laph, L, n_ev, m, d, lo):
     U = synth.random_links(L, T, instance=L, eps=0.6)
     Ud = torch.from_numpy(U).cuda()
     vecs, ev, res = laph.lanczos(Ud, L, n_ev, m, cheb_degree=d, cheb_lo=lo, seed=1)
-    _, ev2, _ = laph.lanczos(Ud, L, n_ev, m, cheb_degree=d, cheb_lo=lo, seed=2)
+    # a second start vector, with the filter in groups of one timeslice and the links read as two rows
+    _, ev2, _ = laph.lanczos(Ud, L, n_ev, m, cheb_degree=d, cheb_lo=lo, seed=2, ts_group=1, link_rows=2)
     v = vecs.cpu().numpy().astype(np.complex128)
     print(f"L={L}: ev {ev[0][:4]} ... {ev[0][-1]:.4f}; max resid {res.max():.2e}; run diff {np.abs(ev - ev2).max():.2e}")
     assert np.all(np.diff(ev, axis=1) >= -1e-9)
@@ -162,3 +166,21 @@ def test_lanczos_at_size_properties(laph, L, n_ev, m, d, lo):
             assert rr <= 1e-3 * 12
             assert abs(rr - res[t, r]) <= 1e-4 + 0.05 * rr
             assert abs(np.vdot(v[t, r], Av[r]).real - ev[t, r]) <= 2e-5
+
+
+def test_lanczos_links_outside_su3_use_all_three_rows(laph):
+    """SU(3) links are read as two rows (the third rebuilt from them); links e^{0.3 i} U are unitary with a
+    determinant other than 1, so the rebuilt row is wrong for them: the solver detects it, reads all three rows,
+    and the eigenpairs still match the dense oracle."""
+    import torch
+    L, T, n_ev = 4, 1, 12
+    U = synth.random_links(L, T, instance=41, eps=None)
+    st = {}
+    vecs, ev, res = laph.lanczos(torch.from_numpy(U).cuda(), L, n_ev, 3 * L ** 3, stats=st)
+    assert st["links_two_rows"] == 1
+    check_against_dense(U, L, n_ev, ev, vecs.cpu().numpy(), res)
+    Up = (U * np.exp(0.3j)).astype(np.complex64)
+    st = {}
+    vecs, ev, res = laph.lanczos(torch.from_numpy(Up).cuda(), L, n_ev, 3 * L ** 3, stats=st)
+    assert st["links_two_rows"] == 0
+    check_against_dense(Up, L, n_ev, ev, vecs.cpu().numpy(), res)
