@@ -364,7 +364,7 @@ def run_projection(args):
 
 LANCZOS = {
     # the LapH eigenvectors of the L=32, T=64, N=64 workload
-    "lanczos": dict(L=32, T=64, n_ev=64, m=160, degree=40, lo=0.95, eps=0.6),
+    "lanczos": dict(L=32, T=64, n_ev=64, m=128, degree=48, lo=0.95, eps=0.6),
     # a small case of the same kernels for profiler captures (one group of 8 timeslices)
     "lanczos-small": dict(L=32, T=8, n_ev=16, m=24, degree=8, lo=0.95, eps=0.6),
 }
@@ -385,7 +385,7 @@ def laplacian_bytes_per_site(with_z: bool, link_rows: int = 3) -> int:
 
 def run_lanczos(args):
     """--workload lanczos: the LapH eigenvectors, the 64 lowest eigenpairs of the 3-d gauge-covariant Laplacian
-    on every timeslice of an L=32, T=64 lattice (batched Lanczos, 160 Krylov steps on a degree-40 Chebyshev
+    on every timeslice of an L=32, T=64 lattice (batched Lanczos, 128 Krylov steps on a degree-48 Chebyshev
     filter), smoothed synthetic links."""
     import torch
     from paper_2510_26313_gb300 import binding as laph

@@ -32,6 +32,17 @@ namespace laph {
 namespace {
 
 constexpr int LAP_THREADS = 256;
+// launch shape of the solver's stencil (tuning: block size, minimum resident
+// blocks per SM, and 1 to read the links past L1)
+#ifndef LAP_SOA_THREADS
+#define LAP_SOA_THREADS 256
+#endif
+#ifndef LAP_SOA_MINB
+#define LAP_SOA_MINB 4
+#endif
+#ifndef LAP_SOA_LINKS_CG
+#define LAP_SOA_LINKS_CG 0
+#endif
 
 __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 acc)   // acc + a b
 {
@@ -158,7 +169,7 @@ __global__ void links_soa_kernel(const float2 *__restrict__ U, float2 *__restric
 // completion of the previous grid before its first access to vectors.
 // R12: the links are SU(3) and only their first two rows are read.
 template <bool R12>
-__global__ void __launch_bounds__(LAP_THREADS, 4) lap_soa_kernel(const float2 *__restrict__ Us,
+__global__ void __launch_bounds__(LAP_SOA_THREADS, LAP_SOA_MINB) lap_soa_kernel(const float2 *__restrict__ Us,
                                                               const float2 *__restrict__ in,
                                                               const float2 *__restrict__ z, float2 *__restrict__ out,
                                                               int L, long long ts_in, long long ts_z, long long ts_out,
@@ -197,8 +208,13 @@ __global__ void __launch_bounds__(LAP_THREADS, 4) lap_soa_kernel(const float2 *_
         }
 #pragma unroll
         for (int k = 0; k < (R12 ? 6 : 9); k++) {
+#if LAP_SOA_LINKS_CG
+            uf[k] = __ldcg(um + k * V + x);
+            ub[k] = __ldcg(um + k * V + dn);
+#else
             uf[k] = __ldg(um + k * V + x);
             ub[k] = __ldg(um + k * V + dn);
+#endif
         }
         if (R12) {
             su3_third_row(uf);
@@ -557,8 +573,8 @@ cudaError_t launch_lap_soa(const float2 *Us, const float2 *in, const float2 *z, 
     const long long V = (long long)L * L * L;
     if (T > 65535 || nvec > 65535) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)((V + LAP_THREADS - 1) / LAP_THREADS), (unsigned)T, (unsigned)nvec);
-    cfg.blockDim = dim3(LAP_THREADS);
+    cfg.gridDim = dim3((unsigned)((V + LAP_SOA_THREADS - 1) / LAP_SOA_THREADS), (unsigned)T, (unsigned)nvec);
+    cfg.blockDim = dim3(LAP_SOA_THREADS);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
