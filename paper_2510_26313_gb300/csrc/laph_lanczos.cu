@@ -54,8 +54,9 @@ __device__ __forceinline__ float2 cfma_conj(float2 a, float2 b, float2 acc)   //
     return make_float2(fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(-a.y, b.x, acc.y)));
 }
 
-// out = a (-Delta in) + b in + c z for the vectors of blockIdx.z of timeslice
-// blockIdx.y; one thread per site.  in/z/out: [T][nvec][V][3] with the given
+// out = a (-Delta in) + b in + c z for vector blockIdx.y of timeslice
+// blockIdx.z (the vectors of a timeslice run together and share its links in
+// L2); one thread per site.  in/z/out: [T][nvec][V][3] with the given
 // per-timeslice strides (in elements of float2); z may be null (c ignored).
 __global__ void __launch_bounds__(LAP_THREADS) lap_kernel(const float2 *__restrict__ U, const float2 *__restrict__ in,
                                                           const float2 *__restrict__ z, float2 *__restrict__ out,
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(LAP_THREADS) lap_kernel(const float2 *__restri
     const long long V = (long long)L * L * L;
     const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= V) return;
-    const int t = blockIdx.y, n = blockIdx.z;
+    const int n = blockIdx.y, t = blockIdx.z;
     const float2 *f = in + t * ts_in + n * V * 3;
     const float2 *Ut = U + (long long)t * 3 * V * 9;
     const int c0 = (int)(x % L), c1 = (int)((x / L) % L), c2 = (int)(x / ((long long)L * L));
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(LAP_SOA_THREADS, LAP_SOA_MINB) lap_soa_kernel(
     const unsigned uL = (unsigned)L, V = uL * uL * uL;
     const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= V) return;
-    const int t = blockIdx.y, n = blockIdx.z;
+    const int n = blockIdx.y, t = blockIdx.z;
     const float2 *f = in + t * ts_in + (long long)n * V * 3;
     const float2 *Ut = Us + (long long)t * 27 * V;
     const unsigned q1 = x / uL, c0 = x - q1 * uL, c2 = q1 / uL, c1 = q1 - c2 * uL;
@@ -491,13 +492,23 @@ __global__ void gather_kernel(const float2 *__restrict__ X, long long ts_X, cons
 // row-major z belongs to d[k]) of the symmetric tridiagonal matrix with diagonal
 // d[0..n) and off-diagonal e[0..n-1), by the QL algorithm with implicit Wilkinson
 // shifts (Givens rotations chased up from the bottom of each unreduced block).
-// Returns 0, or -1 when an eigenvalue needs more than 60 sweeps.
+// The rotations are accumulated into the transpose of z, so that each one
+// updates two contiguous rows.  Returns 0, or -1 when an eigenvalue needs more
+// than 60 sweeps.
+// sqrt(a^2 + b^2), by the direct formula where the squares can neither
+// overflow nor underflow, else by std::hypot
+static inline double pyth(double a, double b)
+{
+    const double m = std::max(std::fabs(a), std::fabs(b));
+    if (m < 1e150 && m > 1e-150) return std::sqrt(a * a + b * b);
+    return std::hypot(a, b);
+}
+
 int tridiag_eigen(int n, double *d, const double *e_in, double *z)
 {
-    std::vector<double> e(n, 0.0);
+    std::vector<double> e(n, 0.0), zt((size_t)n * n, 0.0);
     for (int i = 0; i + 1 < n; i++) e[i] = e_in[i];
-    for (int i = 0; i < n; i++)
-        for (int j = 0; j < n; j++) z[i * n + j] = i == j ? 1.0 : 0.0;
+    for (int i = 0; i < n; i++) zt[(size_t)i * n + i] = 1.0;
     for (int l = 0; l < n; l++) {
         int iter = 0;
         while (true) {
@@ -510,13 +521,13 @@ int tridiag_eigen(int n, double *d, const double *e_in, double *z)
             if (++iter > 60) return -1;
             // shift from the leading 2 x 2 of the block
             double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-            double r = std::hypot(g, 1.0);
+            double r = pyth(g, 1.0);
             g = d[m] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
             double s = 1.0, c = 1.0, p = 0.0;
             int i = m - 1;
             for (; i >= l; i--) {
                 double f = s * e[i], b = c * e[i];
-                r = std::hypot(f, g);
+                r = pyth(f, g);
                 e[i + 1] = r;
                 if (r == 0.0) {
                     d[i + 1] -= p;
@@ -530,10 +541,11 @@ int tridiag_eigen(int n, double *d, const double *e_in, double *z)
                 p = s * r;
                 d[i + 1] = g + p;
                 g = c * r - b;
+                double *z0 = zt.data() + (size_t)i * n, *z1 = z0 + n;
                 for (int k = 0; k < n; k++) {
-                    const double zk1 = z[k * n + i + 1], zk = z[k * n + i];
-                    z[k * n + i + 1] = s * zk + c * zk1;
-                    z[k * n + i] = c * zk - s * zk1;
+                    const double zk1 = z1[k], zk = z0[k];
+                    z1[k] = s * zk + c * zk1;
+                    z0[k] = c * zk - s * zk1;
                 }
             }
             if (r == 0.0 && i >= l) continue;
@@ -546,13 +558,13 @@ int tridiag_eigen(int n, double *d, const double *e_in, double *z)
     std::vector<int> idx(n);
     for (int i = 0; i < n; i++) idx[i] = i;
     std::sort(idx.begin(), idx.end(), [&](int a, int b) { return d[a] < d[b]; });
-    std::vector<double> d2(n), z2((size_t)n * n);
+    std::vector<double> d2(n);
     for (int k = 0; k < n; k++) {
         d2[k] = d[idx[k]];
-        for (int i = 0; i < n; i++) z2[(size_t)i * n + k] = z[(size_t)i * n + idx[k]];
+        const double *col = zt.data() + (size_t)idx[k] * n;
+        for (int i = 0; i < n; i++) z[(size_t)i * n + k] = col[i];
     }
     std::memcpy(d, d2.data(), sizeof(double) * n);
-    std::memcpy(z, z2.data(), sizeof(double) * n * n);
     return 0;
 }
 
@@ -561,7 +573,7 @@ cudaError_t launch_laplacian(const float2 *U, const float2 *in, const float2 *z,
 {
     const long long V = (long long)L * L * L;
     if (T > 65535 || nvec > 65535) return cudaErrorInvalidValue;
-    dim3 g((unsigned)((V + LAP_THREADS - 1) / LAP_THREADS), (unsigned)T, (unsigned)nvec);
+    dim3 g((unsigned)((V + LAP_THREADS - 1) / LAP_THREADS), (unsigned)nvec, (unsigned)T);
     lap_kernel<<<g, LAP_THREADS, 0, s>>>(U, in, z, out, L, ts_in, ts_z, ts_out, a, b, c);
     return cudaGetLastError();
 }
@@ -573,7 +585,7 @@ cudaError_t launch_lap_soa(const float2 *Us, const float2 *in, const float2 *z, 
     const long long V = (long long)L * L * L;
     if (T > 65535 || nvec > 65535) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)((V + LAP_SOA_THREADS - 1) / LAP_SOA_THREADS), (unsigned)T, (unsigned)nvec);
+    cfg.gridDim = dim3((unsigned)((V + LAP_SOA_THREADS - 1) / LAP_SOA_THREADS), (unsigned)nvec, (unsigned)T);
     cfg.blockDim = dim3(LAP_SOA_THREADS);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
