@@ -128,13 +128,76 @@ __device__ __forceinline__ void su3_third_row(float2 *u)
     }
 }
 
-// The solver's own layouts, with every warp access 32 consecutive float2:
-// links Us [T][3][9][V] (direction, row-major colour entry, site) and vectors
-// [3][V] per vector (colour, site).  The transpose of the links runs once per
-// solve; it sets *bad when a link's third row differs from the one rebuilt
-// from its first two by more than tol (the links are not SU(3) to FP32
-// accuracy), in which case the stencil reads all three rows.
+// The solver's own layouts, in which a warp reads consecutive sites:
+// - plain: links Us [T][3][9][V] (direction, row-major colour entry, site),
+//   vectors [3][V] (colour, site);
+// - paired (V even, so that every block is 16-byte aligned): the links of a
+//   direction are entries (0,1), (2,3), (4,5), (6,7) as four [V] arrays of
+//   16-byte pairs, then entry 8 as a [V] array; a vector is colours (0,1) as
+//   a [V] array of pairs, then colour 2 as a [V] array.  A site's vector is two
+//   loads instead of three, a link five instead of nine.
+// The orthogonalisation and Ritz kernels treat a vector as 3V elements in any
+// order; the final gather writes the caller's [V][3].
+template <bool PAIRS>
+__device__ __forceinline__ void load_site(const float2 *__restrict__ f, unsigned V, unsigned x, float2 v[3])
+{
+    if (PAIRS) {
+        const float4 p = reinterpret_cast<const float4 *>(f)[x];
+        v[0] = make_float2(p.x, p.y);
+        v[1] = make_float2(p.z, p.w);
+        v[2] = f[2 * V + x];
+    } else {
+#pragma unroll
+        for (int q = 0; q < 3; q++) v[q] = f[q * V + x];
+    }
+}
+
+template <bool PAIRS>
+__device__ __forceinline__ void store_site(float2 *__restrict__ o, unsigned V, unsigned x, const float2 v[3])
+{
+    if (PAIRS) {
+        reinterpret_cast<float4 *>(o)[x] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+        o[2 * V + x] = v[2];
+    } else {
+#pragma unroll
+        for (int q = 0; q < 3; q++) o[q * V + x] = v[q];
+    }
+}
+
+// The first NE entries of the link of direction block um at site x.
+template <bool PAIRS, int NE>
+__device__ __forceinline__ void load_link(const float2 *__restrict__ um, unsigned V, unsigned x, float2 u[9])
+{
+    if (PAIRS) {
+#pragma unroll
+        for (int b = 0; 2 * b + 1 < NE; b++) {
+#if LAP_SOA_LINKS_CG
+            const float4 p = __ldcg(reinterpret_cast<const float4 *>(um + 2 * b * V) + x);
+#else
+            const float4 p = __ldg(reinterpret_cast<const float4 *>(um + 2 * b * V) + x);
+#endif
+            u[2 * b] = make_float2(p.x, p.y);
+            u[2 * b + 1] = make_float2(p.z, p.w);
+        }
+        if (NE == 9) u[8] = __ldg(um + 8 * V + x);
+    } else {
+#pragma unroll
+        for (int k = 0; k < NE; k++) {
+#if LAP_SOA_LINKS_CG
+            u[k] = __ldcg(um + k * V + x);
+#else
+            u[k] = __ldg(um + k * V + x);
+#endif
+        }
+    }
+}
+
+// The transpose of the links runs once per solve; it sets *bad when a link's
+// third row differs from the one rebuilt from its first two by more than tol
+// (the links are not SU(3) to FP32 accuracy), in which case the stencil reads
+// all three rows.
 constexpr float SU3_TOL = 2e-6f;
+template <bool PAIRS>
 __global__ void links_soa_kernel(const float2 *__restrict__ U, float2 *__restrict__ Us, unsigned V,
                                  int *__restrict__ bad)
 {
@@ -148,9 +211,17 @@ __global__ void links_soa_kernel(const float2 *__restrict__ U, float2 *__restric
         for (int mu = 0; mu < 3; mu++) {
             float2 m[9];
 #pragma unroll
-            for (int rc = 0; rc < 9; rc++) {
-                m[rc] = u[((long long)mu * V + x) * 9 + rc];
-                o[((long long)mu * 9 + rc) * V + x] = m[rc];
+            for (int rc = 0; rc < 9; rc++) m[rc] = u[((long long)mu * V + x) * 9 + rc];
+            float2 *om = o + (long long)mu * 9 * V;
+            if (PAIRS) {
+#pragma unroll
+                for (int b = 0; b < 4; b++)
+                    reinterpret_cast<float4 *>(om + 2 * b * V)[x] =
+                        make_float4(m[2 * b].x, m[2 * b].y, m[2 * b + 1].x, m[2 * b + 1].y);
+                om[8 * V + x] = m[8];
+            } else {
+#pragma unroll
+                for (int rc = 0; rc < 9; rc++) om[(long long)rc * V + x] = m[rc];
             }
             float2 r[9];
 #pragma unroll
@@ -168,8 +239,9 @@ __global__ void links_soa_kernel(const float2 *__restrict__ U, float2 *__restric
 // reads its predecessors' outputs and overwrites the vector read two steps
 // back): it lets the next grid be scheduled at once and waits for the full
 // completion of the previous grid before its first access to vectors.
-// R12: the links are SU(3) and only their first two rows are read.
-template <bool R12>
+// R12: the links are SU(3) and only their first two rows are read.  PAIRS:
+// the paired layouts above.
+template <bool R12, bool PAIRS>
 __global__ void __launch_bounds__(LAP_SOA_THREADS, LAP_SOA_MINB) lap_soa_kernel(const float2 *__restrict__ Us,
                                                               const float2 *__restrict__ in,
                                                               const float2 *__restrict__ z, float2 *__restrict__ out,
@@ -190,33 +262,20 @@ __global__ void __launch_bounds__(LAP_SOA_THREADS, LAP_SOA_MINB) lap_soa_kernel(
     const unsigned cc[3] = {c0, c1, c2};
     const unsigned stride[3] = {1u, uL, uL * uL};
     float2 fx[3], acc[3];
+    load_site<PAIRS>(f, V, x, fx);
 #pragma unroll
-    for (int q = 0; q < 3; q++) {
-        fx[q] = f[q * V + x];
-        acc[q] = make_float2(0.f, 0.f);
-    }
+    for (int q = 0; q < 3; q++) acc[q] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int mu = 0; mu < 3; mu++) {
         const unsigned up = cc[mu] == uL - 1 ? x - (uL - 1) * stride[mu] : x + stride[mu];
         const unsigned dn = cc[mu] == 0 ? x + (uL - 1) * stride[mu] : x - stride[mu];
         const float2 *um = Ut + (long long)mu * 9 * V;
-        // all 24 loads of this direction issued before its multiply-adds
+        // all loads of this direction issued before its multiply-adds
         float2 fu[3], fd[3], uf[9], ub[9];
-#pragma unroll
-        for (int q = 0; q < 3; q++) {
-            fu[q] = f[q * V + up];
-            fd[q] = f[q * V + dn];
-        }
-#pragma unroll
-        for (int k = 0; k < (R12 ? 6 : 9); k++) {
-#if LAP_SOA_LINKS_CG
-            uf[k] = __ldcg(um + k * V + x);
-            ub[k] = __ldcg(um + k * V + dn);
-#else
-            uf[k] = __ldg(um + k * V + x);
-            ub[k] = __ldg(um + k * V + dn);
-#endif
-        }
+        load_site<PAIRS>(f, V, up, fu);
+        load_site<PAIRS>(f, V, dn, fd);
+        load_link<PAIRS, R12 ? 6 : 9>(um, V, x, uf);
+        load_link<PAIRS, R12 ? 6 : 9>(um, V, dn, ub);
         if (R12) {
             su3_third_row(uf);
             su3_third_row(ub);
@@ -230,17 +289,15 @@ __global__ void __launch_bounds__(LAP_SOA_THREADS, LAP_SOA_MINB) lap_soa_kernel(
             }
     }
     float2 *o = out + t * ts_out + (long long)n * V * 3;
-    const float2 *zz = z ? z + t * ts_z + (long long)n * V * 3 : nullptr;
+    float2 zv[3] = {};
+    if (z) load_site<PAIRS>(z + t * ts_z + (long long)n * V * 3, V, x, zv);
+    float2 r[3];
 #pragma unroll
     for (int q = 0; q < 3; q++) {
         const float2 lap = make_float2(6.f * fx[q].x - acc[q].x, 6.f * fx[q].y - acc[q].y);
-        float2 r = make_float2(a * lap.x + b * fx[q].x, a * lap.y + b * fx[q].y);
-        if (zz) {
-            r.x += c * zz[q * V + x].x;
-            r.y += c * zz[q * V + x].y;
-        }
-        o[q * V + x] = r;
+        r[q] = make_float2(a * lap.x + b * fx[q].x + c * zv[q].x, a * lap.y + b * fx[q].y + c * zv[q].y);
     }
+    store_site<PAIRS>(o, V, x, r);
 }
 
 // Block reduction of a double into thread 0.
@@ -471,7 +528,8 @@ __global__ void __launch_bounds__(LAP_THREADS) rayleigh_kernel(const float2 *__r
 }
 
 // out[t][r] = X[t][perm[t][r]] * scale[t][r], from the solver's vector
-// layout [3][V] to the caller's [V][3].
+// layout to the caller's [V][3].
+template <bool PAIRS>
 __global__ void gather_kernel(const float2 *__restrict__ X, long long ts_X, const int *__restrict__ perm,
                               const double *__restrict__ scale, int nr, float2 *__restrict__ out, long long ts_out,
                               long long V)
@@ -482,7 +540,8 @@ __global__ void gather_kernel(const float2 *__restrict__ X, long long ts_X, cons
     const long long x = e / 3;
     const int q = (int)(e - 3 * x);
     const float sc = (float)scale[t * nr + r];
-    const float2 v = X[t * ts_X + (long long)perm[t * nr + r] * 3 * V + q * V + x];
+    const long long src = PAIRS ? (q < 2 ? 2 * x + q : 2 * V + x) : q * V + x;
+    const float2 v = X[t * ts_X + (long long)perm[t * nr + r] * 3 * V + src];
     out[t * ts_out + (long long)r * 3 * V + e] = make_float2(v.x * sc, v.y * sc);
 }
 
@@ -580,7 +639,7 @@ cudaError_t launch_laplacian(const float2 *U, const float2 *in, const float2 *z,
 
 cudaError_t launch_lap_soa(const float2 *Us, const float2 *in, const float2 *z, float2 *out, int L, int T, int nvec,
                            long long ts_in, long long ts_z, long long ts_out, float a, float b, float c, cudaStream_t s,
-                           bool r12, bool pdl = false)
+                           bool r12, bool pairs, bool pdl = false)
 {
     const long long V = (long long)L * L * L;
     if (T > 65535 || nvec > 65535) return cudaErrorInvalidValue;
@@ -593,8 +652,11 @@ cudaError_t launch_lap_soa(const float2 *Us, const float2 *in, const float2 *z, 
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
-    return r12 ? cudaLaunchKernelEx(&cfg, lap_soa_kernel<true>, Us, in, z, out, L, ts_in, ts_z, ts_out, a, b, c)
-               : cudaLaunchKernelEx(&cfg, lap_soa_kernel<false>, Us, in, z, out, L, ts_in, ts_z, ts_out, a, b, c);
+    if (pairs)
+        return r12 ? cudaLaunchKernelEx(&cfg, lap_soa_kernel<true, true>, Us, in, z, out, L, ts_in, ts_z, ts_out, a, b, c)
+                   : cudaLaunchKernelEx(&cfg, lap_soa_kernel<false, true>, Us, in, z, out, L, ts_in, ts_z, ts_out, a, b, c);
+    return r12 ? cudaLaunchKernelEx(&cfg, lap_soa_kernel<true, false>, Us, in, z, out, L, ts_in, ts_z, ts_out, a, b, c)
+               : cudaLaunchKernelEx(&cfg, lap_soa_kernel<false, false>, Us, in, z, out, L, ts_in, ts_z, ts_out, a, b, c);
 }
 
 }  // namespace laph
@@ -739,6 +801,8 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
     const bool want_r12 = prm->link_rows == 2 || (prm->link_rows == 0 && !group_in_l2);
     const bool pdl = prm->pdl != 0;
     bool r12 = false;
+    // paired layouts where every block they split into is 16-byte aligned
+    const bool pairs = V % 2 == 0;
     float2 *Ud, *basis, *w, *ya, *yb, *yc, *vin, *X, *Y;
     double2 *dots;
     double *dscale, *dnorm, *dS, *dred, *dlam;
@@ -786,14 +850,14 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
                 auto at = [&](const float2 *base, long long ts) { return base + (long long)t0 * ts; };
                 float2 *y1 = d == 1 ? w : ya;
                 e = launch_lap_soa(Ug, at(v, ts_v), nullptr, (float2 *)at(y1, K), L, nt, 1, ts_v, 0, K,
-                                     (float)(1.0 / cheb_e), (float)(-cheb_c / cheb_e), 0.f, cs, r12, pdl && t0 > 0);
+                                     (float)(1.0 / cheb_e), (float)(-cheb_c / cheb_e), 0.f, cs, r12, pairs, pdl && t0 > 0);
                 const float2 *prev = v;
                 long long ts_prev = ts_v;
                 float2 *cur = y1;
                 for (int k = 2; k <= d && e == cudaSuccess; k++) {
                     float2 *dst = k == d ? w : (cur != ya && prev != ya ? ya : (cur != yb && prev != yb ? yb : yc));
                     e = launch_lap_soa(Ug, at(cur, K), at(prev, ts_prev), (float2 *)at(dst, K), L, nt, 1, K, ts_prev,
-                                         K, (float)(2.0 / cheb_e), (float)(-2.0 * cheb_c / cheb_e), -1.f, cs, r12, pdl);
+                                         K, (float)(2.0 / cheb_e), (float)(-2.0 * cheb_c / cheb_e), -1.f, cs, r12, pairs, pdl);
                     prev = cur;
                     ts_prev = K;
                     cur = dst;
@@ -808,7 +872,7 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
             if (d == 0) {
                 st.launches++;
                 st.apply_launches++;
-                return launch_lap_soa(Ud, v, nullptr, w, L, T, 1, ts_b, 0, K, 1.f, 0.f, 0.f, s, r12);
+                return launch_lap_soa(Ud, v, nullptr, w, L, T, 1, ts_b, 0, K, 1.f, 0.f, 0.f, s, r12, pairs);
             }
             st.launches += n_filter;
             st.apply_launches += n_filter;
@@ -864,8 +928,11 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
         {
             int *dflag = (int *)(ws + lay.dflag), h_flag = 0;
             LCK(cudaMemsetAsync(dflag, 0, sizeof(int), s));
-            links_soa_kernel<<<dim3((unsigned)((V + LAP_THREADS - 1) / LAP_THREADS), T), LAP_THREADS, 0, s>>>(
-                (const float2 *)U, Ud, (unsigned)V, dflag);
+            const dim3 grid((unsigned)((V + LAP_THREADS - 1) / LAP_THREADS), T);
+            if (pairs)
+                links_soa_kernel<true><<<grid, LAP_THREADS, 0, s>>>((const float2 *)U, Ud, (unsigned)V, dflag);
+            else
+                links_soa_kernel<false><<<grid, LAP_THREADS, 0, s>>>((const float2 *)U, Ud, (unsigned)V, dflag);
             LCK(cudaGetLastError());
             st.launches++;
             LCK(cudaMemcpyAsync(&h_flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -973,7 +1040,7 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
                                                                                    K * nr);
         LCK(cudaGetLastError());
         // Rayleigh quotients and residuals with -Delta (Y reuses the basis)
-        LCK(launch_lap_soa(Ud, X, nullptr, Y, L, T, nr, K * nr, 0, K * nr, 1.f, 0.f, 0.f, s, r12));
+        LCK(launch_lap_soa(Ud, X, nullptr, Y, L, T, nr, K * nr, 0, K * nr, 1.f, 0.f, 0.f, s, r12, pairs));
         LCK(cudaMemsetAsync(dred, 0, sizeof(double) * 2 * T * nr, s));
         st.launches += 5;   // Ritz vectors, -Delta on them, two Rayleigh passes, gather
         {
@@ -1009,8 +1076,12 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
             }
             LCK(cudaMemcpyAsync(dperm, perm.data(), sizeof(int) * T * nr, cudaMemcpyHostToDevice, s));
             LCK(cudaMemcpyAsync(dred, inv_norm.data(), sizeof(double) * T * nr, cudaMemcpyHostToDevice, s));
-            gather_kernel<<<dim3(blocks_e, T, nr), LAP_THREADS, 0, s>>>(X, K * nr, dperm, dred, nr, (float2 *)evecs,
-                                                                        K * nr, V);
+            if (pairs)
+                gather_kernel<true><<<dim3(blocks_e, T, nr), LAP_THREADS, 0, s>>>(X, K * nr, dperm, dred, nr,
+                                                                                (float2 *)evecs, K * nr, V);
+            else
+                gather_kernel<false><<<dim3(blocks_e, T, nr), LAP_THREADS, 0, s>>>(X, K * nr, dperm, dred, nr,
+                                                                                 (float2 *)evecs, K * nr, V);
             LCK(cudaGetLastError());
             if (stats) {
                 float tot = 0.f, setup = 0.f, ritz = 0.f;
