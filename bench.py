@@ -373,7 +373,7 @@ LANCZOS = {
 # DRAM bytes (read + write) of one lap_soa_kernel launch on a group of 8 timeslices at L=32 with links read as three
 # rows, from the ncu capture summarised in profiles/lap_soa_kernel_L32_T8_group8_full.md (warm L2, the launch shape of
 # every filter launch of the L=32, T=64 workload); to be retaken whenever the kernel changes
-LAP_SOA_TRAFFIC = None
+LAP_SOA_TRAFFIC = 12.7e6
 
 
 def laplacian_bytes_per_site(with_z: bool, link_rows: int = 3) -> int:
