@@ -434,6 +434,20 @@ def run_lanczos(args):
     orth_gbs = orth_bytes / (orth_ms / 1e3) / 1e9
     dominant = "apply" if apply_ms >= orth_ms else "orth"
     ach = apply_gbs if dominant == "apply" else orth_gbs
+    # the public laph_laplacian (caller's layouts, no workspace) on one vector of every timeslice, timed alone
+    f1 = evecs[:, :1].contiguous()
+    g1 = torch.empty_like(f1)
+    for _ in range(3):
+        laph.laplacian(U, f1, L, out=g1, stream=stream)
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    for _ in range(20):
+        laph.laplacian(U, f1, L, out=g1, stream=stream)
+    eb.record(stream)
+    torch.cuda.synchronize()
+    lap_ms = ea.elapsed_time(eb) / 20
+    lap_api = {"ms": lap_ms, "gbs": laplacian_bytes_per_site(False) * V * T / (lap_ms / 1e3) / 1e9,
+               "note": "laph_laplacian on [T][1][V][3] with the caller's [T][3][V][3][3] links, algorithmic bytes"}
     e2e = None
     if not args.no_e2e:
         # through the public API with host buffers: links copied in from pinned memory, eigenvectors and
@@ -495,6 +509,7 @@ def run_lanczos(args):
         "convergence": {"max_resid": float(res.max()), "median_resid": float(np.median(res)),
                         "ev_min": float(ev.min()), "ev_max": float(ev.max())},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(sum(s["launches"] for s in stats)), "clocks": clk,
+        "laplacian_api": lap_api,
     }
     print(json.dumps(line), flush=True)
     return 0

@@ -15,9 +15,17 @@
 // enough"), and normalises.  The operator is -Delta itself or the Chebyshev
 // filter T_d((-Delta - c) / e), which maps the unwanted part of the spectrum,
 // [lo, 12], onto [-1, 1] and magnifies the lowest eigenvalues.  The Ritz
-// vectors of the wanted end are formed from the basis, and their eigenvalues
-// and residuals are Rayleigh quotients with -Delta.  Vectors are FP32,
-// inner products FP64.
+// vectors of the wanted end are formed from the basis (host QL on the
+// tridiagonal matrices), and their eigenvalues and residuals are Rayleigh
+// quotients with -Delta.
+//
+// Precision: FP32 vectors and links; inner products are FP32 products summed
+// in FP32 within a thread and a warp and in FP64 across warps and blocks.
+// Layout and scheduling: the solver copies the links into its own
+// structure-of-arrays layout (16-byte pairs where V is even) and keeps its
+// vectors in the matching layout; the filter runs group by group of
+// timeslices that fit in L2, all its steps replayed as one CUDA graph per
+// Krylov step.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -58,7 +66,7 @@ __device__ __forceinline__ float2 cfma_conj(float2 a, float2 b, float2 acc)   //
 // blockIdx.z (the vectors of a timeslice run together and share its links in
 // L2); one thread per site.  in/z/out: [T][nvec][V][3] with the given
 // per-timeslice strides (in elements of float2); z may be null (c ignored).
-__global__ void __launch_bounds__(LAP_THREADS) lap_kernel(const float2 *__restrict__ U, const float2 *__restrict__ in,
+__global__ void __launch_bounds__(LAP_THREADS, 4) lap_kernel(const float2 *__restrict__ U, const float2 *__restrict__ in,
                                                           const float2 *__restrict__ z, float2 *__restrict__ out,
                                                           int L, long long ts_in, long long ts_z, long long ts_out,
                                                           float a, float b, float c)
@@ -82,20 +90,26 @@ __global__ void __launch_bounds__(LAP_THREADS) lap_kernel(const float2 *__restri
     for (int mu = 0; mu < 3; mu++) {
         const long long up = x + (cc[mu] == L - 1 ? -(long long)(L - 1) * stride[mu] : stride[mu]);
         const long long dn = x - (cc[mu] == 0 ? -(long long)(L - 1) * stride[mu] : stride[mu]);
-        const float2 *uf = Ut + (mu * V + x) * 9;     // U_mu(x)
-        const float2 *ub = Ut + (mu * V + dn) * 9;    // U_mu(x - mu)
-        float2 fu[3], fd[3];
+        const float2 *pf = Ut + (mu * V + x) * 9;     // U_mu(x)
+        const float2 *pb = Ut + (mu * V + dn) * 9;    // U_mu(x - mu)
+        // all loads of this direction issued before its multiply-adds
+        float2 fu[3], fd[3], uf[9], ub[9];
 #pragma unroll
         for (int q = 0; q < 3; q++) {
             fu[q] = f[3 * up + q];
             fd[q] = f[3 * dn + q];
         }
 #pragma unroll
+        for (int k = 0; k < 9; k++) {
+            uf[k] = __ldg(pf + k);
+            ub[k] = __ldg(pb + k);
+        }
+#pragma unroll
         for (int r = 0; r < 3; r++)
 #pragma unroll
             for (int q = 0; q < 3; q++) {
-                acc[r] = cfma(__ldg(uf + 3 * r + q), fu[q], acc[r]);          // U_mu(x)_{rq} f_q(x + mu)
-                acc[r] = cfma_conj(__ldg(ub + 3 * q + r), fd[q], acc[r]);     // conj(U_mu(x - mu)_{qr}) f_q(x - mu)
+                acc[r] = cfma(uf[3 * r + q], fu[q], acc[r]);          // U_mu(x)_{rq} f_q(x + mu)
+                acc[r] = cfma_conj(ub[3 * q + r], fd[q], acc[r]);     // conj(U_mu(x - mu)_{qr}) f_q(x - mu)
             }
     }
     float2 *o = out + t * ts_out + n * V * 3 + 3 * x;
