@@ -386,22 +386,32 @@ def laplacian_bytes_per_site(with_z: bool, link_rows: int = 3) -> int:
 def run_lanczos(args):
     """--workload lanczos: the LapH eigenvectors, the 64 lowest eigenpairs of the 3-d gauge-covariant Laplacian
     on every timeslice of an L=32, T=64 lattice (batched Lanczos, 128 Krylov steps on a degree-48 Chebyshev
-    filter), smoothed synthetic links."""
+    filter), smoothed synthetic links.  Under torchrun every rank solves its own seeded batch of T timeslices on
+    its own GPU (the timeslices are independent problems: no collective on the data path); the time is the
+    slowest rank's and the value counts the timeslices of all ranks."""
     import torch
+    import torch.distributed as dist
     from paper_2510_26313_gb300 import binding as laph
     from oracle import oracle as O
-    torch.cuda.set_device(0)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     c = LANCZOS[args.workload]
     L, T, n_ev, m, d, lo = c["L"], c["T"], c["n_ev"], c["m"], c["degree"], c["lo"]
     V = L ** 3
-    U = synth.random_links_device(L, T, c["eps"], synth.SEED_BASE + 21)
+    U = synth.random_links_device(L, T, c["eps"], synth.SEED_BASE + 21 + 1000 * rank)
     evecs = torch.empty((T, n_ev, V, 3), dtype=torch.complex64, device="cuda")
     ws = torch.empty(laph.lanczos_workspace_size(L, T, n_ev, m, d, lo), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         laph.lanczos(U, L, n_ev, m, cheb_degree=d, cheb_lo=lo, out=evecs, workspace=ws, stream=stream)
     torch.cuda.synchronize()
-    clocks = ClockSampler(0)
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
     clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -414,8 +424,10 @@ def run_lanczos(args):
         stats.append(st)
     e1.record(stream)
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, "cuda")
     apply_ms = sum(s["apply_ms"] for s in stats) / args.steps
     orth_ms = sum(s["orth_ms"] for s in stats) / args.steps
     n_apply = stats[0]["apply_launches"]
@@ -462,11 +474,13 @@ def run_lanczos(args):
             laph.lanczos(Ud, L, n_ev, m, cheb_degree=d, cheb_lo=lo, out=evecs, workspace=ws, stream=stream)
             out_host.copy_(evecs, non_blocking=True)
             torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / args.e2e_steps
-        e2e = {"value": T / dt, "unit": "timeslices/s", "h2d_bytes_per_step": U_host.numel() * 8,
+        if world > 1:
+            dist.barrier()
+        dt = max_over_ranks(1e3 * (time.perf_counter() - t0) / args.e2e_steps, "cuda") / 1e3
+        e2e = {"value": world * T / dt, "unit": "timeslices/s", "h2d_bytes_per_step": U_host.numel() * 8,
                "d2h_bytes_per_step": out_host.numel() * 8 + T * n_ev * 16}
     cpu = None
-    if not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline:
         # the oracle has no iterative eigensolver at this size (its reference is a dense Hermitian solve): time its
         # FP64 Laplacian stencil on timeslice 0 and scale to the m (d) operator applications of one solve,
         # leaving out the orthogonalisation (in the CPU's favour)
@@ -483,13 +497,15 @@ def run_lanczos(args):
                          f"{m * d} applications of one solve (orthogonalisation not counted)"}
     line = {
         "metric": f"LapH eigenvectors: timeslices/s for the {n_ev} lowest eigenpairs of the 3-d Laplacian at L={L}",
-        "value": T / (ms / 1e3), "unit": "timeslices/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "value": world * T / (ms / 1e3), "unit": "timeslices/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 vectors, f64 inner products",
         "data": f"synthetic smoothed SU(3) links (polar part of 1 + i {c['eps']} H, H Hermitian Gaussian)",
         "config": {"workload": f"L={L},T={T},n_ev={n_ev} (lanczos: m={m}, Chebyshev degree {d}, lo={lo})",
                    "L": L, "T": T, "n_ev": n_ev, "n_krylov": m, "cheb_degree": d, "cheb_lo": lo,
                    "ts_group": tg, "link_rows": rows,
+                   "parallelism": f"replicas x{world} (independent timeslice batches)",
                    "l2": f"inputs larger than L2: links {U.numel() * 8 / 1e9:.2f} GB, basis "
                          f"{T * (m + 1) * 3 * V * 8 / 1e9:.1f} GB"},
         "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
@@ -511,7 +527,10 @@ def run_lanczos(args):
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(sum(s["launches"] for s in stats)), "clocks": clk,
         "laplacian_api": lap_api,
     }
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
     return 0
 
 
