@@ -117,7 +117,8 @@ def test_entry_points_reject_null_pointers(lib):
                 binding.laph_lanczos_params(40, 8, 0.0, 0),       # filter without a bound
                 binding.laph_lanczos_params(40, 8, 12.5, 0),      # bound above the spectrum
                 binding.laph_lanczos_params(40, -1, 1.0, 0),
-                binding.laph_lanczos_params(40, 0, 0.0, 0, 0, 0, 1)]:   # link rows other than 0, 2, 3
+                binding.laph_lanczos_params(40, 0, 0.0, 0, 0, 0, 1),    # link rows other than 0, 2, 3
+                binding.laph_lanczos_params(40, 8, 1.0, 0, -1)]:        # negative filter group
         assert lib.laph_lanczos(fake, 4, 1, 8, ctypes.byref(bad), fake, ev, None, None, 0, None, None) == binding.LAPH_ERR_ARG
         n = ctypes.c_size_t(0)
         assert lib.laph_lanczos_workspace_size(4, 1, 8, ctypes.byref(bad), ctypes.byref(n)) == binding.LAPH_ERR_ARG
