@@ -184,3 +184,18 @@ def test_lanczos_links_outside_su3_use_all_three_rows(laph):
     vecs, ev, res = laph.lanczos(torch.from_numpy(Up).cuda(), L, n_ev, 3 * L ** 3, stats=st)
     assert st["links_two_rows"] == 0
     check_against_dense(Up, L, n_ev, ev, vecs.cpu().numpy(), res)
+
+
+@pytest.mark.parametrize("link_rows,pdl", [(3, False), (2, True)])
+def test_lanczos_odd_lattice_ragged_filter_groups(laph, link_rows, pdl):
+    """L = 7 (V odd: the solver's plain layouts), T = 3 timeslices filtered in groups of 2 (the last group ragged),
+    links read as three rows or as two (SU(3) rebuilt), filter steps launched plainly or as programmatic dependents;
+    every timeslice against the dense solver.  lo = 1.6 lies above the 17 lowest eigenvalues of each timeslice."""
+    import torch
+    L, T, n_ev = 7, 3, 12
+    U = synth.random_links(L, T, instance=77, eps=0.6)
+    st = {}
+    vecs, ev, res = laph.lanczos(torch.from_numpy(U).cuda(), L, n_ev, 60, cheb_degree=8, cheb_lo=1.6, ts_group=2,
+                                 link_rows=link_rows, pdl=pdl, stats=st)
+    assert st["ts_group"] == 2 and st["links_two_rows"] == (link_rows == 2)
+    check_against_dense(U, L, n_ev, ev, vecs.cpu().numpy(), res)
