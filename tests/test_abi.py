@@ -166,3 +166,27 @@ def test_product_path_does_not_reference_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt and "laph_oracle" not in txt, f
+
+
+def test_binding_validates_links_and_vectors_before_calling_the_library(lib):
+    """The Laplacian and Lanczos wrappers refuse host tensors, wrong dtypes and wrong shapes with ValueError (no
+    library call, no GPU needed)."""
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    from paper_2510_26313_gb300 import binding
+    L = 4
+    U = torch.zeros((1, 3, L ** 3, 3, 3), dtype=torch.complex64)            # host tensor
+    f = torch.zeros((1, 2, L ** 3, 3), dtype=torch.complex64)
+    with pytest.raises(ValueError):
+        binding.laplacian(U, f, L)
+    with pytest.raises(ValueError):
+        binding.lanczos(U, L, 4, 20)
+    with pytest.raises(ValueError):
+        binding.lanczos(U.to(torch.complex128), L, 4, 20)
+    with pytest.raises(ValueError):
+        binding.lanczos(U[:, :2].contiguous(), L, 4, 20)                     # two directions
+    n = binding.lanczos_workspace_size(L, 1, 4, 20)
+    assert n >= 8 * 3 * L ** 3 * (20 + 1 + 4)
+    with pytest.raises(binding.LaphError):
+        binding.lanczos_workspace_size(L, 1, 30, 20)                         # n_ev > n_krylov
+    assert np.isfinite(n)
