@@ -199,9 +199,9 @@ LAPH_API int laph_projection(const void *v, const void *s, int L, int T, int Nv,
 /*   (-Delta f)(x) = sum_mu [ 2 f(x) - U_mu(x) f(x + mu) - U_mu(x - mu)^dagger f(x - mu) ]
  * over the three spatial directions, periodic.  U: device complex64
  * [T][3][L^3][3][3] (row-major SU(3) colour matrices per direction and site);
- * f, out: device complex64 [T][nvec][L^3][3].  Asynchronous on `stream`, no
- * allocation.  LAPH_ERR_ARG for L < 2, T < 1, nvec < 1, null or misaligned
- * pointers. */
+ * f, out: device complex64 [T][nvec][L^3][3], 8-byte aligned.  Asynchronous
+ * on `stream`, no allocation.  LAPH_ERR_ARG for L < 2 or L > 1024, T or nvec
+ * outside [1, 65535], null or misaligned pointers. */
 LAPH_API int laph_laplacian(const void *U, const void *f, void *out, int L, int T, int nvec, void *stream);
 
 typedef struct {
@@ -223,8 +223,8 @@ typedef struct {
  * applications of -Delta (or of the filter); the orthogonalisation with the
  * norm of each new basis vector (including its read-back to the host); the
  * Ritz vectors, Rayleigh quotients and residuals.  Launches of this
- * library's kernels, of which the Laplacian launches (each over all T
- * timeslices, one vector each). */
+ * library's kernels, of which the Laplacian launches (each over one filter
+ * group of timeslices, or all T without a filter, one vector each). */
 typedef struct {
     double total_ms;
     double setup_ms;
@@ -245,16 +245,19 @@ typedef struct {
 LAPH_API int laph_lanczos_workspace_size(int L, int T, int n_ev, const laph_lanczos_params *params, size_t *bytes);
 
 /* The n_ev lowest eigenpairs of -Delta on every timeslice: Lanczos with full
- * reorthogonalisation (FP32 vectors, FP64 inner products) on -Delta or its
- * Chebyshev filter, Ritz vectors, then Rayleigh quotients and residuals with
- * -Delta.  evecs: device complex64 [T][n_ev][L^3][3], unit norm; evals, resid:
+ * reorthogonalisation (two Gram-Schmidt passes; FP32 vectors, inner products
+ * summed in FP32 within a warp and in FP64 across warps and blocks) on -Delta
+ * or its Chebyshev filter, Ritz vectors, then Rayleigh quotients and residuals
+ * with -Delta.  U as for laph_laplacian.  evecs: device complex64 [T][n_ev][L^3][3], unit norm; evals, resid:
  * HOST double [T][n_ev], ascending eigenvalues and |(-Delta) v - lambda v|
  * (resid may be NULL); stats (may be NULL) receives the timings above.
  * workspace: device memory of laph_lanczos_workspace_size bytes, 256-byte
  * aligned (workspace_bytes its size), or NULL to have the call allocate it on
  * `stream` and free it before returning.  Synchronises the stream once per
  * Krylov step and blocks until done.  LAPH_ERR_ARG for bad parameters
- * (2 <= L <= 512, n_ev <= n_krylov, the bounds on n_krylov and the filter above),
+ * (2 <= L <= 512, 1 <= T <= 65535, n_ev <= n_krylov, the bounds on n_krylov
+ * and the filter above, ts_group < 0, link_rows other than 0, 2, 3), for
+ * null or misaligned (8-byte) pointers and when the host QL does not converge,
  * LAPH_ERR_WORKSPACE for a workspace too small or misaligned. */
 LAPH_API int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_params *params, void *evecs,
                           double *evals, double *resid, void *workspace, size_t workspace_bytes,
