@@ -41,6 +41,12 @@ WORKLOADS = {
 }
 METRIC = "baryon+meson block complex TFLOP/s at L=32,N=64,Np=19; tensor-pipe %; rel err vs FP64"
 
+# DRAM bytes (read + write) of tc_kernel per byte of B-operand stage images it consumes, from the ncu capture
+# summarised in profiles/tc_kernel_L24_T2_N64_P19_full.md (2.013 GB of DRAM traffic for 2 x 13 x 1728 stage images
+# of 36,864 B); the contraction's DRAM traffic is dominated by those images, so a launch's traffic is this ratio times
+# its image bytes.  To be retaken whenever the kernel changes.
+TC_DRAM_PER_IMAGE_BYTE = 2.013e9 / (2 * 13 * 1728 * 36864)
+
 
 def momenta_for(name):
     L, T, N, n2 = WORKLOADS[name]
@@ -624,6 +630,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--ref-triples", type=int, default=6000)
     ap.add_argument("--chunk-sites", type=int, default=0)
+    ap.add_argument("--sum-sites", type=int, default=0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -656,7 +663,8 @@ def main():
     # ---- inputs: seeded per rank (weak scaling), host generation, then resident in HBM
     phi_h = synth.random_phi(L, N, T=T, instance=rank)
     phi = torch.from_numpy(phi_h).cuda()
-    plan = laph.Plan([(L, T, N, mom)], mode=args.mode, flags=laph.PLAN_TIMING, chunk_sites=args.chunk_sites)
+    plan = laph.Plan([(L, T, N, mom)], mode=args.mode, flags=laph.PLAN_TIMING, chunk_sites=args.chunk_sites,
+                     sum_sites=args.sum_sites)
     Bs, Ms = plan.alloc_outputs()
     ws = plan.alloc_workspace()
     stream = torch.cuda.current_stream()
@@ -689,6 +697,7 @@ def main():
     n_con = plan.contraction_launches()
     kernel_ms = plan.kernel_times(args.steps * n_con)
     operand_ms = plan.operand_times(args.steps * n_con) if args.mode != "fp32" else []
+    reduce_ms = plan.reduce_times(args.steps * n_con) if args.mode != "fp32" else []
     ms = max_over_ranks(ms, "cuda")
     status = plan.device_status()
 
@@ -700,19 +709,47 @@ def main():
     tc = args.mode != "fp32"
     if tc:
         peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        n_ct = -(-(N * P) // 96)
+        images = T * n_ct * (-(-(3 * V) // 24)) * 36864           # stage images read per step
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": TC_DRAM_PER_IMAGE_BYTE * images / n_con,
+                "traffic_source": "per tc_kernel launch: DRAM bytes per stage-image byte from the ncu capture at "
+                                  "L=24, T=2 (profiles/tc_kernel_L24_T2_N64_P19_full.md) x this launch's image bytes",
                 "peak_source": f"{peak_src} bf16 dense sustained (cuBLAS); FP16 runs at the bf16 rate",
                 "note": "achieved counts algorithmic flops; the 3-term split executes 3x that on the tensor pipe"}
         # B-operand stage images: HBM-bound, algorithmic bytes = images written + phi read once
-        n_ct = -(-(N * P) // 96)
-        n_st = -(-(3 * V) // 32)
-        psi_bytes = T * (n_ct * n_st * 49152 + N * V * 3 * 8)
+        psi_bytes = images + T * N * V * 3 * 8
         o_avg = sum(operand_ms) / args.steps
         hbm = float(peaks.get("hbm_gbs", 6800.0))
+        # the step's own algorithmic bytes: phi in, B and M out (complex128)
+        step_bytes = T * (N * V * 3 * 8 + P * (math.comb(N, 3) + N * N) * 16)
         roof["operand_kernel"] = {"name": "psi_kernel", "ms_per_step": o_avg, "bound": "hbm",
                                   "achieved": psi_bytes / (o_avg / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
-                                  "frac": psi_bytes / (o_avg / 1e3) / 1e9 / hbm}
+                                  "frac": psi_bytes / (o_avg / 1e3) / 1e9 / hbm,
+                                  "image_bytes_per_step": psi_bytes, "step_algorithmic_bytes": step_bytes,
+                                  "images_over_step_bytes": psi_bytes / step_bytes,
+                                  "note": "bytes = stage images written + phi read; the images are an intermediate "
+                                          "of this design, written once and read back by the contraction"}
+        # FP64 site reduction: FP32 partials of every site block read, complex128 outputs written
+        r_avg = sum(reduce_ms) / args.steps
+        sum_sites, n_sc = plan.sum_sites()
+        n_out = P * (math.comb(N, 3) + N * N)
+        red_bytes = T * n_out * (n_sc * 8 + 16)
+        roof["reduce_kernel"] = {"name": "reduce_kernel", "event_ms_per_step": r_avg, "site_blocks": n_sc,
+                                 "sum_sites": sum_sites, "bytes_per_step": red_bytes,
+                                 "note": "runs on a side stream beside the next chunk's B-operand pass, so its event "
+                                         "time includes that overlap; bound by FP64 additions (2 (blocks - 1) per "
+                                         "complex output), not by HBM"}
+        # executed tensor work: every MMA of every tile (3 split terms, padding, triangle waste)
+        mma = plan.tensor_flops()
+        executed = mma / (k_avg / 1e3) / 1e12
+        sm_mhz = (clk.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0)))
+        clock_peak = 152 * 8192 * sm_mhz * 1e6 / 1e12
+        roof["tensor_pipe"] = {"executed_tflops": executed, "executed_over_algorithmic": mma / flops_step,
+                               "frac_of_sustained_peak": executed / peak,
+                               "issue_peak_at_median_clock": clock_peak, "frac_of_issue_peak": executed / clock_peak,
+                               "note": "tensor-pipe utilisation estimated from the MMAs issued: executed flops / "
+                                       "kernel time / (152 SMs x 8192 flops per cycle x median SM clock)"}
     else:
         # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock
         smax = float(peaks.get("sm_max_mhz", 2070.0))

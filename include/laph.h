@@ -70,8 +70,11 @@ extern "C" {
 /* FP32 CUDA-core path: FP32 products and partial sums, FP64 site reduction. */
 #define LAPH_MODE_FP32_SIMT 0
 /* tcgen05 tensor cores, each operand split into hi+lo FP16 after an exact
- * power-of-two rescale; products hi*hi + hi*lo + lo*hi, FP32 accumulation in
- * tensor memory, FP64 reduction across site chunks. */
+ * power-of-two rescale; products hi*hi + hi*lo + lo*hi accumulated in FP32 in
+ * tensor memory, drained every 128 sites (the plan's chunk_sites) into FP32
+ * running sums with round-to-nearest over a block of 4096 sites; the FP32
+ * partials of the blocks are then summed in FP64, in block order, and
+ * scaled back into the complex128 output. */
 #define LAPH_MODE_TC_F16X3 1
 /* as above with BF16 hi+lo. */
 #define LAPH_MODE_TC_BF16X3 2
@@ -257,7 +260,7 @@ LAPH_API int laph_lanczos_workspace_size(int L, int T, int n_ev, const laph_lanc
  * Krylov step and blocks until done.  LAPH_ERR_ARG for bad parameters
  * (2 <= L <= 512, 1 <= T <= 65535, n_ev <= n_krylov, the bounds on n_krylov
  * and the filter above, ts_group < 0, link_rows other than 0, 2, 3), for
- * null or misaligned (8-byte) pointers and when the host QL does not converge,
+ * null or misaligned (8-byte) pointers and when the host tridiagonal solver does not converge,
  * LAPH_ERR_WORKSPACE for a workspace too small or misaligned. */
 LAPH_API int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_params *params, void *evecs,
                           double *evals, double *resid, void *workspace, size_t workspace_bytes,
@@ -265,7 +268,7 @@ LAPH_API int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanc
 
 /* Host utility: eigenvalues (ascending, in d) and orthonormal eigenvectors
  * (z, n x n row-major, column k for d[k]) of the symmetric tridiagonal matrix
- * with diagonal d[0..n) and off-diagonal e[0..n-1); implicit-shift QL.  No
+ * with diagonal d[0..n) and off-diagonal e[0..n-1); symmetric QR with implicit Wilkinson shifts.  No
  * GPU involved.  LAPH_ERR_ARG for bad arguments or no convergence. */
 LAPH_API int laph_tridiag_eigen(int n, double *d, const double *e, double *z);
 
@@ -276,6 +279,28 @@ LAPH_API int laph_tridiag_eigen(int n, double *d, const double *e, double *z);
  * and picks the schedule (LAPH_PLAN_AUTOTUNE times candidates on an internal
  * stream, see laph_plan_schedule).  *plan is set only on success. */
 LAPH_API int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned flags, laph_plan **plan);
+
+/* Numerical parameters of a plan; 0 picks the default. */
+typedef struct {
+    int chunk_sites; /* tensor-core modes: sites the tensor core accumulates in FP32 before its sums are drained
+                        into FP32 running sums with round-to-nearest (default 128; the error of the tensor core's
+                        accumulation grows with it); FP32 mode: sites summed in FP32 before the FP64 reduction
+                        (default 1024) */
+    int sum_sites;   /* tensor-core modes: sites per block of the FP64 site reduction (default 4096, rounded down
+                        to a multiple of 8): a tile covers one block, its running sums become one FP32 partial per
+                        output, and the partials of all blocks are added in FP64 in block order */
+} laph_plan_options;
+
+/* laph_plan_create with numerical parameters (opts may be NULL).  LAPH_ERR_ARG
+ * for a negative value or one above 2^24, plus the conditions of
+ * laph_plan_create. */
+LAPH_API int laph_plan_create_opts(const laph_instance *inst, int n_inst, int mode, unsigned flags,
+                                   const laph_plan_options *opts, laph_plan **plan);
+
+/* Sites per block of the tensor-core path's FP64 site reduction and the
+ * largest number of blocks (FP32 partials per output) of any instance; 0 and
+ * 0 for the FP32 mode.  Either pointer may be NULL. */
+LAPH_API int laph_plan_sum_sites(const laph_plan *plan, int *sum_sites, int *max_site_blocks);
 
 /* Bytes of device workspace laph_plan_execute needs (256-byte aligned). */
 LAPH_API int laph_plan_workspace_size(const laph_plan *plan, size_t *bytes);
@@ -329,6 +354,11 @@ LAPH_API int laph_plan_kernel_times(laph_plan *plan, int n, float *ms);
  * images), one per chunk of timeslices.  LAPH_ERR_ARG for the FP32 mode. */
 LAPH_API int laph_plan_operand_times(laph_plan *plan, int n, float *ms);
 
+/* Same for the FP64 site reductions of the tensor-core path (one per
+ * contraction launch: the FP32 partials of the chunk's site blocks summed in
+ * FP64 into the outputs).  LAPH_ERR_ARG for the FP32 mode. */
+LAPH_API int laph_plan_reduce_times(laph_plan *plan, int n, float *ms);
+
 /* Contraction-kernel launches per laph_plan_execute: the tensor-core path
  * processes the batch's timeslices in chunks whose B-operand images fit its
  * workspace (at most 24 GiB), one launch per chunk. */
@@ -350,6 +380,13 @@ LAPH_API int laph_plan_contraction_launches(const laph_plan *plan, int *n);
  * pointer may be NULL. */
 LAPH_API int laph_plan_schedule(const laph_plan *plan, int64_t *timeslices_per_chunk, int *tile_order, int *n_chunks,
                                int *n_candidates, float *candidate_ms);
+
+/* Floating-point operations the tensor pipe executes per laph_plan_execute
+ * on the tensor-core path: every tcgen05.mma of every tile, 2 x 128 rows x
+ * the tile's real B columns x 16 K entries per k-step, all split terms, the
+ * padding and the triangle waste included (0 for the FP32 mode).  Divided by
+ * the contraction kernels' time it gives the executed tensor rate. */
+LAPH_API int laph_plan_tensor_flops(const laph_plan *plan, double *flops);
 
 /* Number of kernels of this library one laph_plan_execute launches. */
 LAPH_API int laph_plan_launches_per_execute(const laph_plan *plan, int *n);
@@ -374,15 +411,25 @@ LAPH_API int laph_plan_destroy(laph_plan *plan);
  *          at least one of them non-NULL, each 16-byte aligned; the caller
  *          owns both and the outputs need no clearing;
  *   momenta HOST int32 [n_mom][3], read before the function returns.
+ * phi, out_B and out_M must be device memory of the current device and
+ * exactly the sizes listed: the function cannot check the size of a device
+ * buffer, so an undersized or misplaced buffer is undefined behaviour (an
+ * out-of-bounds access on the GPU), not an error code.
  * Limits: 1 <= n_mom <= 64, N >= 3 when out_B is given, N <= 3 L^3, and the
- * scratch (about 8 * n_mom * L^3 bytes of phase table plus 48 bytes per
- * (row tile, column tile, timeslice)) must fit the array: larger inputs
- * return LAPH_ERR_WORKSPACE before any launch.  Asynchronous on `stream`.
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call outside any stream capture.
- * Every call shares the array and leaves its contents behind; each call
- * rewrites what it reads, but calls that may overlap on the GPU (different
- * streams or threads without ordering between them) race on the array. */
+ * scratch (8 * n_mom * L^3 bytes of phase table, plus 72 bytes -- one tile
+ * record -- per (64-row tile, 64-column tile, timeslice), plus the
+ * descriptor and the momenta, each region rounded up to 256 bytes) must fit
+ * the array: larger inputs return LAPH_ERR_WORKSPACE before any launch.
+ * Asynchronous on `stream`.
+ * The array's device address is looked up once per CUDA context (normally
+ * once per device, in its primary context) by the first call made in that
+ * context (cudaGetSymbolAddress); make that first call outside any stream
+ * capture.  A context created later on the same device (after
+ * cudaDeviceReset, or one made current through the driver API) gets its own
+ * lookup.  Every call shares the array and leaves its contents behind; each
+ * call rewrites what it reads, but calls that may overlap on the GPU
+ * (different streams or threads without ordering between them) race on the
+ * array. */
 #define LAPH_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 LAPH_API int laph_blocks_noalloc(const void *phi, int L, int T, int N, const int32_t *momenta, int n_mom, void *out_B,
                                  void *out_M, void *stream);

@@ -47,6 +47,10 @@ class laph_instance(ctypes.Structure):
                 ("momenta", ctypes.POINTER(ctypes.c_int32)), ("n_col", ctypes.c_int)]
 
 
+class laph_plan_options(ctypes.Structure):
+    _fields_ = [("chunk_sites", ctypes.c_int), ("sum_sites", ctypes.c_int)]
+
+
 class laph_lanczos_params(ctypes.Structure):
     _fields_ = [("n_krylov", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("cheb_lo", ctypes.c_double),
                 ("seed", ctypes.c_uint32), ("ts_group", ctypes.c_int), ("pdl", ctypes.c_int),
@@ -84,6 +88,9 @@ def lib() -> ctypes.CDLL:
             "laph_plan_execute_fields": (i32, [vp, vpp, vpp, vp, vp]),
             "laph_projection": (i32, [vp, vp, i32, i32, i32, i32, ip32, i32, vp, i32, vp]),
             "laph_plan_create": (i32, [ctypes.POINTER(laph_instance), i32, i32, ctypes.c_uint, ctypes.POINTER(vp)]),
+            "laph_plan_create_opts": (i32, [ctypes.POINTER(laph_instance), i32, i32, ctypes.c_uint,
+                                            ctypes.POINTER(laph_plan_options), ctypes.POINTER(vp)]),
+            "laph_plan_sum_sites": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
             "laph_plan_workspace_size": (i32, [vp, ctypes.POINTER(sz)]),
             "laph_plan_execute": (i32, [vp, vpp, vpp, vpp, vp, vp]),
             "laph_plan_host_workspace_size": (i32, [vp, ctypes.POINTER(sz)]),
@@ -94,6 +101,8 @@ def lib() -> ctypes.CDLL:
             "laph_plan_set_chunk_sites": (i32, [vp, i32]),
             "laph_plan_kernel_times": (i32, [vp, i32, ctypes.POINTER(ctypes.c_float)]),
             "laph_plan_operand_times": (i32, [vp, i32, ctypes.POINTER(ctypes.c_float)]),
+            "laph_plan_reduce_times": (i32, [vp, i32, ctypes.POINTER(ctypes.c_float)]),
+            "laph_plan_tensor_flops": (i32, [vp, ctypes.POINTER(ctypes.c_double)]),
             "laph_plan_contraction_launches": (i32, [vp, ctypes.POINTER(i32)]),
             "laph_plan_launches_per_execute": (i32, [vp, ctypes.POINTER(i32)]),
             "laph_plan_schedule": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i32),
@@ -340,15 +349,36 @@ def tridiag_eigen(d, e):
     return d, z
 
 
+def _check_out(out, shape, phi, name):
+    """An output tensor must be exactly what the C side will write: complex128, contiguous, the stated
+    shape, on phi's device, which must be the current device."""
+    import torch
+    if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.complex128 and out.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous complex128 CUDA tensor")
+    if tuple(out.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(out.shape)}")
+    if out.device != phi.device or phi.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} and phi must be on the current CUDA device")
+
+
 def blocks_noalloc(phi, L: int, momenta, out_B, out_M, stream=None):
     """FP32 B and/or M into caller-owned outputs with no device allocation.
 
     out_B: complex128 [T][P][C(N,3)] or None; out_M: complex128 [T][P][N][N]
     or None.  Asynchronous on `stream`; the library's fixed scratch array is
-    shared by all calls, so calls must not overlap on the GPU.
+    shared by all calls, so calls must not overlap on the GPU.  The outputs
+    are checked here (dtype, device, contiguity, exact shape) because the C
+    entry point cannot check the size of a device buffer.
     """
     T, N = _check_phi(phi, L)
     mom = _momenta(momenta)
+    P = mom.shape[0]
+    if out_B is None and out_M is None:
+        raise ValueError("at least one of out_B and out_M is needed")
+    if out_B is not None:
+        _check_out(out_B, (T, P, N * (N - 1) * (N - 2) // 6), phi, "out_B")
+    if out_M is not None:
+        _check_out(out_M, (T, P, N, N), phi, "out_M")
     rc = lib().laph_blocks_noalloc(_ptr(phi), L, T, N, mom.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                    mom.shape[0], _ptr(out_B) if out_B is not None else None,
                                    _ptr(out_M) if out_M is not None else None, _stream(stream))
@@ -363,7 +393,7 @@ class Plan:
     B[n] complex128 [T][P][C(N,3)], M[n] complex128 [T][P][N][N].
     """
 
-    def __init__(self, instances, mode="f16x3", flags: int = 0, chunk_sites: int = 0):
+    def __init__(self, instances, mode="f16x3", flags: int = 0, chunk_sites: int = 0, sum_sites: int = 0):
         # (L, T, N, momenta) or, for doublet plans of two vector counts, (L, T, N, momenta, n_col)
         self._moms = [_momenta(inst[3]) for inst in instances]
         self.n_col = [int(inst[4]) if len(inst) > 4 else 0 for inst in instances]
@@ -377,10 +407,10 @@ class Plan:
         self.flags = flags
         self.mode = _mode(mode)
         h = ctypes.c_void_p()
-        _check(lib().laph_plan_create(arr, len(instances), self.mode, flags, ctypes.byref(h)), "laph_plan_create")
+        opts = laph_plan_options(int(chunk_sites), int(sum_sites))
+        _check(lib().laph_plan_create_opts(arr, len(instances), self.mode, flags, ctypes.byref(opts), ctypes.byref(h)),
+               "laph_plan_create_opts")
         self._h = h
-        if chunk_sites:
-            _check(lib().laph_plan_set_chunk_sites(self._h, int(chunk_sites)), "laph_plan_set_chunk_sites")
 
     @property
     def handle(self):
@@ -404,6 +434,12 @@ class Plan:
         return dict(mode=v[0].value, tile_rows=v[1].value, tile_cols=v[2].value, chunk_sites=v[3].value,
                     grid=v[4].value, n_tiles=int(nt.value))
 
+    def sum_sites(self) -> tuple:
+        """(sites per block of the FP64 site reduction, largest number of blocks of any instance)."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(lib().laph_plan_sum_sites(self._h, ctypes.byref(a), ctypes.byref(b)), "laph_plan_sum_sites")
+        return int(a.value), int(b.value)
+
     def kernel_times(self, n: int) -> list:
         """Durations (ms) of the last n contraction-kernel launches (needs PLAN_TIMING)."""
         arr = (ctypes.c_float * n)()
@@ -415,6 +451,18 @@ class Plan:
         arr = (ctypes.c_float * n)()
         _check(lib().laph_plan_operand_times(self._h, n, arr), "laph_plan_operand_times")
         return [float(x) for x in arr]
+
+    def reduce_times(self, n: int) -> list:
+        """Durations (ms) of the last n FP64 site reductions of the tensor-core path (needs PLAN_TIMING)."""
+        arr = (ctypes.c_float * n)()
+        _check(lib().laph_plan_reduce_times(self._h, n, arr), "laph_plan_reduce_times")
+        return [float(x) for x in arr]
+
+    def tensor_flops(self) -> float:
+        """Flops the tensor pipe executes per execute (all split terms, padding and triangle waste)."""
+        v = ctypes.c_double()
+        _check(lib().laph_plan_tensor_flops(self._h, ctypes.byref(v)), "laph_plan_tensor_flops")
+        return float(v.value)
 
     def contraction_launches(self) -> int:
         """Contraction-kernel launches per execute (one per chunk of timeslices)."""

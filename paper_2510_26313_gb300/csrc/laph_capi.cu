@@ -57,6 +57,10 @@ constexpr int32_t MAX_MOM = 1 << 20;
 // error grows linearly with the number of additions, on the split path.
 constexpr int SIMT_DEFAULT_CHUNK = 1024;
 constexpr int TC_DEFAULT_CHUNK = 128;
+// Tensor-core path: sites per block of the FP64 site reduction.  A tile
+// covers one block; its FP32 running sums become one FP32 partial per
+// output, and the partials of all blocks are added in FP64.
+constexpr int TC_DEFAULT_SUM = 8192;
 // Largest B-operand buffer of the tensor-core path: the timeslices of a batch
 // are processed in chunks whose stage images fit in it.
 constexpr size_t PSI_CAP_BYTES = 24ull << 30;
@@ -79,6 +83,7 @@ struct laph_plan {
     long long n_tiles = 0;
     int *d_status = nullptr;
     int tile_rows = 0, tile_cols = 0, chunk_sites = 0, grid = 0;
+    int sum_sites = 0;                         // tensor-core path: sites per block of the FP64 reduction
     int max_staged = 0, max_P = 0;
     size_t ws_bytes = 0, off_maxbits = 0, off_counter = 0, ws_zero_bytes = 0;
     // tensor-core path: chunks of (instance, timeslice) units and their B-operand images
@@ -86,11 +91,17 @@ struct laph_plan {
     std::vector<laph::PsiUnit> h_units;
     // laph_plan_execute_host: copy streams and per-chunk events, made on first use
     cudaStream_t h2d = nullptr, d2h = nullptr;
+    // tensor-core path: the FP64 site reduction of chunk c runs on `side`
+    // while the B-operand pass of chunk c+1 runs on the caller's stream;
+    // ev_tc[c]: contraction c done, ev_red[c]: reduction c done
+    cudaStream_t side = nullptr;
+    std::vector<cudaEvent_t> ev_tc, ev_red;
     std::vector<cudaEvent_t> ev_in, ev_out;
     struct Chunk {
         int unit0, n_units;
         long long n_jobs;
         long long tile0, n_tiles;
+        long long n_red;   // blocks of the FP64 reduction
     };
     std::vector<Chunk> chunks;
     // schedule of the tensor-core path: timeslices per chunk (0: chunks filled by
@@ -100,11 +111,16 @@ struct laph_plan {
     int sched_order = 0;
     bool tuned = false;
     std::vector<float> tune_ms;
-    size_t off_psi = 0;
+    size_t off_psi = 0, off_part = 0;
+    // tensor-core path: flops the tensor pipe executes per execute (every MMA of
+    // every tile: 2 x 128 rows x the tile's real columns x 48 real K entries
+    // per stage x the split terms)
+    double mma_flops = 0.0;
     // LAPH_PLAN_TIMING: ring of event pairs around the contraction launches
     static constexpr int RING = 256;
     // (contraction launches; pv_* for the B-operand launches of the tensor-core path)
-    std::vector<cudaEvent_t> ev_begin, ev_end, pv_begin, pv_end;
+    // (rd_*: the FP64 site reductions, in the slots of their contraction launches)
+    std::vector<cudaEvent_t> ev_begin, ev_end, pv_begin, pv_end, rd_begin, rd_end;
     long long n_timed = 0, n_ptimed = 0;
 };
 
@@ -185,18 +201,24 @@ static void free_plan(laph_plan *p)
     for (cudaEvent_t e : p->ev_out) cudaEventDestroy(e);
     if (p->h2d) cudaStreamDestroy(p->h2d);
     if (p->d2h) cudaStreamDestroy(p->d2h);
+    for (cudaEvent_t e : p->ev_tc) cudaEventDestroy(e);
+    for (cudaEvent_t e : p->ev_red) cudaEventDestroy(e);
+    if (p->side) cudaStreamDestroy(p->side);
     cudaFree(p->d_tiles);
     cudaFree(p->d_status);
     for (cudaEvent_t e : p->ev_begin) cudaEventDestroy(e);
     for (cudaEvent_t e : p->ev_end) cudaEventDestroy(e);
     for (cudaEvent_t e : p->pv_begin) cudaEventDestroy(e);
     for (cudaEvent_t e : p->pv_end) cudaEventDestroy(e);
+    for (cudaEvent_t e : p->rd_begin) cudaEventDestroy(e);
+    for (cudaEvent_t e : p->rd_end) cudaEventDestroy(e);
     delete p;
 }
 
 static int autotune_time(laph_plan *p, const std::vector<std::pair<long long, int>> &cand,
                          const std::function<void(long long, int)> &emit, const std::function<cudaError_t()> &upload,
                          size_t *best);
+static cudaError_t ensure_side(laph_plan *p);
 
 static int tc_supported(int device)
 {
@@ -208,7 +230,15 @@ static int tc_supported(int device)
 
 int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned flags, laph_plan **plan_out)
 {
+    return laph_plan_create_opts(inst, n_inst, mode, flags, nullptr, plan_out);
+}
+
+int laph_plan_create_opts(const laph_instance *inst, int n_inst, int mode, unsigned flags, const laph_plan_options *opts,
+                          laph_plan **plan_out)
+{
     if (!inst || n_inst < 1 || !plan_out) return LAPH_ERR_ARG;
+    const int opt_chunk = opts ? opts->chunk_sites : 0, opt_sum = opts ? opts->sum_sites : 0;
+    if (opt_chunk < 0 || opt_chunk > (1 << 24) || opt_sum < 0 || opt_sum > (1 << 24)) return LAPH_ERR_ARG;
     if (mode < 0 || mode >= LAPH_NUM_MODES) return LAPH_ERR_ARG;
     const bool skipB = flags & LAPH_PLAN_SKIP_B, skipM = flags & LAPH_PLAN_SKIP_M;
     if (skipB && skipM) return LAPH_ERR_ARG;
@@ -243,7 +273,7 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
     const bool tc = is_tc_mode(mode);
     p->tile_rows = tc ? laph::TC_TR : laph::SIMT_TR;
     p->tile_cols = tc ? laph::TC_TC : laph::SIMT_TC;
-    p->chunk_sites = tc ? TC_DEFAULT_CHUNK : SIMT_DEFAULT_CHUNK;
+    p->chunk_sites = opt_chunk ? opt_chunk : (tc ? TC_DEFAULT_CHUNK : SIMT_DEFAULT_CHUNK);
 
     // ---- per-instance descriptors and phase tables
     long long phase_total = 0;
@@ -282,6 +312,8 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
                                       : (long long)I.T * I.n_mom *
                                             (kind == laph::INST_TRIPLETS ? (long long)I.N * I.N * I.N : d.n_trip));
         p->outM_elems.push_back(skipM ? 0 : (long long)I.T * I.n_mom * I.N * d.Nc);
+        p->h_inst.back().n_outB = p->outB_elems.back() / I.T;
+        p->h_inst.back().n_outM = p->outM_elems.back() / I.T;
         phase_off[n] = phase_total;
         phase_total += (long long)I.n_mom * d.Vs;
     }
@@ -336,6 +368,22 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
     std::vector<std::vector<TileDev>> ones(n_inst);
     std::vector<size_t> unit_bytes(n_inst);
     size_t psi_total = 0;
+    // site blocks of the FP64 reduction (tensor-core path) and the workspace
+    // bytes of one (instance, timeslice): its B-operand stage images and the
+    // FP32 partials of all its site blocks
+    auto set_sum = [&](int sum_sites) {
+        p->sum_sites = tc ? sum_sites : 0;
+        psi_total = 0;
+        for (int n = 0; n < n_inst; n++) {
+            InstDev &d = p->h_inst[n];
+            d.sc_stages = tc ? std::max(1, std::min(d.n_st, sum_sites / laph::TC_BS)) : d.n_st;
+            d.n_sc = (d.n_st + d.sc_stages - 1) / d.sc_stages;
+            unit_bytes[n] = tc ? (size_t)d.n_ct * d.n_st * laph::TC_STAGE_BYTES +
+                                     (size_t)d.n_sc * (size_t)(d.n_outB + d.n_outM) * sizeof(float2)
+                               : 0;
+            psi_total += (size_t)d.T * unit_bytes[n];
+        }
+    };
     for (int n = 0; n < n_inst; n++) {
         const InstDev &d = p->h_inst[n];
         std::vector<TileDev> &one = ones[n];
@@ -382,13 +430,13 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
                     const int lead = std::max(0, std::min(nc, (jmin + 1) * d.P - col0));
                     cskip = (lead / 8) * 8;
                 }
-                one.push_back(TileDev{n, 0, row0, col0, v_lo, nv, w_lo, nw, kmin, kmax - kmin + 1, nc, cskip, psi_ct});
+                one.push_back(TileDev{n, 0, row0, col0, v_lo, nv, w_lo, nw, kmin, kmax - kmin + 1, nc, cskip, psi_ct,
+                                      0, d.n_st, 0});
             }
         }
         p->max_P = std::max(p->max_P, d.P);
-        unit_bytes[n] = (size_t)d.n_ct * d.n_st * laph::TC_STAGE_BYTES;
-        psi_total += (size_t)d.T * unit_bytes[n];
     }
+    set_sum(opt_sum ? opt_sum : TC_DEFAULT_SUM);
     int sms = 0;
     PCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
     // units per chunk: one instance -> the count (within the cap) that
@@ -399,7 +447,7 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
     if (tc && (flags & LAPH_PLAN_CHUNK_PER_TIMESLICE)) {
         per_chunk = 1;
     } else if (tc && n_inst == 1) {
-        const long long U = p->h_inst[0].T, tpu = (long long)ones[0].size();
+        const long long U = p->h_inst[0].T, tpu = (long long)ones[0].size() * p->h_inst[0].n_sc;
         const long long n_max = std::max(1LL, std::min(U, (long long)(PSI_CAP_BYTES / std::max<size_t>(unit_bytes[0], 1))));
         long long best = -1, best_rounds = 0;
         for (long long n = 1; n <= n_max; n++) {
@@ -428,52 +476,89 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
         free_plan(p);
         return LAPH_ERR_UNSUPPORTED;
     }
-    size_t psi_max = 0;
+    size_t psi_max = 0, part_max = 0;
     // tile, unit and chunk tables for a schedule (pc timeslices per chunk, or
-    // chunks filled up to psi_target bytes when pc is 0)
+    // chunks filled up to psi_target bytes when pc is 0).  On the tensor-core
+    // path every (row tile, column tile) of a timeslice becomes one tile per
+    // site block; order 0 runs them as (column tile, site block, row tile), so
+    // that the tiles sharing one range of B stage images run side by side,
+    // order 1 as (row tile, site block, column tile).
     std::function<void(long long, int)> emit = [&](long long pc, int tile_order) {
         tiles.clear();
         units.clear();
         p->chunks.clear();
-        psi_max = 0;
-        laph_plan::Chunk cur{0, 0, 0, 0, 0};
-        size_t cur_bytes = 0;
+        psi_max = part_max = 0;
+        laph_plan::Chunk cur{0, 0, 0, 0, 0, 0};
+        size_t cur_bytes = 0, cur_psi = 0;
+        long long cur_part = 0;   // float2 entries of the chunk's partial buffer
         for (int n : order) {
             const InstDev &d = p->h_inst[n];
-            std::vector<TileDev> one = ones[n];
-            if (tile_order == 1)
-                std::stable_sort(one.begin(), one.end(), [](const TileDev &x, const TileDev &y) {
-                    return x.row0 != y.row0 ? x.row0 < y.row0 : x.col0 < y.col0;
+            std::vector<TileDev> one;
+            if (!tc) {
+                one = ones[n];
+            } else {
+                for (const TileDev &u : ones[n])
+                    for (int sc = 0; sc < d.n_sc; sc++) {
+                        TileDev v = u;
+                        v.s0 = sc * d.sc_stages;
+                        v.nst = std::min(d.sc_stages, d.n_st - v.s0);
+                        v.part_off = (long long)sc * (d.n_outB + d.n_outM);
+                        one.push_back(v);
+                    }
+                std::stable_sort(one.begin(), one.end(), [tile_order](const TileDev &x, const TileDev &y) {
+                    const int xa = tile_order ? x.row0 : x.col0, ya = tile_order ? y.row0 : y.col0;
+                    const int xb = tile_order ? x.col0 : x.row0, yb = tile_order ? y.col0 : y.row0;
+                    if (xa != ya) return xa < ya;
+                    if (x.s0 != y.s0) return x.s0 < y.s0;
+                    return xb < yb;
                 });
+            }
             for (int t = 0; t < d.T; t++) {
                 if (tc) {
                     const bool full = pc > 0 ? cur.n_units >= pc : cur_bytes + unit_bytes[n] > psi_target;
                     if (cur.n_units > 0 && full) {
                         p->chunks.push_back(cur);
-                        psi_max = std::max(psi_max, cur_bytes);
-                        cur = laph_plan::Chunk{(int)units.size(), 0, 0, (long long)tiles.size(), 0};
-                        cur_bytes = 0;
+                        psi_max = std::max(psi_max, cur_psi);
+                        part_max = std::max(part_max, (size_t)cur_part * sizeof(float2));
+                        cur = laph_plan::Chunk{(int)units.size(), 0, 0, (long long)tiles.size(), 0, 0};
+                        cur_bytes = cur_psi = 0;
+                        cur_part = 0;
                     }
-                    units.push_back(laph::PsiUnit{n, t, (long long)cur_bytes, cur.n_jobs});
+                    units.push_back(laph::PsiUnit{n, t, (long long)cur_psi, cur.n_jobs, cur_part, cur.n_red});
                     cur.n_units++;
                     cur.n_jobs += (long long)d.n_ct * ((d.n_st + laph::TC_PSI_GROUP - 1) / laph::TC_PSI_GROUP);
+                    cur.n_red += (d.n_outB + d.n_outM + laph::TC_RED_BLOCK - 1) / laph::TC_RED_BLOCK;
                 }
                 for (TileDev u : one) {
                     u.t = t;
-                    if (tc) u.psi_off += (long long)cur_bytes;
+                    if (tc) {
+                        u.psi_off += (long long)cur_psi;
+                        u.part_off += cur_part;
+                    }
                     tiles.push_back(u);
                 }
                 if (tc) {
                     cur.n_tiles += (long long)one.size();
                     cur_bytes += unit_bytes[n];
+                    cur_psi += (size_t)d.n_ct * d.n_st * laph::TC_STAGE_BYTES;
+                    cur_part += (long long)d.n_sc * (d.n_outB + d.n_outM);
                 }
             }
         }
         if (tc && cur.n_units > 0) {
             p->chunks.push_back(cur);
-            psi_max = std::max(psi_max, cur_bytes);
+            psi_max = std::max(psi_max, cur_psi);
+            part_max = std::max(part_max, (size_t)cur_part * sizeof(float2));
         }
         p->n_tiles = (long long)tiles.size();
+        p->mma_flops = 0.0;
+        if (tc) {
+            const int terms = (mode == LAPH_MODE_TC_F16X3 || mode == LAPH_MODE_TC_BF16X3) ? 3 : 1;
+            for (const TileDev &u : tiles) {
+                const int n_real = 2 * ((u.ncols + 7) & ~7) - 2 * u.cskip;
+                p->mma_flops += 2.0 * laph::TC_TR * n_real * (2 * laph::TC_KSTAGE) * terms * u.nst;
+            }
+        }
         p->h_units = units;
         p->sched_per_chunk = pc;
         p->sched_order = tile_order;
@@ -516,6 +601,8 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
             }
             p->off_psi = off;
             off += ((psi_max + 255) / 256) * 256;
+            p->off_part = off;
+            off += ((part_max + 255) / 256) * 256;
             p->ws_bytes = off;
             er = cudaMemcpy(p->d_inst, p->h_inst.data(), sizeof(InstDev) * n_inst, cudaMemcpyHostToDevice);
         } else {
@@ -550,16 +637,21 @@ int laph_plan_create(const laph_instance *inst, int n_inst, int mode, unsigned f
         PCK(upload());
         p->tuned = true;
     }
+    if (tc) PCK(ensure_side(p));
     if (flags & LAPH_PLAN_TIMING) {
         p->ev_begin.resize(laph_plan::RING, nullptr);
         p->ev_end.resize(laph_plan::RING, nullptr);
         p->pv_begin.resize(laph_plan::RING, nullptr);
         p->pv_end.resize(laph_plan::RING, nullptr);
+        p->rd_begin.resize(laph_plan::RING, nullptr);
+        p->rd_end.resize(laph_plan::RING, nullptr);
         for (int r = 0; r < laph_plan::RING; r++) {
             PCK(cudaEventCreate(&p->ev_begin[r]));
             PCK(cudaEventCreate(&p->ev_end[r]));
             PCK(cudaEventCreate(&p->pv_begin[r]));
             PCK(cudaEventCreate(&p->pv_end[r]));
+            PCK(cudaEventCreate(&p->rd_begin[r]));
+            PCK(cudaEventCreate(&p->rd_end[r]));
         }
     }
 #undef PCK
@@ -587,6 +679,16 @@ int laph_plan_describe(const laph_plan *plan, int *mode, int *tile_rows, int *ti
     return LAPH_OK;
 }
 
+int laph_plan_sum_sites(const laph_plan *plan, int *sum_sites, int *max_site_blocks)
+{
+    if (!plan) return LAPH_ERR_ARG;
+    int mx = 0;
+    for (const InstDev &d : plan->h_inst) mx = std::max(mx, is_tc_mode(plan->mode) ? d.n_sc : 0);
+    if (sum_sites) *sum_sites = plan->sum_sites;
+    if (max_site_blocks) *max_site_blocks = mx;
+    return LAPH_OK;
+}
+
 int laph_plan_set_chunk_sites(laph_plan *plan, int chunk_sites)
 {
     if (!plan || chunk_sites < 0 || chunk_sites > (1 << 24)) return LAPH_ERR_ARG;
@@ -608,15 +710,40 @@ static laph::TcConfig tc_config(const laph_plan *p)
     return cfg;
 }
 
-// B-operand pass and contraction of chunk ci (tensor-core path), with the
-// timing events of LAPH_PLAN_TIMING around each launch.
+// The side stream and one pair of events per chunk (made outside any stream
+// capture: at plan creation and before each autotuning candidate).
+static cudaError_t ensure_side(laph_plan *p)
+{
+    cudaError_t e;
+    if (!p->side && (e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    while (p->ev_tc.size() < p->chunks.size()) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        if ((e = cudaEventCreateWithFlags(&a, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&b, cudaEventDisableTiming)) != cudaSuccess) {
+            cudaEventDestroy(a);
+            return e;
+        }
+        p->ev_tc.push_back(a);
+        p->ev_red.push_back(b);
+    }
+    return cudaSuccess;
+}
+
+// B-operand pass, contraction and FP64 site reduction of chunk ci (tensor-core
+// path), with the timing events of LAPH_PLAN_TIMING around each launch.  The
+// reduction runs on the plan's side stream after the contraction (event
+// ev_tc[ci]); the contraction of chunk ci waits for the reduction of chunk
+// ci - 1, which reads the same partial buffer (event ev_red[ci - 1]).  The
+// caller joins ev_red of the last chunk back into `s`.
 static int launch_tc_chunk(laph_plan *p, char *ws, size_t ci, const laph::TcConfig &cfg, cudaStream_t s)
 {
+    if (!p->side || p->ev_tc.size() < p->chunks.size()) return LAPH_ERR_ARG;
     cudaError_t e;
     const bool timing = !p->ev_begin.empty();
     unsigned *maxbits = (unsigned *)(ws + p->off_maxbits);
     uint8_t *psi = (uint8_t *)(ws + p->off_psi);
     unsigned *counters = (unsigned *)(ws + p->off_counter);
+    float2 *part = (float2 *)(ws + p->off_part);
     const laph_plan::Chunk &c = p->chunks[ci];
     const int ps = (int)(p->n_ptimed % laph_plan::RING), cs = (int)(p->n_timed % laph_plan::RING);
     if (timing) CK(cudaEventRecord(p->pv_begin[ps], s));
@@ -625,15 +752,24 @@ static int launch_tc_chunk(laph_plan *p, char *ws, size_t ci, const laph::TcConf
     if (timing) {
         CK(cudaEventRecord(p->pv_end[ps], s));
         p->n_ptimed++;
-        CK(cudaEventRecord(p->ev_begin[cs], s));
     }
-    e = laph::launch_tc(p->d_inst, p->d_tiles + c.tile0, c.n_tiles, maxbits, psi, counters + ci, cfg, p->d_status, s);
+    if (ci > 0) CK(cudaStreamWaitEvent(s, p->ev_red[ci - 1], 0));
+    if (timing) CK(cudaEventRecord(p->ev_begin[cs], s));
+    e = laph::launch_tc(p->d_inst, p->d_tiles + c.tile0, c.n_tiles, maxbits, psi, part, counters + ci, cfg,
+                        p->d_status, s);
     if (e == cudaErrorNotSupported) return LAPH_ERR_UNSUPPORTED;
     if (e != cudaSuccess) return cuda_fail(e, "tc contraction");
     if (timing) {
         CK(cudaEventRecord(p->ev_end[cs], s));
         p->n_timed++;
     }
+    CK(cudaEventRecord(p->ev_tc[ci], s));
+    CK(cudaStreamWaitEvent(p->side, p->ev_tc[ci], 0));
+    if (timing) CK(cudaEventRecord(p->rd_begin[cs], p->side));
+    e = laph::launch_reduce(p->d_inst, p->d_units + c.unit0, c.n_units, c.n_red, maxbits, part, p->side);
+    if (e != cudaSuccess) return cuda_fail(e, "site reduction");
+    if (timing) CK(cudaEventRecord(p->rd_end[cs], p->side));
+    CK(cudaEventRecord(p->ev_red[ci], p->side));
     return LAPH_OK;
 }
 
@@ -683,6 +819,7 @@ static int launch_batch(laph_plan *p, void *workspace, cudaStream_t s)
             const int rc = launch_tc_chunk(p, ws, ci, cfg, s);
             if (rc != LAPH_OK) return rc;
         }
+        if (!p->chunks.empty()) CK(cudaStreamWaitEvent(s, p->ev_red[p->chunks.size() - 1], 0));
     } else {
         laph::SimtConfig cfg;
         cfg.chunk_sites = p->chunk_sites;
@@ -745,6 +882,7 @@ static int autotune_time(laph_plan *p, const std::vector<std::pair<long long, in
     for (size_t k = 0; k < cand.size(); k++) {
         emit(cand[k].first, cand[k].second);
         TCK(upload());
+        TCK(ensure_side(p));
         TCK(cudaMalloc(&ws, std::max<size_t>(p->ws_bytes, 256)));
         TCK(laph::launch_set_pointers(p->d_inst, 0, p->n_inst, phi.data(), needB ? ob.data() : nullptr,
                                       needM ? om.data() : nullptr, ws, st));
@@ -803,6 +941,12 @@ int laph_plan_operand_times(laph_plan *plan, int n, float *ms)
     return ring_times(plan->pv_begin, plan->pv_end, plan->n_ptimed, n, ms);
 }
 
+int laph_plan_reduce_times(laph_plan *plan, int n, float *ms)
+{
+    if (!plan || !is_tc_mode(plan->mode)) return LAPH_ERR_ARG;
+    return ring_times(plan->rd_begin, plan->rd_end, plan->n_timed, n, ms);
+}
+
 int laph_plan_contraction_launches(const laph_plan *plan, int *n)
 {
     if (!plan || !n) return LAPH_ERR_ARG;
@@ -811,12 +955,20 @@ int laph_plan_contraction_launches(const laph_plan *plan, int *n)
     return LAPH_OK;
 }
 
+int laph_plan_tensor_flops(const laph_plan *plan, double *flops)
+{
+    if (!plan || !flops) return LAPH_ERR_ARG;
+    *flops = plan->mma_flops;
+    return LAPH_OK;
+}
+
 int laph_plan_launches_per_execute(const laph_plan *plan, int *n)
 {
     if (!plan || !n) return LAPH_ERR_ARG;
     const int ptr_launches = (plan->n_inst + 63) / 64;
     if (is_tc_mode(plan->mode))
-        *n = ptr_launches + 2 * plan->n_inst /* scale, blockify */ + 2 * (int)plan->chunks.size() /* psi, contraction */;
+        *n = ptr_launches + 2 * plan->n_inst /* scale, blockify */ +
+             3 * (int)plan->chunks.size() /* psi, contraction, FP64 site reduction */;
     else
         *n = ptr_launches + (int)((plan->n_tiles + 0x7ffffffeLL) / 0x7fffffffLL);
     return LAPH_OK;
@@ -952,8 +1104,8 @@ int laph_plan_execute_host(laph_plan *plan, const void *const *phi_host, void *c
         int rc = launch_chunk_prep(plan, ws, ci, s);
         if (rc == LAPH_OK) rc = launch_tc_chunk(plan, ws, ci, cfg, s);
         if (rc != LAPH_OK) return rc;
-        CK(cudaEventRecord(plan->ev_out[ci], s));
-        CK(cudaStreamWaitEvent(plan->d2h, plan->ev_out[ci], 0));
+        // the outputs of chunk ci are final once its site reduction (side stream) is done
+        CK(cudaStreamWaitEvent(plan->d2h, plan->ev_red[ci], 0));
         for (int u = c.unit0; u < c.unit0 + c.n_units; u++) {
             const int n = plan->h_units[u].inst, t = plan->h_units[u].t;
             if (needB) {
@@ -968,6 +1120,7 @@ int laph_plan_execute_host(laph_plan *plan, const void *const *phi_host, void *c
             }
         }
     }
+    if (nc > 0) CK(cudaStreamWaitEvent(s, plan->ev_red[nc - 1], 0));
     CK(cudaStreamSynchronize(plan->d2h));
     CK(cudaStreamSynchronize(s));
     return LAPH_OK;

@@ -52,6 +52,10 @@ struct InstDev {
     int kind;                // INST_BLOCKS, INST_TRIPLETS or INST_DOUBLETS
     int n_fields;            // distinct input fields: 1, 3 (triplets) or 2 (doublets)
     int Nc;                  // vectors of the column field (N, except doublets of two vector counts)
+    int n_sc;                // tensor-core path: site blocks of the FP64 reduction (partials per output)
+    int sc_stages;           // K stages (8-site blocks) per site block of the FP64 reduction
+    long long n_outB;        // output entries per timeslice: B (P C(N,3), or P N^3 for triplets; 0 if skipped)
+    long long n_outM;        //                               M (P N Nc; 0 if skipped)
 };
 
 // Site-blocked layout of the tensor-core path.  phi_blk[t][b][n][TC_SLOT]:
@@ -61,12 +65,15 @@ struct InstDev {
 constexpr int TC_BS = 8;                      // sites per block
 constexpr int TC_SLOT = 3 * TC_BS + 2;        // complex entries per (block, vector): 208 bytes
 
-// One unit of work: a (row tile, column tile) of one timeslice.  v_lo and nv
-// give the contiguous range of vector indices the tile's rows use (the
-// tensor-core path stages exactly these vectors in shared memory; for
+// One unit of work: a (row tile, column tile) of one timeslice -- on the
+// tensor-core path restricted to one block of sites, stages [s0, s0 + nst).
+// v_lo and nv give the contiguous range of vector indices the tile's rows use
+// (the tensor-core path stages exactly these vectors in shared memory; for
 // triplets these are phi_u vectors, and [w_lo, w_lo + nw) of phi_v follow
-// them); psi_off is the byte offset of the tile's B operand stages in the
-// Psi buffer.
+// them); psi_off is the byte offset of the column tile's B operand stage 0
+// in the Psi buffer; part_off is the float2 offset of the tile's site block
+// in the chunk's buffer of FP32 partial sums, laid out per (instance,
+// timeslice) as [site block][n_outB + n_outM] in the output order.
 struct TileDev {
     int inst, t, row0, col0;
     int v_lo, nv;        // vectors used by the rows: [v_lo, v_lo + nv)
@@ -75,16 +82,22 @@ struct TileDev {
     int ncols;           // valid columns of the tile
     int cskip;           // leading columns no row of the tile needs (multiple of 8; tensor-core path)
     long long psi_off;
+    int s0, nst;         // tensor-core path: first stage and number of stages of the tile's site block
+    long long part_off;
 };
 
 // One (instance, timeslice) of a chunk of the tensor-core path: its Psi
 // operand occupies n_ct * n_st stage images from byte psi_off of the chunk's
 // Psi buffer; job0 is the index of its first (column tile, stage group) job
-// within the chunk.
+// within the chunk.  Its FP32 partial sums occupy n_sc * (n_outB + n_outM)
+// float2 from part_off of the chunk's partial buffer; red0 is the index of
+// its first block of the FP64 reduction within the chunk.
 struct PsiUnit {
     int inst, t;
     long long psi_off;
     long long job0;
+    long long part_off;
+    long long red0;
 };
 
 __host__ __device__ inline long long binom2(long long n) { return n * (n - 1) / 2; }
@@ -190,8 +203,15 @@ cudaError_t launch_psi(const InstDev *d_inst, const PsiUnit *d_units, int n_unit
                        const unsigned *d_maxbits, int elem, uint8_t *psi, cudaStream_t s);
 // counter: a zeroed word of device memory; persistent CTAs claim tiles with it.
 cudaError_t launch_tc(const InstDev *d_inst, const TileDev *d_tiles, long long n_tiles,
-                      const unsigned *d_maxbits, const uint8_t *psi, unsigned *counter, const TcConfig &cfg,
-                      int *d_status, cudaStream_t s);
+                      const unsigned *d_maxbits, const uint8_t *psi, float2 *part, unsigned *counter,
+                      const TcConfig &cfg, int *d_status, cudaStream_t s);
+// Output entries handled by one block of the FP64 reduction.
+constexpr int TC_RED_BLOCK = 1024;
+// FP64 reduction of a chunk: every output entry of the units [0, n_units) is
+// the sum over its site blocks, in block order, of the FP32 partials, scaled
+// back and stored to the caller's complex128 outputs.
+cudaError_t launch_reduce(const InstDev *d_inst, const PsiUnit *d_units, int n_units, long long n_blocks,
+                          const unsigned *d_maxbits, const float2 *part, cudaStream_t s);
 int tc_smem_bytes();
 
 }  // namespace laph

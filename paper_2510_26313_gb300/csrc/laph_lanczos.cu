@@ -15,7 +15,7 @@
 // enough"), and normalises.  The operator is -Delta itself or the Chebyshev
 // filter T_d((-Delta - c) / e), which maps the unwanted part of the spectrum,
 // [lo, 12], onto [-1, 1] and magnifies the lowest eigenvalues.  The Ritz
-// vectors of the wanted end are formed from the basis (host QL on the
+// vectors of the wanted end are formed from the basis (host symmetric QR on the
 // tridiagonal matrices), and their eigenvalues and residuals are Rayleigh
 // quotients with -Delta.
 //
@@ -27,6 +27,7 @@
 // timeslices that fit in L2, all its steps replayed as one CUDA graph per
 // Krylov step.
 #include <algorithm>
+#include <limits>
 #include <cmath>
 #include <cstring>
 #include <initializer_list>
@@ -561,76 +562,91 @@ __global__ void gather_kernel(const float2 *__restrict__ X, long long ts_X, cons
 
 }  // namespace
 
-// Eigenvalues d (ascending) and orthonormal eigenvectors z (column k of the n x n
-// row-major z belongs to d[k]) of the symmetric tridiagonal matrix with diagonal
-// d[0..n) and off-diagonal e[0..n-1), by the QL algorithm with implicit Wilkinson
-// shifts (Givens rotations chased up from the bottom of each unreduced block).
-// The rotations are accumulated into the transpose of z, so that each one
-// updates two contiguous rows.  Returns 0, or -1 when an eigenvalue needs more
-// than 60 sweeps.
-// sqrt(a^2 + b^2), by the direct formula where the squares can neither
-// overflow nor underflow, else by std::hypot
-static inline double pyth(double a, double b)
+// Length of the vector (a, b): the plain formula while the squares can neither
+// overflow nor underflow, std::hypot outside that range.
+static inline double norm2(double a, double b)
 {
     const double m = std::max(std::fabs(a), std::fabs(b));
-    if (m < 1e150 && m > 1e-150) return std::sqrt(a * a + b * b);
-    return std::hypot(a, b);
+    return (m > 1e-150 && m < 1e150) ? std::sqrt(a * a + b * b) : std::hypot(a, b);
 }
 
+// One implicit symmetric QR step with a Wilkinson shift on the unreduced block
+// [lo, hi] of the tridiagonal matrix (diagonal a, off-diagonal b; b[i] couples
+// i and i+1), after Golub and Van Loan, "Matrix Computations", the implicit
+// symmetric QR step: the shift mu is the eigenvalue of the trailing 2 x 2 of
+// the block nearer to its last diagonal entry; the first rotation is the one
+// that zeroes the second entry of the first column of (T - mu I), and the
+// bulge it creates below the subdiagonal is chased down the block by one
+// rotation per row.  Rotation k acts on rows and columns k, k+1 as
+// Q = [[c, -s], [s, c]]; every rotation is applied to the rows k, k+1 of zt,
+// the transpose of the eigenvector matrix.
+static void qr_step(int lo, int hi, double *a, double *b, double *zt, int n)
+{
+    const double delta = 0.5 * (a[hi - 1] - a[hi]);
+    const double bt = b[hi - 1];
+    const double den = delta + (delta >= 0.0 ? 1.0 : -1.0) * norm2(delta, bt);
+    const double mu = a[hi] - bt * (bt / den);
+    double x = a[lo] - mu;   // entry kept by the next rotation
+    double y = b[lo];        // entry it annihilates
+    for (int k = lo; k < hi; k++) {
+        const double r = norm2(x, y);
+        double c = 1.0, s = 0.0;
+        if (r > 0.0) {
+            c = x / r;
+            s = y / r;
+        }
+        if (k > lo) b[k - 1] = r;   // the bulge below it is gone
+        const double ak = a[k], ak1 = a[k + 1], bk = b[k];
+        const double cc = c * c, ss = s * s, cs = c * s;
+        a[k] = cc * ak + 2.0 * cs * bk + ss * ak1;
+        a[k + 1] = ss * ak + ak1 * cc - 2.0 * cs * bk;
+        b[k] = cs * (ak1 - ak) + (cc - ss) * bk;
+        if (k + 1 < hi) {
+            // the rotation of columns k, k+1 carries b[k+1] into row k+2, column k
+            x = b[k];
+            y = s * b[k + 1];
+            b[k + 1] *= c;
+        }
+        double *u = zt + (size_t)k * n, *v = u + n;
+        for (int j = 0; j < n; j++) {
+            const double uj = u[j], vj = v[j];
+            u[j] = c * uj + s * vj;
+            v[j] = c * vj - s * uj;
+        }
+    }
+}
+
+// Eigenvalues d (ascending) and orthonormal eigenvectors z (column k of the n x n
+// row-major z belongs to d[k]) of the symmetric tridiagonal matrix with diagonal
+// d[0..n) and off-diagonal e[0..n-1), by the symmetric QR algorithm: off-diagonal
+// entries below DBL_EPSILON times their two diagonal neighbours are set to zero,
+// and the lowest unreduced block that is left takes one implicit QR step, until
+// the matrix is diagonal.  Returns 0, or -1 after 60 n steps without
+// convergence.
 int tridiag_eigen(int n, double *d, const double *e_in, double *z)
 {
-    std::vector<double> e(n, 0.0), zt((size_t)n * n, 0.0);
-    for (int i = 0; i + 1 < n; i++) e[i] = e_in[i];
+    std::vector<double> b(n > 1 ? n - 1 : 1, 0.0), zt((size_t)n * n, 0.0);
+    for (int i = 0; i + 1 < n; i++) b[i] = e_in[i];
     for (int i = 0; i < n; i++) zt[(size_t)i * n + i] = 1.0;
-    for (int l = 0; l < n; l++) {
-        int iter = 0;
-        while (true) {
-            int m = l;
-            for (; m + 1 < n; m++) {
-                const double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
-                if (std::fabs(e[m]) <= 1e-16 * dd) break;
-            }
-            if (m == l) break;
-            if (++iter > 60) return -1;
-            // shift from the leading 2 x 2 of the block
-            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-            double r = pyth(g, 1.0);
-            g = d[m] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
-            double s = 1.0, c = 1.0, p = 0.0;
-            int i = m - 1;
-            for (; i >= l; i--) {
-                double f = s * e[i], b = c * e[i];
-                r = pyth(f, g);
-                e[i + 1] = r;
-                if (r == 0.0) {
-                    d[i + 1] -= p;
-                    e[m] = 0.0;
-                    break;
-                }
-                s = f / r;
-                c = g / r;
-                g = d[i + 1] - p;
-                r = (d[i] - g) * s + 2.0 * c * b;
-                p = s * r;
-                d[i + 1] = g + p;
-                g = c * r - b;
-                double *z0 = zt.data() + (size_t)i * n, *z1 = z0 + n;
-                for (int k = 0; k < n; k++) {
-                    const double zk1 = z1[k], zk = z0[k];
-                    z1[k] = s * zk + c * zk1;
-                    z0[k] = c * zk - s * zk1;
-                }
-            }
-            if (r == 0.0 && i >= l) continue;
-            d[l] -= p;
-            e[l] = g;
-            e[m] = 0.0;
-        }
+    const double eps = std::numeric_limits<double>::epsilon();
+    long long steps = 0;
+    int hi = n - 1;
+    while (hi > 0) {
+        for (int i = 0; i < hi; i++)
+            if (std::fabs(b[i]) <= eps * (std::fabs(d[i]) + std::fabs(d[i + 1])) ||
+                std::fabs(b[i]) < std::numeric_limits<double>::min())
+                b[i] = 0.0;
+        while (hi > 0 && b[hi - 1] == 0.0) hi--;   // trailing entries already diagonal
+        if (hi == 0) break;
+        int lo = hi - 1;
+        while (lo > 0 && b[lo - 1] != 0.0) lo--;
+        if (++steps > 60LL * n) return -1;
+        qr_step(lo, hi, d, b.data(), zt.data(), n);
     }
     // ascending order
     std::vector<int> idx(n);
     for (int i = 0; i < n; i++) idx[i] = i;
-    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return d[a] < d[b]; });
+    std::sort(idx.begin(), idx.end(), [&](int x, int y) { return d[x] < d[y]; });
     std::vector<double> d2(n);
     for (int k = 0; k < n; k++) {
         d2[k] = d[idx[k]];

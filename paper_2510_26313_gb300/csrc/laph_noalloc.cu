@@ -15,10 +15,13 @@
 // call rewrites every byte it reads before reading it, so nothing has to
 // start at zero.  Calls whose work overlaps on the GPU (different streams, or
 // different host threads, without ordering between them) race on the array.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "../../include/laph.h"
 #include "laph_internal.cuh"
@@ -27,35 +30,81 @@ namespace laph {
 namespace {
 
 constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)LAPH_NOALLOC_SCRATCH_BYTES;
-constexpr int NOALLOC_MAX_DEVICES = 64;
 constexpr int NOALLOC_MAX_MOM = 64;
 constexpr int NOALLOC_MAX_ROW_TILES = 4096;
+// the public header states the scratch use of one tile record
+static_assert(sizeof(TileDev) == 72, "the documented tile-record size in laph.h");
 
 // The scratch array.  Host code must not pass its name to a kernel: on the
 // host it is only a stand-in symbol; its device address is obtained with
 // cudaGetSymbolAddress (see scratch_on_current_device).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
+// The array's device address is a property of the CUDA context it was
+// loaded into.  It is looked up once per context -- in the normal case once
+// per device, in the device's primary context -- and cached under the
+// context's unique ID, so that a context created after a device reset (or a
+// context the caller made current through the driver API) gets its own
+// lookup instead of a stale address.
+struct ScratchAddr {
+    unsigned long long ctx_id;
+    void *addr;
+};
 std::mutex g_setup_mutex;
-void *g_scratch_addr[NOALLOC_MAX_DEVICES] = {nullptr};
+std::vector<ScratchAddr> g_scratch_addr;
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the first call on a device must therefore not be made while
-// the stream is being captured).
+// Driver functions reached through the runtime (so that the library itself
+// loads on a host without the driver, e.g. to be inspected).
+PFN_cuCtxGetCurrent_v4000 g_ctx_current = nullptr;
+PFN_cuCtxGetId_v12000 g_ctx_id = nullptr;
+
+// ID of the current context, after the runtime has made one current.
+cudaError_t current_context_id(unsigned long long *id)
+{
+    cudaError_t e;
+    if (!g_ctx_current || !g_ctx_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = cudaDriverEntryPointSymbolNotFound;
+        if ((e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 4000, cudaEnableDefault, &q1)) != cudaSuccess)
+            return e;
+        if ((e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2)) != cudaSuccess)
+            return e;
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return cudaErrorNotSupported;
+        g_ctx_current = (PFN_cuCtxGetCurrent_v4000)f1;
+        g_ctx_id = (PFN_cuCtxGetId_v12000)f2;
+    }
+    CUcontext ctx = nullptr;
+    if (g_ctx_current(&ctx) != CUDA_SUCCESS) return cudaErrorInitializationError;
+    if (!ctx) {
+        // no context yet on this thread: the lookup below initialises the
+        // current device's primary context and makes it current
+        void *p = nullptr;
+        if ((e = cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess) return e;
+        if (g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorInitializationError;
+    }
+    return g_ctx_id(ctx, id) == CUDA_SUCCESS ? cudaSuccess : cudaErrorInitializationError;
+}
+
+// Device address of the scratch array in the current context (the first call
+// in a context looks it up, so it must not be made while a stream is being
+// captured).
 cudaError_t scratch_on_current_device(unsigned char **addr)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
-    }
-    *addr = (unsigned char *)g_scratch_addr[dev];
+    unsigned long long id = 0;
+    cudaError_t e = current_context_id(&id);
+    if (e != cudaSuccess) return e;
+    for (const ScratchAddr &a : g_scratch_addr)
+        if (a.ctx_id == id) {
+            *addr = (unsigned char *)a.addr;
+            return cudaSuccess;
+        }
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_addr.push_back(ScratchAddr{id, p});
+    *addr = (unsigned char *)p;
     return cudaSuccess;
 }
 

@@ -16,11 +16,13 @@
 // Its FP32 accumulation does not round to nearest, so its error grows with
 // the number of additions; the accumulator is drained every `chunk_stages`
 // K stages into a second tensor-memory region of FP32 running sums kept by
-// CUDA cores with round-to-nearest, and at the end of a tile the sums are
-// scaled back and written to the complex128 output in FP64.  At chunk
-// boundaries the MMAs of the two column halves of the accumulator are issued
-// and committed separately, so that the drain of one half overlaps the MMAs
-// of the other.
+// CUDA cores with round-to-nearest.  A tile covers one block of sites (at
+// most sc_stages K stages); at its end the running sums are stored as FP32
+// partials, and reduce_kernel adds the partials of all site blocks of an
+// output in FP64, in block order, scales them back and writes the
+// complex128 output.  At chunk boundaries the MMAs of the two column halves
+// of the accumulator are issued and committed separately, so that the drain
+// of one half overlaps the MMAs of the other.
 //
 // Tile: 128 rows x 96 complex columns (UMMA M = 128, N = 192).  A K stage is
 // one site block: TC_BS = 8 sites = 24 complex = 48 real K entries, three
@@ -44,7 +46,7 @@
 //         warp half h forms the 12 K entries of sites 4h..4h+3 of its row
 //         (diquark or conj(phi)), splits them and tcgen05.st's them;
 //   16-19 epilogue: drains ACC into SUM, one column half at a time, writes
-//         the output at tile end;
+//         the FP32 partials at tile end;
 //   20    loader: claims the next tile, then the stage ring's bulk copies;
 //   21    TMEM allocation and single-thread MMA issue.
 // Every wait on an mbarrier is bounded; on expiry the CTA records
@@ -414,6 +416,7 @@ struct KParams {
     const TileDev *tiles;
     const unsigned *maxbits;
     const uint8_t *psi;   // B stage images of the chunk
+    float2 *part;         // FP32 partial sums of the chunk's site blocks
     unsigned *counter;    // tile counter of this launch (zero at launch)
     int *status;
     int n_tiles;
@@ -484,12 +487,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
             if (tile < 0) break;
             const TileDev td = kp.tiles[tile];
             const InstDev &I = kp.insts[td.inst];
-            const int nst = I.nblk;
-            // row vectors: [v_lo, v_lo + nv) of phi_u, then (triplets) [w_lo, w_lo + nw) of phi_v
+            const int nst = td.nst;
+            // row vectors: [v_lo, v_lo + nv) of phi_u, then (triplets) [w_lo, w_lo + nw) of phi_v,
+            // from site block s0 of the tile's site range on
             const uint32_t bytesA = td.nv * SLOT_BYTES, bytesW = td.nw * SLOT_BYTES;
-            const uint8_t *bsrc = kp.psi + td.psi_off;
-            const float2 *asrc = I.phi_blk + ((long long)td.t * nst * I.N + td.v_lo) * TC_SLOT;
-            const float2 *wsrc = I.blk_v + ((long long)td.t * nst * I.N + td.w_lo) * TC_SLOT;
+            const uint8_t *bsrc = kp.psi + td.psi_off + (long long)td.s0 * BIMG_BYTES;
+            const long long blk0 = ((long long)td.t * I.nblk + td.s0) * I.N;
+            const float2 *asrc = I.phi_blk + (blk0 + td.v_lo) * TC_SLOT;
+            const float2 *wsrc = I.blk_v + (blk0 + td.w_lo) * TC_SLOT;
             const long long astep = (long long)I.N * TC_SLOT;
             for (int st = 0; st < nst; st++) {
                 if (!warp_wait(c, &S->empty[rs.slot], rs.phase ^ 1u)) {
@@ -528,7 +533,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
             if (tile < 0) break;
             const TileDev td = kp.tiles[tile];
             const InstDev &I = kp.insts[td.inst];
-            const int nst = I.nblk;
+            const int nst = td.nst;
             const int gr = td.row0 + r;
             int kind = 0, vi = 0, vj = 0;
             const bool trip = I.kind == INST_TRIPLETS;
@@ -632,9 +637,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
                     pair_of(q, pi_, pj);
                 }
             }
-            const int s = scale_exp(kp.maxbits[I.ts_base + td.t]);
-            const double fac = meson ? pow2d(-2 * s) : pow2d(-3 * s);
-            const int n_ch = (I.nblk + kp.chunk_stages - 1) / kp.chunk_stages;
+            const int n_ch = (td.nst + kp.chunk_stages - 1) / kp.chunk_stages;
             const int n_lo = n_real >= 32 ? ((n_real / 2 + 15) & ~15) : n_real;
             for (int ch = 0; ch < n_ch && ok; ch++) {
                 for (int h = 0; h < 2; h++) {
@@ -666,11 +669,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
                 }
             }
             if (!ok) break;
-            // tile done: FP32 sums -> FP64 output, scale undone
-            const long long tP = (long long)td.t * I.P;
+            // tile done: the FP32 sums of its site block go to the partial
+            // buffer in the output order of one timeslice (B entries, then M
+            // entries), still scaled; the FP64 reduction over site blocks
+            // scales them back
             const int P = I.P, N = I.N;
             const long long n_trip = I.n_trip;
-            double2 *outM = I.outM, *outB = I.outB;
+            float2 *part = kp.part + td.part_off;
             for (int b = 0; b * 16 < n_real; b++) {
                 uint32_t v[16];
                 tmem_ld16(tmem + lane_base + SUM_COL + 16u * b, v);
@@ -681,17 +686,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
                     if (!rvalid || cc >= ncols) continue;
                     const int col = td.col0 + cc;
                     const int k = col / P, p = col - k * P;
-                    double2 *dst;
+                    long long e;
                     if (meson) {
-                        dst = outM + ((tP + p) * N + gr) * I.Nc + k;   // [t][p][i][k], k < Nc
+                        e = I.n_outB + ((long long)p * N + gr) * I.Nc + k;   // [p][i][k], k < Nc
                     } else if (trip) {
-                        dst = outB + (((tP + p) * N + pi_) * N + pj) * N + k;   // dense [t][p][i][j][k]
+                        e = (((long long)p * N + pi_) * N + pj) * N + k;    // dense [p][i][j][k]
                     } else {
                         if (k <= pj) continue;
-                        dst = outB + (tP + p) * n_trip + binom3(k) + q;
+                        e = (long long)p * n_trip + binom3(k) + q;
                     }
-                    *dst = make_double2((double)__uint_as_float(v[2 * u]) * fac,
-                                        (double)__uint_as_float(v[2 * u + 1]) * fac);
+                    part[e] = make_float2(__uint_as_float(v[2 * u]), __uint_as_float(v[2 * u + 1]));
                 }
             }
         }
@@ -705,8 +709,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
             const int tile = next_tile(c, rt, ok);
             if (tile < 0) break;
             const TileDev td = kp.tiles[tile];
-            const InstDev &I = kp.insts[td.inst];
-            const int nst = I.nblk;
+            const int nst = td.nst;
             // the first cskip columns (2 cskip real B rows, 64 bytes per column in
             // every atom column) are not needed by any row of the tile
             const int n_real = 2 * ((td.ncols + 7) & ~7) - 2 * td.cskip;
@@ -886,6 +889,105 @@ __global__ void __launch_bounds__(192) psi_kernel(const InstDev *__restrict__ in
 }
 static_assert(2 * TC_TC == 192, "psi_kernel maps 96 columns x 2 chunks onto 192 threads");
 
+// ------------------------------------------------------------ FP64 site reduction
+
+// Exact FP32 -> FP64 widening done on the integer units (GB300 runs FP64
+// instructions at a small fraction of the FP32 rate, so the reduction keeps
+// its FP64 instructions to the additions): a normal float's sign, exponent
+// (rebiased by 1023 - 127) and mantissa are placed in the double's fields;
+// zeros, subnormals and non-finite values take the hardware conversion.
+__device__ __forceinline__ double widen(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t ex = (u >> 23) & 0xffu;
+    if (ex == 0u || ex == 0xffu) return (double)f;
+    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(ex + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
+// v * 2^k for the exact power-of-two rescale, by adding k to the exponent
+// field when the result stays a normal number (else one multiplication).
+__device__ __forceinline__ double scale2(double v, int k)
+{
+    const long long b = __double_as_longlong(v);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex != 0 && ex != 0x7ff && ex + k > 0 && ex + k < 0x7ff) return __longlong_as_double(b + (long long)k * (1LL << 52));
+    return v * pow2d(k);
+}
+
+// Block = TC_RED_BLOCK consecutive output entries of one (instance,
+// timeslice) unit; the unit is the last one whose red0 <= block.  Entry e of
+// the unit's output order (B entries [p][...] first, then M entries
+// [p][i][k]) is the FP64 sum over site blocks sc = 0, 1, ... of the FP32
+// partials part[part_off + sc * n_out + e], times 2^-3s (B) or 2^-2s (M), s
+// the timeslice's exponent.  Each thread owns RED_PER_THREAD entries, TC_RED_BLOCK /
+// RED_PER_THREAD apart, and adds each entry's partials in block order.
+constexpr int RED_THREADS = 256;
+constexpr int RED_PER_THREAD = TC_RED_BLOCK / RED_THREADS;
+static_assert(RED_PER_THREAD * RED_THREADS == TC_RED_BLOCK, "reduction block shape");
+
+__global__ void __launch_bounds__(RED_THREADS) reduce_kernel(const InstDev *__restrict__ insts,
+                                                             const PsiUnit *__restrict__ units, int n_units,
+                                                             long long n_blocks, const unsigned *__restrict__ maxbits,
+                                                             const float2 *__restrict__ part)
+{
+    for (long long blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
+        int lo = 0, hi = n_units - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (units[mid].red0 <= blk)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const PsiUnit un = units[lo];
+        const InstDev &I = insts[un.inst];
+        const long long nB = I.n_outB, n_out = nB + I.n_outM;
+        const long long e0 = (blk - un.red0) * TC_RED_BLOCK + threadIdx.x;
+        const float2 *src = part + un.part_off;
+        const int n_sc = I.n_sc;
+        double re[RED_PER_THREAD], im[RED_PER_THREAD];
+#pragma unroll
+        for (int q = 0; q < RED_PER_THREAD; q++) {
+            const long long e = e0 + q * RED_THREADS;
+            const float2 v = e < n_out ? __ldcs(src + e) : make_float2(0.f, 0.f);
+            re[q] = widen(v.x);
+            im[q] = widen(v.y);
+        }
+        for (int sc = 1; sc < n_sc; sc++) {
+            const float2 *ps = src + (long long)sc * n_out;
+            float2 v[RED_PER_THREAD];
+#pragma unroll
+            for (int q = 0; q < RED_PER_THREAD; q++) {
+                const long long e = e0 + q * RED_THREADS;
+                v[q] = e < n_out ? __ldcs(ps + e) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < RED_PER_THREAD; q++) {
+                re[q] += widen(v[q].x);
+                im[q] += widen(v[q].y);
+            }
+        }
+        const int s = scale_exp(maxbits[I.ts_base + un.t]);
+#pragma unroll
+        for (int q = 0; q < RED_PER_THREAD; q++) {
+            const long long e = e0 + q * RED_THREADS;
+            if (e >= n_out) continue;
+            double2 *dst;
+            int k;
+            if (e < nB) {
+                dst = I.outB + (long long)un.t * nB + e;
+                k = -3 * s;
+            } else {
+                dst = I.outM + (long long)un.t * I.n_outM + (e - nB);
+                k = -2 * s;
+            }
+            *dst = make_double2(scale2(re[q], k), scale2(im[q], k));
+        }
+    }
+}
+
 int stage_bytes_for(int max_staged)
 {
     const int b = BIMG_BYTES + max_staged * SLOT_BYTES;
@@ -898,13 +1000,15 @@ int smem_for(int ns, int stage_bytes) { return ns * stage_bytes + (int)sizeof(Sh
 
 template <int ELEM, int TERMS>
 cudaError_t launch_one(const InstDev *d_inst, const TileDev *d_tiles, long long n_tiles, const unsigned *maxbits,
-                       const uint8_t *psi, unsigned *counter, const TcConfig &cfg, int *status, cudaStream_t s)
+                       const uint8_t *psi, float2 *part, unsigned *counter, const TcConfig &cfg, int *status,
+                       cudaStream_t s)
 {
     KParams kp;
     kp.insts = d_inst;
     kp.tiles = d_tiles;
     kp.maxbits = maxbits;
     kp.psi = psi;
+    kp.part = part;
     kp.counter = counter;
     kp.status = status;
     kp.n_tiles = (int)n_tiles;
@@ -935,19 +1039,29 @@ cudaError_t launch_one(const InstDev *d_inst, const TileDev *d_tiles, long long 
 int tc_smem_bytes() { return smem_for(2, stage_bytes_for(TC_MAX_STAGED)); }
 
 cudaError_t launch_tc(const InstDev *d_inst, const TileDev *d_tiles, long long n_tiles, const unsigned *d_maxbits,
-                      const uint8_t *psi, unsigned *counter, const TcConfig &cfg, int *d_status, cudaStream_t s)
+                      const uint8_t *psi, float2 *part, unsigned *counter, const TcConfig &cfg, int *d_status,
+                      cudaStream_t s)
 {
     if (n_tiles <= 0) return cudaSuccess;
     if (n_tiles > 0x7fffffffLL || cfg.max_staged > TC_MAX_STAGED) return cudaErrorNotSupported;
     if (cfg.elem == 0 && cfg.terms == 3)
-        return launch_one<0, 3>(d_inst, d_tiles, n_tiles, d_maxbits, psi, counter, cfg, d_status, s);
+        return launch_one<0, 3>(d_inst, d_tiles, n_tiles, d_maxbits, psi, part, counter, cfg, d_status, s);
     if (cfg.elem == 1 && cfg.terms == 3)
-        return launch_one<1, 3>(d_inst, d_tiles, n_tiles, d_maxbits, psi, counter, cfg, d_status, s);
+        return launch_one<1, 3>(d_inst, d_tiles, n_tiles, d_maxbits, psi, part, counter, cfg, d_status, s);
     if (cfg.elem == 0 && cfg.terms == 1)
-        return launch_one<0, 1>(d_inst, d_tiles, n_tiles, d_maxbits, psi, counter, cfg, d_status, s);
+        return launch_one<0, 1>(d_inst, d_tiles, n_tiles, d_maxbits, psi, part, counter, cfg, d_status, s);
     if (cfg.elem == 1 && cfg.terms == 1)
-        return launch_one<1, 1>(d_inst, d_tiles, n_tiles, d_maxbits, psi, counter, cfg, d_status, s);
+        return launch_one<1, 1>(d_inst, d_tiles, n_tiles, d_maxbits, psi, part, counter, cfg, d_status, s);
     return cudaErrorNotSupported;
+}
+
+cudaError_t launch_reduce(const InstDev *d_inst, const PsiUnit *d_units, int n_units, long long n_blocks,
+                          const unsigned *d_maxbits, const float2 *part, cudaStream_t s)
+{
+    if (n_blocks <= 0 || n_units <= 0) return cudaSuccess;
+    const long long grid = n_blocks < (1LL << 20) ? n_blocks : (1LL << 20);
+    reduce_kernel<<<(unsigned)grid, RED_THREADS, 0, s>>>(d_inst, d_units, n_units, n_blocks, d_maxbits, part);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_psi(const InstDev *d_inst, const PsiUnit *d_units, int n_units, long long n_jobs,

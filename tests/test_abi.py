@@ -133,7 +133,7 @@ def test_entry_points_reject_null_pointers(lib):
 
 @pytest.mark.parametrize("n", [1, 2, 3, 17, 150])
 def test_tridiagonal_eigensolver_against_numpy(lib, n):
-    """The host QL solver behind the Lanczos Ritz values: eigenvalues against numpy's dense solver, eigenvectors
+    """The host tridiagonal solver behind the Lanczos Ritz values: eigenvalues against numpy's dense solver, eigenvectors
     through the eigen-equation and orthonormality, on random matrices with some zero couplings (split blocks)."""
     import numpy as np
     from paper_2510_26313_gb300 import binding
@@ -146,6 +146,30 @@ def test_tridiagonal_eigensolver_against_numpy(lib, n):
     np.testing.assert_allclose(w, np.linalg.eigvalsh(Tm), atol=1e-12 * max(1.0, np.abs(w).max()))
     np.testing.assert_allclose(Tm @ z, z * w, atol=1e-12 * max(1.0, np.abs(w).max()))
     np.testing.assert_allclose(z.T @ z, np.eye(n), atol=1e-12)
+
+
+@pytest.mark.parametrize("kind", ["wilkinson21", "graded", "zero_diagonal", "clustered"])
+def test_tridiagonal_eigensolver_on_hard_spectra(lib, kind):
+    """Matrices that stress the shift and the deflation test: Wilkinson's W21+ (pairs of eigenvalues agreeing to
+    about 1e-14), a graded matrix spanning 13 decades, a zero diagonal (eigenvalues in +- pairs) and a cluster of
+    nearly equal diagonal entries with tiny couplings; eigenvalues against numpy, eigen-equation and orthonormality."""
+    import numpy as np
+    from paper_2510_26313_gb300 import binding
+    if kind == "wilkinson21":
+        d, e = np.abs(np.arange(-10, 11)).astype(float), np.ones(20)
+    elif kind == "graded":
+        d, e = 10.0 ** (-np.arange(40) / 3), 10.0 ** (-np.arange(39) / 3 - 0.1)
+    elif kind == "zero_diagonal":
+        d, e = np.zeros(30), np.random.default_rng(1).standard_normal(29)
+    else:
+        d, e = 1.0 + 1e-14 * np.arange(50), np.full(49, 1e-10)
+    Tm = np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+    w, z = binding.tridiag_eigen(d, e)
+    sc = max(1.0, np.abs(w).max())
+    np.testing.assert_allclose(w, np.linalg.eigvalsh(Tm), rtol=0, atol=1e-13 * sc)
+    np.testing.assert_allclose(Tm @ z, z * w, rtol=0, atol=1e-13 * sc)
+    np.testing.assert_allclose(z.T @ z, np.eye(len(d)), rtol=0, atol=1e-13)
+    assert np.all(np.diff(w) >= 0)
 
 
 def test_tridiagonal_eigensolver_on_the_free_chain():
