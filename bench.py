@@ -123,6 +123,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def pinned_copy_rates(nbytes: int = 1 << 30):
+    """This box's pinned host <-> device copy rates (GB/s) on one buffer of nbytes, timed with CUDA events; they
+    vary a lot between boxes and bound the end-to-end figure."""
+    import torch
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    with torch.cuda.stream(s):
+        d.copy_(h, non_blocking=True)
+        h.copy_(d, non_blocking=True)
+        ev[0].record()
+        d.copy_(h, non_blocking=True)
+        ev[1].record()
+        h.copy_(d, non_blocking=True)
+        ev[2].record()
+    torch.cuda.synchronize()
+    out = {"h2d_gbs": nbytes / ev[0].elapsed_time(ev[1]) / 1e6, "d2h_gbs": nbytes / ev[1].elapsed_time(ev[2]) / 1e6}
+    del h, d
+    return out
+
+
 def max_over_ranks(ms: float, device) -> float:
     """The largest of a per-rank duration over all ranks of the process group (the duration
     itself for one rank): the job's time is its slowest rank's."""
@@ -263,6 +285,135 @@ def measure_triplets(laph, L, T, N, mom, mode, steps, warmup, n_sample=0, timed_
     del Bs, ws, fields
     torch.cuda.empty_cache()
     return out
+
+
+LARGE = dict(L=48, T=96, N=128, n2=4)   # 33 momenta: |n|^2 <= 4
+
+
+def measure_large(laph, L, T, N, mom, mode, steps, warmup, n_sample=0, timed_oracle=False):
+    """The large streamed form: T timeslices of N complex64 vectors on L^3 sites flow through HBM one at a time.  The
+    vectors of timeslice t+1 are drawn on the device (torch's generator, seeded per timeslice, entries complex
+    Gaussian / sqrt(3V)) on a side stream into the other half of a double buffer while timeslice t is contracted by a
+    one-timeslice plan; B and M of every timeslice land in [T]-sized outputs.  Returns the device time per pass over
+    the T timeslices, the kernel times and, with n_sample > 0, the relative errors of sampled baryon triples and of the
+    meson blocks of 12 vectors, for the first and the last timeslice, against the FP64 oracle."""
+    import torch
+    P = mom.shape[0]
+    V = L ** 3
+    plan = laph.Plan([(L, 1, N, mom)], mode=mode, flags=laph.PLAN_TIMING)
+    ws = plan.alloc_workspace()
+    B = torch.empty((T, P, math.comb(N, 3)), dtype=torch.complex128, device="cuda")
+    M = torch.empty((T, P, N, N), dtype=torch.complex128, device="cuda")
+    bufs = [torch.empty((1, N, V, 3), dtype=torch.complex64, device="cuda") for _ in range(2)]
+    main = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
+    gen = torch.Generator(device="cuda")
+    ev_gen = [torch.cuda.Event() for _ in range(2)]
+    ev_used = [torch.cuda.Event() for _ in range(2)]
+    for e in ev_used:
+        e.record(main)
+    sd = 1.0 / math.sqrt(2 * 3 * V)        # re and im each N(0, 1/(6V)): E|phi|^2 = 1 per vector
+
+    def generate(t, out, stream):
+        with torch.cuda.stream(stream):
+            gen.manual_seed(synth.SEED_BASE + 31 + t)
+            torch.view_as_real(out).normal_(0.0, sd, generator=gen)
+
+    def one_pass():
+        slot = 0
+        side.wait_event(ev_used[0])
+        generate(0, bufs[0], side)
+        ev_gen[0].record(side)
+        for t in range(T):
+            slot = t % 2
+            if t + 1 < T:
+                nxt = (t + 1) % 2
+                side.wait_event(ev_used[nxt])
+                generate(t + 1, bufs[nxt], side)
+                ev_gen[nxt].record(side)
+            main.wait_event(ev_gen[slot])
+            plan.execute([bufs[slot]], [B[t:t + 1]], [M[t:t + 1]], ws, stream=main)
+            ev_used[slot].record(main)
+
+    for _ in range(warmup):
+        one_pass()
+    torch.cuda.synchronize()
+    if plan.device_status() != laph.LAPH_OK:
+        raise RuntimeError("device status not OK after warm-up (large workload)")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(main)
+    for _ in range(steps):
+        one_pass()
+    e1.record(main)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    n = steps * T * plan.contraction_launches()
+    k_ms = sum(plan.kernel_times(min(n, 256))) * (n / min(n, 256)) / steps
+    flops = T * flops_per_timeslice(L, N, P)
+    out = {"ms_per_step": ms, "kernel_ms": k_ms, "flops_per_step": flops, "value": flops / (ms / 1e3) / 1e12,
+           "kernel_tflops": flops / (k_ms / 1e3) / 1e12, "device_status": plan.device_status(),
+           "launches": plan.launches_per_execute() * T * steps, "sum_sites": plan.sum_sites()}
+    if n_sample:
+        from oracle import oracle as O
+        rng = np.random.default_rng(12)
+        trip = sorted({tuple(int(v) for v in sorted(rng.choice(N, 3, replace=False))) for _ in range(n_sample)})
+        idx = [math.comb(k, 3) + math.comb(j, 2) + i for (i, j, k) in trip]
+        sub = np.sort(rng.choice(N, 12, replace=False))
+        errs = {}
+        dt = 0.0
+        for t in (0, T - 1):
+            phi = torch.empty((1, N, V, 3), dtype=torch.complex64, device="cuda")
+            generate(t, phi, main)
+            ph = phi[0].cpu().numpy()
+            t0 = time.perf_counter()
+            ref = O.baryon_triples(ph, L, mom, trip)
+            rM = O.meson_blocks(ph[sub], L, mom)
+            dt += time.perf_counter() - t0
+            errs[f"t{t}"] = {"B": rel_frob(B[t][:, idx].cpu().numpy().T, ref),
+                             "M": rel_frob(M[t].cpu().numpy()[:, sub][:, :, sub], rM)}
+        out["rel_err"] = dict(errs, sample=f"{len(trip)} random i<j<k triples x {P} momenta and the meson blocks of "
+                                           f"12 random vectors, timeslices 0 and {T - 1}")
+        if timed_oracle:
+            fl = 2 * 8.0 * 3 * V * (len(trip) + 144) * P
+            out["cpu_baseline"] = {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": O.num_threads(),
+                                   "kind": "oracle", "sample": out["rel_err"]["sample"] + f" ({dt:.1f} s)"}
+    plan.close()
+    del B, M, bufs, ws
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_large(args):
+    """--workload large: L=48 (110,592 sites), T=96, N=128, 33 momenta, streamed timeslice by timeslice with the
+    next timeslice's vectors generated on the device beside the current contraction."""
+    import torch
+    from paper_2510_26313_gb300 import binding as laph
+    torch.cuda.set_device(0)
+    L, T, N = LARGE["L"], LARGE["T"], LARGE["N"]
+    mom = synth.momentum_shell(LARGE["n2"])
+    clocks = ClockSampler(0)
+    clocks.start()
+    r = measure_large(laph, L, T, N, mom, args.mode, args.steps, args.warmup,
+                      n_sample=0 if args.no_cpu_baseline else 200, timed_oracle=not args.no_cpu_baseline)
+    clk = clocks.stop()
+    peaks, src = measured_peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    line = {
+        "metric": f"baryon+meson block complex TFLOP/s at L={L},N={N},Np={mom.shape[0]} (streamed)",
+        "value": r["value"], "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": f"{args.mode}->f32/f64", "data": "synthetic (seeded complex Gaussian generated on the device)",
+        "config": {"workload": f"L={L},T={T},N={N},P={mom.shape[0]} (large, streamed)", "L": L, "T": T, "N": N,
+                   "P": int(mom.shape[0]), "mode": args.mode,
+                   "l2": "inputs larger than L2 (phi %.2f GB per timeslice)" % (N * L ** 3 * 24 / 1e9)},
+        "roofline": {"bound": "tensor", "achieved": r["kernel_tflops"], "peak": peak, "unit": "TFLOP/s",
+                     "frac": r["kernel_tflops"] / peak, "traffic": None, "peak_source": src},
+        "cpu_baseline": r.get("cpu_baseline"), "e2e": None, "gpu_launches": r["launches"], "clocks": clk,
+        "rel_err": r.get("rel_err"), "kernel_ms": r["kernel_ms"], "device_status": r["device_status"],
+        "sum_sites": r["sum_sites"],
+    }
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_triplets(args):
@@ -486,21 +637,20 @@ def run_lanczos(args):
         e2e = {"value": world * T / dt, "unit": "timeslices/s", "h2d_bytes_per_step": U_host.numel() * 8,
                "d2h_bytes_per_step": out_host.numel() * 8 + T * n_ev * 16}
     cpu = None
+    parity = None
     if rank == 0 and not args.no_cpu_baseline:
-        # the oracle has no iterative eigensolver at this size (its reference is a dense Hermitian solve): time its
-        # FP64 Laplacian stencil on timeslice 0 and scale to the m (d) operator applications of one solve,
-        # leaving out the orthogonalisation (in the CPU's favour)
+        # the oracle's plain FP64 Lanczos (same m, filter degree and bound, two Gram-Schmidt passes per step, its own
+        # FP64 stencil) solves timeslice 0 of the same links: the timed CPU baseline, and a full-size check of the GPU's
+        # eigenvalues of that timeslice
         U0 = U[0].cpu().numpy()
-        f = evecs[0, :8].cpu().numpy()
         t0 = time.perf_counter()
-        reps = 0
-        while time.perf_counter() - t0 < 10.0:
-            O.laplacian(U0, f, L)
-            reps += 1
-        per_apply = (time.perf_counter() - t0) / (reps * f.shape[0])
-        cpu = {"value": 1.0 / (per_apply * m * d), "unit": "timeslices/s", "cores": O.num_threads(), "kind": "oracle",
-               "sample": f"{reps} x 8 applications of the oracle's FP64 Laplacian on timeslice 0, scaled to the "
-                         f"{m * d} applications of one solve (orthogonalisation not counted)"}
+        lam, rcpu = O.lanczos_eigenpairs(U0, L, n_ev, m, d, lo)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1.0 / dt, "unit": "timeslices/s", "cores": O.num_threads(), "kind": "oracle",
+               "sample": f"timeslice 0: one whole FP64 Lanczos solve (m={m}, degree {d}, {n_ev} eigenpairs) "
+                         f"({dt:.1f} s)"}
+        parity = {"max_abs_dlambda_t0": float(np.abs(ev[0] - lam).max()), "oracle_max_resid": float(rcpu.max()),
+                  "note": "GPU eigenvalues of timeslice 0 against the oracle's FP64 Lanczos on the same links"}
     line = {
         "metric": f"LapH eigenvectors: timeslices/s for the {n_ev} lowest eigenpairs of the 3-d Laplacian at L={L}",
         "value": world * T / (ms / 1e3), "unit": "timeslices/s", "n_gpus": world, "steps": args.steps,
@@ -531,7 +681,7 @@ def run_lanczos(args):
         "convergence": {"max_resid": float(res.max()), "median_resid": float(np.median(res)),
                         "ev_min": float(ev.min()), "ev_max": float(ev.max())},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(sum(s["launches"] for s in stats)), "clocks": clk,
-        "laplacian_api": lap_api,
+        "laplacian_api": lap_api, "parity": parity,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -624,13 +774,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="f16x3")
-    ap.add_argument("--workload", default="metric", choices=sorted(WORKLOADS) + ["ragged", "triplets", "projection"] + sorted(LANCZOS))
+    ap.add_argument("--workload", default="metric", choices=sorted(WORKLOADS) + ["ragged", "triplets", "projection", "large"] + sorted(LANCZOS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--ref-triples", type=int, default=6000)
     ap.add_argument("--chunk-sites", type=int, default=0)
     ap.add_argument("--sum-sites", type=int, default=0)
+    ap.add_argument("--tile-cols", type=int, default=0)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="metric workload: the default schedule instead of the autotuned one")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -638,6 +791,8 @@ def main():
         return run_ragged(args)
     if args.workload == "triplets":
         return run_triplets(args)
+    if args.workload == "large":
+        return run_large(args)
     if args.workload == "projection":
         return run_projection(args)
     if args.workload in LANCZOS:
@@ -663,8 +818,21 @@ def main():
     # ---- inputs: seeded per rank (weak scaling), host generation, then resident in HBM
     phi_h = synth.random_phi(L, N, T=T, instance=rank)
     phi = torch.from_numpy(phi_h).cuda()
-    plan = laph.Plan([(L, T, N, mom)], mode=args.mode, flags=laph.PLAN_TIMING, chunk_sites=args.chunk_sites,
-                     sum_sites=args.sum_sites)
+    tune = args.mode != "fp32" and not args.no_autotune
+    t_plan = time.perf_counter()
+    plan = laph.Plan([(L, T, N, mom)], mode=args.mode,
+                     flags=laph.PLAN_TIMING | (laph.PLAN_AUTOTUNE if tune else 0), chunk_sites=args.chunk_sites,
+                     sum_sites=args.sum_sites, tile_cols=args.tile_cols)
+    t_plan = time.perf_counter() - t_plan
+    desc = plan.describe()
+    schedule = {"tile_cols": desc["tile_cols"], "chunk_sites": desc["chunk_sites"], "sum_sites": plan.sum_sites()[0],
+                "timeslices_per_chunk": plan.schedule()["timeslices_per_chunk"],
+                "tile_order": plan.schedule()["tile_order"], "autotuned": tune, "plan_create_s": t_plan}
+    if tune:
+        schedule["candidates"] = [[r["tile_cols"], r["tile_order"], r["timeslices_per_chunk"], r["sum_sites"],
+                                   r["chunk_sites"], round(r["ms"], 2), r["probe_err"]] for r in plan.tuning()]
+        schedule["candidate_fields"] = ["tile_cols", "tile_order", "timeslices_per_chunk", "sum_sites", "chunk_sites",
+                                        "ms", "probe_err"]
     Bs, Ms = plan.alloc_outputs()
     ws = plan.alloc_workspace()
     stream = torch.cuda.current_stream()
@@ -709,8 +877,9 @@ def main():
     tc = args.mode != "fp32"
     if tc:
         peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
-        n_ct = -(-(N * P) // 96)
-        images = T * n_ct * (-(-(3 * V) // 24)) * 36864           # stage images read per step
+        nc = desc["tile_cols"]
+        n_ct = -(-(N * P) // nc)
+        images = T * n_ct * (-(-(3 * V) // 24)) * 384 * nc        # stage images read per step (384 nc B each)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": TC_DRAM_PER_IMAGE_BYTE * images / n_con,
                 "traffic_source": "per tc_kernel launch: DRAM bytes per stage-image byte from the ncu capture at "
@@ -791,6 +960,14 @@ def main():
                                   "frac": df_bytes / (df_ms / 1e3) / 1e9 / hbm},
         }
         del D, dense
+        # the large streamed form (L=48, N=128, 33 momenta), two timeslices
+        if args.mode in ("f16x3", "bf16x3"):
+            lg = measure_large(laph, LARGE["L"], 2, LARGE["N"], synth.momentum_shell(LARGE["n2"]), args.mode, 1, 1,
+                               n_sample=0 if args.no_cpu_baseline else 200)
+            aux["large_streamed"] = {"workload": f"L={LARGE['L']},T=2,N={LARGE['N']},P=33 (streamed)",
+                                     "ms": lg["ms_per_step"], "kernel_ms": lg["kernel_ms"], "value": lg["value"],
+                                     "kernel_tflops": lg["kernel_tflops"], "unit": "TFLOP/s",
+                                     "rel_err": lg.get("rel_err"), "device_status": lg["device_status"]}
         # the next row of the path: three-field triplets at the workload's shape, 4 timeslices
         if args.mode in ("f16x3", "bf16x3"):
             tr = measure_triplets(laph, L, min(4, T), N, mom, args.mode, 2, 1,
@@ -831,7 +1008,7 @@ def main():
         e2e = {"value": weak_scaling_value(flops_step, 1e3 * e2e_s, world), "unit": "TFLOP/s",
                "h2d_bytes_per_step": int(phi_pin.numel() * 8),
                "d2h_bytes_per_step": int(Bh[0].numel() * 16 + Mh[0].numel() * 16),
-               "ms_per_step": 1e3 * e2e_s}
+               "ms_per_step": 1e3 * e2e_s, "pinned_copy_rates": pinned_copy_rates()}
 
     if rank == 0:
         line = {
@@ -842,7 +1019,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": f"L={L},T={T},N={N},P={P} ({args.workload})", "L": L, "T": T, "N": N, "P": P,
                        "mode": args.mode, "l2": "inputs larger than L2 (phi %.2f GB)" % (phi_h.nbytes / 1e9),
-                       "parallelism": f"replicas x{world} (independent timeslice batches)"},
+                       "parallelism": f"replicas x{world} (independent timeslice batches)",
+                       "schedule": schedule},
             "roofline": roof,
             "aux_kernels": aux,
             "cpu_baseline": cpu,

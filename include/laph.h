@@ -286,14 +286,16 @@ typedef struct {
                         into FP32 running sums with round-to-nearest (default 128; the error of the tensor core's
                         accumulation grows with it); FP32 mode: sites summed in FP32 before the FP64 reduction
                         (default 1024) */
-    int sum_sites;   /* tensor-core modes: sites per block of the FP64 site reduction (default 4096, rounded down
+    int sum_sites;   /* tensor-core modes: sites per block of the FP64 site reduction (default 8192, rounded down
                         to a multiple of 8): a tile covers one block, its running sums become one FP32 partial per
                         output, and the partials of all blocks are added in FP64 in block order */
+    int tile_cols;   /* tensor-core modes: complex columns per tile, 96 (default) or 64 */
 } laph_plan_options;
 
 /* laph_plan_create with numerical parameters (opts may be NULL).  LAPH_ERR_ARG
- * for a negative value or one above 2^24, plus the conditions of
- * laph_plan_create. */
+ * for a negative value or one above 2^24, a tile width other than 0, 64 or
+ * 96, plus the conditions of laph_plan_create.  With LAPH_PLAN_AUTOTUNE the
+ * options are the starting point of the search (see laph_plan_tuning). */
 LAPH_API int laph_plan_create_opts(const laph_instance *inst, int n_inst, int mode, unsigned flags,
                                    const laph_plan_options *opts, laph_plan **plan);
 
@@ -372,11 +374,9 @@ LAPH_API int laph_plan_contraction_launches(const laph_plan *plan, int *n);
  *                         tiles outer;
  *   n_chunks:             chunks (contraction launches) per execute.
  * Without LAPH_PLAN_AUTOTUNE the chunk size minimises partly filled waves of
- * persistent CTAs and the order is 0.  With it, plan creation times the
- * candidates (both orders x {that chunk size, the largest chunk within the
- * 24 GiB cap}) on seeded synthetic inputs of the plan's shapes, allocating
- * inputs, outputs and a workspace for the duration, and keeps the fastest;
- * *n_candidates and candidate_ms (room for 8) report their times.  Any
+ * persistent CTAs and the order is 0.  With it, plan creation times candidate
+ * schedules (laph_plan_tuning) and keeps the fastest; *n_candidates receives
+ * their number and candidate_ms (room for 8) the times of the first 8.  Any
  * pointer may be NULL. */
 LAPH_API int laph_plan_schedule(const laph_plan *plan, int64_t *timeslices_per_chunk, int *tile_order, int *n_chunks,
                                int *n_candidates, float *candidate_ms);
@@ -387,6 +387,35 @@ LAPH_API int laph_plan_schedule(const laph_plan *plan, int64_t *timeslices_per_c
  * padding and the triangle waste included (0 for the FP32 mode).  Divided by
  * the contraction kernels' time it gives the executed tensor rate. */
 LAPH_API int laph_plan_tensor_flops(const laph_plan *plan, double *flops);
+
+/* One candidate schedule timed by LAPH_PLAN_AUTOTUNE. */
+typedef struct {
+    int tile_cols;                  /* complex columns per tile (96 or 64) */
+    int sum_sites;                  /* sites per block of the FP64 site reduction */
+    int chunk_sites;                /* drain interval of the tensor core's FP32 accumulation, in sites */
+    int tile_order;                 /* 0: column tiles outer, 1: row tiles outer */
+    int64_t timeslices_per_chunk;   /* 0: chunks filled by bytes (several instances) */
+    float ms;                       /* one execute on the synthetic inputs */
+    double probe_err;               /* relative error of (instance 0, timeslice 0) against the FP32 path, or -1 when
+                                       not probed */
+} laph_tune_record;
+
+/* The autotuner's record.  With LAPH_PLAN_AUTOTUNE, plan creation times
+ * candidate schedules on seeded synthetic inputs of the plan's shapes
+ * (pseudo-random entries in [-1, 1); inputs, outputs and a workspace are
+ * allocated for the duration; one warm-up and one timed execute each) by a
+ * coordinate search: tile width (96 and 64 columns) x tile order x chunking
+ * (the wave model and, for one instance, the largest chunk within the 24 GiB
+ * cap); then, from the fastest, half and twice the site-block size of the
+ * FP64 reduction; then half and 1.5 times the drain interval.  A drain
+ * interval is accepted only if the relative error of (instance 0, timeslice 0)
+ * against the FP32 CUDA-core path stays within 5e-6 (half the 1e-5 bound) or
+ * within the default interval's own error; plans of several fields keep the
+ * default interval.  The fastest accepted candidate is applied (see
+ * laph_plan_describe, laph_plan_schedule, laph_plan_sum_sites).
+ * Writes min(cap, number of candidates) records; *n_candidates (may be NULL)
+ * receives the number of candidates (0 without LAPH_PLAN_AUTOTUNE). */
+LAPH_API int laph_plan_tuning(const laph_plan *plan, int cap, laph_tune_record *rec, int *n_candidates);
 
 /* Number of kernels of this library one laph_plan_execute launches. */
 LAPH_API int laph_plan_launches_per_execute(const laph_plan *plan, int *n);

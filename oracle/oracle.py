@@ -262,3 +262,49 @@ def lowest_eigenpairs(U: np.ndarray, L: int, n: int):
     (small L only): numpy's Hermitian eigensolver on the dense matrix."""
     w, v = np.linalg.eigh(laplacian_matrix(U, L))
     return w[:n], v[:, :n].T.reshape(n, L ** 3, 3)
+
+
+def lanczos_eigenpairs(U: np.ndarray, L: int, n_ev: int, m: int, degree: int = 0, lo: float = 0.0, seed: int = 0):
+    """The n_ev lowest eigenvalues of -Delta on one timeslice by plain FP64 Lanczos (paper, section "Innovations",
+    subsection "Scalable Lanczos Eigensolver"), in the conventions the GPU solver states: m steps from a seeded
+    random unit vector, each new vector orthogonalised against the whole basis by two classical Gram-Schmidt passes,
+    alpha_j from the first pass and beta_j the norm after the second; the operator is -Delta (this module's stencil)
+    or, for degree d > 0, the Chebyshev filter T_d((-Delta - c) / e) with c = (12 + lo) / 2, e = (12 - lo) / 2;
+    the Ritz vectors of the wanted end of the tridiagonal matrix's spectrum (numpy's eigh as the step: the smallest
+    for d = 0, the largest for even d, the most negative for odd d); eigenvalues are Rayleigh quotients with -Delta,
+    residuals |(-Delta) x - lambda x| / |x|.  U complex [3][L^3][3][3].  Returns (eigenvalues ascending, residuals)."""
+    V = L ** 3
+    n = 3 * V
+    U = np.ascontiguousarray(U, dtype=np.complex128)
+    A = lambda x: laplacian(U, x.reshape(V, 3), L).reshape(n)
+
+    def op(v):
+        if degree == 0:
+            return A(v)
+        c, e = 0.5 * (12.0 + lo), 0.5 * (12.0 - lo)
+        y0, y1 = v, (A(v) - c * v) / e
+        for _ in range(2, degree + 1):
+            y0, y1 = y1, 2.0 * (A(y1) - c * y1) / e - y0
+        return y1
+
+    rng = np.random.default_rng(seed)
+    Q = np.zeros((m + 1, n), dtype=np.complex128)
+    v = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    Q[0] = v / np.linalg.norm(v)
+    alpha, beta = np.zeros(m), np.zeros(m)
+    for j in range(m):
+        w = op(Q[j])
+        c1 = Q[: j + 1].conj() @ w
+        w = w - Q[: j + 1].T @ c1
+        w = w - Q[: j + 1].T @ (Q[: j + 1].conj() @ w)
+        alpha[j], beta[j] = c1[j].real, np.linalg.norm(w)
+        Q[j + 1] = w / beta[j]
+    Tm = np.diag(alpha) + np.diag(beta[:-1], 1) + np.diag(beta[:-1], -1)
+    _, S = np.linalg.eigh(Tm)
+    pick = np.arange(m - 1, m - 1 - n_ev, -1) if (degree > 0 and degree % 2 == 0) else np.arange(n_ev)
+    X = S[:, pick].T @ Q[:m]
+    AX = np.stack([A(x) for x in X])
+    lam = np.einsum("ij,ij->i", X.conj(), AX).real / np.einsum("ij,ij->i", X.conj(), X).real
+    res = np.linalg.norm(AX - lam[:, None] * X, axis=1) / np.linalg.norm(X, axis=1)
+    order = np.argsort(lam)
+    return lam[order], res[order]

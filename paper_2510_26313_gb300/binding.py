@@ -48,7 +48,13 @@ class laph_instance(ctypes.Structure):
 
 
 class laph_plan_options(ctypes.Structure):
-    _fields_ = [("chunk_sites", ctypes.c_int), ("sum_sites", ctypes.c_int)]
+    _fields_ = [("chunk_sites", ctypes.c_int), ("sum_sites", ctypes.c_int), ("tile_cols", ctypes.c_int)]
+
+
+class laph_tune_record(ctypes.Structure):
+    _fields_ = [("tile_cols", ctypes.c_int), ("sum_sites", ctypes.c_int), ("chunk_sites", ctypes.c_int),
+                ("tile_order", ctypes.c_int), ("timeslices_per_chunk", ctypes.c_int64), ("ms", ctypes.c_float),
+                ("probe_err", ctypes.c_double)]
 
 
 class laph_lanczos_params(ctypes.Structure):
@@ -91,6 +97,7 @@ def lib() -> ctypes.CDLL:
             "laph_plan_create_opts": (i32, [ctypes.POINTER(laph_instance), i32, i32, ctypes.c_uint,
                                             ctypes.POINTER(laph_plan_options), ctypes.POINTER(vp)]),
             "laph_plan_sum_sites": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+            "laph_plan_tuning": (i32, [vp, i32, ctypes.POINTER(laph_tune_record), ctypes.POINTER(i32)]),
             "laph_plan_workspace_size": (i32, [vp, ctypes.POINTER(sz)]),
             "laph_plan_execute": (i32, [vp, vpp, vpp, vpp, vp, vp]),
             "laph_plan_host_workspace_size": (i32, [vp, ctypes.POINTER(sz)]),
@@ -393,7 +400,8 @@ class Plan:
     B[n] complex128 [T][P][C(N,3)], M[n] complex128 [T][P][N][N].
     """
 
-    def __init__(self, instances, mode="f16x3", flags: int = 0, chunk_sites: int = 0, sum_sites: int = 0):
+    def __init__(self, instances, mode="f16x3", flags: int = 0, chunk_sites: int = 0, sum_sites: int = 0,
+                 tile_cols: int = 0):
         # (L, T, N, momenta) or, for doublet plans of two vector counts, (L, T, N, momenta, n_col)
         self._moms = [_momenta(inst[3]) for inst in instances]
         self.n_col = [int(inst[4]) if len(inst) > 4 else 0 for inst in instances]
@@ -407,7 +415,7 @@ class Plan:
         self.flags = flags
         self.mode = _mode(mode)
         h = ctypes.c_void_p()
-        opts = laph_plan_options(int(chunk_sites), int(sum_sites))
+        opts = laph_plan_options(int(chunk_sites), int(sum_sites), int(tile_cols))
         _check(lib().laph_plan_create_opts(arr, len(instances), self.mode, flags, ctypes.byref(opts), ctypes.byref(h)),
                "laph_plan_create_opts")
         self._h = h
@@ -478,7 +486,16 @@ class Plan:
         _check(lib().laph_plan_schedule(self._h, ctypes.byref(pc), ctypes.byref(order), ctypes.byref(nc),
                                         ctypes.byref(ncand), ms), "laph_plan_schedule")
         return {"timeslices_per_chunk": int(pc.value), "tile_order": int(order.value), "n_chunks": int(nc.value),
-                "candidate_ms": [float(ms[k]) for k in range(ncand.value)]}
+                "candidate_ms": [float(ms[k]) for k in range(min(ncand.value, 8))]}
+
+    def tuning(self) -> list:
+        """The autotuner's candidates (PLAN_AUTOTUNE): dicts of tile_cols, sum_sites, chunk_sites, tile_order,
+        timeslices_per_chunk, ms and probe_err (-1 when not probed)."""
+        n = ctypes.c_int()
+        _check(lib().laph_plan_tuning(self._h, 0, None, ctypes.byref(n)), "laph_plan_tuning")
+        recs = (laph_tune_record * max(n.value, 1))()
+        _check(lib().laph_plan_tuning(self._h, n.value, recs, None), "laph_plan_tuning")
+        return [{k: getattr(recs[i], k) for k, _ in laph_tune_record._fields_} for i in range(n.value)]
 
     def launches_per_execute(self) -> int:
         v = ctypes.c_int()

@@ -67,6 +67,18 @@ constexpr size_t PSI_CAP_BYTES = 24ull << 30;
 
 }  // namespace
 
+namespace laph {
+// A schedule of the tensor-core path: tile width (complex columns), sites per
+// block of the FP64 site reduction, drain interval of the tensor core's FP32
+// accumulation, timeslices per chunk (-1: the wave model, -2: the largest
+// chunk within the workspace cap; resolved when applied) and tile order.
+struct Sched {
+    int tile_cols, sum_sites, chunk_sites;
+    long long per_chunk;
+    int order;
+};
+}  // namespace laph
+
 struct laph_plan {
     int mode = 0;
     unsigned flags = 0;
@@ -76,6 +88,7 @@ struct laph_plan {
     std::vector<InstDev> h_inst;               // pointer fields unset
     std::vector<long long> phi_elems;          // complex64 entries of phi per instance
     std::vector<long long> outB_elems, outM_elems;
+    std::vector<int32_t> momenta0;             // instance 0's momenta (the autotuner's accuracy probe)
     std::vector<int> h_T, h_ts_base;
     InstDev *d_inst = nullptr;
     float2 *d_phase = nullptr;
@@ -109,8 +122,13 @@ struct laph_plan {
     // tiles outer); with LAPH_PLAN_AUTOTUNE the candidates' timings
     long long sched_per_chunk = 0;
     int sched_order = 0;
+    laph::Sched sched{};
     bool tuned = false;
+    // LAPH_PLAN_AUTOTUNE: every candidate, its time (ms) and its probe error (-1: not probed)
+    std::vector<laph::Sched> tune_cand;
+    std::vector<long long> tune_pc;
     std::vector<float> tune_ms;
+    std::vector<double> tune_err;
     size_t off_psi = 0, off_part = 0;
     // tensor-core path: flops the tensor pipe executes per execute (every MMA of
     // every tile: 2 x 128 rows x the tile's real columns x 48 real K entries
@@ -215,9 +233,8 @@ static void free_plan(laph_plan *p)
     delete p;
 }
 
-static int autotune_time(laph_plan *p, const std::vector<std::pair<long long, int>> &cand,
-                         const std::function<void(long long, int)> &emit, const std::function<cudaError_t()> &upload,
-                         size_t *best);
+static int autotune(laph_plan *p, const laph::Sched &def,
+                    const std::function<cudaError_t(const laph::Sched &)> &apply);
 static cudaError_t ensure_side(laph_plan *p);
 
 static int tc_supported(int device)
@@ -239,6 +256,7 @@ int laph_plan_create_opts(const laph_instance *inst, int n_inst, int mode, unsig
     if (!inst || n_inst < 1 || !plan_out) return LAPH_ERR_ARG;
     const int opt_chunk = opts ? opts->chunk_sites : 0, opt_sum = opts ? opts->sum_sites : 0;
     if (opt_chunk < 0 || opt_chunk > (1 << 24) || opt_sum < 0 || opt_sum > (1 << 24)) return LAPH_ERR_ARG;
+    if (opts && opts->tile_cols != 0 && opts->tile_cols != 64 && opts->tile_cols != 96) return LAPH_ERR_ARG;
     if (mode < 0 || mode >= LAPH_NUM_MODES) return LAPH_ERR_ARG;
     const bool skipB = flags & LAPH_PLAN_SKIP_B, skipM = flags & LAPH_PLAN_SKIP_M;
     if (skipB && skipM) return LAPH_ERR_ARG;
@@ -274,6 +292,7 @@ int laph_plan_create_opts(const laph_instance *inst, int n_inst, int mode, unsig
     p->tile_rows = tc ? laph::TC_TR : laph::SIMT_TR;
     p->tile_cols = tc ? laph::TC_TC : laph::SIMT_TC;
     p->chunk_sites = opt_chunk ? opt_chunk : (tc ? TC_DEFAULT_CHUNK : SIMT_DEFAULT_CHUNK);
+    p->momenta0.assign(inst[0].momenta, inst[0].momenta + 3 * inst[0].n_mom);
 
     // ---- per-instance descriptors and phase tables
     long long phase_total = 0;
@@ -364,10 +383,70 @@ int laph_plan_create_opts(const laph_instance *inst, int n_inst, int mode, unsig
     // CTAs that share a stage image run side by side.
     std::vector<TileDev> tiles;
     std::vector<laph::PsiUnit> units;
-    const int TR = p->tile_rows, TC = p->tile_cols;
+    const int TR = p->tile_rows;
     std::vector<std::vector<TileDev>> ones(n_inst);
     std::vector<size_t> unit_bytes(n_inst);
     size_t psi_total = 0;
+    // the (row tile, column tile) pairs of one timeslice of every instance for
+    // tiles of TC complex columns
+    auto build_tiles = [&](int TC) {
+        p->tile_cols = TC;
+        p->max_staged = 0;
+        for (int n = 0; n < n_inst; n++) {
+            InstDev &d = p->h_inst[n];
+            d.n_ct = (d.cols + TC - 1) / TC;
+            std::vector<TileDev> &one = ones[n];
+            one.clear();
+            for (int col0 = 0; col0 < d.cols; col0 += TC) {
+                const int nc = std::min(TC, d.cols - col0);
+                const int kmin = col0 / d.P, kmax = (col0 + nc - 1) / d.P;
+                const bool trip = d.kind == laph::INST_TRIPLETS;
+                for (int row0 = 0; row0 < d.rows; row0 += TR) {
+                    // baryon blocks: rows of pairs i < j need only columns k > j
+                    int jmin = -1;
+                    if (row0 >= d.mes_rows && !trip) {
+                        int i, j;
+                        laph::pair_of(row0 - d.mes_rows, i, j);
+                        jmin = j;
+                    }
+                    if (jmin >= 0 && kmax <= jmin) continue;
+                    // contiguous range of vectors used by the rows of this tile (for
+                    // triplets: of phi_u, and [w_lo, w_hi] of phi_v)
+                    int v_lo = d.N, v_hi = -1, w_lo = d.N, w_hi = -1;
+                    for (int g = row0; g < std::min(row0 + TR, d.rows); g++) {
+                        if (g < d.mes_rows) {
+                            v_lo = std::min(v_lo, g);
+                            v_hi = std::max(v_hi, g);
+                        } else if (trip) {
+                            const int q = g - d.mes_rows, i = q / d.N, j = q - i * d.N;
+                            v_lo = std::min(v_lo, i);
+                            v_hi = std::max(v_hi, i);
+                            w_lo = std::min(w_lo, j);
+                            w_hi = std::max(w_hi, j);
+                        } else {
+                            int i, j;
+                            laph::pair_of(g - d.mes_rows, i, j);
+                            v_lo = std::min(v_lo, i);
+                            v_hi = std::max(v_hi, j);
+                        }
+                    }
+                    const int nv = v_hi - v_lo + 1;
+                    const int nw = trip ? w_hi - w_lo + 1 : 0;
+                    if (!trip) w_lo = 0;
+                    p->max_staged = std::max(p->max_staged, tc ? nv + nw : nv + (kmax - kmin + 1));
+                    const long long psi_ct = tc ? (long long)(col0 / TC) * d.n_st * laph::tc_stage_bytes(TC) : 0;
+                    int cskip = 0;
+                    if (tc && jmin >= 0) {
+                        const int lead = std::max(0, std::min(nc, (jmin + 1) * d.P - col0));
+                        cskip = (lead / 8) * 8;
+                    }
+                    one.push_back(TileDev{n, 0, row0, col0, v_lo, nv, w_lo, nw, kmin, kmax - kmin + 1, nc, cskip,
+                                          psi_ct, 0, d.n_st, 0});
+                }
+            }
+            p->max_P = std::max(p->max_P, d.P);
+        }
+    };
     // site blocks of the FP64 reduction (tensor-core path) and the workspace
     // bytes of one (instance, timeslice): its B-operand stage images and the
     // FP32 partials of all its site blocks
@@ -378,104 +457,54 @@ int laph_plan_create_opts(const laph_instance *inst, int n_inst, int mode, unsig
             InstDev &d = p->h_inst[n];
             d.sc_stages = tc ? std::max(1, std::min(d.n_st, sum_sites / laph::TC_BS)) : d.n_st;
             d.n_sc = (d.n_st + d.sc_stages - 1) / d.sc_stages;
-            unit_bytes[n] = tc ? (size_t)d.n_ct * d.n_st * laph::TC_STAGE_BYTES +
+            unit_bytes[n] = tc ? (size_t)d.n_ct * d.n_st * laph::tc_stage_bytes(p->tile_cols) +
                                      (size_t)d.n_sc * (size_t)(d.n_outB + d.n_outM) * sizeof(float2)
                                : 0;
             psi_total += (size_t)d.T * unit_bytes[n];
         }
     };
-    for (int n = 0; n < n_inst; n++) {
-        const InstDev &d = p->h_inst[n];
-        std::vector<TileDev> &one = ones[n];
-        for (int col0 = 0; col0 < d.cols; col0 += TC) {
-            const int nc = std::min(TC, d.cols - col0);
-            const int kmin = col0 / d.P, kmax = (col0 + nc - 1) / d.P;
-            const bool trip = d.kind == laph::INST_TRIPLETS;
-            for (int row0 = 0; row0 < d.rows; row0 += TR) {
-                // baryon blocks: rows of pairs i < j need only columns k > j
-                int jmin = -1;
-                if (row0 >= d.mes_rows && !trip) {
-                    int i, j;
-                    laph::pair_of(row0 - d.mes_rows, i, j);
-                    jmin = j;
-                }
-                if (jmin >= 0 && kmax <= jmin) continue;
-                // contiguous range of vectors used by the rows of this tile (for
-                // triplets: of phi_u, and [w_lo, w_hi] of phi_v)
-                int v_lo = d.N, v_hi = -1, w_lo = d.N, w_hi = -1;
-                for (int g = row0; g < std::min(row0 + TR, d.rows); g++) {
-                    if (g < d.mes_rows) {
-                        v_lo = std::min(v_lo, g);
-                        v_hi = std::max(v_hi, g);
-                    } else if (trip) {
-                        const int q = g - d.mes_rows, i = q / d.N, j = q - i * d.N;
-                        v_lo = std::min(v_lo, i);
-                        v_hi = std::max(v_hi, i);
-                        w_lo = std::min(w_lo, j);
-                        w_hi = std::max(w_hi, j);
-                    } else {
-                        int i, j;
-                        laph::pair_of(g - d.mes_rows, i, j);
-                        v_lo = std::min(v_lo, i);
-                        v_hi = std::max(v_hi, j);
-                    }
-                }
-                const int nv = v_hi - v_lo + 1;
-                const int nw = trip ? w_hi - w_lo + 1 : 0;
-                if (!trip) w_lo = 0;
-                p->max_staged = std::max(p->max_staged, tc ? nv + nw : nv + (kmax - kmin + 1));
-                const long long psi_ct = (long long)(col0 / TC) * d.n_st * laph::TC_STAGE_BYTES;
-                int cskip = 0;
-                if (tc && jmin >= 0) {
-                    const int lead = std::max(0, std::min(nc, (jmin + 1) * d.P - col0));
-                    cskip = (lead / 8) * 8;
-                }
-                one.push_back(TileDev{n, 0, row0, col0, v_lo, nv, w_lo, nw, kmin, kmax - kmin + 1, nc, cskip, psi_ct,
-                                      0, d.n_st, 0});
-            }
-        }
-        p->max_P = std::max(p->max_P, d.P);
-    }
-    set_sum(opt_sum ? opt_sum : TC_DEFAULT_SUM);
     int sms = 0;
     PCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
     // units per chunk: one instance -> the count (within the cap) that
-    // leaves the fewest partly filled waves of persistent CTAs; several
-    // instances -> chunks filled in order up to an even share of the total.
-    long long per_chunk = 0;
+    // leaves the fewest partly filled waves of persistent CTAs (want_largest:
+    // the largest count within the cap); several instances -> chunks filled
+    // in order up to an even share of the total (per_chunk 0)
     size_t psi_target = 0;
-    if (tc && (flags & LAPH_PLAN_CHUNK_PER_TIMESLICE)) {
-        per_chunk = 1;
-    } else if (tc && n_inst == 1) {
-        const long long U = p->h_inst[0].T, tpu = (long long)ones[0].size() * p->h_inst[0].n_sc;
-        const long long n_max = std::max(1LL, std::min(U, (long long)(PSI_CAP_BYTES / std::max<size_t>(unit_bytes[0], 1))));
-        long long best = -1, best_rounds = 0;
-        for (long long n = 1; n <= n_max; n++) {
-            const long long full = U / n, rest = U % n;
-            const long long rounds = full * ((n * tpu + sms - 1) / sms) + (rest * tpu + sms - 1) / sms;
-            if (best < 0 || rounds <= best_rounds) {
-                best = n;
-                best_rounds = rounds;
+    auto chunking = [&](bool want_largest) -> long long {
+        psi_target = 0;
+        if (!tc) return 0;
+        if (flags & LAPH_PLAN_CHUNK_PER_TIMESLICE) return 1;
+        if (n_inst == 1) {
+            const long long U = p->h_inst[0].T, tpu = (long long)ones[0].size() * p->h_inst[0].n_sc;
+            const long long n_max =
+                std::max(1LL, std::min(U, (long long)(PSI_CAP_BYTES / std::max<size_t>(unit_bytes[0], 1))));
+            if (want_largest) return n_max;
+            long long best = -1, best_rounds = 0;
+            for (long long n = 1; n <= n_max; n++) {
+                const long long full = U / n, rest = U % n;
+                const long long rounds = full * ((n * tpu + sms - 1) / sms) + (rest * tpu + sms - 1) / sms;
+                if (best < 0 || rounds <= best_rounds) {
+                    best = n;
+                    best_rounds = rounds;
+                }
             }
+            return best;
         }
-        per_chunk = best;
-    } else if (tc) {
         const long long n_chunks = (long long)((psi_total + PSI_CAP_BYTES - 1) / PSI_CAP_BYTES);
         psi_target = (psi_total + n_chunks - 1) / (size_t)std::max(1LL, n_chunks);
-    }
+        return 0;
+    };
     // instances in decreasing order of work per timeslice (stages x tiles),
     // so that the dynamically scheduled tiles of a chunk start with the longest
     std::vector<int> order(n_inst);
-    for (int n = 0; n < n_inst; n++) order[n] = n;
-    if (tc)
-        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-            return (long long)p->h_inst[a].n_st * (long long)ones[a].size() >
-                   (long long)p->h_inst[b].n_st * (long long)ones[b].size();
-        });
-    if (tc && p->max_staged > laph::TC_MAX_STAGED) {
-        free_plan(p);
-        return LAPH_ERR_UNSUPPORTED;
-    }
+    auto make_order = [&]() {
+        for (int n = 0; n < n_inst; n++) order[n] = n;
+        if (tc)
+            std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+                return (long long)p->h_inst[a].n_st * (long long)ones[a].size() >
+                       (long long)p->h_inst[b].n_st * (long long)ones[b].size();
+            });
+    };
     size_t psi_max = 0, part_max = 0;
     // tile, unit and chunk tables for a schedule (pc timeslices per chunk, or
     // chunks filled up to psi_target bytes when pc is 0).  On the tensor-core
@@ -540,7 +569,7 @@ int laph_plan_create_opts(const laph_instance *inst, int n_inst, int mode, unsig
                 if (tc) {
                     cur.n_tiles += (long long)one.size();
                     cur_bytes += unit_bytes[n];
-                    cur_psi += (size_t)d.n_ct * d.n_st * laph::TC_STAGE_BYTES;
+                    cur_psi += (size_t)d.n_ct * d.n_st * laph::tc_stage_bytes(p->tile_cols);
                     cur_part += (long long)d.n_sc * (d.n_outB + d.n_outM);
                 }
             }
@@ -611,30 +640,36 @@ int laph_plan_create_opts(const laph_instance *inst, int n_inst, int mode, unsig
         }
         return er;
     };
-    emit(per_chunk, 0);
-    PCK(upload());
+    // a whole schedule: tile width, site block, drain interval, chunking
+    // (-1: the wave model, -2: the largest chunk within the cap) and tile order
+    std::function<cudaError_t(const laph::Sched &)> apply = [&](const laph::Sched &c) -> cudaError_t {
+        build_tiles(tc ? c.tile_cols : laph::SIMT_TC);
+        set_sum(c.sum_sites);
+        make_order();
+        p->chunk_sites = c.chunk_sites;
+        const long long model = chunking(c.per_chunk == -2);   // also sets psi_target for several instances
+        const long long pc = c.per_chunk >= 0 ? c.per_chunk : model;
+        emit(pc, c.order);
+        p->sched = c;
+        return upload();
+    };
+    const int opt_cols = opts ? opts->tile_cols : 0;
+    const laph::Sched def{opt_cols ? opt_cols : laph::TC_TC, opt_sum ? opt_sum : TC_DEFAULT_SUM, p->chunk_sites, -1, 0};
+    PCK(apply(def));
+    if (tc && p->max_staged > laph::TC_MAX_STAGED) {
+        free_plan(p);
+        return LAPH_ERR_UNSUPPORTED;
+    }
     if (tc && (flags & LAPH_PLAN_AUTOTUNE)) {
-        // candidates: both tile orders x {the wave-model chunk size, the largest
-        // chunk within the cap} (one instance), each timed on seeded synthetic
-        // inputs of the plan's shapes; the fastest is kept
-        std::vector<std::pair<long long, int>> cand;
-        std::vector<long long> pcs{per_chunk};
-        if (n_inst == 1 && per_chunk > 0 && !(flags & LAPH_PLAN_CHUNK_PER_TIMESLICE)) {
-            const long long U = p->h_inst[0].T;
-            const long long n_max =
-                std::max(1LL, std::min(U, (long long)(PSI_CAP_BYTES / std::max<size_t>(unit_bytes[0], 1))));
-            if (n_max != per_chunk) pcs.push_back(n_max);
-        }
-        for (long long pc : pcs)
-            for (int o = 0; o < 2; o++) cand.push_back({pc, o});
-        size_t best = 0;
-        const int rc_t = autotune_time(p, cand, emit, upload, &best);
+        // candidates, each timed on seeded synthetic inputs of the plan's
+        // shapes (autotune_time); a coordinate search over tile width x tile
+        // order x chunking, then the site-block size, then the drain interval
+        // (kept only within the accuracy limit of the probe)
+        const int rc_t = autotune(p, def, apply);
         if (rc_t != LAPH_OK) {
             free_plan(p);
             return rc_t;
         }
-        emit(cand[best].first, cand[best].second);
-        PCK(upload());
         p->tuned = true;
     }
     if (tc) PCK(ensure_side(p));
@@ -704,6 +739,7 @@ static laph::TcConfig tc_config(const laph_plan *p)
     cfg.elem = (p->mode == LAPH_MODE_TC_BF16X3 || p->mode == LAPH_MODE_TC_BF16) ? 1 : 0;
     cfg.terms = (p->mode == LAPH_MODE_TC_F16X3 || p->mode == LAPH_MODE_TC_BF16X3) ? 3 : 1;
     cfg.chunk_sites = p->chunk_sites;
+    cfg.ncols = p->tile_cols;
     cfg.grid = p->grid;
     cfg.max_staged = p->max_staged;
     cfg.debug_stall = (p->flags & LAPH_PLAN_DEBUG_STALL) ? 1 : 0;
@@ -747,7 +783,7 @@ static int launch_tc_chunk(laph_plan *p, char *ws, size_t ci, const laph::TcConf
     const laph_plan::Chunk &c = p->chunks[ci];
     const int ps = (int)(p->n_ptimed % laph_plan::RING), cs = (int)(p->n_timed % laph_plan::RING);
     if (timing) CK(cudaEventRecord(p->pv_begin[ps], s));
-    e = laph::launch_psi(p->d_inst, p->d_units + c.unit0, c.n_units, c.n_jobs, maxbits, cfg.elem, psi, s);
+    e = laph::launch_psi(p->d_inst, p->d_units + c.unit0, c.n_units, c.n_jobs, maxbits, cfg.elem, cfg.ncols, psi, s);
     if (e != cudaSuccess) return cuda_fail(e, "psi");
     if (timing) {
         CK(cudaEventRecord(p->pv_end[ps], s));
@@ -848,20 +884,132 @@ static int ring_times(const std::vector<cudaEvent_t> &b, const std::vector<cudaE
     return LAPH_OK;
 }
 
-// Times every candidate schedule: seeded synthetic inputs of the plan's
-// shapes, a workspace of the candidate's size, one warm-up execute and one
-// timed execute on an internal stream.  *best = the fastest candidate.
-static int autotune_time(laph_plan *p, const std::vector<std::pair<long long, int>> &cand,
-                         const std::function<void(long long, int)> &emit, const std::function<cudaError_t()> &upload,
-                         size_t *best)
-{
-    const bool needB = !(p->flags & LAPH_PLAN_SKIP_B), needM = !(p->flags & LAPH_PLAN_SKIP_M);
-    std::vector<void *> phi(p->n_inst, nullptr), ob(p->n_inst, nullptr), om(p->n_inst, nullptr);
+// The autotuner.  Every candidate schedule is applied to the plan and timed
+// on seeded synthetic inputs of the plan's shapes (pseudo-random entries in
+// [-1, 1), outputs and a workspace allocated for the duration): one warm-up
+// execute and one timed execute on an internal stream.  The search is by
+// coordinates: tile width (96, 64 columns) x tile order x chunking (the wave
+// model, the largest chunk within the cap), then the site-block size of the
+// FP64 reduction (half and twice the default), then the drain interval of the
+// tensor core's accumulation (half and one and a half times the default).
+// A drain interval is kept only if the error of (instance 0, timeslice 0)
+// against the FP32 CUDA-core path (its accuracy probe) stays within
+// TUNE_ERR_LIMIT or within the default's own probe error; plans of several
+// fields have no FP32 path and keep the default interval.  The fastest
+// accepted candidate is applied.
+constexpr double TUNE_ERR_LIMIT = 5e-6;   // half the 1e-5 bound of the split-precision modes
+
+struct TuneState {
+    std::vector<void *> phi, ob, om;
     cudaStream_t st = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    laph_plan *ref = nullptr;                // FP32 plan of instance 0, timeslice 0
+    void *refB = nullptr, *refM = nullptr;
+    double *acc = nullptr;                   // device: difference and reference norms
+};
+
+static int tune_time(laph_plan *p, TuneState &ts, float *ms)
+{
+    const bool needB = !(p->flags & LAPH_PLAN_SKIP_B), needM = !(p->flags & LAPH_PLAN_SKIP_M);
+    const bool fields = p->flags & LAPH_PLAN_FIELDS;
     void *ws = nullptr;
+    cudaError_t e;
+    int rc = LAPH_OK;
+    if ((e = ensure_side(p)) != cudaSuccess) return cuda_fail(e, "ensure_side");
+    if ((e = cudaMalloc(&ws, std::max<size_t>(p->ws_bytes, 256))) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if (fields) {
+        // one field buffer serves every field of an instance (timing and accuracy probe only)
+        const int nf = (p->flags & LAPH_PLAN_SKIP_M) ? 3 : 2;
+        std::vector<const void *> f;
+        std::vector<void *> o;
+        for (int n = 0; n < p->n_inst; n++) {
+            for (int k = 0; k < nf; k++) f.push_back(ts.phi[n]);
+            o.push_back(nf == 3 ? ts.ob[n] : ts.om[n]);
+        }
+        e = laph::launch_set_pointers(p->d_inst, 0, p->n_inst, nullptr, nf == 3 ? o.data() : nullptr,
+                                      nf == 3 ? nullptr : o.data(), ws, ts.st, f.data(), nf);
+    } else {
+        e = laph::launch_set_pointers(p->d_inst, 0, p->n_inst, ts.phi.data(), needB ? ts.ob.data() : nullptr,
+                                      needM ? ts.om.data() : nullptr, ws, ts.st);
+    }
+    if (e != cudaSuccess) rc = cuda_fail(e, "set_pointers");
+    if (rc == LAPH_OK) rc = launch_batch(p, ws, ts.st);
+    if (rc == LAPH_OK && (e = cudaEventRecord(ts.e0, ts.st)) != cudaSuccess) rc = cuda_fail(e, "event");
+    if (rc == LAPH_OK) rc = launch_batch(p, ws, ts.st);
+    if (rc == LAPH_OK && (e = cudaEventRecord(ts.e1, ts.st)) != cudaSuccess) rc = cuda_fail(e, "event");
+    if (rc == LAPH_OK && (e = cudaEventSynchronize(ts.e1)) != cudaSuccess) rc = cuda_fail(e, "event");
+    if (rc == LAPH_OK && (e = cudaEventElapsedTime(ms, ts.e0, ts.e1)) != cudaSuccess) rc = cuda_fail(e, "event");
+    cudaStreamSynchronize(ts.st);
+    cudaFree(ws);
+    return rc;
+}
+
+// Relative Frobenius error of (instance 0, timeslice 0) of the last timed
+// execute against the FP32 path (the larger of the B and M errors).
+static int tune_probe(laph_plan *p, TuneState &ts, double *err)
+{
+    cudaError_t e;
+    const bool needB = !(p->flags & LAPH_PLAN_SKIP_B), needM = !(p->flags & LAPH_PLAN_SKIP_M);
+    const InstDev &d = p->h_inst[0];
+    if (!ts.ref) {
+        laph_instance one{d.L, 1, d.N, d.P, p->momenta0.data(), 0};
+        laph_plan_options o{};
+        int rc = laph_plan_create_opts(&one, 1, LAPH_MODE_FP32_SIMT, p->flags & (LAPH_PLAN_SKIP_B | LAPH_PLAN_SKIP_M),
+                                       &o, &ts.ref);
+        if (rc != LAPH_OK) return rc;
+        if (needB && (e = cudaMalloc(&ts.refB, std::max<long long>(d.n_outB, 1) * sizeof(double2))) != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc");
+        if (needM && (e = cudaMalloc(&ts.refM, std::max<long long>(d.n_outM, 1) * sizeof(double2))) != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc");
+        if ((e = cudaMalloc((void **)&ts.acc, 4 * sizeof(double))) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+        const void *ph[1] = {ts.phi[0]};
+        void *rb[1] = {ts.refB}, *rm[1] = {ts.refM};
+        rc = laph_plan_execute(ts.ref, ph, needB ? rb : nullptr, needM ? rm : nullptr, nullptr, ts.st);
+        if (rc != LAPH_OK) return rc;
+    }
+    if ((e = cudaMemsetAsync(ts.acc, 0, 4 * sizeof(double), ts.st)) != cudaSuccess) return cuda_fail(e, "memset");
+    if (needB && (e = laph::launch_diff_norms((const double2 *)ts.ob[0], (const double2 *)ts.refB, d.n_outB, ts.acc,
+                                              ts.st)) != cudaSuccess)
+        return cuda_fail(e, "diff_norms");
+    if (needM && (e = laph::launch_diff_norms((const double2 *)ts.om[0], (const double2 *)ts.refM, d.n_outM,
+                                              ts.acc + 2, ts.st)) != cudaSuccess)
+        return cuda_fail(e, "diff_norms");
+    double h[4] = {0, 0, 0, 0};
+    if ((e = cudaMemcpyAsync(h, ts.acc, sizeof(h), cudaMemcpyDeviceToHost, ts.st)) != cudaSuccess)
+        return cuda_fail(e, "memcpy");
+    if ((e = cudaStreamSynchronize(ts.st)) != cudaSuccess) return cuda_fail(e, "sync");
+    const double eb = h[1] > 0 ? std::sqrt(h[0] / h[1]) : 0.0, em = h[3] > 0 ? std::sqrt(h[2] / h[3]) : 0.0;
+    *err = std::max(eb, em);
+    return LAPH_OK;
+}
+
+static int autotune(laph_plan *p, const laph::Sched &def, const std::function<cudaError_t(const laph::Sched &)> &apply)
+{
+    const bool needB = !(p->flags & LAPH_PLAN_SKIP_B), needM = !(p->flags & LAPH_PLAN_SKIP_M);
+    const bool fields = p->flags & LAPH_PLAN_FIELDS;
+    TuneState ts;
     int rc = LAPH_OK;
     cudaError_t e = cudaSuccess;
+    size_t best = 0;
+    p->tune_cand.clear();
+    p->tune_pc.clear();
+    p->tune_ms.clear();
+    p->tune_err.clear();
+    auto run = [&](const laph::Sched &c, bool probe) -> int {
+        cudaError_t er = apply(c);
+        if (er != cudaSuccess) return cuda_fail(er, "autotune apply");
+        if (p->max_staged > laph::TC_MAX_STAGED) return LAPH_ERR_UNSUPPORTED;
+        float ms = 0.f;
+        int r = tune_time(p, ts, &ms);
+        if (r != LAPH_OK) return r;
+        double err = -1.0;
+        if (probe && (r = tune_probe(p, ts, &err)) != LAPH_OK) return r;
+        p->tune_cand.push_back(c);
+        p->tune_pc.push_back(p->sched_per_chunk);
+        p->tune_ms.push_back(ms);
+        p->tune_err.push_back(err);
+        return LAPH_OK;
+    };
 #define TCK(call)                            \
     do {                                     \
         if ((e = (call)) != cudaSuccess) {   \
@@ -869,50 +1017,79 @@ static int autotune_time(laph_plan *p, const std::vector<std::pair<long long, in
             goto done;                       \
         }                                    \
     } while (0)
-    TCK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-    TCK(cudaEventCreate(&e0));
-    TCK(cudaEventCreate(&e1));
+#define TRC(call)                            \
+    do {                                     \
+        if ((rc = (call)) != LAPH_OK) goto done; \
+    } while (0)
+    TCK(cudaStreamCreateWithFlags(&ts.st, cudaStreamNonBlocking));
+    TCK(cudaEventCreate(&ts.e0));
+    TCK(cudaEventCreate(&ts.e1));
+    ts.phi.assign(p->n_inst, nullptr);
+    ts.ob.assign(p->n_inst, nullptr);
+    ts.om.assign(p->n_inst, nullptr);
     for (int n = 0; n < p->n_inst; n++) {
-        TCK(cudaMalloc(&phi[n], p->phi_elems[n] * sizeof(float2)));
-        TCK(laph::launch_fill_pattern((float2 *)phi[n], p->phi_elems[n], 1000u + (unsigned)n, st));
-        if (needB) TCK(cudaMalloc(&ob[n], std::max<long long>(p->outB_elems[n], 1) * sizeof(double2)));
-        if (needM) TCK(cudaMalloc(&om[n], std::max<long long>(p->outM_elems[n], 1) * sizeof(double2)));
+        TCK(cudaMalloc(&ts.phi[n], p->phi_elems[n] * sizeof(float2)));
+        TCK(laph::launch_fill_pattern((float2 *)ts.phi[n], p->phi_elems[n], 1000u + (unsigned)n, ts.st));
+        if (needB) TCK(cudaMalloc(&ts.ob[n], std::max<long long>(p->outB_elems[n], 1) * sizeof(double2)));
+        if (needM) TCK(cudaMalloc(&ts.om[n], std::max<long long>(p->outM_elems[n], 1) * sizeof(double2)));
     }
-    p->tune_ms.clear();
-    for (size_t k = 0; k < cand.size(); k++) {
-        emit(cand[k].first, cand[k].second);
-        TCK(upload());
-        TCK(ensure_side(p));
-        TCK(cudaMalloc(&ws, std::max<size_t>(p->ws_bytes, 256)));
-        TCK(laph::launch_set_pointers(p->d_inst, 0, p->n_inst, phi.data(), needB ? ob.data() : nullptr,
-                                      needM ? om.data() : nullptr, ws, st));
-        if ((rc = launch_batch(p, ws, st)) != LAPH_OK) goto done;
-        TCK(cudaEventRecord(e0, st));
-        if ((rc = launch_batch(p, ws, st)) != LAPH_OK) goto done;
-        TCK(cudaEventRecord(e1, st));
-        TCK(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        TCK(cudaEventElapsedTime(&ms, e0, e1));
-        p->tune_ms.push_back(ms);
-        TCK(cudaFree(ws));
-        ws = nullptr;
+    {
+        // 1: tile width x tile order x chunking (the largest chunk only for one instance)
+        const bool one_inst = p->n_inst == 1 && !(p->flags & LAPH_PLAN_CHUNK_PER_TIMESLICE);
+        for (int nc : {def.tile_cols, def.tile_cols == 96 ? 64 : 96})
+            for (long long pc : {-1LL, -2LL})
+                for (int o = 0; o < 2; o++) {
+                    if (pc == -2 && !one_inst) continue;
+                    TRC(run(laph::Sched{nc, def.sum_sites, def.chunk_sites, pc, o}, false));
+                }
+        for (size_t k = 1; k < p->tune_ms.size(); k++)
+            if (p->tune_ms[k] < p->tune_ms[best]) best = k;
+        // 2: site-block size of the FP64 reduction
+        const laph::Sched b1 = p->tune_cand[best];
+        for (int sum : {def.sum_sites / 2, def.sum_sites * 2}) {
+            if (sum < 1024 || sum > (1 << 20)) continue;
+            laph::Sched c = b1;
+            c.sum_sites = sum;
+            TRC(run(c, false));
+            if (p->tune_ms.back() < p->tune_ms[best]) best = p->tune_ms.size() - 1;
+        }
+        // 3: drain interval, within the accuracy limit of the probe
+        if (!fields) {
+            const laph::Sched b2 = p->tune_cand[best];
+            TRC(run(b2, true));   // the accuracy of the default interval
+            const double err_def = p->tune_err.back();
+            const size_t def_k = p->tune_ms.size() - 1;
+            if (p->tune_ms[def_k] < p->tune_ms[best]) best = def_k;
+            for (int cs : {def.chunk_sites / 2, (def.chunk_sites * 3) / 2}) {
+                if (cs < 8) continue;
+                laph::Sched c = b2;
+                c.chunk_sites = cs;
+                TRC(run(c, true));
+                const double err = p->tune_err.back();
+                if ((err <= TUNE_ERR_LIMIT || err <= err_def) && p->tune_ms.back() < p->tune_ms[best])
+                    best = p->tune_ms.size() - 1;
+            }
+        }
     }
-    *best = 0;
-    for (size_t k = 1; k < cand.size(); k++)
-        if (p->tune_ms[k] < p->tune_ms[*best]) *best = k;
-    TCK(cudaMemsetAsync(p->d_status, 0, sizeof(int), st));
-    TCK(cudaStreamSynchronize(st));
+    TCK(apply(p->tune_cand[best]));
+    TCK(cudaMemsetAsync(p->d_status, 0, sizeof(int), ts.st));
+    TCK(cudaStreamSynchronize(ts.st));
 done:
 #undef TCK
-    cudaFree(ws);
-    for (int n = 0; n < p->n_inst; n++) {
-        cudaFree(phi[n]);
-        cudaFree(ob[n]);
-        cudaFree(om[n]);
+#undef TRC
+    if (ts.st) cudaStreamSynchronize(ts.st);
+    if (ts.ref) laph_plan_destroy(ts.ref);
+    cudaFree(ts.refB);
+    cudaFree(ts.refM);
+    cudaFree(ts.acc);
+    for (int n = 0; n < (int)ts.phi.size(); n++) {
+        cudaFree(ts.phi[n]);
+        cudaFree(ts.ob[n]);
+        cudaFree(ts.om[n]);
     }
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    if (st) cudaStreamDestroy(st);
+    if (ts.e0) cudaEventDestroy(ts.e0);
+    if (ts.e1) cudaEventDestroy(ts.e1);
+    if (ts.st) cudaStreamDestroy(ts.st);
     return rc;
 }
 
@@ -925,7 +1102,25 @@ int laph_plan_schedule(const laph_plan *plan, int64_t *timeslices_per_chunk, int
     if (n_chunks) *n_chunks = (int)plan->chunks.size();
     if (n_candidates) *n_candidates = (int)plan->tune_ms.size();
     if (candidate_ms)
-        for (size_t k = 0; k < plan->tune_ms.size(); k++) candidate_ms[k] = plan->tune_ms[k];
+        for (size_t k = 0; k < plan->tune_ms.size() && k < 8; k++) candidate_ms[k] = plan->tune_ms[k];
+    return LAPH_OK;
+}
+
+int laph_plan_tuning(const laph_plan *plan, int cap, laph_tune_record *rec, int *n_candidates)
+{
+    if (!plan || cap < 0 || (cap > 0 && !rec)) return LAPH_ERR_ARG;
+    const int n = (int)plan->tune_ms.size();
+    if (n_candidates) *n_candidates = n;
+    for (int k = 0; k < n && k < cap; k++) {
+        const laph::Sched &c = plan->tune_cand[k];
+        rec[k].tile_cols = c.tile_cols;
+        rec[k].sum_sites = c.sum_sites;
+        rec[k].chunk_sites = c.chunk_sites;
+        rec[k].tile_order = c.order;
+        rec[k].timeslices_per_chunk = plan->tune_pc[k];
+        rec[k].ms = plan->tune_ms[k];
+        rec[k].probe_err = plan->tune_err[k];
+    }
     return LAPH_OK;
 }
 

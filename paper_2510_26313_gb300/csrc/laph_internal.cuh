@@ -47,7 +47,7 @@ struct InstDev {
     int cols;                // N * P
     int ts_base;             // index of (this instance, t = 0) among all timeslices of the batch
     int nblk;                // site blocks: ceil(V / TC_BS)
-    int n_ct;                // column tiles of the tensor-core path: ceil(cols / TC_TC)
+    int n_ct;                // column tiles of the tensor-core path: ceil(cols / the plan's tile width)
     int n_st;                // K stages of the tensor-core path: one per site block (= nblk)
     int kind;                // INST_BLOCKS, INST_TRIPLETS or INST_DOUBLETS
     int n_fields;            // distinct input fields: 1, 3 (triplets) or 2 (doublets)
@@ -164,6 +164,8 @@ cudaError_t launch_scale_max(const InstDev *d_inst, int n_inst, const int *h_ts_
 cudaError_t launch_diquarks(const float2 *phi, int L, int T, int N, float2 *out, cudaStream_t s);
 // Seeded pseudo-random complex entries in [-1, 1) (inputs the library makes itself).
 cudaError_t launch_fill_pattern(float2 *out, long long n, unsigned seed, cudaStream_t s);
+// acc[0] += sum |a - b|^2, acc[1] += sum |b|^2 (FP64; acc zeroed by the caller).
+cudaError_t launch_diff_norms(const double2 *a, const double2 *b, long long n, double *acc, cudaStream_t s);
 cudaError_t launch_dense_fill(const double2 *packed, int T, int N, int P, double2 *dense, cudaStream_t s);
 // Site-blocked copies of phi_u (and, for triplets, phi_v).
 cudaError_t launch_blockify(const InstDev *d_inst, int inst, const InstDev &h, const unsigned *d_maxbits,
@@ -186,6 +188,7 @@ cudaError_t launch_simt(const InstDev *d_inst, const TileDev *d_tiles, long long
 // laph_tc.cu
 struct TcConfig {
     int elem;          // 0 = FP16 hi/lo, 1 = BF16 hi/lo
+    int ncols;         // tile width in complex columns: 96 or 64
     int terms;         // 3 (split) or 1 (plain)
     int chunk_sites;   // sites accumulated by the tensor core between FP32 drains
     int grid;          // persistent CTAs
@@ -193,14 +196,16 @@ struct TcConfig {
     int debug_stall;   // test hook
 };
 constexpr int TC_TR = 128;   // tile rows (UMMA M)
-constexpr int TC_TC = 96;    // tile columns (complex), UMMA N = 2 * TC_TC real
+constexpr int TC_TC = 96;    // default tile columns (complex), UMMA N = 2 * TC_TC real; 64 is the other width
 constexpr int TC_KSTAGE = 3 * TC_BS;  // complex K entries per stage: one site block
-constexpr int TC_STAGE_BYTES = 2 * (2 * TC_TC) * (2 * TC_KSTAGE) * 2;  // one B stage image: hi + lo, 192 rows x 48 FP16 each
+// One B stage image of a tile of nc complex columns: hi + lo, 2 nc real rows x 48 FP16 each.
+constexpr int tc_stage_bytes(int nc) { return 2 * (2 * nc) * (2 * TC_KSTAGE) * 2; }
+constexpr int TC_STAGE_BYTES = tc_stage_bytes(TC_TC);
 constexpr int TC_MAX_STAGED = 160;  // staged row vectors per tile
 constexpr int TC_PSI_GROUP = 16;    // stages per job of the B-operand pass
 // Psi stage images of a chunk: jobs [0, n_jobs) over the units [0, n_units).
 cudaError_t launch_psi(const InstDev *d_inst, const PsiUnit *d_units, int n_units, long long n_jobs,
-                       const unsigned *d_maxbits, int elem, uint8_t *psi, cudaStream_t s);
+                       const unsigned *d_maxbits, int elem, int ncols, uint8_t *psi, cudaStream_t s);
 // counter: a zeroed word of device memory; persistent CTAs claim tiles with it.
 cudaError_t launch_tc(const InstDev *d_inst, const TileDev *d_tiles, long long n_tiles,
                       const unsigned *d_maxbits, const uint8_t *psi, float2 *part, unsigned *counter,

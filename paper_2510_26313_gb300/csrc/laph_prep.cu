@@ -122,6 +122,50 @@ cudaError_t launch_fill_pattern(float2 *out, long long n, unsigned seed, cudaStr
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- difference norms
+// acc[0] += sum |a - b|^2, acc[1] += sum |b|^2 over n complex128 entries
+// (the autotuner's accuracy probe of a candidate schedule against the FP32
+// path; FP64 sums, one atomic pair per block).
+__global__ void diff_norms_kernel(const double2 *__restrict__ a, const double2 *__restrict__ b, long long n,
+                                  double *acc)
+{
+    __shared__ double sd[8], sb[8];
+    double d2 = 0.0, b2 = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double2 x = a[i], y = b[i];
+        const double dr = x.x - y.x, di = x.y - y.y;
+        d2 += dr * dr + di * di;
+        b2 += y.x * y.x + y.y * y.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+        b2 += __shfl_xor_sync(0xffffffffu, b2, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        sd[w] = d2;
+        sb[w] = b2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); k++) {
+            d2 += sd[k];
+            b2 += sb[k];
+        }
+        atomicAdd(acc, d2);
+        atomicAdd(acc + 1, b2);
+    }
+}
+
+cudaError_t launch_diff_norms(const double2 *a, const double2 *b, long long n, double *acc, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    diff_norms_kernel<<<(unsigned)blocks, 256, 0, s>>>(a, b, n, acc);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- scale
 // Largest |re|, |im| of phi per timeslice, as FP32 bits (non-negative floats
 // order like their bit patterns).  The tensor-core kernel turns it into an

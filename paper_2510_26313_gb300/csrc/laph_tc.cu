@@ -66,10 +66,6 @@ constexpr int WARP_LOAD = 20;
 constexpr int WARP_MMA = 21;
 constexpr int KSTAGE = TC_KSTAGE;                     // complex K entries per stage (one site block)
 constexpr int KSTEPS = 2 * KSTAGE / 16;               // MMA k-steps per stage
-constexpr int B_ROWS = 2 * TC_TC;                     // real B rows per tile (192)
-constexpr int ATOM_COL_BYTES = (B_ROWS / 8) * 256;    // one k-step of hi (or lo): 24 atoms of 8 rows x 32 B
-constexpr int B_BYTES = KSTEPS * ATOM_COL_BYTES;      // hi (or lo) of one stage
-constexpr int BIMG_BYTES = 2 * B_BYTES;               // hi + lo
 constexpr int SLOT_BYTES = TC_SLOT * 8;               // 208 B = 52 words: LDS.128 of 8 consecutive slots hit distinct banks
 constexpr int HALF_BYTES = (TC_BS / 2) * 3 * 8;       // 4 sites x 3 colours: one A warp's share of a slot
 constexpr int MAX_NS = 6;
@@ -77,17 +73,28 @@ constexpr int TRING = 4;                              // tile ring entries
 constexpr int N_TILE_READERS = N_AWARPS + 4 + 1;     // A producers, epilogue, MMA
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t ACC_COL = 0;
-constexpr uint32_t SUM_COL = 192;
 constexpr uint32_t A_COL = 384;
 constexpr uint32_t A_SLOT_COLS = 64;
 constexpr uint32_t A_LO = KSTAGE;                     // lo columns follow the 24 hi columns
 constexpr long long WAIT_LIMIT = 4000000000LL;        // cycles (about 2 s at the top clock)
 
-static_assert(TC_TR == 128 && TC_TC == 96, "layout assumes 128 x 96 tiles");
+static_assert(TC_TR == 128, "layout assumes 128-row tiles (UMMA M = 128, one tensor-memory lane per row)");
 static_assert(TC_BS == 8 && KSTAGE == 24 && KSTEPS == 3, "a stage is one 8-site block");
-static_assert(BIMG_BYTES == TC_STAGE_BYTES, "stage image size");
-static_assert(A_LO + KSTAGE <= A_SLOT_COLS && SUM_COL + 192 <= A_COL && A_COL + 2 * A_SLOT_COLS == TMEM_COLS,
-              "tensor memory budget");
+static_assert(A_LO + KSTAGE <= A_SLOT_COLS && A_COL + 2 * A_SLOT_COLS == TMEM_COLS, "tensor memory budget");
+
+// Sizes that follow from the tile width NC (complex columns; UMMA N = 2 NC
+// real B rows).  Tensor memory: the accumulator in columns [0, 2 NC), the
+// FP32 running sums in [2 NC, 4 NC), the two A slots from column 384.
+template <int NC>
+struct Shape {
+    static constexpr int B_ROWS = 2 * NC;                  // real B rows per tile
+    static constexpr int ATOM_COL_BYTES = (B_ROWS / 8) * 256;   // one k-step of hi (or lo): atoms of 8 rows x 32 B
+    static constexpr int B_BYTES = KSTEPS * ATOM_COL_BYTES;     // hi (or lo) of one stage
+    static constexpr int BIMG_BYTES = 2 * B_BYTES;              // hi + lo
+    static constexpr uint32_t SUM_COL = 2 * NC;
+    static_assert(NC % 16 == 0 && NC <= 96 && 4 * NC <= (int)A_COL, "tile width within the tensor-memory budget");
+    static_assert(BIMG_BYTES == tc_stage_bytes(NC), "stage image size");
+};
 
 struct Shared {
     // full: data of stage k landed, barrier k mod 2 NS (every barrier serves
@@ -426,9 +433,12 @@ struct KParams {
     int debug_stall;
 };
 
-template <int ELEM, int TERMS>
+template <int ELEM, int TERMS, int NC>
 __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
 {
+    using SH = Shape<NC>;
+    constexpr int BIMG_BYTES = SH::BIMG_BYTES, B_BYTES = SH::B_BYTES, ATOM_COL_BYTES = SH::ATOM_COL_BYTES;
+    constexpr uint32_t SUM_COL = SH::SUM_COL;
     extern __shared__ uint8_t smem_raw[];
     // align to 1024 bytes by offsetting the __shared__ array itself, so that
     // the compiler keeps every derived pointer in the shared address space
@@ -816,11 +826,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
 // image, in the K-major 32-byte-swizzled layout the contraction's
 // descriptors expect.  Every store instruction of a warp writes sixteen
 // whole 32-byte rows.
-template <int ELEM>
-__global__ void __launch_bounds__(192) psi_kernel(const InstDev *__restrict__ insts, const PsiUnit *__restrict__ units,
-                                                  int n_units, long long n_jobs, const unsigned *__restrict__ maxbits,
-                                                  uint8_t *__restrict__ psi)
+template <int ELEM, int NC>
+__global__ void __launch_bounds__(2 * NC) psi_kernel(const InstDev *__restrict__ insts, const PsiUnit *__restrict__ units,
+                                                     int n_units, long long n_jobs, const unsigned *__restrict__ maxbits,
+                                                     uint8_t *__restrict__ psi)
 {
+    using SH = Shape<NC>;
+    constexpr int BIMG_BYTES = SH::BIMG_BYTES, B_BYTES = SH::B_BYTES, ATOM_COL_BYTES = SH::ATOM_COL_BYTES;
     const int cu = threadIdx.x >> 1, j = threadIdx.x & 1;
     for (long long job = blockIdx.x; job < n_jobs; job += gridDim.x) {
         int lo = 0, hi = n_units - 1;
@@ -839,8 +851,8 @@ __global__ void __launch_bounds__(192) psi_kernel(const InstDev *__restrict__ in
         const int ct = jl / n_grp;
         const int st0 = (jl - ct * n_grp) * TC_PSI_GROUP;
         const int st1 = min(st0 + TC_PSI_GROUP, n_st);
-        const int col0 = ct * TC_TC;
-        const bool valid = cu < min(TC_TC, I.cols - col0);
+        const int col0 = ct * NC;
+        const bool valid = cu < min(NC, I.cols - col0);
         const int V = (int)I.V;
         const float sc = pow2f(scale_exp(maxbits[I.ts_base + un.t]));
         int k = 0, p = 0;
@@ -887,7 +899,6 @@ __global__ void __launch_bounds__(192) psi_kernel(const InstDev *__restrict__ in
         }
     }
 }
-static_assert(2 * TC_TC == 192, "psi_kernel maps 96 columns x 2 chunks onto 192 threads");
 
 // ------------------------------------------------------------ FP64 site reduction
 
@@ -988,9 +999,9 @@ __global__ void __launch_bounds__(RED_THREADS) reduce_kernel(const InstDev *__re
     }
 }
 
-int stage_bytes_for(int max_staged)
+int stage_bytes_for(int max_staged, int nc)
 {
-    const int b = BIMG_BYTES + max_staged * SLOT_BYTES;
+    const int b = tc_stage_bytes(nc) + max_staged * SLOT_BYTES;
     return (b + 1023) & ~1023;
 }
 
@@ -998,7 +1009,7 @@ constexpr int SMEM_LIMIT = 227 * 1024;
 
 int smem_for(int ns, int stage_bytes) { return ns * stage_bytes + (int)sizeof(Shared) + 1024; }
 
-template <int ELEM, int TERMS>
+template <int ELEM, int TERMS, int NC>
 cudaError_t launch_one(const InstDev *d_inst, const TileDev *d_tiles, long long n_tiles, const unsigned *maxbits,
                        const uint8_t *psi, float2 *part, unsigned *counter, const TcConfig &cfg, int *status,
                        cudaStream_t s)
@@ -1014,7 +1025,7 @@ cudaError_t launch_one(const InstDev *d_inst, const TileDev *d_tiles, long long 
     kp.n_tiles = (int)n_tiles;
     kp.chunk_stages = (cfg.chunk_sites * 3) / KSTAGE;
     if (kp.chunk_stages < 1) kp.chunk_stages = 1;
-    kp.stage_bytes = stage_bytes_for(cfg.max_staged);
+    kp.stage_bytes = stage_bytes_for(cfg.max_staged, NC);
     kp.debug_stall = cfg.debug_stall;
     // deepest stage ring that fits
     kp.ns = 0;
@@ -1026,17 +1037,17 @@ cudaError_t launch_one(const InstDev *d_inst, const TileDev *d_tiles, long long 
     }
     if (!kp.ns) return cudaErrorNotSupported;
     const int smem = smem_for(kp.ns, kp.stage_bytes);
-    cudaError_t e = cudaFuncSetAttribute(tc_kernel<ELEM, TERMS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(tc_kernel<ELEM, TERMS, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int grid = cfg.grid > 0 ? cfg.grid : 148;
     if ((long long)grid > n_tiles) grid = (int)n_tiles;
-    tc_kernel<ELEM, TERMS><<<grid, NTHREADS, smem, s>>>(kp);
+    tc_kernel<ELEM, TERMS, NC><<<grid, NTHREADS, smem, s>>>(kp);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-int tc_smem_bytes() { return smem_for(2, stage_bytes_for(TC_MAX_STAGED)); }
+int tc_smem_bytes() { return smem_for(2, stage_bytes_for(TC_MAX_STAGED, TC_TC)); }
 
 cudaError_t launch_tc(const InstDev *d_inst, const TileDev *d_tiles, long long n_tiles, const unsigned *d_maxbits,
                       const uint8_t *psi, float2 *part, unsigned *counter, const TcConfig &cfg, int *d_status,
@@ -1044,14 +1055,18 @@ cudaError_t launch_tc(const InstDev *d_inst, const TileDev *d_tiles, long long n
 {
     if (n_tiles <= 0) return cudaSuccess;
     if (n_tiles > 0x7fffffffLL || cfg.max_staged > TC_MAX_STAGED) return cudaErrorNotSupported;
-    if (cfg.elem == 0 && cfg.terms == 3)
-        return launch_one<0, 3>(d_inst, d_tiles, n_tiles, d_maxbits, psi, part, counter, cfg, d_status, s);
-    if (cfg.elem == 1 && cfg.terms == 3)
-        return launch_one<1, 3>(d_inst, d_tiles, n_tiles, d_maxbits, psi, part, counter, cfg, d_status, s);
-    if (cfg.elem == 0 && cfg.terms == 1)
-        return launch_one<0, 1>(d_inst, d_tiles, n_tiles, d_maxbits, psi, part, counter, cfg, d_status, s);
-    if (cfg.elem == 1 && cfg.terms == 1)
-        return launch_one<1, 1>(d_inst, d_tiles, n_tiles, d_maxbits, psi, part, counter, cfg, d_status, s);
+#define LAPH_TC_CASE(E, TM, NC)                                                                      \
+    if (cfg.elem == E && cfg.terms == TM && cfg.ncols == NC)                                         \
+        return launch_one<E, TM, NC>(d_inst, d_tiles, n_tiles, d_maxbits, psi, part, counter, cfg, d_status, s);
+    LAPH_TC_CASE(0, 3, 96)
+    LAPH_TC_CASE(1, 3, 96)
+    LAPH_TC_CASE(0, 1, 96)
+    LAPH_TC_CASE(1, 1, 96)
+    LAPH_TC_CASE(0, 3, 64)
+    LAPH_TC_CASE(1, 3, 64)
+    LAPH_TC_CASE(0, 1, 64)
+    LAPH_TC_CASE(1, 1, 64)
+#undef LAPH_TC_CASE
     return cudaErrorNotSupported;
 }
 
@@ -1065,14 +1080,20 @@ cudaError_t launch_reduce(const InstDev *d_inst, const PsiUnit *d_units, int n_u
 }
 
 cudaError_t launch_psi(const InstDev *d_inst, const PsiUnit *d_units, int n_units, long long n_jobs,
-                       const unsigned *d_maxbits, int elem, uint8_t *psi, cudaStream_t s)
+                       const unsigned *d_maxbits, int elem, int ncols, uint8_t *psi, cudaStream_t s)
 {
     if (n_jobs <= 0 || n_units <= 0) return cudaSuccess;
-    const long long grid = n_jobs < (1LL << 20) ? n_jobs : (1LL << 20);
-    if (elem == 0)
-        psi_kernel<0><<<(unsigned)grid, 192, 0, s>>>(d_inst, d_units, n_units, n_jobs, d_maxbits, psi);
+    const unsigned grid = (unsigned)(n_jobs < (1LL << 20) ? n_jobs : (1LL << 20));
+    if (ncols == 96 && elem == 0)
+        psi_kernel<0, 96><<<grid, 192, 0, s>>>(d_inst, d_units, n_units, n_jobs, d_maxbits, psi);
+    else if (ncols == 96 && elem == 1)
+        psi_kernel<1, 96><<<grid, 192, 0, s>>>(d_inst, d_units, n_units, n_jobs, d_maxbits, psi);
+    else if (ncols == 64 && elem == 0)
+        psi_kernel<0, 64><<<grid, 128, 0, s>>>(d_inst, d_units, n_units, n_jobs, d_maxbits, psi);
+    else if (ncols == 64 && elem == 1)
+        psi_kernel<1, 64><<<grid, 128, 0, s>>>(d_inst, d_units, n_units, n_jobs, d_maxbits, psi);
     else
-        psi_kernel<1><<<(unsigned)grid, 192, 0, s>>>(d_inst, d_units, n_units, n_jobs, d_maxbits, psi);
+        return cudaErrorNotSupported;
     return cudaGetLastError();
 }
 

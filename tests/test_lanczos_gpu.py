@@ -168,6 +168,22 @@ def test_lanczos_at_size_properties(laph, L, n_ev, m, d, lo):
             assert abs(np.vdot(v[t, r], Av[r]).real - ev[t, r]) <= 2e-5
 
 
+def test_lanczos_benchmark_shape_matches_the_oracle_lanczos(laph):
+    """L = 32, 64 eigenpairs, m = 128 Krylov steps on the degree-48 Chebyshev filter with lo = 0.95 (the benchmark's
+    parameters), smoothed links: the eigenvalues of the GPU solver against the oracle's FP64 Lanczos with the same
+    parameters on the same links, at 5e-5 (no dense oracle exists at this size)."""
+    import torch
+    L, n_ev, m, d, lo = 32, 64, 128, 48, 0.95
+    U = synth.random_links(L, 1, instance=132, eps=0.6)
+    _, ev, res = laph.lanczos(torch.from_numpy(U).cuda(), L, n_ev, m, cheb_degree=d, cheb_lo=lo)
+    lam, rcpu = O.lanczos_eigenpairs(U[0], L, n_ev, m, d, lo)
+    err = np.abs(ev[0] - lam).max()
+    print(f"L=32 benchmark shape: max |GPU - oracle Lanczos| {err:.2e}; residuals GPU {res.max():.2e}, "
+          f"oracle {rcpu.max():.2e}")
+    assert rcpu.max() <= 1e-8
+    assert err <= 5e-5
+
+
 def test_lanczos_links_outside_su3_use_all_three_rows(laph):
     """SU(3) links are read as two rows (the third rebuilt from them); links e^{0.3 i} U are unitary with a
     determinant other than 1, so the rebuilt row is wrong for them: the solver detects it, reads all three rows,

@@ -1,10 +1,10 @@
-"""CPU model of the eigensolver's algorithm (no GPU): Lanczos with two classical Gram-Schmidt passes per step, on -Delta
-or on the Chebyshev filter T_d((-Delta - c) / e) that maps [lo, 12] onto [-1, 1], Ritz pairs of the tridiagonal
-matrix at the wanted end (smallest for -Delta; for the filter the largest when d is even and the most negative when d
-is odd), eigenvalues as Rayleigh quotients with -Delta.  Plain FP64 numpy on the oracle's dense Laplacian, checked
-against numpy's dense Hermitian eigensolver: it pins the conventions the CUDA solver follows (paper, section
+"""The oracle's FP64 Lanczos (oracle.lanczos_eigenpairs, no GPU): Lanczos with two classical Gram-Schmidt passes per
+step, on -Delta or on the Chebyshev filter T_d((-Delta - c) / e) that maps [lo, 12] onto [-1, 1], Ritz pairs of the
+tridiagonal matrix at the wanted end (smallest for -Delta; for the filter the largest when d is even and the most
+negative when d is odd), eigenvalues as Rayleigh quotients with -Delta.  Pinned against numpy's dense Hermitian
+eigensolver on the oracle's dense Laplacian: it fixes the conventions the CUDA solver follows (paper, section
 "Innovations", subsection "Scalable Lanczos Eigensolver", which names a batched Lanczos eigensolver and leaves these
-choices open).
+choices open).  The negative controls apply the wrong conventions to the same problem.
 """
 import numpy as np
 import pytest
@@ -22,49 +22,22 @@ def chebyshev(A, v, d, lo):
     return y1
 
 
-def lanczos_model(A, n_ev, m, d=0, lo=0.0, seed=0):
-    n = A.shape[0]
-    rng = np.random.default_rng(seed)
-    Q = np.zeros((m + 1, n), dtype=np.complex128)
-    v = rng.standard_normal(n) + 1j * rng.standard_normal(n)
-    Q[0] = v / np.linalg.norm(v)
-    alpha, beta = np.zeros(m), np.zeros(m)
-    for j in range(m):
-        w = A @ Q[j] if d == 0 else chebyshev(A, Q[j], d, lo)
-        c1 = Q[: j + 1].conj() @ w
-        w = w - Q[: j + 1].T @ c1
-        w = w - Q[: j + 1].T @ (Q[: j + 1].conj() @ w)
-        alpha[j], beta[j] = c1[j].real, np.linalg.norm(w)
-        Q[j + 1] = w / beta[j]
-    Tm = np.diag(alpha) + np.diag(beta[:-1], 1) + np.diag(beta[:-1], -1)
-    theta, S = np.linalg.eigh(Tm)
-    if d == 0:
-        pick = np.arange(n_ev)
-    elif d % 2 == 0:
-        pick = np.arange(m - 1, m - 1 - n_ev, -1)
-    else:
-        pick = np.arange(n_ev)
-    X = S[:, pick].T @ Q[:m]
-    lam = np.einsum("ij,ij->i", X.conj(), X @ A.T).real / np.einsum("ij,ij->i", X.conj(), X).real
-    res = np.linalg.norm(X @ A.T - lam[:, None] * X, axis=1) / np.linalg.norm(X, axis=1)
-    order = np.argsort(lam)
-    return lam[order], res[order]
+L6 = 6
 
 
 @pytest.fixture(scope="module")
 def problem():
-    L = 6
-    U = synth.random_links(L, 1, instance=66, eps=0.6)[0]
-    A = O.laplacian_matrix(U, L)
-    return A, np.linalg.eigvalsh(A)
+    U = synth.random_links(L6, 1, instance=66, eps=0.6)[0]
+    A = O.laplacian_matrix(U, L6)
+    return A, np.linalg.eigvalsh(A), U
 
 
 @pytest.mark.parametrize("d,m", [(0, 300), (7, 60), (8, 60)])
-def test_model_finds_the_lowest_eigenpairs(problem, d, m):
-    A, w = problem
+def test_oracle_lanczos_finds_the_lowest_eigenpairs(problem, d, m):
+    A, w, U = problem
     n_ev = 20
     lo = 0.5 * (w[n_ev + 2] + w[n_ev + 3])          # a bound in the gap above the wanted eigenvalues
-    lam, res = lanczos_model(A, n_ev, m, d, lo)
+    lam, res = O.lanczos_eigenpairs(U, L6, n_ev, m, d, lo)
     np.testing.assert_allclose(lam, w[:n_ev], atol=1e-9)
     assert res.max() < 1e-6
 
@@ -72,7 +45,7 @@ def test_model_finds_the_lowest_eigenpairs(problem, d, m):
 def test_model_with_the_wrong_sign_convention_misses_them(problem):
     """For an odd degree the filter is large and negative below lo: taking the largest Ritz values, as for an even
     degree, returns pairs from the damped part of the spectrum."""
-    A, w = problem
+    A, w, _ = problem
     n_ev, d, m = 20, 7, 60
     lo = 0.5 * (w[n_ev + 2] + w[n_ev + 3])
     n = A.shape[0]
@@ -98,8 +71,8 @@ def test_model_with_the_wrong_sign_convention_misses_them(problem):
 def test_model_with_the_bound_below_the_wanted_eigenvalues_does_not_converge(problem):
     """lo must lie above the wanted eigenvalues: with lo below the 20th eigenvalue, the pairs between lo and the
     20th eigenvalue are damped like the rest of the spectrum and are not resolved."""
-    A, w = problem
+    _, w, U = problem
     n_ev, d, m = 20, 8, 60
     lo = 0.5 * (w[9] + w[10])
-    lam, res = lanczos_model(A, n_ev, m, d, lo)
+    lam, res = O.lanczos_eigenpairs(U, L6, n_ev, m, d, lo)
     assert res.max() > 1e-3 or np.abs(lam - w[:n_ev]).max() > 1e-3

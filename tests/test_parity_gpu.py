@@ -317,9 +317,43 @@ def test_large_streamed_shape_sampled_parity(laph):
     plan.close()
 
 
+@pytest.mark.parametrize("mode", ["f16x3", "bf16x3", "f16"])
+def test_64_column_tiles_match_oracle(laph, mode):
+    """Tiles of 64 complex columns (UMMA N = 128): single instances with ragged column tails and several site
+    blocks, and a ragged batch in one plan."""
+    import torch
+    for L, T, N, mom, inst in [CASES[2], CASES[4], CASES[5]]:
+        phi_h = synth.random_phi(L, N, T=T, instance=inst)
+        plan = laph.Plan([(L, T, N, mom)], mode=mode, tile_cols=64)
+        assert plan.describe()["tile_cols"] == 64
+        Bs, Ms = plan.alloc_outputs()
+        ws = plan.alloc_workspace()
+        plan.execute([torch.from_numpy(phi_h).cuda()], Bs, Ms, ws)
+        torch.cuda.synchronize()
+        assert plan.device_status() == laph.LAPH_OK
+        rB, rM = _oracle(phi_h, L, mom)
+        eB, eM = rel_frob(Bs[0].cpu().numpy(), rB), rel_frob(Ms[0].cpu().numpy(), rM)
+        print(f"64 columns mode={mode} L={L} N={N}: rel B {eB:.2e} M {eM:.2e}")
+        assert eB <= tol_for(mode) and eM <= tol_for(mode)
+        plan.close()
+    specs = [(4, 2, 5, synth.momentum_shell(1)), (5, 3, 8, synth.momentum_shell(2)),
+             (3, 1, 20, np.array([[1, 1, 1], [0, 0, 0]], dtype=np.int32))]
+    plan = laph.Plan(specs, mode=mode, tile_cols=64)
+    phis_h = [synth.random_phi(L, N, T=T, instance=140 + n) for n, (L, T, N, _) in enumerate(specs)]
+    Bs, Ms = plan.alloc_outputs()
+    plan.execute([torch.from_numpy(p).cuda() for p in phis_h], Bs, Ms, plan.alloc_workspace())
+    torch.cuda.synchronize()
+    for n, (L, T, N, mom) in enumerate(specs):
+        rB, rM = _oracle(phis_h[n], L, mom)
+        assert rel_frob(Bs[n].cpu().numpy(), rB) <= tol_for(mode)
+        assert rel_frob(Ms[n].cpu().numpy(), rM) <= tol_for(mode)
+    plan.close()
+
+
 def test_autotuned_plan_matches_oracle(laph):
-    """PLAN_AUTOTUNE times the candidate schedules at creation and keeps the fastest; the
-    chosen schedule gives the same blocks."""
+    """PLAN_AUTOTUNE times candidate schedules at creation -- tile widths, tile orders, chunkings, site-block sizes
+    and drain intervals, the last checked by the accuracy probe -- and keeps the fastest; the chosen schedule gives
+    the same blocks."""
     import torch
     L, T, N = 6, 3, 20
     mom = synth.momentum_shell(1)
@@ -327,6 +361,16 @@ def test_autotuned_plan_matches_oracle(laph):
     sch = plan.schedule()
     assert len(sch["candidate_ms"]) >= 2 and all(ms > 0 for ms in sch["candidate_ms"])
     assert sch["tile_order"] in (0, 1) and sch["n_chunks"] == plan.contraction_launches()
+    rec = plan.tuning()
+    assert len(rec) >= 10 and {r["tile_cols"] for r in rec} == {64, 96}
+    assert len({r["sum_sites"] for r in rec}) >= 2 and len({r["chunk_sites"] for r in rec}) >= 2
+    probed = [r for r in rec if r["probe_err"] >= 0]
+    assert len(probed) >= 2 and all(r["probe_err"] < 1e-4 for r in probed)
+    desc = plan.describe()
+    assert any(r["tile_cols"] == desc["tile_cols"] and r["chunk_sites"] == desc["chunk_sites"] and
+               r["sum_sites"] == plan.sum_sites()[0] for r in rec)
+    print("autotune:", [(r["tile_cols"], r["tile_order"], r["sum_sites"], r["chunk_sites"], round(r["ms"], 3),
+                         r["probe_err"]) for r in rec], "chosen", desc)
     phi_h = synth.random_phi(L, N, T=T, instance=95)
     Bs, Ms = plan.alloc_outputs()
     ws = plan.alloc_workspace()
