@@ -123,6 +123,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def schedule_of(plan, tuned: bool) -> dict:
+    """The tensor-core schedule a plan runs (and, when autotuned, every candidate it timed)."""
+    d = plan.describe()
+    sch = plan.schedule()
+    out = {"layout": 1 if d["tile_rows"] == 64 else 0, "tile_cols": d["tile_cols"], "tile_rows": d["tile_rows"],
+           "chunk_sites": d["chunk_sites"], "sum_sites": plan.sum_sites()[0],
+           "timeslices_per_chunk": sch["timeslices_per_chunk"], "tile_order": sch["tile_order"], "autotuned": tuned}
+    if tuned:
+        out["candidates"] = [[r["layout"], r["tile_cols"], r["tile_order"], r["timeslices_per_chunk"], r["sum_sites"],
+                              r["chunk_sites"], round(r["ms"], 3), r["probe_err"]] for r in plan.tuning()]
+        out["candidate_fields"] = ["layout", "tile_cols", "tile_order", "timeslices_per_chunk", "sum_sites",
+                                   "chunk_sites", "ms", "probe_err"]
+    return out
+
+
 def pinned_copy_rates(nbytes: int = 1 << 30):
     """This box's pinned host <-> device copy rates (GB/s) on one buffer of nbytes, timed with CUDA events; they
     vary a lot between boxes and bound the end-to-end figure."""
@@ -230,7 +245,7 @@ def triplet_flops_per_timeslice(L, N, P):
     return 8.0 * 3 * L ** 3 * N ** 3 * P
 
 
-def measure_triplets(laph, L, T, N, mom, mode, steps, warmup, n_sample=0, timed_oracle=False):
+def measure_triplets(laph, L, T, N, mom, mode, steps, warmup, n_sample=0, timed_oracle=False, tune=False):
     """Three-field triplets B3 (dense) through a LAPH_PLAN_FIELDS plan: device time per step, contraction
     kernel time, and (n_sample > 0) the relative error of sampled (i, j, k) of timeslice 0 against the
     oracle, with the oracle's own rate when timed_oracle."""
@@ -243,7 +258,9 @@ def measure_triplets(laph, L, T, N, mom, mode, steps, warmup, n_sample=0, timed_
     for _ in range(3):
         z = torch.randn((T, N, V, 3, 2), generator=gen, device="cuda", dtype=torch.float32)
         fields.append(torch.view_as_complex(z).contiguous() / math.sqrt(3 * V))
-    plan = laph.Plan([(L, T, N, mom)], mode=mode, flags=laph.PLAN_FIELDS | laph.PLAN_SKIP_M | laph.PLAN_TIMING)
+    plan = laph.Plan([(L, T, N, mom)], mode=mode,
+                     flags=laph.PLAN_FIELDS | laph.PLAN_SKIP_M | laph.PLAN_TIMING | (laph.PLAN_AUTOTUNE if tune else 0))
+    sched = schedule_of(plan, tune)
     Bs, _ = plan.alloc_outputs()
     ws = plan.alloc_workspace()
     stream = torch.cuda.current_stream()
@@ -265,7 +282,7 @@ def measure_triplets(laph, L, T, N, mom, mode, steps, warmup, n_sample=0, timed_
     flops = T * triplet_flops_per_timeslice(L, N, P)
     out = {"ms_per_step": ms, "kernel_ms": k_ms, "operand_ms": o_ms, "flops_per_step": flops,
            "value": flops / (ms / 1e3) / 1e12, "kernel_tflops": flops / (k_ms / 1e3) / 1e12,
-           "launches": plan.launches_per_execute() * steps, "device_status": status}
+           "launches": plan.launches_per_execute() * steps, "device_status": status, "schedule": sched}
     if n_sample:
         from oracle import oracle as O
         rng = np.random.default_rng(5)
@@ -290,7 +307,7 @@ def measure_triplets(laph, L, T, N, mom, mode, steps, warmup, n_sample=0, timed_
 LARGE = dict(L=48, T=96, N=128, n2=4)   # 33 momenta: |n|^2 <= 4
 
 
-def measure_large(laph, L, T, N, mom, mode, steps, warmup, n_sample=0, timed_oracle=False):
+def measure_large(laph, L, T, N, mom, mode, steps, warmup, n_sample=0, timed_oracle=False, tune=False):
     """The large streamed form: T timeslices of N complex64 vectors on L^3 sites flow through HBM one at a time.  The
     vectors of timeslice t+1 are drawn on the device (torch's generator, seeded per timeslice, entries complex
     Gaussian / sqrt(3V)) on a side stream into the other half of a double buffer while timeslice t is contracted by a
@@ -300,7 +317,8 @@ def measure_large(laph, L, T, N, mom, mode, steps, warmup, n_sample=0, timed_ora
     import torch
     P = mom.shape[0]
     V = L ** 3
-    plan = laph.Plan([(L, 1, N, mom)], mode=mode, flags=laph.PLAN_TIMING)
+    plan = laph.Plan([(L, 1, N, mom)], mode=mode, flags=laph.PLAN_TIMING | (laph.PLAN_AUTOTUNE if tune else 0))
+    sched = schedule_of(plan, tune)
     ws = plan.alloc_workspace()
     B = torch.empty((T, P, math.comb(N, 3)), dtype=torch.complex128, device="cuda")
     M = torch.empty((T, P, N, N), dtype=torch.complex128, device="cuda")
@@ -352,7 +370,7 @@ def measure_large(laph, L, T, N, mom, mode, steps, warmup, n_sample=0, timed_ora
     flops = T * flops_per_timeslice(L, N, P)
     out = {"ms_per_step": ms, "kernel_ms": k_ms, "flops_per_step": flops, "value": flops / (ms / 1e3) / 1e12,
            "kernel_tflops": flops / (k_ms / 1e3) / 1e12, "device_status": plan.device_status(),
-           "launches": plan.launches_per_execute() * T * steps, "sum_sites": plan.sum_sites()}
+           "launches": plan.launches_per_execute() * T * steps, "schedule": sched}
     if n_sample:
         from oracle import oracle as O
         rng = np.random.default_rng(12)
@@ -394,7 +412,8 @@ def run_large(args):
     clocks = ClockSampler(0)
     clocks.start()
     r = measure_large(laph, L, T, N, mom, args.mode, args.steps, args.warmup,
-                      n_sample=0 if args.no_cpu_baseline else 200, timed_oracle=not args.no_cpu_baseline)
+                      n_sample=0 if args.no_cpu_baseline else 200, timed_oracle=not args.no_cpu_baseline,
+                      tune=not args.no_autotune)
     clk = clocks.stop()
     peaks, src = measured_peaks()
     peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
@@ -410,7 +429,7 @@ def run_large(args):
                      "frac": r["kernel_tflops"] / peak, "traffic": None, "peak_source": src},
         "cpu_baseline": r.get("cpu_baseline"), "e2e": None, "gpu_launches": r["launches"], "clocks": clk,
         "rel_err": r.get("rel_err"), "kernel_ms": r["kernel_ms"], "device_status": r["device_status"],
-        "sum_sites": r["sum_sites"],
+        "schedule": r["schedule"],
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -427,7 +446,8 @@ def run_triplets(args):
     clocks = ClockSampler(0)
     clocks.start()
     r = measure_triplets(laph, L, T, N, mom, args.mode, args.steps, args.warmup,
-                         n_sample=0 if args.no_cpu_baseline else 150000, timed_oracle=not args.no_cpu_baseline)
+                         n_sample=0 if args.no_cpu_baseline else 150000, timed_oracle=not args.no_cpu_baseline,
+                         tune=not args.no_autotune)
     clk = clocks.stop()
     peaks, _ = measured_peaks()
     peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
@@ -437,7 +457,7 @@ def run_triplets(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": f"{args.mode}->f32/f64",
         "data": "synthetic (seeded complex Gaussian fields phi, psi, chi)",
         "config": {"workload": f"L={L},T={T},N={N},P={mom.shape[0]} (triplets)", "L": L, "T": T, "N": N,
-                   "P": int(mom.shape[0]), "mode": args.mode},
+                   "P": int(mom.shape[0]), "mode": args.mode, "schedule": r["schedule"]},
         "roofline": {"bound": "tensor", "achieved": r["kernel_tflops"], "peak": peak, "unit": "TFLOP/s",
                      "frac": r["kernel_tflops"] / peak, "traffic": None,
                      "note": "achieved counts algorithmic flops; the 3-term split executes 3x that"},
@@ -465,8 +485,10 @@ def run_projection(args):
     for n in (Nv, Ns):
         z = torch.randn((T, n, V, 3, 2), generator=gen, device="cuda", dtype=torch.float32)
         fields.append(torch.view_as_complex(z).contiguous() / math.sqrt(3 * V))
+    tune = not args.no_autotune
     plan = laph.Plan([(L, T, Nv, mom, Ns)], mode=args.mode,
-                     flags=laph.PLAN_FIELDS | laph.PLAN_SKIP_B | laph.PLAN_TIMING)
+                     flags=laph.PLAN_FIELDS | laph.PLAN_SKIP_B | laph.PLAN_TIMING | (laph.PLAN_AUTOTUNE if tune else 0))
+    sched = schedule_of(plan, tune)
     _, Ms = plan.alloc_outputs()
     ws = plan.alloc_workspace()
     stream = torch.cuda.current_stream()
@@ -507,7 +529,7 @@ def run_projection(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": f"{args.mode}->f32/f64", "data": "synthetic (seeded complex Gaussian v and s)",
         "config": {"workload": f"L={L},T={T},Nv={Nv},Ns={Ns},P=1 (projection)", "L": L, "T": T, "Nv": Nv, "Ns": Ns,
-                   "mode": args.mode},
+                   "mode": args.mode, "schedule": sched},
         "roofline": {"bound": "tensor", "achieved": flops / (k_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                      "frac": flops / (k_ms / 1e3) / 1e12 / peak, "traffic": None,
                      "note": "achieved counts algorithmic flops; the 3-term split executes 3x that",
@@ -761,7 +783,7 @@ def run_ragged(args):
                      "frac": flops_step / (k_ms / 1e3) / 1e12 / peak, "traffic": None},
         "per_instance_plans": {"ms_per_step": ms_single, "value": flops_step / (ms_single / 1e3) / 1e12},
         "gpu_launches": plan.launches_per_execute() * args.steps, "clocks": clk, "rel_err": rel,
-        "contraction_launches": n_con, "kernel_ms": k_ms,
+        "contraction_launches": n_con, "kernel_ms": k_ms, "schedule": schedule_of(plan, False),
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -782,6 +804,7 @@ def main():
     ap.add_argument("--chunk-sites", type=int, default=0)
     ap.add_argument("--sum-sites", type=int, default=0)
     ap.add_argument("--tile-cols", type=int, default=0)
+    ap.add_argument("--layout", type=int, default=0, help="tensor-core layout of the complex product (0 or 1)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="metric workload: the default schedule instead of the autotuned one")
     args = ap.parse_args()
@@ -822,17 +845,10 @@ def main():
     t_plan = time.perf_counter()
     plan = laph.Plan([(L, T, N, mom)], mode=args.mode,
                      flags=laph.PLAN_TIMING | (laph.PLAN_AUTOTUNE if tune else 0), chunk_sites=args.chunk_sites,
-                     sum_sites=args.sum_sites, tile_cols=args.tile_cols)
+                     sum_sites=args.sum_sites, tile_cols=args.tile_cols, layout=args.layout)
     t_plan = time.perf_counter() - t_plan
     desc = plan.describe()
-    schedule = {"tile_cols": desc["tile_cols"], "chunk_sites": desc["chunk_sites"], "sum_sites": plan.sum_sites()[0],
-                "timeslices_per_chunk": plan.schedule()["timeslices_per_chunk"],
-                "tile_order": plan.schedule()["tile_order"], "autotuned": tune, "plan_create_s": t_plan}
-    if tune:
-        schedule["candidates"] = [[r["tile_cols"], r["tile_order"], r["timeslices_per_chunk"], r["sum_sites"],
-                                   r["chunk_sites"], round(r["ms"], 2), r["probe_err"]] for r in plan.tuning()]
-        schedule["candidate_fields"] = ["tile_cols", "tile_order", "timeslices_per_chunk", "sum_sites", "chunk_sites",
-                                        "ms", "probe_err"]
+    schedule = dict(schedule_of(plan, tune), plan_create_s=t_plan)
     Bs, Ms = plan.alloc_outputs()
     ws = plan.alloc_workspace()
     stream = torch.cuda.current_stream()
@@ -879,7 +895,8 @@ def main():
         peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
         nc = desc["tile_cols"]
         n_ct = -(-(N * P) // nc)
-        images = T * n_ct * (-(-(3 * V) // 24)) * 384 * nc        # stage images read per step (384 nc B each)
+        img_b = 192 * nc if desc["tile_rows"] == 64 else 384 * nc  # one stage image (layout 1: one B row per column)
+        images = T * n_ct * (-(-(3 * V) // 24)) * img_b            # stage images read per step
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": TC_DRAM_PER_IMAGE_BYTE * images / n_con,
                 "traffic_source": "per tc_kernel launch: DRAM bytes per stage-image byte from the ncu capture at "

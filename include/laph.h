@@ -289,7 +289,13 @@ typedef struct {
     int sum_sites;   /* tensor-core modes: sites per block of the FP64 site reduction (default 8192, rounded down
                         to a multiple of 8): a tile covers one block, its running sums become one FP32 partial per
                         output, and the partials of all blocks are added in FP64 in block order */
-    int tile_cols;   /* tensor-core modes: complex columns per tile, 96 (default) or 64 */
+    int tile_cols;   /* tensor-core modes: complex columns per tile: 96 (default) or 64 in layout 0; 176
+                        (default), 192 or 128 in layout 1 */
+    int layout;      /* tensor-core modes: how the complex product is laid out on the real tensor cores.
+                        0 (default): every complex column of the phased operand is two real rows (re, im) of the
+                        MMA's B operand, 128 complex rows per tile; 1: every complex row of the diquark / meson
+                        operand is two real rows of the MMA's A operand (tensor-memory lanes 2r, 2r+1), 64 complex
+                        rows per tile, and the phased operand's stage images are half as large */
 } laph_plan_options;
 
 /* laph_plan_create with numerical parameters (opts may be NULL).  LAPH_ERR_ARG
@@ -390,7 +396,8 @@ LAPH_API int laph_plan_tensor_flops(const laph_plan *plan, double *flops);
 
 /* One candidate schedule timed by LAPH_PLAN_AUTOTUNE. */
 typedef struct {
-    int tile_cols;                  /* complex columns per tile (96 or 64) */
+    int tile_cols;                  /* complex columns per tile */
+    int layout;                     /* laph_plan_options.layout */
     int sum_sites;                  /* sites per block of the FP64 site reduction */
     int chunk_sites;                /* drain interval of the tensor core's FP32 accumulation, in sites */
     int tile_order;                 /* 0: column tiles outer, 1: row tiles outer */
@@ -404,7 +411,8 @@ typedef struct {
  * candidate schedules on seeded synthetic inputs of the plan's shapes
  * (pseudo-random entries in [-1, 1); inputs, outputs and a workspace are
  * allocated for the duration; one warm-up and one timed execute each) by a
- * coordinate search: tile width (96 and 64 columns) x tile order x chunking
+ * coordinate search: tile shape (layout 0 with 96 and 64 columns, layout 1
+ * with 176, 192 and 128 columns) x tile order x chunking
  * (the wave model and, for one instance, the largest chunk within the 24 GiB
  * cap); then, from the fastest, half and twice the site-block size of the
  * FP64 reduction; then half and 1.5 times the drain interval.  A drain

@@ -48,11 +48,13 @@ class laph_instance(ctypes.Structure):
 
 
 class laph_plan_options(ctypes.Structure):
-    _fields_ = [("chunk_sites", ctypes.c_int), ("sum_sites", ctypes.c_int), ("tile_cols", ctypes.c_int)]
+    _fields_ = [("chunk_sites", ctypes.c_int), ("sum_sites", ctypes.c_int), ("tile_cols", ctypes.c_int),
+                ("layout", ctypes.c_int)]
 
 
 class laph_tune_record(ctypes.Structure):
-    _fields_ = [("tile_cols", ctypes.c_int), ("sum_sites", ctypes.c_int), ("chunk_sites", ctypes.c_int),
+    _fields_ = [("tile_cols", ctypes.c_int), ("layout", ctypes.c_int), ("sum_sites", ctypes.c_int),
+                ("chunk_sites", ctypes.c_int),
                 ("tile_order", ctypes.c_int), ("timeslices_per_chunk", ctypes.c_int64), ("ms", ctypes.c_float),
                 ("probe_err", ctypes.c_double)]
 
@@ -401,7 +403,7 @@ class Plan:
     """
 
     def __init__(self, instances, mode="f16x3", flags: int = 0, chunk_sites: int = 0, sum_sites: int = 0,
-                 tile_cols: int = 0):
+                 tile_cols: int = 0, layout: int = 0):
         # (L, T, N, momenta) or, for doublet plans of two vector counts, (L, T, N, momenta, n_col)
         self._moms = [_momenta(inst[3]) for inst in instances]
         self.n_col = [int(inst[4]) if len(inst) > 4 else 0 for inst in instances]
@@ -415,7 +417,7 @@ class Plan:
         self.flags = flags
         self.mode = _mode(mode)
         h = ctypes.c_void_p()
-        opts = laph_plan_options(int(chunk_sites), int(sum_sites), int(tile_cols))
+        opts = laph_plan_options(int(chunk_sites), int(sum_sites), int(tile_cols), int(layout))
         _check(lib().laph_plan_create_opts(arr, len(instances), self.mode, flags, ctypes.byref(opts), ctypes.byref(h)),
                "laph_plan_create_opts")
         self._h = h

@@ -76,6 +76,7 @@ struct Sched {
     int tile_cols, sum_sites, chunk_sites;
     long long per_chunk;
     int order;
+    int rows2;   // 1: the row-doubled layout of the complex product (64 complex rows per tile)
 };
 }  // namespace laph
 
@@ -96,6 +97,7 @@ struct laph_plan {
     long long n_tiles = 0;
     int *d_status = nullptr;
     int tile_rows = 0, tile_cols = 0, chunk_sites = 0, grid = 0;
+    int rows2 = 0;                             // tensor-core path: the row-doubled layout
     int sum_sites = 0;                         // tensor-core path: sites per block of the FP64 reduction
     int max_staged = 0, max_P = 0;
     size_t ws_bytes = 0, off_maxbits = 0, off_counter = 0, ws_zero_bytes = 0;
@@ -256,7 +258,8 @@ int laph_plan_create_opts(const laph_instance *inst, int n_inst, int mode, unsig
     if (!inst || n_inst < 1 || !plan_out) return LAPH_ERR_ARG;
     const int opt_chunk = opts ? opts->chunk_sites : 0, opt_sum = opts ? opts->sum_sites : 0;
     if (opt_chunk < 0 || opt_chunk > (1 << 24) || opt_sum < 0 || opt_sum > (1 << 24)) return LAPH_ERR_ARG;
-    if (opts && opts->tile_cols != 0 && opts->tile_cols != 64 && opts->tile_cols != 96) return LAPH_ERR_ARG;
+    if (opts && (opts->layout < 0 || opts->layout > 1)) return LAPH_ERR_ARG;
+    if (opts && opts->tile_cols != 0 && !laph::tc_shape_supported(opts->tile_cols, opts->layout)) return LAPH_ERR_ARG;
     if (mode < 0 || mode >= LAPH_NUM_MODES) return LAPH_ERR_ARG;
     const bool skipB = flags & LAPH_PLAN_SKIP_B, skipM = flags & LAPH_PLAN_SKIP_M;
     if (skipB && skipM) return LAPH_ERR_ARG;
@@ -383,14 +386,17 @@ int laph_plan_create_opts(const laph_instance *inst, int n_inst, int mode, unsig
     // CTAs that share a stage image run side by side.
     std::vector<TileDev> tiles;
     std::vector<laph::PsiUnit> units;
-    const int TR = p->tile_rows;
     std::vector<std::vector<TileDev>> ones(n_inst);
     std::vector<size_t> unit_bytes(n_inst);
     size_t psi_total = 0;
     // the (row tile, column tile) pairs of one timeslice of every instance for
     // tiles of TC complex columns
-    auto build_tiles = [&](int TC) {
+    auto build_tiles = [&](int TC, int rows2) {
         p->tile_cols = TC;
+        p->rows2 = tc ? rows2 : 0;
+        p->tile_rows = !tc ? laph::SIMT_TR : (rows2 ? laph::TC_TR_ROWS2 : laph::TC_TR);
+        const int TR = p->tile_rows;
+        const int skip_step = rows2 ? 16 : 8;   // column skips keep the UMMA N a multiple of 16
         p->max_staged = 0;
         for (int n = 0; n < n_inst; n++) {
             InstDev &d = p->h_inst[n];
@@ -434,11 +440,12 @@ int laph_plan_create_opts(const laph_instance *inst, int n_inst, int mode, unsig
                     const int nw = trip ? w_hi - w_lo + 1 : 0;
                     if (!trip) w_lo = 0;
                     p->max_staged = std::max(p->max_staged, tc ? nv + nw : nv + (kmax - kmin + 1));
-                    const long long psi_ct = tc ? (long long)(col0 / TC) * d.n_st * laph::tc_stage_bytes(TC) : 0;
+                    const long long psi_ct =
+                        tc ? (long long)(col0 / TC) * d.n_st * laph::tc_stage_bytes(TC, rows2) : 0;
                     int cskip = 0;
                     if (tc && jmin >= 0) {
                         const int lead = std::max(0, std::min(nc, (jmin + 1) * d.P - col0));
-                        cskip = (lead / 8) * 8;
+                        cskip = (lead / skip_step) * skip_step;
                     }
                     one.push_back(TileDev{n, 0, row0, col0, v_lo, nv, w_lo, nw, kmin, kmax - kmin + 1, nc, cskip,
                                           psi_ct, 0, d.n_st, 0});
@@ -457,7 +464,7 @@ int laph_plan_create_opts(const laph_instance *inst, int n_inst, int mode, unsig
             InstDev &d = p->h_inst[n];
             d.sc_stages = tc ? std::max(1, std::min(d.n_st, sum_sites / laph::TC_BS)) : d.n_st;
             d.n_sc = (d.n_st + d.sc_stages - 1) / d.sc_stages;
-            unit_bytes[n] = tc ? (size_t)d.n_ct * d.n_st * laph::tc_stage_bytes(p->tile_cols) +
+            unit_bytes[n] = tc ? (size_t)d.n_ct * d.n_st * laph::tc_stage_bytes(p->tile_cols, p->rows2) +
                                      (size_t)d.n_sc * (size_t)(d.n_outB + d.n_outM) * sizeof(float2)
                                : 0;
             psi_total += (size_t)d.T * unit_bytes[n];
@@ -569,7 +576,7 @@ int laph_plan_create_opts(const laph_instance *inst, int n_inst, int mode, unsig
                 if (tc) {
                     cur.n_tiles += (long long)one.size();
                     cur_bytes += unit_bytes[n];
-                    cur_psi += (size_t)d.n_ct * d.n_st * laph::tc_stage_bytes(p->tile_cols);
+                    cur_psi += (size_t)d.n_ct * d.n_st * laph::tc_stage_bytes(p->tile_cols, p->rows2);
                     cur_part += (long long)d.n_sc * (d.n_outB + d.n_outM);
                 }
             }
@@ -584,7 +591,7 @@ int laph_plan_create_opts(const laph_instance *inst, int n_inst, int mode, unsig
         if (tc) {
             const int terms = (mode == LAPH_MODE_TC_F16X3 || mode == LAPH_MODE_TC_BF16X3) ? 3 : 1;
             for (const TileDev &u : tiles) {
-                const int n_real = 2 * ((u.ncols + 7) & ~7) - 2 * u.cskip;
+                const int n_real = p->rows2 ? ((u.ncols + 15) & ~15) - u.cskip : 2 * ((u.ncols + 7) & ~7) - 2 * u.cskip;
                 p->mma_flops += 2.0 * laph::TC_TR * n_real * (2 * laph::TC_KSTAGE) * terms * u.nst;
             }
         }
@@ -643,7 +650,7 @@ int laph_plan_create_opts(const laph_instance *inst, int n_inst, int mode, unsig
     // a whole schedule: tile width, site block, drain interval, chunking
     // (-1: the wave model, -2: the largest chunk within the cap) and tile order
     std::function<cudaError_t(const laph::Sched &)> apply = [&](const laph::Sched &c) -> cudaError_t {
-        build_tiles(tc ? c.tile_cols : laph::SIMT_TC);
+        build_tiles(tc ? c.tile_cols : laph::SIMT_TC, c.rows2);
         set_sum(c.sum_sites);
         make_order();
         p->chunk_sites = c.chunk_sites;
@@ -653,8 +660,9 @@ int laph_plan_create_opts(const laph_instance *inst, int n_inst, int mode, unsig
         p->sched = c;
         return upload();
     };
-    const int opt_cols = opts ? opts->tile_cols : 0;
-    const laph::Sched def{opt_cols ? opt_cols : laph::TC_TC, opt_sum ? opt_sum : TC_DEFAULT_SUM, p->chunk_sites, -1, 0};
+    const int opt_cols = opts ? opts->tile_cols : 0, opt_layout = opts ? opts->layout : 0;
+    const laph::Sched def{opt_cols ? opt_cols : (opt_layout ? 176 : laph::TC_TC),
+                          opt_sum ? opt_sum : TC_DEFAULT_SUM, p->chunk_sites, -1, 0, opt_layout};
     PCK(apply(def));
     if (tc && p->max_staged > laph::TC_MAX_STAGED) {
         free_plan(p);
@@ -740,6 +748,7 @@ static laph::TcConfig tc_config(const laph_plan *p)
     cfg.terms = (p->mode == LAPH_MODE_TC_F16X3 || p->mode == LAPH_MODE_TC_BF16X3) ? 3 : 1;
     cfg.chunk_sites = p->chunk_sites;
     cfg.ncols = p->tile_cols;
+    cfg.rows2 = p->rows2;
     cfg.grid = p->grid;
     cfg.max_staged = p->max_staged;
     cfg.debug_stall = (p->flags & LAPH_PLAN_DEBUG_STALL) ? 1 : 0;
@@ -783,7 +792,8 @@ static int launch_tc_chunk(laph_plan *p, char *ws, size_t ci, const laph::TcConf
     const laph_plan::Chunk &c = p->chunks[ci];
     const int ps = (int)(p->n_ptimed % laph_plan::RING), cs = (int)(p->n_timed % laph_plan::RING);
     if (timing) CK(cudaEventRecord(p->pv_begin[ps], s));
-    e = laph::launch_psi(p->d_inst, p->d_units + c.unit0, c.n_units, c.n_jobs, maxbits, cfg.elem, cfg.ncols, psi, s);
+    e = laph::launch_psi(p->d_inst, p->d_units + c.unit0, c.n_units, c.n_jobs, maxbits, cfg.elem, cfg.ncols, cfg.rows2,
+                         psi, s);
     if (e != cudaSuccess) return cuda_fail(e, "psi");
     if (timing) {
         CK(cudaEventRecord(p->pv_end[ps], s));
@@ -1036,12 +1046,16 @@ static int autotune(laph_plan *p, const laph::Sched &def, const std::function<cu
     {
         // 1: tile width x tile order x chunking (the largest chunk only for one instance)
         const bool one_inst = p->n_inst == 1 && !(p->flags & LAPH_PLAN_CHUNK_PER_TIMESLICE);
-        for (int nc : {def.tile_cols, def.tile_cols == 96 ? 64 : 96})
+        const std::pair<int, int> shapes[] = {{def.tile_cols, def.rows2}, {96, 0}, {64, 0}, {176, 1}, {192, 1}, {128, 1}};
+        for (size_t k = 0; k < sizeof(shapes) / sizeof(shapes[0]); k++) {
+            const int nc = shapes[k].first, r2 = shapes[k].second;
+            if (k > 0 && nc == def.tile_cols && r2 == def.rows2) continue;
             for (long long pc : {-1LL, -2LL})
                 for (int o = 0; o < 2; o++) {
                     if (pc == -2 && !one_inst) continue;
-                    TRC(run(laph::Sched{nc, def.sum_sites, def.chunk_sites, pc, o}, false));
+                    TRC(run(laph::Sched{nc, def.sum_sites, def.chunk_sites, pc, o, r2}, false));
                 }
+        }
         for (size_t k = 1; k < p->tune_ms.size(); k++)
             if (p->tune_ms[k] < p->tune_ms[best]) best = k;
         // 2: site-block size of the FP64 reduction
@@ -1114,6 +1128,7 @@ int laph_plan_tuning(const laph_plan *plan, int cap, laph_tune_record *rec, int 
     for (int k = 0; k < n && k < cap; k++) {
         const laph::Sched &c = plan->tune_cand[k];
         rec[k].tile_cols = c.tile_cols;
+        rec[k].layout = c.rows2;
         rec[k].sum_sites = c.sum_sites;
         rec[k].chunk_sites = c.chunk_sites;
         rec[k].tile_order = c.order;

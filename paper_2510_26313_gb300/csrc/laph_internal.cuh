@@ -188,7 +188,8 @@ cudaError_t launch_simt(const InstDev *d_inst, const TileDev *d_tiles, long long
 // laph_tc.cu
 struct TcConfig {
     int elem;          // 0 = FP16 hi/lo, 1 = BF16 hi/lo
-    int ncols;         // tile width in complex columns: 96 or 64
+    int ncols;         // tile width in complex columns: 96 or 64; row-doubled layout 192, 176 or 128
+    int rows2;         // 1: row-doubled layout (two real A rows per complex row, 64 complex rows per tile)
     int terms;         // 3 (split) or 1 (plain)
     int chunk_sites;   // sites accumulated by the tensor core between FP32 drains
     int grid;          // persistent CTAs
@@ -198,14 +199,18 @@ struct TcConfig {
 constexpr int TC_TR = 128;   // tile rows (UMMA M)
 constexpr int TC_TC = 96;    // default tile columns (complex), UMMA N = 2 * TC_TC real; 64 is the other width
 constexpr int TC_KSTAGE = 3 * TC_BS;  // complex K entries per stage: one site block
-// One B stage image of a tile of nc complex columns: hi + lo, 2 nc real rows x 48 FP16 each.
-constexpr int tc_stage_bytes(int nc) { return 2 * (2 * nc) * (2 * TC_KSTAGE) * 2; }
+// One B stage image of a tile of nc complex columns: hi + lo, 2 nc real rows
+// (nc in the row-doubled layout) x 48 FP16 each.
+constexpr int tc_stage_bytes(int nc, bool rows2 = false) { return 2 * (rows2 ? nc : 2 * nc) * (2 * TC_KSTAGE) * 2; }
 constexpr int TC_STAGE_BYTES = tc_stage_bytes(TC_TC);
+constexpr int TC_TR_ROWS2 = 64;   // complex rows per tile in the row-doubled layout
+// Tile widths with compiled kernels for each layout.
+bool tc_shape_supported(int ncols, int rows2);
 constexpr int TC_MAX_STAGED = 160;  // staged row vectors per tile
 constexpr int TC_PSI_GROUP = 16;    // stages per job of the B-operand pass
 // Psi stage images of a chunk: jobs [0, n_jobs) over the units [0, n_units).
 cudaError_t launch_psi(const InstDev *d_inst, const PsiUnit *d_units, int n_units, long long n_jobs,
-                       const unsigned *d_maxbits, int elem, int ncols, uint8_t *psi, cudaStream_t s);
+                       const unsigned *d_maxbits, int elem, int ncols, int rows2, uint8_t *psi, cudaStream_t s);
 // counter: a zeroed word of device memory; persistent CTAs claim tiles with it.
 cudaError_t launch_tc(const InstDev *d_inst, const TileDev *d_tiles, long long n_tiles,
                       const unsigned *d_maxbits, const uint8_t *psi, float2 *part, unsigned *counter,

@@ -82,19 +82,33 @@ static_assert(TC_TR == 128, "layout assumes 128-row tiles (UMMA M = 128, one ten
 static_assert(TC_BS == 8 && KSTAGE == 24 && KSTEPS == 3, "a stage is one 8-site block");
 static_assert(A_LO + KSTAGE <= A_SLOT_COLS && A_COL + 2 * A_SLOT_COLS == TMEM_COLS, "tensor memory budget");
 
-// Sizes that follow from the tile width NC (complex columns; UMMA N = 2 NC
-// real B rows).  Tensor memory: the accumulator in columns [0, 2 NC), the
-// FP32 running sums in [2 NC, 4 NC), the two A slots from column 384.
-template <int NC>
+// Sizes that follow from the tile width NC (complex columns) and the layout
+// of the complex product.  RD false: every complex column is two real B rows
+// (re-row, im-row), UMMA N = 2 NC, and a tile has 128 complex rows; RD true:
+// every complex row is two real A rows (tensor-memory lanes 2r, 2r+1), UMMA
+// N = NC, and a tile has 64 complex rows.  Tensor memory: the accumulator in
+// columns [0, B_ROWS), the FP32 running sums in [B_ROWS, 2 B_ROWS), the two
+// A slots from column 384.
+template <int NC, bool RD>
 struct Shape {
-    static constexpr int B_ROWS = 2 * NC;                  // real B rows per tile
+    static constexpr int B_ROWS = RD ? NC : 2 * NC;        // real B rows per tile (UMMA N)
     static constexpr int ATOM_COL_BYTES = (B_ROWS / 8) * 256;   // one k-step of hi (or lo): atoms of 8 rows x 32 B
     static constexpr int B_BYTES = KSTEPS * ATOM_COL_BYTES;     // hi (or lo) of one stage
     static constexpr int BIMG_BYTES = 2 * B_BYTES;              // hi + lo
-    static constexpr uint32_t SUM_COL = 2 * NC;
-    static_assert(NC % 16 == 0 && NC <= 96 && 4 * NC <= (int)A_COL, "tile width within the tensor-memory budget");
-    static_assert(BIMG_BYTES == tc_stage_bytes(NC), "stage image size");
+    static constexpr uint32_t SUM_COL = B_ROWS;
+    static_assert(B_ROWS % 16 == 0 && B_ROWS <= 192 && 2 * B_ROWS <= (int)A_COL,
+                  "tile width within the tensor-memory budget");
+    static_assert(BIMG_BYTES == tc_stage_bytes(NC, RD), "stage image size");
 };
+
+// Accumulator columns of a tile (UMMA N): its valid columns rounded up, less
+// the leading columns no row needs (RD: multiples of 16 complex columns, one
+// real B row each; otherwise multiples of 8, two real B rows each).
+template <bool RD>
+__device__ __forceinline__ int acc_cols(int ncols, int cskip)
+{
+    return RD ? ((ncols + 15) & ~15) - cskip : 2 * ((ncols + 7) & ~7) - 2 * cskip;
+}
 
 struct Shared {
     // full: data of stage k landed, barrier k mod 2 NS (every barrier serves
@@ -406,6 +420,47 @@ __device__ __forceinline__ void a_quarter(int kind, const uint8_t *pu, const uin
     }
 }
 
+// Row-doubled layout: lanes 2r (part 0) and 2r+1 (part 1) hold the two real
+// rows of complex row r.  Each lane forms half of the row's 12 K entries of
+// sites 4h..4h+3 (part p: sites 4h+2p, 4h+2p+1), the pair exchanges them, and
+// every lane splits all 12 in its own form: (re, -im) for the re-row, (im, re)
+// for the im-row, so that with B rows (Psi_re, Psi_im) the re-row gives the
+// real part of the product and the im-row its imaginary part.
+template <int ELEM>
+__device__ __forceinline__ void a_pair(int kind, int part, const uint8_t *pu, const uint8_t *pv, uint32_t (&hi)[12],
+                                       uint32_t (&lo)[12])
+{
+    float2 u[6], v[6], mine[6], other[6];
+#pragma unroll
+    for (int h = 0; h < 3; h++) {
+        const float4 a = reinterpret_cast<const float4 *>(pu)[3 * part + h];
+        const float4 b = reinterpret_cast<const float4 *>(pv)[3 * part + h];
+        u[2 * h] = make_float2(a.x, a.y);
+        u[2 * h + 1] = make_float2(a.z, a.w);
+        v[2 * h] = make_float2(b.x, b.y);
+        v[2 * h + 1] = make_float2(b.z, b.w);
+    }
+#pragma unroll
+    for (int e = 0; e < 6; e++) {
+        float2 x;
+        if (kind == 2)
+            x = cross8(u + 3 * (e / 3), v + 3 * (e / 3), e % 3);
+        else if (kind == 1)
+            x = make_float2(u[e].x, -u[e].y);
+        else
+            x = make_float2(0.f, 0.f);
+        mine[e] = x;
+        other[e] = make_float2(__shfl_xor_sync(0xffffffffu, x.x, 1), __shfl_xor_sync(0xffffffffu, x.y, 1));
+    }
+    // entries 0..5 belong to sites 4h, 4h+1 (part 0's), 6..11 to sites 4h+2, 4h+3 (part 1's)
+#pragma unroll
+    for (int e = 0; e < 12; e++) {
+        const float2 x = e < 6 ? (part == 0 ? mine[e] : other[e]) : (part == 0 ? other[e - 6] : mine[e - 6]);
+        const float re = part == 0 ? x.x : x.y, im = part == 0 ? -x.y : x.x;
+        split2<ELEM>(re, im, hi[e], lo[e]);
+    }
+}
+
 // hi words to columns ta..ta+11, lo words to ta + A_LO ..
 __device__ __forceinline__ void a_store(uint32_t ta, const uint32_t (&hi)[12], const uint32_t (&lo)[12])
 {
@@ -433,10 +488,10 @@ struct KParams {
     int debug_stall;
 };
 
-template <int ELEM, int TERMS, int NC>
+template <int ELEM, int TERMS, int NC, bool RD>
 __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
 {
-    using SH = Shape<NC>;
+    using SH = Shape<NC, RD>;
     constexpr int BIMG_BYTES = SH::BIMG_BYTES, B_BYTES = SH::B_BYTES, ATOM_COL_BYTES = SH::ATOM_COL_BYTES;
     constexpr uint32_t SUM_COL = SH::SUM_COL;
     extern __shared__ uint8_t smem_raw[];
@@ -532,7 +587,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
     } else if (warp < N_AWARPS) {
         // ---------------------------------------------------------- A producers
         const int quad = warp & 3, half = (warp >> 2) & 1, grp = warp >> 3;
-        const int r = quad * 32 + lane;
+        const int r = RD ? (quad * 32 + lane) >> 1 : quad * 32 + lane;   // the lane's (complex) row of the tile
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
         const uint32_t ta0 = tmem + lane_base + A_COL + (uint32_t)grp * A_SLOT_COLS + 12u * half;
         uint32_t G = 0;   // global index of the tile's first stage
@@ -589,7 +644,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
                 }
                 const uint8_t *buf = smem + s * kp.stage_bytes;
                 uint32_t hi[12], lo[12];
-                a_quarter<ELEM>(kind, buf + off_u, buf + off_v, hi, lo);
+                if (RD)
+                    a_pair<ELEM>(kind, lane & 1, buf + off_u, buf + off_v, hi, lo);
+                else
+                    a_quarter<ELEM>(kind, buf + off_u, buf + off_v, hi, lo);
                 if (!warp_wait(c, &S->empty[s2], ph2)) {
                     ok = false;
                     break;
@@ -620,7 +678,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
     } else if (warp < WARP_LOAD) {
         // ---------------------------------------------------------- epilogue
         const int quad = warp & 3;
-        const int r = quad * 32 + lane;
+        const int r = RD ? (quad * 32 + lane) >> 1 : quad * 32 + lane;   // the lane's (complex) row of the tile
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
         uint32_t gc = 0, gc1 = 0;   // drains done of the low / high column half
         bool ok = true;
@@ -631,7 +689,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
             const TileDev td = kp.tiles[tile];
             const InstDev &I = kp.insts[td.inst];
             const int ncols = td.ncols, cskip = td.cskip;
-            const int n_real = 2 * ((ncols + 7) & ~7) - 2 * cskip;   // accumulator columns: tile columns cskip..
+            const int n_real = acc_cols<RD>(ncols, cskip);   // accumulator columns: tile columns cskip..
             const int gr = td.row0 + r;
             const bool rvalid = gr < I.rows;
             const bool meson = gr < I.mes_rows;
@@ -690,6 +748,30 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
                 uint32_t v[16];
                 tmem_ld16(tmem + lane_base + SUM_COL + 16u * b, v);
                 tmem_wait_ld();
+                if (RD) {
+                    // lane 2r holds the real parts of complex row r, lane 2r+1
+                    // the imaginary parts: the pair's even lane writes
+#pragma unroll
+                    for (int u = 0; u < 16; u++) {
+                        const uint32_t o = __shfl_xor_sync(0xffffffffu, v[u], 1);
+                        if (lane & 1) continue;
+                        const int cc = cskip + 16 * b + u;
+                        if (!rvalid || cc >= ncols) continue;
+                        const int col = td.col0 + cc;
+                        const int k = col / P, p = col - k * P;
+                        long long e;
+                        if (meson) {
+                            e = I.n_outB + ((long long)p * N + gr) * I.Nc + k;
+                        } else if (trip) {
+                            e = (((long long)p * N + pi_) * N + pj) * N + k;
+                        } else {
+                            if (k <= pj) continue;
+                            e = (long long)p * n_trip + binom3(k) + q;
+                        }
+                        part[e] = make_float2(__uint_as_float(v[u]), __uint_as_float(o));
+                    }
+                    continue;
+                }
 #pragma unroll 1
                 for (int u = 0; u < 8; u++) {
                     const int cc = cskip + 8 * b + u;
@@ -720,11 +802,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
             if (tile < 0) break;
             const TileDev td = kp.tiles[tile];
             const int nst = td.nst;
-            // the first cskip columns (2 cskip real B rows, 64 bytes per column in
-            // every atom column) are not needed by any row of the tile
-            const int n_real = 2 * ((td.ncols + 7) & ~7) - 2 * td.cskip;
+            // the first cskip columns (2 cskip real B rows, or cskip in the
+            // row-doubled layout; 32 bytes per B row in every atom column) are
+            // not needed by any row of the tile
+            const int n_real = acc_cols<RD>(td.ncols, td.cskip);
             const uint32_t idesc = idesc_f16(n_real, ELEM);
-            const uint64_t bskip = (uint64_t)(td.cskip * 64) >> 4;
+            const uint64_t bskip = (uint64_t)(td.cskip * (RD ? 32 : 64)) >> 4;
             // column halves [0, n_lo) and [n_lo, n_real) of the accumulator
             const int n_lo = n_real >= 32 ? ((n_real / 2 + 15) & ~15) : n_real;
             const int nh = n_real > n_lo ? 2 : 1;
@@ -826,12 +909,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
 // image, in the K-major 32-byte-swizzled layout the contraction's
 // descriptors expect.  Every store instruction of a warp writes sixteen
 // whole 32-byte rows.
-template <int ELEM, int NC>
+template <int ELEM, int NC, bool RD>
 __global__ void __launch_bounds__(2 * NC) psi_kernel(const InstDev *__restrict__ insts, const PsiUnit *__restrict__ units,
                                                      int n_units, long long n_jobs, const unsigned *__restrict__ maxbits,
                                                      uint8_t *__restrict__ psi)
 {
-    using SH = Shape<NC>;
+    using SH = Shape<NC, RD>;
     constexpr int BIMG_BYTES = SH::BIMG_BYTES, B_BYTES = SH::B_BYTES, ATOM_COL_BYTES = SH::ATOM_COL_BYTES;
     const int cu = threadIdx.x >> 1, j = threadIdx.x & 1;
     for (long long job = blockIdx.x; job < n_jobs; job += gridDim.x) {
@@ -863,7 +946,8 @@ __global__ void __launch_bounds__(2 * NC) psi_kernel(const InstDev *__restrict__
         const float2 *ph = I.phase + (long long)p * I.Vs;
         const float2 *phk = I.phi + ((long long)un.t * I.Nc + k) * V * 3;
         uint8_t *img = psi + un.psi_off + ((long long)ct * n_st + st0) * BIMG_BYTES;
-        const int n0 = 2 * cu, n1 = n0 + 1;
+        // real B rows of the column: re-row 2 cu and im-row 2 cu + 1, or (row-doubled layout) row cu
+        const int n0 = RD ? cu : 2 * cu, n1 = n0 + 1;
         const uint32_t o0 = sw32(n0, j), o1 = sw32(n1, j);
         for (int st = st0; st < st1; st++, img += BIMG_BYTES) {
 #pragma unroll
@@ -885,12 +969,22 @@ __global__ void __launch_bounds__(2 * NC) psi_kernel(const InstDev *__restrict__
                     const float2 z = cmulf(w[(c0 + v) / 3], make_float2(f[v].x * sc, f[v].y * sc));
                     uint32_t h, l;
                     split2<ELEM>(z.x, z.y, h, l);
-                    rh[v] = h ^ 0x80000000u;            // (re, -im)
-                    rl[v] = l ^ 0x80000000u;
-                    ih[v] = __byte_perm(h, 0, 0x1032);  // (im, re)
-                    il[v] = __byte_perm(l, 0, 0x1032);
+                    if (RD) {
+                        rh[v] = h;                          // (re, im)
+                        rl[v] = l;
+                    } else {
+                        rh[v] = h ^ 0x80000000u;            // (re, -im)
+                        rl[v] = l ^ 0x80000000u;
+                        ih[v] = __byte_perm(h, 0, 0x1032);  // (im, re)
+                        il[v] = __byte_perm(l, 0, 0x1032);
+                    }
                 }
                 uint8_t *out = img + ks * ATOM_COL_BYTES;
+                if (RD) {
+                    *reinterpret_cast<uint4 *>(out + o0) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+                    *reinterpret_cast<uint4 *>(out + B_BYTES + o0) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+                    continue;
+                }
                 *reinterpret_cast<uint4 *>(out + o0) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
                 *reinterpret_cast<uint4 *>(out + o1) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
                 *reinterpret_cast<uint4 *>(out + B_BYTES + o0) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
@@ -999,9 +1093,9 @@ __global__ void __launch_bounds__(RED_THREADS) reduce_kernel(const InstDev *__re
     }
 }
 
-int stage_bytes_for(int max_staged, int nc)
+int stage_bytes_for(int max_staged, int nc, bool rd)
 {
-    const int b = tc_stage_bytes(nc) + max_staged * SLOT_BYTES;
+    const int b = tc_stage_bytes(nc, rd) + max_staged * SLOT_BYTES;
     return (b + 1023) & ~1023;
 }
 
@@ -1009,7 +1103,7 @@ constexpr int SMEM_LIMIT = 227 * 1024;
 
 int smem_for(int ns, int stage_bytes) { return ns * stage_bytes + (int)sizeof(Shared) + 1024; }
 
-template <int ELEM, int TERMS, int NC>
+template <int ELEM, int TERMS, int NC, bool RD>
 cudaError_t launch_one(const InstDev *d_inst, const TileDev *d_tiles, long long n_tiles, const unsigned *maxbits,
                        const uint8_t *psi, float2 *part, unsigned *counter, const TcConfig &cfg, int *status,
                        cudaStream_t s)
@@ -1025,7 +1119,7 @@ cudaError_t launch_one(const InstDev *d_inst, const TileDev *d_tiles, long long 
     kp.n_tiles = (int)n_tiles;
     kp.chunk_stages = (cfg.chunk_sites * 3) / KSTAGE;
     if (kp.chunk_stages < 1) kp.chunk_stages = 1;
-    kp.stage_bytes = stage_bytes_for(cfg.max_staged, NC);
+    kp.stage_bytes = stage_bytes_for(cfg.max_staged, NC, RD);
     kp.debug_stall = cfg.debug_stall;
     // deepest stage ring that fits
     kp.ns = 0;
@@ -1037,17 +1131,33 @@ cudaError_t launch_one(const InstDev *d_inst, const TileDev *d_tiles, long long 
     }
     if (!kp.ns) return cudaErrorNotSupported;
     const int smem = smem_for(kp.ns, kp.stage_bytes);
-    cudaError_t e = cudaFuncSetAttribute(tc_kernel<ELEM, TERMS, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(tc_kernel<ELEM, TERMS, NC, RD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int grid = cfg.grid > 0 ? cfg.grid : 148;
     if ((long long)grid > n_tiles) grid = (int)n_tiles;
-    tc_kernel<ELEM, TERMS, NC><<<grid, NTHREADS, smem, s>>>(kp);
+    tc_kernel<ELEM, TERMS, NC, RD><<<grid, NTHREADS, smem, s>>>(kp);
     return cudaGetLastError();
+}
+
+template <int NC, bool RD>
+void psi_launch(int elem, unsigned grid, const InstDev *d_inst, const PsiUnit *d_units, int n_units, long long n_jobs,
+                const unsigned *d_maxbits, uint8_t *psi, cudaStream_t s)
+{
+    if (elem == 0)
+        psi_kernel<0, NC, RD><<<grid, 2 * NC, 0, s>>>(d_inst, d_units, n_units, n_jobs, d_maxbits, psi);
+    else
+        psi_kernel<1, NC, RD><<<grid, 2 * NC, 0, s>>>(d_inst, d_units, n_units, n_jobs, d_maxbits, psi);
 }
 
 }  // namespace
 
-int tc_smem_bytes() { return smem_for(2, stage_bytes_for(TC_MAX_STAGED, TC_TC)); }
+int tc_smem_bytes() { return smem_for(2, stage_bytes_for(TC_MAX_STAGED, TC_TC, false)); }
+
+bool tc_shape_supported(int ncols, int rows2)
+{
+    return rows2 ? (ncols == 192 || ncols == 176 || ncols == 128) : (ncols == 96 || ncols == 64);
+}
 
 cudaError_t launch_tc(const InstDev *d_inst, const TileDev *d_tiles, long long n_tiles, const unsigned *d_maxbits,
                       const uint8_t *psi, float2 *part, unsigned *counter, const TcConfig &cfg, int *d_status,
@@ -1055,17 +1165,22 @@ cudaError_t launch_tc(const InstDev *d_inst, const TileDev *d_tiles, long long n
 {
     if (n_tiles <= 0) return cudaSuccess;
     if (n_tiles > 0x7fffffffLL || cfg.max_staged > TC_MAX_STAGED) return cudaErrorNotSupported;
-#define LAPH_TC_CASE(E, TM, NC)                                                                      \
-    if (cfg.elem == E && cfg.terms == TM && cfg.ncols == NC)                                         \
-        return launch_one<E, TM, NC>(d_inst, d_tiles, n_tiles, d_maxbits, psi, part, counter, cfg, d_status, s);
-    LAPH_TC_CASE(0, 3, 96)
-    LAPH_TC_CASE(1, 3, 96)
-    LAPH_TC_CASE(0, 1, 96)
-    LAPH_TC_CASE(1, 1, 96)
-    LAPH_TC_CASE(0, 3, 64)
-    LAPH_TC_CASE(1, 3, 64)
-    LAPH_TC_CASE(0, 1, 64)
-    LAPH_TC_CASE(1, 1, 64)
+#define LAPH_TC_CASE(NC, RD)                                                                                    \
+    if (cfg.ncols == NC && cfg.rows2 == (RD ? 1 : 0)) {                                                         \
+        if (cfg.elem == 0 && cfg.terms == 3)                                                                    \
+            return launch_one<0, 3, NC, RD>(d_inst, d_tiles, n_tiles, d_maxbits, psi, part, counter, cfg, d_status, s); \
+        if (cfg.elem == 1 && cfg.terms == 3)                                                                    \
+            return launch_one<1, 3, NC, RD>(d_inst, d_tiles, n_tiles, d_maxbits, psi, part, counter, cfg, d_status, s); \
+        if (cfg.elem == 0 && cfg.terms == 1)                                                                    \
+            return launch_one<0, 1, NC, RD>(d_inst, d_tiles, n_tiles, d_maxbits, psi, part, counter, cfg, d_status, s); \
+        if (cfg.elem == 1 && cfg.terms == 1)                                                                    \
+            return launch_one<1, 1, NC, RD>(d_inst, d_tiles, n_tiles, d_maxbits, psi, part, counter, cfg, d_status, s); \
+    }
+    LAPH_TC_CASE(96, false)
+    LAPH_TC_CASE(64, false)
+    LAPH_TC_CASE(192, true)
+    LAPH_TC_CASE(176, true)
+    LAPH_TC_CASE(128, true)
 #undef LAPH_TC_CASE
     return cudaErrorNotSupported;
 }
@@ -1080,18 +1195,20 @@ cudaError_t launch_reduce(const InstDev *d_inst, const PsiUnit *d_units, int n_u
 }
 
 cudaError_t launch_psi(const InstDev *d_inst, const PsiUnit *d_units, int n_units, long long n_jobs,
-                       const unsigned *d_maxbits, int elem, int ncols, uint8_t *psi, cudaStream_t s)
+                       const unsigned *d_maxbits, int elem, int ncols, int rows2, uint8_t *psi, cudaStream_t s)
 {
     if (n_jobs <= 0 || n_units <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)(n_jobs < (1LL << 20) ? n_jobs : (1LL << 20));
-    if (ncols == 96 && elem == 0)
-        psi_kernel<0, 96><<<grid, 192, 0, s>>>(d_inst, d_units, n_units, n_jobs, d_maxbits, psi);
-    else if (ncols == 96 && elem == 1)
-        psi_kernel<1, 96><<<grid, 192, 0, s>>>(d_inst, d_units, n_units, n_jobs, d_maxbits, psi);
-    else if (ncols == 64 && elem == 0)
-        psi_kernel<0, 64><<<grid, 128, 0, s>>>(d_inst, d_units, n_units, n_jobs, d_maxbits, psi);
-    else if (ncols == 64 && elem == 1)
-        psi_kernel<1, 64><<<grid, 128, 0, s>>>(d_inst, d_units, n_units, n_jobs, d_maxbits, psi);
+    if (!rows2 && ncols == 96)
+        psi_launch<96, false>(elem, grid, d_inst, d_units, n_units, n_jobs, d_maxbits, psi, s);
+    else if (!rows2 && ncols == 64)
+        psi_launch<64, false>(elem, grid, d_inst, d_units, n_units, n_jobs, d_maxbits, psi, s);
+    else if (rows2 && ncols == 192)
+        psi_launch<192, true>(elem, grid, d_inst, d_units, n_units, n_jobs, d_maxbits, psi, s);
+    else if (rows2 && ncols == 176)
+        psi_launch<176, true>(elem, grid, d_inst, d_units, n_units, n_jobs, d_maxbits, psi, s);
+    else if (rows2 && ncols == 128)
+        psi_launch<128, true>(elem, grid, d_inst, d_units, n_units, n_jobs, d_maxbits, psi, s);
     else
         return cudaErrorNotSupported;
     return cudaGetLastError();

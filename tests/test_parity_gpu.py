@@ -350,6 +350,68 @@ def test_64_column_tiles_match_oracle(laph, mode):
     plan.close()
 
 
+@pytest.mark.parametrize("mode", ["f16x3", "bf16x3", "f16"])
+@pytest.mark.parametrize("cols", [176, 192, 128])
+def test_row_doubled_layout_matches_oracle(laph, mode, cols):
+    """Layout 1 (two real A rows per complex row, 64 complex rows per tile, half-size B stage images): single
+    instances with several row tiles that mix meson and diquark rows, ragged column tails, skipped leading columns
+    and several site blocks, and a ragged batch in one plan."""
+    import torch
+    for L, T, N, mom, inst in [CASES[0], CASES[2], CASES[4], CASES[5]]:
+        phi_h = synth.random_phi(L, N, T=T, instance=inst)
+        plan = laph.Plan([(L, T, N, mom)], mode=mode, tile_cols=cols, layout=1)
+        d = plan.describe()
+        assert d["tile_cols"] == cols and d["tile_rows"] == 64
+        Bs, Ms = plan.alloc_outputs()
+        plan.execute([torch.from_numpy(phi_h).cuda()], Bs, Ms, plan.alloc_workspace())
+        torch.cuda.synchronize()
+        assert plan.device_status() == laph.LAPH_OK
+        rB, rM = _oracle(phi_h, L, mom)
+        eB, eM = rel_frob(Bs[0].cpu().numpy(), rB), rel_frob(Ms[0].cpu().numpy(), rM)
+        print(f"layout 1, {cols} columns, mode={mode} L={L} N={N}: rel B {eB:.2e} M {eM:.2e}")
+        assert eB <= tol_for(mode) and eM <= tol_for(mode)
+        plan.close()
+    specs = [(4, 2, 5, synth.momentum_shell(1)), (5, 3, 8, synth.momentum_shell(2)),
+             (3, 1, 20, np.array([[1, 1, 1], [0, 0, 0]], dtype=np.int32))]
+    plan = laph.Plan(specs, mode=mode, tile_cols=cols, layout=1)
+    phis_h = [synth.random_phi(L, N, T=T, instance=150 + n) for n, (L, T, N, _) in enumerate(specs)]
+    Bs, Ms = plan.alloc_outputs()
+    plan.execute([torch.from_numpy(p).cuda() for p in phis_h], Bs, Ms, plan.alloc_workspace())
+    torch.cuda.synchronize()
+    for n, (L, T, N, mom) in enumerate(specs):
+        rB, rM = _oracle(phis_h[n], L, mom)
+        assert rel_frob(Bs[n].cpu().numpy(), rB) <= tol_for(mode)
+        assert rel_frob(Ms[n].cpu().numpy(), rM) <= tol_for(mode)
+    plan.close()
+
+
+def test_row_doubled_layout_fields_and_projection(laph):
+    """Layout 1 on the several-field plans: three-field triplets and a projection of two vector counts against the
+    oracle."""
+    import torch
+    L, T, N = 4, 2, 9
+    mom = synth.momentum_shell(1)
+    f = [synth.random_phi(L, N, T=T, instance=160 + k, orthonormal=False) for k in range(3)]
+    plan = laph.Plan([(L, T, N, mom)], mode="f16x3", flags=laph.PLAN_FIELDS | laph.PLAN_SKIP_M, layout=1)
+    Bs, _ = plan.alloc_outputs()
+    plan.execute_fields([[torch.from_numpy(x).cuda() for x in f]], Bs, plan.alloc_workspace())
+    torch.cuda.synchronize()
+    for t in range(T):
+        ref = O.triplet_blocks(f[0][t], f[1][t], f[2][t], L, mom)
+        assert rel_frob(Bs[0][t].cpu().numpy(), ref) <= 1e-5
+    plan.close()
+    v = synth.random_phi(L, 7, T=T, instance=170, orthonormal=False)
+    sv = synth.random_phi(L, 30, T=T, instance=171, orthonormal=False)
+    plan = laph.Plan([(L, T, 7, np.zeros((1, 3), dtype=np.int32), 30)], mode="f16x3",
+                     flags=laph.PLAN_FIELDS | laph.PLAN_SKIP_B, layout=1, tile_cols=128)
+    _, Ms = plan.alloc_outputs()
+    plan.execute_fields([[torch.from_numpy(v).cuda(), torch.from_numpy(sv).cuda()]], Ms, plan.alloc_workspace())
+    torch.cuda.synchronize()
+    for t in range(T):
+        assert rel_frob(Ms[0][t].cpu().numpy(), O.projection(v[t], sv[t], L)) <= 1e-5
+    plan.close()
+
+
 def test_autotuned_plan_matches_oracle(laph):
     """PLAN_AUTOTUNE times candidate schedules at creation -- tile widths, tile orders, chunkings, site-block sizes
     and drain intervals, the last checked by the accuracy probe -- and keeps the fastest; the chosen schedule gives
@@ -362,7 +424,7 @@ def test_autotuned_plan_matches_oracle(laph):
     assert len(sch["candidate_ms"]) >= 2 and all(ms > 0 for ms in sch["candidate_ms"])
     assert sch["tile_order"] in (0, 1) and sch["n_chunks"] == plan.contraction_launches()
     rec = plan.tuning()
-    assert len(rec) >= 10 and {r["tile_cols"] for r in rec} == {64, 96}
+    assert len(rec) >= 10 and {(r["tile_cols"], r["layout"]) for r in rec} >= {(64, 0), (96, 0), (176, 1)}
     assert len({r["sum_sites"] for r in rec}) >= 2 and len({r["chunk_sites"] for r in rec}) >= 2
     probed = [r for r in rec if r["probe_err"] >= 0]
     assert len(probed) >= 2 and all(r["probe_err"] < 1e-4 for r in probed)
