@@ -289,8 +289,8 @@ typedef struct {
     int sum_sites;   /* tensor-core modes: sites per block of the FP64 site reduction (default 8192, rounded down
                         to a multiple of 8): a tile covers one block, its running sums become one FP32 partial per
                         output, and the partials of all blocks are added in FP64 in block order */
-    int tile_cols;   /* tensor-core modes: complex columns per tile: 96 (default) or 64 in layout 0; 176
-                        (default), 192 or 128 in layout 1 */
+    int tile_cols;   /* tensor-core modes: complex columns per tile: 96 (default), 80 or 64 in layout 0;
+                        176 (default), 192 or 128 in layout 1 */
     int layout;      /* tensor-core modes: how the complex product is laid out on the real tensor cores.
                         0 (default): every complex column of the phased operand is two real rows (re, im) of the
                         MMA's B operand, 128 complex rows per tile; 1: every complex row of the diquark / meson
@@ -411,7 +411,7 @@ typedef struct {
  * candidate schedules on seeded synthetic inputs of the plan's shapes
  * (pseudo-random entries in [-1, 1); inputs, outputs and a workspace are
  * allocated for the duration; one warm-up and one timed execute each) by a
- * coordinate search: tile shape (layout 0 with 96 and 64 columns, layout 1
+ * coordinate search: tile shape (layout 0 with 96, 80 and 64 columns, layout 1
  * with 176, 192 and 128 columns) x tile order x chunking
  * (the wave model and, for one instance, the largest chunk within the 24 GiB
  * cap); then, from the fastest, half and twice the site-block size of the

@@ -1046,7 +1046,8 @@ static int autotune(laph_plan *p, const laph::Sched &def, const std::function<cu
     {
         // 1: tile width x tile order x chunking (the largest chunk only for one instance)
         const bool one_inst = p->n_inst == 1 && !(p->flags & LAPH_PLAN_CHUNK_PER_TIMESLICE);
-        const std::pair<int, int> shapes[] = {{def.tile_cols, def.rows2}, {96, 0}, {64, 0}, {176, 1}, {192, 1}, {128, 1}};
+        const std::pair<int, int> shapes[] = {{def.tile_cols, def.rows2}, {96, 0}, {80, 0}, {64, 0},
+                                              {176, 1},           {192, 1}, {128, 1}};
         for (size_t k = 0; k < sizeof(shapes) / sizeof(shapes[0]); k++) {
             const int nc = shapes[k].first, r2 = shapes[k].second;
             if (k > 0 && nc == def.tile_cols && r2 == def.rows2) continue;

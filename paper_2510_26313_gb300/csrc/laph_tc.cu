@@ -1156,7 +1156,7 @@ int tc_smem_bytes() { return smem_for(2, stage_bytes_for(TC_MAX_STAGED, TC_TC, f
 
 bool tc_shape_supported(int ncols, int rows2)
 {
-    return rows2 ? (ncols == 192 || ncols == 176 || ncols == 128) : (ncols == 96 || ncols == 64);
+    return rows2 ? (ncols == 192 || ncols == 176 || ncols == 128) : (ncols == 96 || ncols == 80 || ncols == 64);
 }
 
 cudaError_t launch_tc(const InstDev *d_inst, const TileDev *d_tiles, long long n_tiles, const unsigned *d_maxbits,
@@ -1177,6 +1177,7 @@ cudaError_t launch_tc(const InstDev *d_inst, const TileDev *d_tiles, long long n
             return launch_one<1, 1, NC, RD>(d_inst, d_tiles, n_tiles, d_maxbits, psi, part, counter, cfg, d_status, s); \
     }
     LAPH_TC_CASE(96, false)
+    LAPH_TC_CASE(80, false)
     LAPH_TC_CASE(64, false)
     LAPH_TC_CASE(192, true)
     LAPH_TC_CASE(176, true)
@@ -1201,6 +1202,8 @@ cudaError_t launch_psi(const InstDev *d_inst, const PsiUnit *d_units, int n_unit
     const unsigned grid = (unsigned)(n_jobs < (1LL << 20) ? n_jobs : (1LL << 20));
     if (!rows2 && ncols == 96)
         psi_launch<96, false>(elem, grid, d_inst, d_units, n_units, n_jobs, d_maxbits, psi, s);
+    else if (!rows2 && ncols == 80)
+        psi_launch<80, false>(elem, grid, d_inst, d_units, n_units, n_jobs, d_maxbits, psi, s);
     else if (!rows2 && ncols == 64)
         psi_launch<64, false>(elem, grid, d_inst, d_units, n_units, n_jobs, d_maxbits, psi, s);
     else if (rows2 && ncols == 192)
