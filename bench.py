@@ -42,10 +42,10 @@ WORKLOADS = {
 METRIC = "baryon+meson block complex TFLOP/s at L=32,N=64,Np=19; tensor-pipe %; rel err vs FP64"
 
 # DRAM bytes (read + write) of tc_kernel per byte of B-operand stage images it consumes, from the ncu capture
-# summarised in profiles/tc_kernel_L24_T2_N64_P19_full.md (2.013 GB of DRAM traffic for 2 x 13 x 1728 stage images
+# summarised in profiles/tc_kernel_L24_T2_N64_P19_full.md (2.004 GB of DRAM traffic for 2 x 13 x 1728 stage images
 # of 36,864 B); the contraction's DRAM traffic is dominated by those images, so a launch's traffic is this ratio times
 # its image bytes.  To be retaken whenever the kernel changes.
-TC_DRAM_PER_IMAGE_BYTE = 2.013e9 / (2 * 13 * 1728 * 36864)
+TC_DRAM_PER_IMAGE_BYTE = 2.004e9 / (2 * 13 * 1728 * 36864)
 
 
 def momenta_for(name):

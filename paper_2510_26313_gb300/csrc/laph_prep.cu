@@ -402,15 +402,30 @@ __global__ void __launch_bounds__(256) dense_fill_kernel(const double2 *__restri
     const double2 *pk = packed + tp * n_trip;
     double2 *row = dense + (tp * N + a) * (long long)N * N;
     const int nn = N * N;
-#pragma unroll 4
-    for (int r = threadIdx.x; r < nn; r += 256) {
-        const int b = r / N, c = r - b * N;
-        const int lo = min(a, min(b, c)), hi = max(a, max(b, c)), mid = a + b + c - lo - hi;
-        const bool neg = (b < a) ^ (c < a) ^ (c < b);
-        const bool rep = (a == b) | (b == c) | (a == c);
-        const long long idx = binom3(hi) + binom2(mid) + lo;
-        const double2 w = rep ? make_double2(0.0, 0.0) : __ldg(pk + idx);
-        row[r] = (neg && !rep) ? make_double2(-w.x, -w.y) : w;
+    // eight gathers per thread are issued before their stores, so that enough
+    // of the (L2-resident) packed loads are in flight to keep the writes streaming
+    constexpr int BATCH = 8;
+    for (int r0 = 0; r0 < nn; r0 += 256 * BATCH) {
+        double2 w[BATCH];
+        bool neg[BATCH];
+#pragma unroll
+        for (int q = 0; q < BATCH; q++) {
+            const int r = r0 + q * 256 + threadIdx.x;
+            w[q] = make_double2(0.0, 0.0);
+            neg[q] = false;
+            if (r < nn) {
+                const int b = r / N, c = r - b * N;
+                const int lo = min(a, min(b, c)), hi = max(a, max(b, c)), mid = a + b + c - lo - hi;
+                const bool rep = (a == b) | (b == c) | (a == c);
+                neg[q] = !rep && ((b < a) ^ (c < a) ^ (c < b));   // repeated indices give +0
+                if (!rep) w[q] = __ldg(pk + binom3(hi) + binom2(mid) + lo);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < BATCH; q++) {
+            const int r = r0 + q * 256 + threadIdx.x;
+            if (r < nn) row[r] = neg[q] ? make_double2(-w[q].x, -w[q].y) : w[q];
+        }
     }
 }
 

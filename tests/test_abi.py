@@ -91,6 +91,23 @@ def test_plan_create_rejects_bad_arguments_before_touching_cuda(lib):
         assert lib.laph_plan_create(arr, 1, 1, flags, ctypes.byref(h)) == binding.LAPH_ERR_ARG
 
 
+def test_plan_options_are_checked_before_touching_cuda(lib):
+    """laph_plan_create_opts refuses negative or oversized drain intervals and site blocks, tile widths without a
+    compiled kernel and unknown layouts, before any CUDA call."""
+    from paper_2510_26313_gb300 import binding
+    mom = (ctypes.c_int32 * 3)(0, 0, 0)
+    h = ctypes.c_void_p()
+    arr = (binding.laph_instance * 1)(binding.laph_instance(4, 1, 8, 1, mom))
+    for opts in [binding.laph_plan_options(-1, 0, 0, 0), binding.laph_plan_options(0, -8, 0, 0),
+                 binding.laph_plan_options(1 << 25, 0, 0, 0), binding.laph_plan_options(0, 0, 72, 0),
+                 binding.laph_plan_options(0, 0, 176, 0), binding.laph_plan_options(0, 0, 96, 1),
+                 binding.laph_plan_options(0, 0, 0, 2), binding.laph_plan_options(0, 0, 0, -1)]:
+        assert lib.laph_plan_create_opts(arr, 1, 1, 0, ctypes.byref(opts), ctypes.byref(h)) == binding.LAPH_ERR_ARG
+    assert lib.laph_plan_tuning(None, 0, None, None) == binding.LAPH_ERR_ARG
+    assert lib.laph_plan_sum_sites(None, None, None) == binding.LAPH_ERR_ARG
+    assert lib.laph_plan_tensor_flops(None, None) == binding.LAPH_ERR_ARG
+
+
 def test_entry_points_reject_null_pointers(lib):
     from paper_2510_26313_gb300 import binding
     mom = (ctypes.c_int32 * 3)(0, 0, 0)

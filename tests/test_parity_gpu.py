@@ -127,7 +127,8 @@ def test_dense_fill_is_exact(laph):
         (T, P, N * (N - 1) * (N - 2) // 6))
     dense = laph.baryon_dense(torch.from_numpy(packed).cuda(), N).cpu().numpy()
     for t in range(T):
-        assert np.array_equal(dense[t], O.baryon_dense(packed[t], N))
+        ref = O.baryon_dense(packed[t], N)
+        assert np.array_equal(dense[t].view(np.uint64), ref.view(np.uint64))   # bit for bit, signed zeros included
 
 
 def test_plan_ragged_batch_matches_oracle(laph):
@@ -410,6 +411,38 @@ def test_row_doubled_layout_fields_and_projection(laph):
     for t in range(T):
         assert rel_frob(Ms[0][t].cpu().numpy(), O.projection(v[t], sv[t], L)) <= 1e-5
     plan.close()
+
+
+@pytest.mark.parametrize("mode", ALL_MODES)
+def test_degenerate_lattices_and_minimal_shapes(laph, mode):
+    """L = 1 (one site: every momentum phase is 1, one site block), L = 2 with N = 3V = 24 (a complete basis), and N = 3
+    (a single triple): every mode against the oracle."""
+    for L, N, mom, inst in [(1, 3, np.array([[0, 0, 0], [1, 0, 0]], dtype=np.int32), 180),
+                            (2, 24, synth.momentum_shell(1), 181), (3, 3, synth.momentum_shell(2), 182)]:
+        phi_h = synth.random_phi(L, N, T=2, instance=inst)
+        B, M = _run(laph, phi_h, L, mom, mode)
+        rB, rM = _oracle(phi_h, L, mom)
+        tol = tol_for(mode)
+        assert rel_frob(B, rB) <= tol and rel_frob(M, rM) <= tol, (L, N, mode)
+
+
+def test_many_vectors_beyond_the_staging_limit(laph):
+    """N = 200 vectors: the tensor-core path cannot stage a tile's row vectors (more than 160) and says so with
+    LAPH_ERR_UNSUPPORTED at plan creation; the FP32 path computes the blocks, checked against the oracle on sampled
+    triples and on whole meson blocks."""
+    import torch
+    L, N = 4, 180
+    mom = synth.momentum_shell(1)
+    with pytest.raises(laph.LaphError) as e:
+        laph.Plan([(L, 1, N, mom)], mode="f16x3")
+    assert e.value.status == laph.LAPH_ERR_UNSUPPORTED
+    phi_h = synth.random_phi(L, N, T=1, instance=183)
+    phi = torch.from_numpy(phi_h).cuda()
+    B = laph.baryon_blocks(phi, L, mom, mode="fp32").cpu().numpy()
+    M = laph.meson_blocks(phi, L, mom, mode="fp32").cpu().numpy()
+    trip, idx = _sampled_triples(N, 300, 9)
+    assert rel_frob(B[0][:, idx].T, O.baryon_triples(phi_h[0], L, mom, trip)) <= 1e-5
+    assert rel_frob(M[0], O.meson_blocks(phi_h[0], L, mom)) <= 1e-5
 
 
 def test_autotuned_plan_matches_oracle(laph):
