@@ -413,6 +413,38 @@ def test_row_doubled_layout_fields_and_projection(laph):
     plan.close()
 
 
+def test_row_doubled_layout_in_a_cuda_graph_with_host_buffers_and_chunks(laph):
+    """Layout 1 through the other execution paths: a plan captured in a CUDA graph and replayed, one timeslice per
+    chunk (several B-operand passes, contractions and FP64 reductions per execute), and the host-buffer execute."""
+    import torch
+    L, T, N = 6, 3, 12
+    mom = synth.momentum_shell(1)
+    phi_h = synth.random_phi(L, N, T=T, instance=190)
+    rB, rM = _oracle(phi_h, L, mom)
+    for flags in (0, laph.PLAN_CHUNK_PER_TIMESLICE):
+        plan = laph.Plan([(L, T, N, mom)], mode="f16x3", flags=flags, layout=1, sum_sites=64)
+        assert plan.sum_sites()[1] >= 2                        # several site blocks per output
+        phi = torch.from_numpy(phi_h).cuda()
+        Bs, Ms = plan.alloc_outputs()
+        ws = plan.alloc_workspace()
+        s = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            plan.execute([phi], Bs, Ms, ws, stream=s)
+        Bs[0].zero_()
+        Ms[0].zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert rel_frob(Bs[0].cpu().numpy(), rB) <= 1e-5 and rel_frob(Ms[0].cpu().numpy(), rM) <= 1e-5
+        hws = torch.empty(plan.host_workspace_size(), dtype=torch.uint8, device="cuda")
+        Bh = np.zeros((T, len(mom), N * (N - 1) * (N - 2) // 6), dtype=np.complex128)
+        Mh = np.zeros((T, len(mom), N, N), dtype=np.complex128)
+        plan.execute_host([phi_h], [Bh], [Mh], hws)
+        assert rel_frob(Bh, rB) <= 1e-5 and rel_frob(Mh, rM) <= 1e-5
+        plan.close()
+
+
 @pytest.mark.parametrize("mode", ALL_MODES)
 def test_degenerate_lattices_and_minimal_shapes(laph, mode):
     """L = 1 (one site: every momentum phase is 1, one site block), L = 2 with N = 3V = 24 (a complete basis), and N = 3
