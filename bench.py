@@ -799,7 +799,7 @@ def main():
     ap.add_argument("--workload", default="metric", choices=sorted(WORKLOADS) + ["ragged", "triplets", "projection", "large"] + sorted(LANCZOS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--ref-triples", type=int, default=6000)
     ap.add_argument("--chunk-sites", type=int, default=0)
     ap.add_argument("--sum-sites", type=int, default=0)
@@ -1016,16 +1016,24 @@ def main():
         plan.execute_host([phi_pin], Bh, Mh, hws, stream=stream)   # warm-up
         if world > 1:
             dist.barrier()
+        clocks_e2e = ClockSampler(local)
+        clocks_e2e.start()
+        step_ms = []
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            plan.execute_host([phi_pin], Bh, Mh, hws, stream=stream)
+            t1 = time.perf_counter()
+            plan.execute_host([phi_pin], Bh, Mh, hws, stream=stream)   # returns after its copies out
+            step_ms.append(1e3 * (time.perf_counter() - t1))
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        clk_e2e = clocks_e2e.stop()
         e2e_s = max_over_ranks(e2e_s, "cuda")
         e2e = {"value": weak_scaling_value(flops_step, 1e3 * e2e_s, world), "unit": "TFLOP/s",
                "h2d_bytes_per_step": int(phi_pin.numel() * 8),
                "d2h_bytes_per_step": int(Bh[0].numel() * 16 + Mh[0].numel() * 16),
-               "ms_per_step": 1e3 * e2e_s, "pinned_copy_rates": pinned_copy_rates()}
+               "ms_per_step": 1e3 * e2e_s, "step_ms": [round(x, 2) for x in step_ms],
+               "median_step_ms": statistics.median(step_ms), "clocks": clk_e2e,
+               "pinned_copy_rates": pinned_copy_rates()}
 
     if rank == 0:
         line = {

@@ -13,7 +13,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/laph.h"
+#include "laph.h"
 #include "laph_internal.cuh"
 
 using laph::InstDev;
@@ -898,8 +898,9 @@ static int ring_times(const std::vector<cudaEvent_t> &b, const std::vector<cudaE
 // on seeded synthetic inputs of the plan's shapes (pseudo-random entries in
 // [-1, 1), outputs and a workspace allocated for the duration): one warm-up
 // execute and one timed execute on an internal stream.  The search is by
-// coordinates: tile width (96, 64 columns) x tile order x chunking (the wave
-// model, the largest chunk within the cap), then the site-block size of the
+// coordinates: tile shape (layout 0 at 96, 80 and 64 columns, layout 1 at
+// 176, 192 and 128 columns) x tile order x chunking (the wave model, the
+// largest chunk within the cap), then the site-block size of the
 // FP64 reduction (half and twice the default), then the drain interval of the
 // tensor core's accumulation (half and one and a half times the default).
 // A drain interval is kept only if the error of (instance 0, timeslice 0)
@@ -1281,9 +1282,11 @@ int laph_plan_execute_host(laph_plan *plan, const void *const *phi_host, void *c
         return LAPH_OK;
     }
 
-    // tensor-core path, chunk by chunk: the inputs of chunk c are copied in on
-    // one stream while chunk c-1 computes, and its outputs are copied out on a
-    // second stream while chunk c+1 computes
+    // tensor-core path, chunk by chunk: the inputs of every chunk are queued
+    // on one copy stream up front (chunk c lands while chunk c-1 computes), and
+    // the outputs of chunk c are copied out on a second stream while chunk c+1
+    // computes.  The inputs go first so that no copy in of a later chunk is
+    // queued behind a copy out that waits for an earlier chunk's results.
     const size_t nc = plan->chunks.size();
     if (!plan->h2d) {
         CK(cudaStreamCreateWithFlags(&plan->h2d, cudaStreamNonBlocking));
@@ -1311,6 +1314,9 @@ int laph_plan_execute_host(laph_plan *plan, const void *const *phi_host, void *c
                                cudaMemcpyHostToDevice, plan->h2d));
         }
         CK(cudaEventRecord(plan->ev_in[ci], plan->h2d));
+    }
+    for (size_t ci = 0; ci < nc; ci++) {
+        const laph_plan::Chunk &c = plan->chunks[ci];
         CK(cudaStreamWaitEvent(s, plan->ev_in[ci], 0));
         int rc = launch_chunk_prep(plan, ws, ci, s);
         if (rc == LAPH_OK) rc = launch_tc_chunk(plan, ws, ci, cfg, s);

@@ -23,7 +23,7 @@
 #include <mutex>
 #include <vector>
 
-#include "../../include/laph.h"
+#include "laph.h"
 #include "laph_internal.cuh"
 
 namespace laph {
