@@ -72,7 +72,8 @@ extern "C" {
 /* tcgen05 tensor cores, each operand split into hi+lo FP16 after an exact
  * power-of-two rescale; products hi*hi + hi*lo + lo*hi accumulated in FP32 in
  * tensor memory, drained every 128 sites (the plan's chunk_sites) into FP32
- * running sums with round-to-nearest over a block of 4096 sites; the FP32
+ * running sums with round-to-nearest over a block of sites (the plan's
+ * sum_sites, 8192 by default); the FP32
  * partials of the blocks are then summed in FP64, in block order, and
  * scaled back into the complex128 output. */
 #define LAPH_MODE_TC_F16X3 1
@@ -289,8 +290,8 @@ typedef struct {
     int sum_sites;   /* tensor-core modes: sites per block of the FP64 site reduction (default 8192, rounded down
                         to a multiple of 8): a tile covers one block, its running sums become one FP32 partial per
                         output, and the partials of all blocks are added in FP64 in block order */
-    int tile_cols;   /* tensor-core modes: complex columns per tile: 96 (default), 80 or 64 in layout 0;
-                        176 (default), 192 or 128 in layout 1 */
+    int tile_cols;   /* tensor-core modes: complex columns per tile: 104 (default), 96, 80 or 64 in layout 0;
+                        176 (default), 192, 208 or 128 in layout 1 */
     int layout;      /* tensor-core modes: how the complex product is laid out on the real tensor cores.
                         0 (default): every complex column of the phased operand is two real rows (re, im) of the
                         MMA's B operand, 128 complex rows per tile; 1: every complex row of the diquark / meson
@@ -299,8 +300,9 @@ typedef struct {
 } laph_plan_options;
 
 /* laph_plan_create with numerical parameters (opts may be NULL).  LAPH_ERR_ARG
- * for a negative value or one above 2^24, a tile width other than 0, 64 or
- * 96, plus the conditions of laph_plan_create.  With LAPH_PLAN_AUTOTUNE the
+ * for a negative value or one above 2^24, a tile width other than 0 or one
+ * listed for the layout above, a layout other than 0 or 1, plus the
+ * conditions of laph_plan_create.  With LAPH_PLAN_AUTOTUNE the
  * options are the starting point of the search (see laph_plan_tuning). */
 LAPH_API int laph_plan_create_opts(const laph_instance *inst, int n_inst, int mode, unsigned flags,
                                    const laph_plan_options *opts, laph_plan **plan);
@@ -411,8 +413,8 @@ typedef struct {
  * candidate schedules on seeded synthetic inputs of the plan's shapes
  * (pseudo-random entries in [-1, 1); inputs, outputs and a workspace are
  * allocated for the duration; one warm-up and one timed execute each) by a
- * coordinate search: tile shape (layout 0 with 96, 80 and 64 columns, layout 1
- * with 176, 192 and 128 columns) x tile order x chunking
+ * coordinate search: tile shape (layout 0 with 104, 96, 80 and 64 columns, layout 1
+ * with 176, 192, 208 and 128 columns) x tile order x chunking
  * (the wave model and, for one instance, the largest chunk within the 24 GiB
  * cap); then, from the fastest, half and twice the site-block size of the
  * FP64 reduction; then half and 1.5 times the drain interval.  A drain

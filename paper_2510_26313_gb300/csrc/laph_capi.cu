@@ -661,9 +661,17 @@ int laph_plan_create_opts(const laph_instance *inst, int n_inst, int mode, unsig
         return upload();
     };
     const int opt_cols = opts ? opts->tile_cols : 0, opt_layout = opts ? opts->layout : 0;
-    const laph::Sched def{opt_cols ? opt_cols : (opt_layout ? 176 : laph::TC_TC),
-                          opt_sum ? opt_sum : TC_DEFAULT_SUM, p->chunk_sites, -1, 0, opt_layout};
+    laph::Sched def{opt_cols ? opt_cols : (opt_layout ? 176 : laph::TC_TC),
+                    opt_sum ? opt_sum : TC_DEFAULT_SUM, p->chunk_sites, -1, 0, opt_layout};
     PCK(apply(def));
+    // the default width is the widest whose stage ring stays 4 deep for the
+    // plan's row vectors (the staged vectors depend on the row tiles only):
+    // a shallower ring costs more than the wider tile gains
+    if (tc && !opt_cols && !opt_layout && laph::tc_ring_depth(p->max_staged, def.tile_cols, 0) < 4 &&
+        laph::tc_ring_depth(p->max_staged, 96, 0) > laph::tc_ring_depth(p->max_staged, def.tile_cols, 0)) {
+        def.tile_cols = 96;
+        PCK(apply(def));
+    }
     if (tc && p->max_staged > laph::TC_MAX_STAGED) {
         free_plan(p);
         return LAPH_ERR_UNSUPPORTED;
@@ -898,8 +906,8 @@ static int ring_times(const std::vector<cudaEvent_t> &b, const std::vector<cudaE
 // on seeded synthetic inputs of the plan's shapes (pseudo-random entries in
 // [-1, 1), outputs and a workspace allocated for the duration): one warm-up
 // execute and one timed execute on an internal stream.  The search is by
-// coordinates: tile shape (layout 0 at 96, 80 and 64 columns, layout 1 at
-// 176, 192 and 128 columns) x tile order x chunking (the wave model, the
+// coordinates: tile shape (layout 0 at 104, 96, 80 and 64 columns, layout 1 at
+// 176, 192, 208 and 128 columns) x tile order x chunking (the wave model, the
 // largest chunk within the cap), then the site-block size of the
 // FP64 reduction (half and twice the default), then the drain interval of the
 // tensor core's accumulation (half and one and a half times the default).
@@ -1047,8 +1055,8 @@ static int autotune(laph_plan *p, const laph::Sched &def, const std::function<cu
     {
         // 1: tile width x tile order x chunking (the largest chunk only for one instance)
         const bool one_inst = p->n_inst == 1 && !(p->flags & LAPH_PLAN_CHUNK_PER_TIMESLICE);
-        const std::pair<int, int> shapes[] = {{def.tile_cols, def.rows2}, {96, 0}, {80, 0}, {64, 0},
-                                              {176, 1},           {192, 1}, {128, 1}};
+        const std::pair<int, int> shapes[] = {{def.tile_cols, def.rows2}, {104, 0}, {96, 0},  {80, 0}, {64, 0},
+                                              {176, 1},           {192, 1}, {208, 1}, {128, 1}};
         for (size_t k = 0; k < sizeof(shapes) / sizeof(shapes[0]); k++) {
             const int nc = shapes[k].first, r2 = shapes[k].second;
             if (k > 0 && nc == def.tile_cols && r2 == def.rows2) continue;

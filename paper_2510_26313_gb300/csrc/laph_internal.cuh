@@ -197,7 +197,7 @@ struct TcConfig {
     int debug_stall;   // test hook
 };
 constexpr int TC_TR = 128;   // tile rows (UMMA M)
-constexpr int TC_TC = 96;    // default tile columns (complex), UMMA N = 2 * TC_TC real; 64 is the other width
+constexpr int TC_TC = 104;   // default tile columns (complex), UMMA N = 2 * TC_TC real (the widest that fits)
 constexpr int TC_KSTAGE = 3 * TC_BS;  // complex K entries per stage: one site block
 // One B stage image of a tile of nc complex columns: hi + lo, 2 nc real rows
 // (nc in the row-doubled layout) x 48 FP16 each.
@@ -223,5 +223,8 @@ constexpr int TC_RED_BLOCK = 1024;
 cudaError_t launch_reduce(const InstDev *d_inst, const PsiUnit *d_units, int n_units, long long n_blocks,
                           const unsigned *d_maxbits, const float2 *part, cudaStream_t s);
 int tc_smem_bytes();
+// Stages in the contraction's shared-memory ring for tiles staging up to
+// max_staged row vectors (0: none fits).
+int tc_ring_depth(int max_staged, int ncols, int rows2);
 
 }  // namespace laph

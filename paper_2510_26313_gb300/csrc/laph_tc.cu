@@ -24,10 +24,12 @@
 // of the accumulator are issued and committed separately, so that the drain
 // of one half overlaps the MMAs of the other.
 //
-// Tile: 128 rows x 96 complex columns (UMMA M = 128, N = 192).  A K stage is
-// one site block: TC_BS = 8 sites = 24 complex = 48 real K entries, three
-// MMA k-steps of 16.  Tensor memory (512 columns): ACC [0,192) |
-// SUM [192,384) | two A slots of 64 (hi in 24 columns, lo in the next 24).
+// Tile: 128 rows x 104 complex columns by default (UMMA M = 128, N = 208, the
+// widest that fits; 96, 80 and 64 columns, and 64 rows x 208, 192, 176 or
+// 128 columns in the row-doubled layout, are the other shapes).  A K stage is one site block:
+// TC_BS = 8 sites = 24 complex = 48 real K entries, three MMA k-steps of 16.
+// Tensor memory (512 columns): ACC [0,N) | SUM [N,2N) | two A slots of 48
+// from column 416 (hi in 24 columns, lo in the next 24).
 //
 // The B operand does not depend on the row tile, so psi_kernel builds it
 // once per (timeslice, column tile): a memory-bound pass that writes every
@@ -73,8 +75,8 @@ constexpr int TRING = 4;                              // tile ring entries
 constexpr int N_TILE_READERS = N_AWARPS + 4 + 1;     // A producers, epilogue, MMA
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t ACC_COL = 0;
-constexpr uint32_t A_COL = 384;
-constexpr uint32_t A_SLOT_COLS = 64;
+constexpr uint32_t A_COL = 416;
+constexpr uint32_t A_SLOT_COLS = 48;
 constexpr uint32_t A_LO = KSTAGE;                     // lo columns follow the 24 hi columns
 constexpr long long WAIT_LIMIT = 4000000000LL;        // cycles (about 2 s at the top clock)
 
@@ -88,7 +90,7 @@ static_assert(A_LO + KSTAGE <= A_SLOT_COLS && A_COL + 2 * A_SLOT_COLS == TMEM_CO
 // every complex row is two real A rows (tensor-memory lanes 2r, 2r+1), UMMA
 // N = NC, and a tile has 64 complex rows.  Tensor memory: the accumulator in
 // columns [0, B_ROWS), the FP32 running sums in [B_ROWS, 2 B_ROWS), the two
-// A slots from column 384.
+// A slots from column 416.
 template <int NC, bool RD>
 struct Shape {
     static constexpr int B_ROWS = RD ? NC : 2 * NC;        // real B rows per tile (UMMA N)
@@ -96,7 +98,7 @@ struct Shape {
     static constexpr int B_BYTES = KSTEPS * ATOM_COL_BYTES;     // hi (or lo) of one stage
     static constexpr int BIMG_BYTES = 2 * B_BYTES;              // hi + lo
     static constexpr uint32_t SUM_COL = B_ROWS;
-    static_assert(B_ROWS % 16 == 0 && B_ROWS <= 192 && 2 * B_ROWS <= (int)A_COL,
+    static_assert(B_ROWS % 16 == 0 && B_ROWS <= 208 && 2 * B_ROWS <= (int)A_COL,
                   "tile width within the tensor-memory budget");
     static_assert(BIMG_BYTES == tc_stage_bytes(NC, RD), "stage image size");
 };
@@ -1121,14 +1123,7 @@ cudaError_t launch_one(const InstDev *d_inst, const TileDev *d_tiles, long long 
     if (kp.chunk_stages < 1) kp.chunk_stages = 1;
     kp.stage_bytes = stage_bytes_for(cfg.max_staged, NC, RD);
     kp.debug_stall = cfg.debug_stall;
-    // deepest stage ring that fits
-    kp.ns = 0;
-    for (int ns = MAX_NS; ns >= 2; ns--) {
-        if (smem_for(ns, kp.stage_bytes) <= SMEM_LIMIT) {
-            kp.ns = ns;
-            break;
-        }
-    }
+    kp.ns = tc_ring_depth(cfg.max_staged, NC, RD);   // deepest stage ring that fits
     if (!kp.ns) return cudaErrorNotSupported;
     const int smem = smem_for(kp.ns, kp.stage_bytes);
     cudaError_t e =
@@ -1154,9 +1149,18 @@ void psi_launch(int elem, unsigned grid, const InstDev *d_inst, const PsiUnit *d
 
 int tc_smem_bytes() { return smem_for(2, stage_bytes_for(TC_MAX_STAGED, TC_TC, false)); }
 
+int tc_ring_depth(int max_staged, int ncols, int rows2)
+{
+    const int sb = stage_bytes_for(max_staged, ncols, rows2 != 0);
+    for (int ns = MAX_NS; ns >= 2; ns--)
+        if (smem_for(ns, sb) <= SMEM_LIMIT) return ns;
+    return 0;
+}
+
 bool tc_shape_supported(int ncols, int rows2)
 {
-    return rows2 ? (ncols == 192 || ncols == 176 || ncols == 128) : (ncols == 96 || ncols == 80 || ncols == 64);
+    return rows2 ? (ncols == 208 || ncols == 192 || ncols == 176 || ncols == 128)
+                 : (ncols == 104 || ncols == 96 || ncols == 80 || ncols == 64);
 }
 
 cudaError_t launch_tc(const InstDev *d_inst, const TileDev *d_tiles, long long n_tiles, const unsigned *d_maxbits,
@@ -1176,9 +1180,11 @@ cudaError_t launch_tc(const InstDev *d_inst, const TileDev *d_tiles, long long n
         if (cfg.elem == 1 && cfg.terms == 1)                                                                    \
             return launch_one<1, 1, NC, RD>(d_inst, d_tiles, n_tiles, d_maxbits, psi, part, counter, cfg, d_status, s); \
     }
+    LAPH_TC_CASE(104, false)
     LAPH_TC_CASE(96, false)
     LAPH_TC_CASE(80, false)
     LAPH_TC_CASE(64, false)
+    LAPH_TC_CASE(208, true)
     LAPH_TC_CASE(192, true)
     LAPH_TC_CASE(176, true)
     LAPH_TC_CASE(128, true)
@@ -1200,12 +1206,16 @@ cudaError_t launch_psi(const InstDev *d_inst, const PsiUnit *d_units, int n_unit
 {
     if (n_jobs <= 0 || n_units <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)(n_jobs < (1LL << 20) ? n_jobs : (1LL << 20));
-    if (!rows2 && ncols == 96)
+    if (!rows2 && ncols == 104)
+        psi_launch<104, false>(elem, grid, d_inst, d_units, n_units, n_jobs, d_maxbits, psi, s);
+    else if (!rows2 && ncols == 96)
         psi_launch<96, false>(elem, grid, d_inst, d_units, n_units, n_jobs, d_maxbits, psi, s);
     else if (!rows2 && ncols == 80)
         psi_launch<80, false>(elem, grid, d_inst, d_units, n_units, n_jobs, d_maxbits, psi, s);
     else if (!rows2 && ncols == 64)
         psi_launch<64, false>(elem, grid, d_inst, d_units, n_units, n_jobs, d_maxbits, psi, s);
+    else if (rows2 && ncols == 208)
+        psi_launch<208, true>(elem, grid, d_inst, d_units, n_units, n_jobs, d_maxbits, psi, s);
     else if (rows2 && ncols == 192)
         psi_launch<192, true>(elem, grid, d_inst, d_units, n_units, n_jobs, d_maxbits, psi, s);
     else if (rows2 && ncols == 176)

@@ -318,15 +318,30 @@ def test_large_streamed_shape_sampled_parity(laph):
     plan.close()
 
 
+def test_default_tile_width_keeps_a_four_deep_stage_ring(laph):
+    """The default tile is 104 columns wide unless the row vectors a tile stages would then leave a stage ring shallower
+    than four buffers (about N > 80 at 128 rows), where it is 96; an explicit width or layout is kept."""
+    mom = synth.momentum_shell(1)
+    for N, cols in [(64, 104), (40, 104), (96, 96)]:
+        plan = laph.Plan([(4, 1, N, mom)], mode="f16x3")
+        assert plan.describe()["tile_cols"] == cols, (N, plan.describe())
+        plan.close()
+    plan = laph.Plan([(4, 1, 96, mom)], mode="f16x3", tile_cols=104)
+    assert plan.describe()["tile_cols"] == 104
+    plan.close()
+
+
 @pytest.mark.parametrize("mode", ["f16x3", "bf16x3", "f16"])
-def test_64_column_tiles_match_oracle(laph, mode):
-    """Tiles of 64 complex columns (UMMA N = 128): single instances with ragged column tails and several site
-    blocks, and a ragged batch in one plan."""
+@pytest.mark.parametrize("cols", [64, 80, 104])
+def test_other_column_widths_match_oracle(laph, mode, cols):
+    """Tiles of 64, 80 and 104 complex columns (UMMA N = 128, 160 and 208; at 208 the accumulator and the running
+    sums fill tensor memory up to the A slots): single instances with ragged column tails and several site blocks,
+    and a ragged batch in one plan."""
     import torch
     for L, T, N, mom, inst in [CASES[2], CASES[4], CASES[5]]:
         phi_h = synth.random_phi(L, N, T=T, instance=inst)
-        plan = laph.Plan([(L, T, N, mom)], mode=mode, tile_cols=64)
-        assert plan.describe()["tile_cols"] == 64
+        plan = laph.Plan([(L, T, N, mom)], mode=mode, tile_cols=cols)
+        assert plan.describe()["tile_cols"] == cols
         Bs, Ms = plan.alloc_outputs()
         ws = plan.alloc_workspace()
         plan.execute([torch.from_numpy(phi_h).cuda()], Bs, Ms, ws)
@@ -334,12 +349,12 @@ def test_64_column_tiles_match_oracle(laph, mode):
         assert plan.device_status() == laph.LAPH_OK
         rB, rM = _oracle(phi_h, L, mom)
         eB, eM = rel_frob(Bs[0].cpu().numpy(), rB), rel_frob(Ms[0].cpu().numpy(), rM)
-        print(f"64 columns mode={mode} L={L} N={N}: rel B {eB:.2e} M {eM:.2e}")
+        print(f"{cols} columns mode={mode} L={L} N={N}: rel B {eB:.2e} M {eM:.2e}")
         assert eB <= tol_for(mode) and eM <= tol_for(mode)
         plan.close()
     specs = [(4, 2, 5, synth.momentum_shell(1)), (5, 3, 8, synth.momentum_shell(2)),
              (3, 1, 20, np.array([[1, 1, 1], [0, 0, 0]], dtype=np.int32))]
-    plan = laph.Plan(specs, mode=mode, tile_cols=64)
+    plan = laph.Plan(specs, mode=mode, tile_cols=cols)
     phis_h = [synth.random_phi(L, N, T=T, instance=140 + n) for n, (L, T, N, _) in enumerate(specs)]
     Bs, Ms = plan.alloc_outputs()
     plan.execute([torch.from_numpy(p).cuda() for p in phis_h], Bs, Ms, plan.alloc_workspace())
@@ -352,7 +367,7 @@ def test_64_column_tiles_match_oracle(laph, mode):
 
 
 @pytest.mark.parametrize("mode", ["f16x3", "bf16x3", "f16"])
-@pytest.mark.parametrize("cols", [176, 192, 128])
+@pytest.mark.parametrize("cols", [176, 192, 208, 128])
 def test_row_doubled_layout_matches_oracle(laph, mode, cols):
     """Layout 1 (two real A rows per complex row, 64 complex rows per tile, half-size B stage images): single
     instances with several row tiles that mix meson and diquark rows, ragged column tails, skipped leading columns
