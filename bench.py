@@ -130,13 +130,14 @@ def schedule_of(plan, tuned: bool) -> dict:
     d = plan.describe()
     sch = plan.schedule()
     out = {"layout": 1 if d["tile_rows"] == 64 else 0, "tile_cols": d["tile_cols"], "tile_rows": d["tile_rows"],
-           "chunk_sites": d["chunk_sites"], "sum_sites": plan.sum_sites()[0],
+           "chunk_sites": d["chunk_sites"], "chunk_sites_b": plan.drain_sites()[1], "sum_sites": plan.sum_sites()[0],
            "timeslices_per_chunk": sch["timeslices_per_chunk"], "tile_order": sch["tile_order"], "autotuned": tuned}
     if tuned:
         out["candidates"] = [[r["layout"], r["tile_cols"], r["tile_order"], r["timeslices_per_chunk"], r["sum_sites"],
-                              r["chunk_sites"], round(r["ms"], 3), r["probe_err"]] for r in plan.tuning()]
+                              r["chunk_sites"], r["chunk_sites_b"], round(r["ms"], 3), r["probe_err"]]
+                             for r in plan.tuning()]
         out["candidate_fields"] = ["layout", "tile_cols", "tile_order", "timeslices_per_chunk", "sum_sites",
-                                   "chunk_sites", "ms", "probe_err"]
+                                   "chunk_sites", "chunk_sites_b", "ms", "probe_err"]
     return out
 
 

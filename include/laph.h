@@ -297,6 +297,9 @@ typedef struct {
                         MMA's B operand, 128 complex rows per tile; 1: every complex row of the diquark / meson
                         operand is two real rows of the MMA's A operand (tensor-memory lanes 2r, 2r+1), 64 complex
                         rows per tile, and the phased operand's stage images are half as large */
+    int chunk_sites_b; /* tensor-core modes: drain interval of the tiles that hold no meson rows (0: chunk_sites).
+                          Baryon and triplet sums are incoherent, so their error grows more slowly with the interval
+                          than that of the meson sums, whose diagonal entries add coherently */
 } laph_plan_options;
 
 /* laph_plan_create with numerical parameters (opts may be NULL).  LAPH_ERR_ARG
@@ -402,6 +405,7 @@ typedef struct {
     int layout;                     /* laph_plan_options.layout */
     int sum_sites;                  /* sites per block of the FP64 site reduction */
     int chunk_sites;                /* drain interval of the tensor core's FP32 accumulation, in sites */
+    int chunk_sites_b;              /* drain interval of the tiles without meson rows, in sites */
     int tile_order;                 /* 0: column tiles outer, 1: row tiles outer */
     int64_t timeslices_per_chunk;   /* 0: chunks filled by bytes (several instances) */
     float ms;                       /* one execute on the synthetic inputs */
@@ -417,7 +421,8 @@ typedef struct {
  * with 176, 192, 208 and 128 columns) x tile order x chunking
  * (the wave model and, for one instance, the largest chunk within the 24 GiB
  * cap); then, from the fastest, half and twice the site-block size of the
- * FP64 reduction; then half and 1.5 times the drain interval.  A drain
+ * FP64 reduction; then half and 1.5 times the drain interval (for all
+ * tiles; chunk_sites_b is kept as given).  A drain
  * interval is accepted only if the relative error of (instance 0, timeslice 0)
  * against the FP32 CUDA-core path stays within 5e-6 (half the 1e-5 bound) or
  * within the default interval's own error; plans of several fields keep the
@@ -426,6 +431,12 @@ typedef struct {
  * Writes min(cap, number of candidates) records; *n_candidates (may be NULL)
  * receives the number of candidates (0 without LAPH_PLAN_AUTOTUNE). */
 LAPH_API int laph_plan_tuning(const laph_plan *plan, int cap, laph_tune_record *rec, int *n_candidates);
+
+/* Drain intervals (sites) the plan runs: *chunk_sites for tiles with meson
+ * rows, *chunk_sites_b for the others (equal unless set apart by
+ * laph_plan_options.chunk_sites_b or the autotuner).  Either pointer may be
+ * NULL. */
+LAPH_API int laph_plan_drain_sites(const laph_plan *plan, int *chunk_sites, int *chunk_sites_b);
 
 /* Number of kernels of this library one laph_plan_execute launches. */
 LAPH_API int laph_plan_launches_per_execute(const laph_plan *plan, int *n);

@@ -49,12 +49,12 @@ class laph_instance(ctypes.Structure):
 
 class laph_plan_options(ctypes.Structure):
     _fields_ = [("chunk_sites", ctypes.c_int), ("sum_sites", ctypes.c_int), ("tile_cols", ctypes.c_int),
-                ("layout", ctypes.c_int)]
+                ("layout", ctypes.c_int), ("chunk_sites_b", ctypes.c_int)]
 
 
 class laph_tune_record(ctypes.Structure):
     _fields_ = [("tile_cols", ctypes.c_int), ("layout", ctypes.c_int), ("sum_sites", ctypes.c_int),
-                ("chunk_sites", ctypes.c_int),
+                ("chunk_sites", ctypes.c_int), ("chunk_sites_b", ctypes.c_int),
                 ("tile_order", ctypes.c_int), ("timeslices_per_chunk", ctypes.c_int64), ("ms", ctypes.c_float),
                 ("probe_err", ctypes.c_double)]
 
@@ -100,6 +100,7 @@ def lib() -> ctypes.CDLL:
                                             ctypes.POINTER(laph_plan_options), ctypes.POINTER(vp)]),
             "laph_plan_sum_sites": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
             "laph_plan_tuning": (i32, [vp, i32, ctypes.POINTER(laph_tune_record), ctypes.POINTER(i32)]),
+            "laph_plan_drain_sites": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
             "laph_plan_workspace_size": (i32, [vp, ctypes.POINTER(sz)]),
             "laph_plan_execute": (i32, [vp, vpp, vpp, vpp, vp, vp]),
             "laph_plan_host_workspace_size": (i32, [vp, ctypes.POINTER(sz)]),
@@ -403,7 +404,7 @@ class Plan:
     """
 
     def __init__(self, instances, mode="f16x3", flags: int = 0, chunk_sites: int = 0, sum_sites: int = 0,
-                 tile_cols: int = 0, layout: int = 0):
+                 tile_cols: int = 0, layout: int = 0, chunk_sites_b: int = 0):
         # (L, T, N, momenta) or, for doublet plans of two vector counts, (L, T, N, momenta, n_col)
         self._moms = [_momenta(inst[3]) for inst in instances]
         self.n_col = [int(inst[4]) if len(inst) > 4 else 0 for inst in instances]
@@ -417,7 +418,7 @@ class Plan:
         self.flags = flags
         self.mode = _mode(mode)
         h = ctypes.c_void_p()
-        opts = laph_plan_options(int(chunk_sites), int(sum_sites), int(tile_cols), int(layout))
+        opts = laph_plan_options(int(chunk_sites), int(sum_sites), int(tile_cols), int(layout), int(chunk_sites_b))
         _check(lib().laph_plan_create_opts(arr, len(instances), self.mode, flags, ctypes.byref(opts), ctypes.byref(h)),
                "laph_plan_create_opts")
         self._h = h
@@ -489,6 +490,12 @@ class Plan:
                                         ctypes.byref(ncand), ms), "laph_plan_schedule")
         return {"timeslices_per_chunk": int(pc.value), "tile_order": int(order.value), "n_chunks": int(nc.value),
                 "candidate_ms": [float(ms[k]) for k in range(min(ncand.value, 8))]}
+
+    def drain_sites(self) -> tuple:
+        """(drain interval of tiles with meson rows, of the others), in sites."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(lib().laph_plan_drain_sites(self._h, ctypes.byref(a), ctypes.byref(b)), "laph_plan_drain_sites")
+        return int(a.value), int(b.value)
 
     def tuning(self) -> list:
         """The autotuner's candidates (PLAN_AUTOTUNE): dicts of tile_cols, sum_sites, chunk_sites, tile_order,

@@ -188,10 +188,11 @@ cudaError_t launch_simt(const InstDev *d_inst, const TileDev *d_tiles, long long
 // laph_tc.cu
 struct TcConfig {
     int elem;          // 0 = FP16 hi/lo, 1 = BF16 hi/lo
-    int ncols;         // tile width in complex columns: 96 or 64; row-doubled layout 192, 176 or 128
+    int ncols;         // tile width in complex columns: 104, 96, 80 or 64; row-doubled layout 208, 192, 176 or 128
     int rows2;         // 1: row-doubled layout (two real A rows per complex row, 64 complex rows per tile)
     int terms;         // 3 (split) or 1 (plain)
     int chunk_sites;   // sites accumulated by the tensor core between FP32 drains
+    int chunk_sites_b; // the same for tiles without meson rows
     int grid;          // persistent CTAs
     int max_staged;    // largest number of staged row vectors (nv) of any tile
     int debug_stall;   // test hook

@@ -15,8 +15,9 @@
 // accumulates hi*hi + hi*lo + lo*hi (hi*hi only in the plain modes) in FP32.
 // Its FP32 accumulation does not round to nearest, so its error grows with
 // the number of additions; the accumulator is drained every `chunk_stages`
-// K stages into a second tensor-memory region of FP32 running sums kept by
-// CUDA cores with round-to-nearest.  A tile covers one block of sites (at
+// K stages (chunk_stages_b for tiles without meson rows, whose incoherent
+// sums tolerate a longer interval) into a second tensor-memory region of
+// FP32 running sums kept by CUDA cores with round-to-nearest.  A tile covers one block of sites (at
 // most sc_stages K stages); at its end the running sums are stored as FP32
 // partials, and reduce_kernel adds the partials of all site blocks of an
 // output in FP64, in block order, scales them back and writes the
@@ -484,7 +485,8 @@ struct KParams {
     unsigned *counter;    // tile counter of this launch (zero at launch)
     int *status;
     int n_tiles;
-    int chunk_stages;
+    int chunk_stages;     // drain interval in K stages
+    int chunk_stages_b;   // the same for tiles without meson rows
     int stage_bytes;      // one stage buffer: B image, then the row vectors' block slots
     int ns;               // stage buffers
     int debug_stall;
@@ -707,7 +709,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
                     pair_of(q, pi_, pj);
                 }
             }
-            const int n_ch = (td.nst + kp.chunk_stages - 1) / kp.chunk_stages;
+            const int cs = td.row0 >= I.mes_rows ? kp.chunk_stages_b : kp.chunk_stages;   // drain interval
+            const int n_ch = (td.nst + cs - 1) / cs;
             const int n_lo = n_real >= 32 ? ((n_real / 2 + 15) & ~15) : n_real;
             for (int ch = 0; ch < n_ch && ok; ch++) {
                 for (int h = 0; h < 2; h++) {
@@ -804,6 +807,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
             if (tile < 0) break;
             const TileDev td = kp.tiles[tile];
             const int nst = td.nst;
+            const int chunk = td.row0 >= kp.insts[td.inst].mes_rows ? kp.chunk_stages_b : kp.chunk_stages;
             // the first cskip columns (2 cskip real B rows, or cskip in the
             // row-doubled layout; 32 bytes per B row in every atom column) are
             // not needed by any row of the tile
@@ -817,7 +821,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
             int cs = 0;   // stage within the current accumulation chunk
             for (int st = 0; st < nst; st++) {
                 const bool chunk_start = cs == 0;
-                const bool chunk_end = cs + 1 == kp.chunk_stages || st + 1 == nst;
+                const bool chunk_end = cs + 1 == chunk || st + 1 == nst;
                 // Every producer warp of the stage waited for the stage's data
                 // (its full barrier) before its release-arrive on a_full, so the
                 // acquire of a_full also orders the MMAs after the bulk copies;
@@ -1121,6 +1125,8 @@ cudaError_t launch_one(const InstDev *d_inst, const TileDev *d_tiles, long long 
     kp.n_tiles = (int)n_tiles;
     kp.chunk_stages = (cfg.chunk_sites * 3) / KSTAGE;
     if (kp.chunk_stages < 1) kp.chunk_stages = 1;
+    kp.chunk_stages_b = ((cfg.chunk_sites_b > 0 ? cfg.chunk_sites_b : cfg.chunk_sites) * 3) / KSTAGE;
+    if (kp.chunk_stages_b < 1) kp.chunk_stages_b = 1;
     kp.stage_bytes = stage_bytes_for(cfg.max_staged, NC, RD);
     kp.debug_stall = cfg.debug_stall;
     kp.ns = tc_ring_depth(cfg.max_staged, NC, RD);   // deepest stage ring that fits

@@ -103,9 +103,11 @@ def test_plan_options_are_checked_before_touching_cuda(lib):
                  binding.laph_plan_options(0, 0, 176, 0), binding.laph_plan_options(0, 0, 96, 1),
                  binding.laph_plan_options(0, 0, 112, 0), binding.laph_plan_options(0, 0, 104, 1),
                  binding.laph_plan_options(0, 0, 224, 1),
-                 binding.laph_plan_options(0, 0, 0, 2), binding.laph_plan_options(0, 0, 0, -1)]:
+                 binding.laph_plan_options(0, 0, 0, 2), binding.laph_plan_options(0, 0, 0, -1),
+                 binding.laph_plan_options(0, 0, 0, 0, -8), binding.laph_plan_options(0, 0, 0, 0, 1 << 25)]:
         assert lib.laph_plan_create_opts(arr, 1, 1, 0, ctypes.byref(opts), ctypes.byref(h)) == binding.LAPH_ERR_ARG
     assert lib.laph_plan_tuning(None, 0, None, None) == binding.LAPH_ERR_ARG
+    assert lib.laph_plan_drain_sites(None, None, None) == binding.LAPH_ERR_ARG
     assert lib.laph_plan_sum_sites(None, None, None) == binding.LAPH_ERR_ARG
     assert lib.laph_plan_tensor_flops(None, None) == binding.LAPH_ERR_ARG
 

@@ -318,6 +318,27 @@ def test_large_streamed_shape_sampled_parity(laph):
     plan.close()
 
 
+@pytest.mark.parametrize("mode", ["f16x3", "bf16x3"])
+def test_separate_drain_interval_for_tiles_without_mesons(laph, mode):
+    """laph_plan_options.chunk_sites_b: tiles without meson rows drain at another interval than the tiles that hold
+    meson rows (here 2x and 1/2x); several row tiles of both kinds, ragged site blocks; blocks within the bound."""
+    import torch
+    for L, T, N, mom, inst in [CASES[2], CASES[4], CASES[5]]:
+        phi_h = synth.random_phi(L, N, T=T, instance=inst)
+        rB, rM = _oracle(phi_h, L, mom)
+        for csb in (256, 64):
+            plan = laph.Plan([(L, T, N, mom)], mode=mode, chunk_sites_b=csb)
+            assert plan.drain_sites() == (128, csb)
+            Bs, Ms = plan.alloc_outputs()
+            plan.execute([torch.from_numpy(phi_h).cuda()], Bs, Ms, plan.alloc_workspace())
+            torch.cuda.synchronize()
+            assert plan.device_status() == laph.LAPH_OK
+            eB, eM = rel_frob(Bs[0].cpu().numpy(), rB), rel_frob(Ms[0].cpu().numpy(), rM)
+            print(f"chunk_sites_b={csb} mode={mode} L={L} N={N}: rel B {eB:.2e} M {eM:.2e}")
+            assert eB <= tol_for(mode) and eM <= tol_for(mode)
+            plan.close()
+
+
 def test_default_tile_width_keeps_a_four_deep_stage_ring(laph):
     """The default tile is 104 columns wide unless the row vectors a tile stages would then leave a stage ring shallower
     than four buffers (about N > 80 at 128 rows), where it is 96; an explicit width or layout is kept."""
@@ -510,9 +531,9 @@ def test_autotuned_plan_matches_oracle(laph):
     assert len(probed) >= 2 and all(r["probe_err"] < 1e-4 for r in probed)
     desc = plan.describe()
     assert any(r["tile_cols"] == desc["tile_cols"] and r["chunk_sites"] == desc["chunk_sites"] and
-               r["sum_sites"] == plan.sum_sites()[0] for r in rec)
-    print("autotune:", [(r["tile_cols"], r["tile_order"], r["sum_sites"], r["chunk_sites"], round(r["ms"], 3),
-                         r["probe_err"]) for r in rec], "chosen", desc)
+               r["chunk_sites_b"] == plan.drain_sites()[1] and r["sum_sites"] == plan.sum_sites()[0] for r in rec)
+    print("autotune:", [(r["tile_cols"], r["tile_order"], r["sum_sites"], r["chunk_sites"], r["chunk_sites_b"],
+                         round(r["ms"], 3), r["probe_err"]) for r in rec], "chosen", desc, plan.drain_sites())
     phi_h = synth.random_phi(L, N, T=T, instance=95)
     Bs, Ms = plan.alloc_outputs()
     ws = plan.alloc_workspace()
