@@ -108,6 +108,12 @@ extern "C" {
  *       out_M: device complex128 [T][P][N][N].
  * Tensor-core modes only (LAPH_ERR_UNSUPPORTED otherwise); N >= 1. */
 #define LAPH_PLAN_FIELDS 0x40000u
+/* Tensor-core modes: outputs (B, M, B3, M2, device or host) are complex64
+ * instead of complex128, the FP64 site sums rounded once to FP32 (half the
+ * output bytes; the rounding adds a relative error of at most 2^-24 per
+ * component).  LAPH_ERR_UNSUPPORTED in the FP32 mode, which accumulates in
+ * its complex128 outputs. */
+#define LAPH_PLAN_OUT_C64 0x80000u
 
 /* One independent problem of a (possibly ragged) batch. */
 typedef struct {
@@ -337,8 +343,8 @@ LAPH_API int laph_plan_execute_fields(laph_plan *plan, const void *const *fields
                                       void *stream);
 
 /* Same batch with HOST buffers: phi_host[n] (complex64, pinned or pageable)
- * is copied in, computed, and out_B_host[n]/out_M_host[n] (complex128) are
- * copied back, timeslice chunk by chunk with copies overlapping compute.
+ * is copied in, computed, and out_B_host[n]/out_M_host[n] (complex128, or
+ * complex64 with LAPH_PLAN_OUT_C64) are copied back, timeslice chunk by chunk with copies overlapping compute.
  * Device staging comes from `workspace`, which must hold
  * laph_plan_host_workspace_size bytes.  Returns after the stream is
  * synchronised. */

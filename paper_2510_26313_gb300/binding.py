@@ -31,6 +31,7 @@ PLAN_TIMING = 0x8
 PLAN_DEBUG_STALL = 0x10000
 PLAN_CHUNK_PER_TIMESLICE = 0x20000
 PLAN_FIELDS = 0x40000
+PLAN_OUT_C64 = 0x80000
 
 _lib = None
 
@@ -518,18 +519,52 @@ class Plan:
             return None
         return torch.empty(n, dtype=torch.uint8, device=device or "cuda")
 
+    def output_shapes(self):
+        """Per instance, the shapes of its B (or B3) and M (or M2) outputs; None where skipped."""
+        out = []
+        for n, (L, T, N, m) in enumerate(self.instances):
+            P = m.shape[0]
+            shapeB = (T, P, N, N, N) if self.flags & PLAN_FIELDS else (T, P, N * (N - 1) * (N - 2) // 6)
+            Nc = self.n_col[n] or N
+            out.append((None if self.flags & PLAN_SKIP_B else shapeB, None if self.flags & PLAN_SKIP_M else (T, P, N, Nc)))
+        return out
+
+    @property
+    def out_dtype(self):
+        """torch dtype of the outputs: complex64 with PLAN_OUT_C64, else complex128."""
+        import torch
+        return torch.complex64 if self.flags & PLAN_OUT_C64 else torch.complex128
+
     def alloc_outputs(self, device=None):
         import torch
         Bs, Ms = [], []
-        for (L, T, N, m) in self.instances:
-            P = m.shape[0]
-            shapeB = (T, P, N, N, N) if self.flags & PLAN_FIELDS else (T, P, N * (N - 1) * (N - 2) // 6)
-            Bs.append(None if self.flags & PLAN_SKIP_B else
-                      torch.empty(shapeB, dtype=torch.complex128, device=device or "cuda"))
-            Nc = self.n_col[len(Ms)] or N
-            Ms.append(None if self.flags & PLAN_SKIP_M else
-                      torch.empty((T, P, N, Nc), dtype=torch.complex128, device=device or "cuda"))
+        for sB, sM in self.output_shapes():
+            Bs.append(None if sB is None else torch.empty(sB, dtype=self.out_dtype, device=device or "cuda"))
+            Ms.append(None if sM is None else torch.empty(sM, dtype=self.out_dtype, device=device or "cuda"))
         return Bs, Ms
+
+    def _check_outputs(self, Bs, Ms, host=False):
+        """Every output the plan writes must be a contiguous buffer of the plan's dtype and exact shape (the C side
+        cannot check the size of a buffer); device outputs on the current CUDA device."""
+        import torch
+        want = np.complex64 if self.flags & PLAN_OUT_C64 else np.complex128
+        for n, (sB, sM) in enumerate(self.output_shapes()):
+            for outs, shape, name in ((Bs, sB, "B"), (Ms, sM, "M")):
+                if shape is None:
+                    continue
+                t = outs[n] if outs is not None and n < len(outs) else None
+                if t is None:
+                    raise ValueError(f"{name}[{n}] is required")
+                if isinstance(t, torch.Tensor):
+                    ok = t.dtype == self.out_dtype and t.is_contiguous() and tuple(t.shape) == tuple(shape)
+                    ok = ok and (not t.is_cuda if host else (t.is_cuda and t.device.index == torch.cuda.current_device()))
+                else:
+                    ok = host and isinstance(t, np.ndarray) and t.dtype == want and t.flags.c_contiguous and \
+                        tuple(t.shape) == tuple(shape)
+                if not ok:
+                    where = "host" if host else "current-device CUDA"
+                    raise ValueError(f"{name}[{n}] must be a contiguous {where} {np.dtype(want).name} buffer of shape "
+                                     f"{tuple(shape)}")
 
     @staticmethod
     def _ptr_array(ts):
@@ -541,6 +576,7 @@ class Plan:
     def execute(self, phis, Bs, Ms, workspace, stream=None):
         for (L, T, N, _), phi in zip(self.instances, phis):
             _check_phi(phi, L)
+        self._check_outputs(Bs, Ms)
         pa = self._ptr_array(phis)
         ba = self._ptr_array(Bs) if Bs is not None else None
         ma = self._ptr_array(Ms) if Ms is not None else None
@@ -554,6 +590,10 @@ class Plan:
         for (L, T, N, _), fs in zip(self.instances, fields):
             _check_fields(tuple(fs), L, same_n=not (self.flags & PLAN_SKIP_B))
             flat.extend(fs)
+        if self.flags & PLAN_SKIP_M:
+            self._check_outputs(outs, None)
+        else:
+            self._check_outputs(None, outs)
         fa = self._ptr_array(flat)
         oa = self._ptr_array(outs)
         ws = ctypes.c_void_p(workspace.data_ptr()) if workspace is not None else ctypes.c_void_p()
@@ -565,6 +605,7 @@ class Plan:
             if a is None:
                 return None
             return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+        self._check_outputs(Bs_host, Ms_host, host=True)
         pa = (ctypes.c_void_p * len(phis_host))(*[addr(a) for a in phis_host])
         ba = (ctypes.c_void_p * len(Bs_host))(*[addr(a) for a in Bs_host]) if Bs_host is not None else None
         ma = (ctypes.c_void_p * len(Ms_host))(*[addr(a) for a in Ms_host]) if Ms_host is not None else None

@@ -99,6 +99,7 @@ struct laph_plan {
     int *d_status = nullptr;
     int tile_rows = 0, tile_cols = 0, chunk_sites = 0, grid = 0;
     int chunk_sites_b = 0;   // drain interval of tiles without meson rows (0: chunk_sites)
+    size_t out_bytes = 16;   // bytes per output entry: complex128, or complex64 with LAPH_PLAN_OUT_C64
     int rows2 = 0;                             // tensor-core path: the row-doubled layout
     int sum_sites = 0;                         // tensor-core path: sites per block of the FP64 reduction
     int max_staged = 0, max_P = 0;
@@ -265,6 +266,7 @@ int laph_plan_create_opts(const laph_instance *inst, int n_inst, int mode, unsig
     if (opts && (opts->layout < 0 || opts->layout > 1)) return LAPH_ERR_ARG;
     if (opts && opts->tile_cols != 0 && !laph::tc_shape_supported(opts->tile_cols, opts->layout)) return LAPH_ERR_ARG;
     if (mode < 0 || mode >= LAPH_NUM_MODES) return LAPH_ERR_ARG;
+    if ((flags & LAPH_PLAN_OUT_C64) && !is_tc_mode(mode)) return LAPH_ERR_UNSUPPORTED;
     const bool skipB = flags & LAPH_PLAN_SKIP_B, skipM = flags & LAPH_PLAN_SKIP_M;
     if (skipB && skipM) return LAPH_ERR_ARG;
     // several fields: triplets (skip M) or doublets (skip B), tensor-core modes only
@@ -300,6 +302,7 @@ int laph_plan_create_opts(const laph_instance *inst, int n_inst, int mode, unsig
     p->tile_cols = tc ? laph::TC_TC : laph::SIMT_TC;
     p->chunk_sites = opt_chunk ? opt_chunk : (tc ? TC_DEFAULT_CHUNK : SIMT_DEFAULT_CHUNK);
     p->chunk_sites_b = opt_chunk_b;
+    p->out_bytes = (flags & LAPH_PLAN_OUT_C64) ? sizeof(float2) : sizeof(double2);
     p->momenta0.assign(inst[0].momenta, inst[0].momenta + 3 * inst[0].n_mom);
 
     // ---- per-instance descriptors and phase tables
@@ -320,6 +323,7 @@ int laph_plan_create_opts(const laph_instance *inst, int n_inst, int mode, unsig
         d.nblk = (int)((d.V + laph::TC_BS - 1) / laph::TC_BS);
         d.n_trip = laph::binom3(I.N);
         d.kind = kind;
+        d.out_c64 = (flags & LAPH_PLAN_OUT_C64) ? 1 : 0;
         d.n_fields = kind == laph::INST_TRIPLETS ? 3 : (kind == laph::INST_DOUBLETS ? 2 : 1);
         d.blkv_off = -1;
         d.mes_rows = skipM ? 0 : I.N;
@@ -997,11 +1001,12 @@ static int tune_probe(laph_plan *p, TuneState &ts, double *err)
         if (rc != LAPH_OK) return rc;
     }
     if ((e = cudaMemsetAsync(ts.acc, 0, 4 * sizeof(double), ts.st)) != cudaSuccess) return cuda_fail(e, "memset");
-    if (needB && (e = laph::launch_diff_norms((const double2 *)ts.ob[0], (const double2 *)ts.refB, d.n_outB, ts.acc,
-                                              ts.st)) != cudaSuccess)
+    const bool c64 = p->out_bytes == sizeof(float2);
+    if (needB && (e = laph::launch_diff_norms(ts.ob[0], c64, (const double2 *)ts.refB, d.n_outB, ts.acc, ts.st)) !=
+                     cudaSuccess)
         return cuda_fail(e, "diff_norms");
-    if (needM && (e = laph::launch_diff_norms((const double2 *)ts.om[0], (const double2 *)ts.refM, d.n_outM,
-                                              ts.acc + 2, ts.st)) != cudaSuccess)
+    if (needM && (e = laph::launch_diff_norms(ts.om[0], c64, (const double2 *)ts.refM, d.n_outM, ts.acc + 2, ts.st)) !=
+                     cudaSuccess)
         return cuda_fail(e, "diff_norms");
     double h[4] = {0, 0, 0, 0};
     if ((e = cudaMemcpyAsync(h, ts.acc, sizeof(h), cudaMemcpyDeviceToHost, ts.st)) != cudaSuccess)
@@ -1059,8 +1064,8 @@ static int autotune(laph_plan *p, const laph::Sched &def, const std::function<cu
     for (int n = 0; n < p->n_inst; n++) {
         TCK(cudaMalloc(&ts.phi[n], p->phi_elems[n] * sizeof(float2)));
         TCK(laph::launch_fill_pattern((float2 *)ts.phi[n], p->phi_elems[n], 1000u + (unsigned)n, ts.st));
-        if (needB) TCK(cudaMalloc(&ts.ob[n], std::max<long long>(p->outB_elems[n], 1) * sizeof(double2)));
-        if (needM) TCK(cudaMalloc(&ts.om[n], std::max<long long>(p->outM_elems[n], 1) * sizeof(double2)));
+        if (needB) TCK(cudaMalloc(&ts.ob[n], std::max<long long>(p->outB_elems[n], 1) * p->out_bytes));
+        if (needM) TCK(cudaMalloc(&ts.om[n], std::max<long long>(p->outM_elems[n], 1) * p->out_bytes));
     }
     {
         // 1: tile width x tile order x chunking (the largest chunk only for one instance)
@@ -1263,8 +1268,8 @@ int laph_plan_host_workspace_size(const laph_plan *plan, size_t *bytes)
     size_t total = ((plan->ws_bytes + 255) / 256) * 256;
     for (int n = 0; n < plan->n_inst; n++) {
         total += ((plan->phi_elems[n] * sizeof(float2) + 255) / 256) * 256;
-        total += ((plan->outB_elems[n] * sizeof(double2) + 255) / 256) * 256;
-        total += ((plan->outM_elems[n] * sizeof(double2) + 255) / 256) * 256;
+        total += ((plan->outB_elems[n] * plan->out_bytes + 255) / 256) * 256;
+        total += ((plan->outM_elems[n] * plan->out_bytes + 255) / 256) * 256;
     }
     *bytes = total;
     return LAPH_OK;
@@ -1287,9 +1292,9 @@ int laph_plan_execute_host(laph_plan *plan, const void *const *phi_host, void *c
         dphi[n] = ws + off;
         off += ((plan->phi_elems[n] * sizeof(float2) + 255) / 256) * 256;
         dB[n] = ws + off;
-        off += ((plan->outB_elems[n] * sizeof(double2) + 255) / 256) * 256;
+        off += ((plan->outB_elems[n] * plan->out_bytes + 255) / 256) * 256;
         dM[n] = ws + off;
-        off += ((plan->outM_elems[n] * sizeof(double2) + 255) / 256) * 256;
+        off += ((plan->outM_elems[n] * plan->out_bytes + 255) / 256) * 256;
     }
     cudaError_t e = laph::launch_set_pointers(plan->d_inst, 0, plan->n_inst, dphi.data(), needB ? dB.data() : nullptr,
                                               needM ? dM.data() : nullptr, ws, s);
@@ -1303,9 +1308,11 @@ int laph_plan_execute_host(laph_plan *plan, const void *const *phi_host, void *c
         if (rc != LAPH_OK) return rc;
         for (int n = 0; n < plan->n_inst; n++) {
             if (needB)
-                CK(cudaMemcpyAsync(out_B_host[n], dB[n], plan->outB_elems[n] * sizeof(double2), cudaMemcpyDeviceToHost, s));
+                CK(cudaMemcpyAsync(out_B_host[n], dB[n], plan->outB_elems[n] * plan->out_bytes, cudaMemcpyDeviceToHost,
+                                   s));
             if (needM)
-                CK(cudaMemcpyAsync(out_M_host[n], dM[n], plan->outM_elems[n] * sizeof(double2), cudaMemcpyDeviceToHost, s));
+                CK(cudaMemcpyAsync(out_M_host[n], dM[n], plan->outM_elems[n] * plan->out_bytes, cudaMemcpyDeviceToHost,
+                                   s));
         }
         CK(cudaStreamSynchronize(s));
         return LAPH_OK;
@@ -1355,12 +1362,12 @@ int laph_plan_execute_host(laph_plan *plan, const void *const *phi_host, void *c
         for (int u = c.unit0; u < c.unit0 + c.n_units; u++) {
             const int n = plan->h_units[u].inst, t = plan->h_units[u].t;
             if (needB) {
-                const size_t bytes = plan->outB_elems[n] / plan->h_T[n] * sizeof(double2);
+                const size_t bytes = plan->outB_elems[n] / plan->h_T[n] * plan->out_bytes;
                 CK(cudaMemcpyAsync((char *)out_B_host[n] + t * bytes, (char *)dB[n] + t * bytes, bytes,
                                    cudaMemcpyDeviceToHost, plan->d2h));
             }
             if (needM) {
-                const size_t bytes = plan->outM_elems[n] / plan->h_T[n] * sizeof(double2);
+                const size_t bytes = plan->outM_elems[n] / plan->h_T[n] * plan->out_bytes;
                 CK(cudaMemcpyAsync((char *)out_M_host[n] + t * bytes, (char *)dM[n] + t * bytes, bytes,
                                    cudaMemcpyDeviceToHost, plan->d2h));
             }

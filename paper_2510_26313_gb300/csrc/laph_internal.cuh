@@ -30,8 +30,8 @@ struct InstDev {
     const float2 *phi;       // [T][N][V][3] column field (phi; chi for triplets, psi for doublets)
     const float2 *phi_u;     // [T][N][V][3] first row field (phi)
     const float2 *phi_v;     // [T][N][V][3] second row field (phi; psi for triplets)
-    double2 *outB;           // [T][P][C(N,3)]
-    double2 *outM;           // [T][P][N][N]
+    double2 *outB;           // [T][P][C(N,3)] (float2 entries when out_c64)
+    double2 *outM;           // [T][P][N][N] (float2 entries when out_c64)
     const float2 *phase;     // [P][Vs], FP32 rounding of the FP64 phase
     float2 *phi_blk;         // tensor-core path: scaled, site-blocked copy of phi_u in the workspace
     float2 *blk_v;           // the same for phi_v (triplets only)
@@ -54,6 +54,7 @@ struct InstDev {
     int Nc;                  // vectors of the column field (N, except doublets of two vector counts)
     int n_sc;                // tensor-core path: site blocks of the FP64 reduction (partials per output)
     int sc_stages;           // K stages (8-site blocks) per site block of the FP64 reduction
+    int out_c64;             // tensor-core path: outputs are complex64, the FP64 sums rounded once
     long long n_outB;        // output entries per timeslice: B (P C(N,3), or P N^3 for triplets; 0 if skipped)
     long long n_outM;        //                               M (P N Nc; 0 if skipped)
 };
@@ -165,7 +166,7 @@ cudaError_t launch_diquarks(const float2 *phi, int L, int T, int N, float2 *out,
 // Seeded pseudo-random complex entries in [-1, 1) (inputs the library makes itself).
 cudaError_t launch_fill_pattern(float2 *out, long long n, unsigned seed, cudaStream_t s);
 // acc[0] += sum |a - b|^2, acc[1] += sum |b|^2 (FP64; acc zeroed by the caller).
-cudaError_t launch_diff_norms(const double2 *a, const double2 *b, long long n, double *acc, cudaStream_t s);
+cudaError_t launch_diff_norms(const void *a, bool a_c64, const double2 *b, long long n, double *acc, cudaStream_t s);
 cudaError_t launch_dense_fill(const double2 *packed, int T, int N, int P, double2 *dense, cudaStream_t s);
 // Site-blocked copies of phi_u (and, for triplets, phi_v).
 cudaError_t launch_blockify(const InstDev *d_inst, int inst, const InstDev &h, const unsigned *d_maxbits,

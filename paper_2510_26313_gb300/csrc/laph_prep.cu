@@ -123,16 +123,18 @@ cudaError_t launch_fill_pattern(float2 *out, long long n, unsigned seed, cudaStr
 }
 
 // ---------------------------------------------------------------- difference norms
-// acc[0] += sum |a - b|^2, acc[1] += sum |b|^2 over n complex128 entries
-// (the autotuner's accuracy probe of a candidate schedule against the FP32
-// path; FP64 sums, one atomic pair per block).
-__global__ void diff_norms_kernel(const double2 *__restrict__ a, const double2 *__restrict__ b, long long n,
-                                  double *acc)
+// acc[0] += sum |a - b|^2, acc[1] += sum |b|^2 over n complex entries, a
+// complex128 or complex64 (A), b complex128 (the autotuner's accuracy probe of
+// a candidate schedule against the FP32 path; FP64 sums, one atomic pair per
+// block).
+template <typename A>
+__global__ void diff_norms_kernel(const A *__restrict__ a, const double2 *__restrict__ b, long long n, double *acc)
 {
     __shared__ double sd[8], sb[8];
     double d2 = 0.0, b2 = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const double2 x = a[i], y = b[i];
+        const A xa = a[i];
+        const double2 x = make_double2((double)xa.x, (double)xa.y), y = b[i];
         const double dr = x.x - y.x, di = x.y - y.y;
         d2 += dr * dr + di * di;
         b2 += y.x * y.x + y.y * y.y;
@@ -157,12 +159,15 @@ __global__ void diff_norms_kernel(const double2 *__restrict__ a, const double2 *
     }
 }
 
-cudaError_t launch_diff_norms(const double2 *a, const double2 *b, long long n, double *acc, cudaStream_t s)
+cudaError_t launch_diff_norms(const void *a, bool a_c64, const double2 *b, long long n, double *acc, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     long long blocks = (n + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
-    diff_norms_kernel<<<(unsigned)blocks, 256, 0, s>>>(a, b, n, acc);
+    if (a_c64)
+        diff_norms_kernel<float2><<<(unsigned)blocks, 256, 0, s>>>((const float2 *)a, b, n, acc);
+    else
+        diff_norms_kernel<double2><<<(unsigned)blocks, 256, 0, s>>>((const double2 *)a, b, n, acc);
     return cudaGetLastError();
 }
 

@@ -1032,7 +1032,8 @@ __device__ __forceinline__ double scale2(double v, int k)
 // the unit's output order (B entries [p][...] first, then M entries
 // [p][i][k]) is the FP64 sum over site blocks sc = 0, 1, ... of the FP32
 // partials part[part_off + sc * n_out + e], times 2^-3s (B) or 2^-2s (M), s
-// the timeslice's exponent.  Each thread owns RED_PER_THREAD entries, TC_RED_BLOCK /
+// the timeslice's exponent, written as complex128 or, for complex64 outputs,
+// rounded once to FP32.  Each thread owns RED_PER_THREAD entries, TC_RED_BLOCK /
 // RED_PER_THREAD apart, and adds each entry's partials in block order.
 constexpr int RED_THREADS = 256;
 constexpr int RED_PER_THREAD = TC_RED_BLOCK / RED_THREADS;
@@ -1085,16 +1086,23 @@ __global__ void __launch_bounds__(RED_THREADS) reduce_kernel(const InstDev *__re
         for (int q = 0; q < RED_PER_THREAD; q++) {
             const long long e = e0 + q * RED_THREADS;
             if (e >= n_out) continue;
-            double2 *dst;
+            long long o;
             int k;
+            void *base;
             if (e < nB) {
-                dst = I.outB + (long long)un.t * nB + e;
+                base = I.outB;
+                o = (long long)un.t * nB + e;
                 k = -3 * s;
             } else {
-                dst = I.outM + (long long)un.t * I.n_outM + (e - nB);
+                base = I.outM;
+                o = (long long)un.t * I.n_outM + (e - nB);
                 k = -2 * s;
             }
-            *dst = make_double2(scale2(re[q], k), scale2(im[q], k));
+            const double vr = scale2(re[q], k), vi = scale2(im[q], k);
+            if (I.out_c64)
+                reinterpret_cast<float2 *>(base)[o] = make_float2(__double2float_rn(vr), __double2float_rn(vi));
+            else
+                reinterpret_cast<double2 *>(base)[o] = make_double2(vr, vi);
         }
     }
 }

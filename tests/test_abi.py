@@ -106,6 +106,9 @@ def test_plan_options_are_checked_before_touching_cuda(lib):
                  binding.laph_plan_options(0, 0, 0, 2), binding.laph_plan_options(0, 0, 0, -1),
                  binding.laph_plan_options(0, 0, 0, 0, -8), binding.laph_plan_options(0, 0, 0, 0, 1 << 25)]:
         assert lib.laph_plan_create_opts(arr, 1, 1, 0, ctypes.byref(opts), ctypes.byref(h)) == binding.LAPH_ERR_ARG
+    # complex64 outputs are a tensor-core option: the FP32 mode accumulates in its complex128 outputs
+    assert lib.laph_plan_create_opts(arr, 1, 0, binding.PLAN_OUT_C64, None, ctypes.byref(h)) == \
+        binding.LAPH_ERR_UNSUPPORTED
     assert lib.laph_plan_tuning(None, 0, None, None) == binding.LAPH_ERR_ARG
     assert lib.laph_plan_drain_sites(None, None, None) == binding.LAPH_ERR_ARG
     assert lib.laph_plan_sum_sites(None, None, None) == binding.LAPH_ERR_ARG

@@ -339,6 +339,66 @@ def test_separate_drain_interval_for_tiles_without_mesons(laph, mode):
             plan.close()
 
 
+@pytest.mark.parametrize("mode", ["f16x3", "bf16x3"])
+def test_complex64_outputs_are_the_rounded_complex128_outputs(laph, mode):
+    """PLAN_OUT_C64: every B and M entry is the complex128 result of the same schedule rounded once to complex64
+    (bitwise), through the device execute, a ragged batch and the host-buffer execute; the binding refuses
+    complex128 buffers for such a plan."""
+    import torch
+    specs = [(L, T, N, mom) for (L, T, N, mom, _) in (CASES[2], CASES[4], CASES[5])]
+    phis_h = [synth.random_phi(L, N, T=T, instance=170 + n) for n, (L, T, N, _) in enumerate(specs)]
+    phis = [torch.from_numpy(p).cuda() for p in phis_h]
+    ref = laph.Plan(specs, mode=mode)
+    rB, rM = ref.alloc_outputs()
+    ref.execute(phis, rB, rM, ref.alloc_workspace())
+    plan = laph.Plan(specs, mode=mode, flags=laph.PLAN_OUT_C64)
+    Bs, Ms = plan.alloc_outputs()
+    assert Bs[0].dtype == torch.complex64
+    plan.execute(phis, Bs, Ms, plan.alloc_workspace())
+    torch.cuda.synchronize()
+    assert plan.device_status() == laph.LAPH_OK
+    for n, (L, T, N, mom) in enumerate(specs):
+        b128, m128 = rB[n].cpu().numpy(), rM[n].cpu().numpy()
+        assert np.array_equal(Bs[n].cpu().numpy(), b128.astype(np.complex64))
+        assert np.array_equal(Ms[n].cpu().numpy(), m128.astype(np.complex64))
+        oB, oM = _oracle(phis_h[n], L, mom)
+        assert rel_frob(Bs[n].cpu().numpy(), oB) <= tol_for(mode) and rel_frob(Ms[n].cpu().numpy(), oM) <= tol_for(mode)
+    # host buffers
+    L, T, N, mom = specs[0]
+    one = laph.Plan([specs[0]], mode=mode, flags=laph.PLAN_OUT_C64)
+    hws = torch.empty(one.host_workspace_size(), dtype=torch.uint8, device="cuda")
+    Bh = np.zeros((T, len(mom), N * (N - 1) * (N - 2) // 6), dtype=np.complex64)
+    Mh = np.zeros((T, len(mom), N, N), dtype=np.complex64)
+    one.execute_host([phis_h[0]], [Bh], [Mh], hws)
+    assert np.array_equal(Bh, rB[0].cpu().numpy().astype(np.complex64))
+    assert np.array_equal(Mh, rM[0].cpu().numpy().astype(np.complex64))
+    with pytest.raises(ValueError):
+        one.execute_host([phis_h[0]], [Bh.astype(np.complex128)], [Mh], hws)
+    with pytest.raises(ValueError):
+        one.execute([phis[0]], [rB[0]], [Ms[0]], one.alloc_workspace())
+    for p_ in (ref, plan, one):
+        p_.close()
+
+
+def test_complex64_triplets_and_doublets(laph):
+    """PLAN_OUT_C64 with several fields: dense triplets and doublets equal the complex128 results rounded once."""
+    import torch
+    L, T, N = 5, 2, 9
+    mom = synth.momentum_shell(1)
+    f = [torch.from_numpy(synth.random_phi(L, N, T=T, instance=180 + q)).cuda() for q in range(3)]
+    for skip, nf in ((laph.PLAN_SKIP_M, 3), (laph.PLAN_SKIP_B, 2)):
+        outs = []
+        for extra in (0, laph.PLAN_OUT_C64):
+            plan = laph.Plan([(L, T, N, mom)], mode="f16x3", flags=laph.PLAN_FIELDS | skip | extra)
+            Bs, Ms = plan.alloc_outputs()
+            o = Bs if skip == laph.PLAN_SKIP_M else Ms
+            plan.execute_fields([f[:nf]], o, plan.alloc_workspace())
+            torch.cuda.synchronize()
+            outs.append(o[0].cpu().numpy())
+            plan.close()
+        assert outs[1].dtype == np.complex64 and np.array_equal(outs[1], outs[0].astype(np.complex64))
+
+
 def test_default_tile_width_keeps_a_four_deep_stage_ring(laph):
     """The default tile is 104 columns wide unless the row vectors a tile stages would then leave a stage ring shallower
     than four buffers (about N > 80 at 128 rows), where it is 96; an explicit width or layout is kept."""
