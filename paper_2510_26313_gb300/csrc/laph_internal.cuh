@@ -204,7 +204,6 @@ constexpr int TC_KSTAGE = 3 * TC_BS;  // complex K entries per stage: one site b
 // One B stage image of a tile of nc complex columns: hi + lo, 2 nc real rows
 // (nc in the row-doubled layout) x 48 FP16 each.
 constexpr int tc_stage_bytes(int nc, bool rows2 = false) { return 2 * (rows2 ? nc : 2 * nc) * (2 * TC_KSTAGE) * 2; }
-constexpr int TC_STAGE_BYTES = tc_stage_bytes(TC_TC);
 constexpr int TC_TR_ROWS2 = 64;   // complex rows per tile in the row-doubled layout
 // Tile widths with compiled kernels for each layout.
 bool tc_shape_supported(int ncols, int rows2);
@@ -224,7 +223,6 @@ constexpr int TC_RED_BLOCK = 1024;
 // back and stored to the caller's complex128 outputs.
 cudaError_t launch_reduce(const InstDev *d_inst, const PsiUnit *d_units, int n_units, long long n_blocks,
                           const unsigned *d_maxbits, const float2 *part, cudaStream_t s);
-int tc_smem_bytes();
 // Stages in the contraction's shared-memory ring for tiles staging up to
 // max_staged row vectors (0: none fits).
 int tc_ring_depth(int max_staged, int ncols, int rows2);

@@ -1161,8 +1161,6 @@ void psi_launch(int elem, unsigned grid, const InstDev *d_inst, const PsiUnit *d
 
 }  // namespace
 
-int tc_smem_bytes() { return smem_for(2, stage_bytes_for(TC_MAX_STAGED, TC_TC, false)); }
-
 int tc_ring_depth(int max_staged, int ncols, int rows2)
 {
     const int sb = stage_bytes_for(max_staged, ncols, rows2 != 0);
