@@ -376,7 +376,16 @@ def test_complex64_outputs_are_the_rounded_complex128_outputs(laph, mode):
         one.execute_host([phis_h[0]], [Bh.astype(np.complex128)], [Mh], hws)
     with pytest.raises(ValueError):
         one.execute([phis[0]], [rB[0]], [Ms[0]], one.alloc_workspace())
-    for p_ in (ref, plan, one):
+    # the autotuner's accuracy probe reads complex64 outputs too
+    tuned = laph.Plan([specs[0]], mode=mode, flags=laph.PLAN_OUT_C64 | laph.PLAN_AUTOTUNE)
+    probed = [r["probe_err"] for r in tuned.tuning() if r["probe_err"] >= 0]
+    assert probed and all(0 < e < 1e-4 for e in probed)
+    tB, tM = tuned.alloc_outputs()
+    tuned.execute([phis[0]], tB, tM, tuned.alloc_workspace())
+    torch.cuda.synchronize()
+    oB, oM = _oracle(phis_h[0], L, mom)
+    assert rel_frob(tB[0].cpu().numpy(), oB) <= tol_for(mode) and rel_frob(tM[0].cpu().numpy(), oM) <= tol_for(mode)
+    for p_ in (ref, plan, one, tuned):
         p_.close()
 
 
