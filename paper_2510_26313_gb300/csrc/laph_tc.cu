@@ -41,17 +41,22 @@
 // warp fills a stage with two bulk copies completing on one mbarrier, and
 // the MMA's commit frees it.
 //
-// Warp roles (704 threads, persistent CTAs; the loader claims tiles from a
-// global counter and hands them to the other roles through a small ring):
+// Warp roles (persistent CTAs; the loader claims tiles from a global counter
+// and hands them to the other roles through a small ring):
 //   0-15  A producers in two groups of eight; group g forms the stages whose
 //         global index has parity g, in A slot g, so that two stages are
 //         formed at once.  Within a group, two warps per TMEM lane quadrant:
 //         warp half h forms the 12 K entries of sites 4h..4h+3 of its row
 //         (diquark or conj(phi)), splits them and tcgen05.st's them;
-//   16-19 epilogue: drains ACC into SUM, one column half at a time, writes
-//         the FP32 partials at tile end;
-//   20    loader: claims the next tile, then the stage ring's bulk copies;
-//   21    TMEM allocation and single-thread MMA issue.
+//   16-23 epilogue, two warps per TMEM lane quadrant taking alternate blocks
+//         of 16 columns (row-doubled layout: 16-19, one per quadrant): drains
+//         ACC into SUM, one column half at a time, writes the FP32 partials
+//         at tile end;
+//   then  the loader: claims the next tile, then the stage ring's bulk
+//         copies; and TMEM allocation and single-thread MMA issue.
+// 26 warps (832 threads, at most 72 registers a thread so that seven warps
+// fit one scheduler's register file); the row-doubled layout, whose
+// producers need more registers, keeps 22 warps at 80 registers.
 // Every wait on an mbarrier is bounded; on expiry the CTA records
 // STATUS_TIMEOUT, raises a shared abort flag and all roles return.
 #include <cuda_bf16.h>
@@ -62,18 +67,24 @@
 namespace laph {
 namespace {
 
-constexpr int NTHREADS = 704;
 constexpr int N_AGROUP = 8;                           // A producer warps per group (one stage)
 constexpr int N_AWARPS = 2 * N_AGROUP;
-constexpr int WARP_LOAD = 20;
-constexpr int WARP_MMA = 21;
+// Warp counts of the two layouts: the epilogue warps (two per lane quadrant
+// halve the drain time) and the loader and MMA warps after them.
+template <bool RD>
+struct Roles {
+    static constexpr int EPI_WARPS = RD ? 4 : 8;
+    static constexpr int WARP_LOAD = N_AWARPS + EPI_WARPS;
+    static constexpr int WARP_MMA = WARP_LOAD + 1;
+    static constexpr int NTHREADS = (WARP_MMA + 1) * 32;
+    static constexpr int N_TILE_READERS = N_AWARPS + EPI_WARPS + 1;   // A producers, epilogue, MMA
+};
 constexpr int KSTAGE = TC_KSTAGE;                     // complex K entries per stage (one site block)
 constexpr int KSTEPS = 2 * KSTAGE / 16;               // MMA k-steps per stage
 constexpr int SLOT_BYTES = TC_SLOT * 8;               // 208 B = 52 words: LDS.128 of 8 consecutive slots hit distinct banks
 constexpr int HALF_BYTES = (TC_BS / 2) * 3 * 8;       // 4 sites x 3 colours: one A warp's share of a slot
 constexpr int MAX_NS = 6;
 constexpr int TRING = 4;                              // tile ring entries
-constexpr int N_TILE_READERS = N_AWARPS + 4 + 1;     // A producers, epilogue, MMA
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t ACC_COL = 0;
 constexpr uint32_t A_COL = 416;
@@ -493,9 +504,11 @@ struct KParams {
 };
 
 template <int ELEM, int TERMS, int NC, bool RD>
-__global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
+__global__ void __launch_bounds__(Roles<RD>::NTHREADS, 1) tc_kernel(const KParams kp)
 {
     using SH = Shape<NC, RD>;
+    using R = Roles<RD>;
+    constexpr int WARP_LOAD = R::WARP_LOAD, WARP_MMA = R::WARP_MMA, N_TILE_READERS = R::N_TILE_READERS;
     constexpr int BIMG_BYTES = SH::BIMG_BYTES, B_BYTES = SH::B_BYTES, ATOM_COL_BYTES = SH::ATOM_COL_BYTES;
     constexpr uint32_t SUM_COL = SH::SUM_COL;
     extern __shared__ uint8_t smem_raw[];
@@ -522,7 +535,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
         }
         for (int h = 0; h < 2; h++) {
             mbar_init(&S->acc_full[h], 1);
-            mbar_init(&S->acc_empty[h], 4);
+            mbar_init(&S->acc_empty[h], R::EPI_WARPS);
         }
         mbar_init(&S->done, 1);
         S->abort = 0;
@@ -682,6 +695,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
     } else if (warp < WARP_LOAD) {
         // ---------------------------------------------------------- epilogue
         const int quad = warp & 3;
+        constexpr int N_EH = R::EPI_WARPS / 4;            // epilogue warps per lane quadrant
+        const int eh = (warp - N_AWARPS) >> 2;            // this warp's share: 16-column blocks b with b % N_EH == eh
         const int r = RD ? (quad * 32 + lane) >> 1 : quad * 32 + lane;   // the lane's (complex) row of the tile
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
         uint32_t gc = 0, gc1 = 0;   // drains done of the low / high column half
@@ -723,6 +738,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
                     }
                     tc_fence_after();
                     for (int b = c0 / 16; b * 16 < c1; b++) {
+                        if (N_EH > 1 && b % N_EH != eh) continue;
                         uint32_t va[16], vs[16];
                         tmem_ld16(tmem + lane_base + ACC_COL + 16u * b, va);
                         if (ch > 0) tmem_ld16(tmem + lane_base + SUM_COL + 16u * b, vs);
@@ -750,6 +766,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_kernel(const KParams kp)
             const long long n_trip = I.n_trip;
             float2 *part = kp.part + td.part_off;
             for (int b = 0; b * 16 < n_real; b++) {
+                if (N_EH > 1 && b % N_EH != eh) continue;
                 uint32_t v[16];
                 tmem_ld16(tmem + lane_base + SUM_COL + 16u * b, v);
                 tmem_wait_ld();
@@ -1145,7 +1162,7 @@ cudaError_t launch_one(const InstDev *d_inst, const TileDev *d_tiles, long long 
     if (e != cudaSuccess) return e;
     int grid = cfg.grid > 0 ? cfg.grid : 148;
     if ((long long)grid > n_tiles) grid = (int)n_tiles;
-    tc_kernel<ELEM, TERMS, NC, RD><<<grid, NTHREADS, smem, s>>>(kp);
+    tc_kernel<ELEM, TERMS, NC, RD><<<grid, Roles<RD>::NTHREADS, smem, s>>>(kp);
     return cudaGetLastError();
 }
 
