@@ -42,11 +42,11 @@ WORKLOADS = {
 METRIC = "baryon+meson block complex TFLOP/s at L=32,N=64,Np=19; tensor-pipe %; rel err vs FP64"
 
 # DRAM bytes (read + write) of tc_kernel per byte of B-operand stage images it consumes, from the ncu capture
-# summarised in profiles/tc_kernel_L24_T2_N64_P19_full.md (1.922 GB of DRAM traffic for 2 x 12 x 1728 stage images
+# summarised in profiles/tc_kernel_L24_T2_N64_P19_full.md (1.915 GB of DRAM traffic for 2 x 12 x 1728 stage images
 # of 39,936 B, tc_kernel<0,3,104,0>); the contraction's DRAM traffic is dominated by those images, so a launch's
 # traffic is this ratio times its image bytes.  It holds for the captured kernel only (layout 0, 104 columns): for
 # another tile shape the line reports no traffic.  To be retaken whenever the kernel changes.
-TC_DRAM_PER_IMAGE_BYTE = 1.922e9 / (2 * 12 * 1728 * 39936)
+TC_DRAM_PER_IMAGE_BYTE = 1.915e9 / (2 * 12 * 1728 * 39936)
 TC_CAPTURED_SHAPE = (128, 104)   # (tile rows, tile columns) of the captured kernel
 
 
