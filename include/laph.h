@@ -428,7 +428,8 @@ typedef struct {
  * (the wave model and, for one instance, the largest chunk within the 24 GiB
  * cap); then, from the fastest, half and twice the site-block size of the
  * FP64 reduction; then half and 1.5 times the drain interval (for all
- * tiles; chunk_sites_b is kept as given).  A drain
+ * tiles; chunk_sites_b is kept as given); finally the three fastest accepted
+ * schedules are timed twice more and each keeps its lowest time.  A drain
  * interval is accepted only if the relative error of (instance 0, timeslice 0)
  * against the FP32 CUDA-core path stays within 5e-6 (half the 1e-5 bound) or
  * within the default interval's own error; plans of several fields keep the

@@ -924,12 +924,12 @@ static int ring_times(const std::vector<cudaEvent_t> &b, const std::vector<cudaE
 // tensor core's accumulation (half and one and a half times the default; the
 // separate interval of tiles without meson rows is left to the caller: at the
 // 64-timeslice L=32 workload 1.5 times the default gained under 1% and raised
-// the baryon error from 2.8e-6 to 4.1e-6).
-// A drain interval is kept only if the error of (instance 0, timeslice 0)
-// against the FP32 CUDA-core path (its accuracy probe) stays within
-// TUNE_ERR_LIMIT or within the default's own probe error; plans of several
-// fields have no FP32 path and keep the default interval.  The fastest
-// accepted candidate is applied.
+// the baryon error from 2.8e-6 to 4.1e-6).  A drain interval is kept only if
+// the error of (instance 0, timeslice 0) against the FP32 CUDA-core path (its
+// accuracy probe) stays within TUNE_ERR_LIMIT or within the default's own
+// probe error; plans of several fields have no FP32 path and keep the default
+// interval.  Finally the three fastest accepted schedules are timed twice
+// more, each keeps its lowest time, and the fastest is applied.
 constexpr double TUNE_ERR_LIMIT = 5e-6;   // half the 1e-5 bound of the split-precision modes
 
 struct TuneState {
@@ -1025,6 +1025,7 @@ static int autotune(laph_plan *p, const laph::Sched &def, const std::function<cu
     int rc = LAPH_OK;
     cudaError_t e = cudaSuccess;
     size_t best = 0;
+    std::vector<char> accepted;   // candidates within the accuracy limit (all but rejected drain intervals)
     p->tune_cand.clear();
     p->tune_pc.clear();
     p->tune_ms.clear();
@@ -1042,6 +1043,7 @@ static int autotune(laph_plan *p, const laph::Sched &def, const std::function<cu
         p->tune_pc.push_back(p->sched_per_chunk);
         p->tune_ms.push_back(ms);
         p->tune_err.push_back(err);
+        accepted.push_back(1);
         return LAPH_OK;
     };
 #define TCK(call)                            \
@@ -1106,10 +1108,41 @@ static int autotune(laph_plan *p, const laph::Sched &def, const std::function<cu
                 c.chunk_sites_b = 0;
                 TRC(run(c, true));
                 const double err = p->tune_err.back();
-                if ((err <= TUNE_ERR_LIMIT || err <= err_def) && p->tune_ms.back() < p->tune_ms[best])
-                    best = p->tune_ms.size() - 1;
+                accepted.back() = err <= TUNE_ERR_LIMIT || err <= err_def;
+                if (accepted.back() && p->tune_ms.back() < p->tune_ms[best]) best = p->tune_ms.size() - 1;
             }
-
+        }
+        // 4: the three fastest accepted schedules are timed twice more, and
+        // each keeps the lowest of its times, so that one noisy timing does
+        // not decide between close candidates
+        std::vector<size_t> top;
+        for (size_t k = 0; k < p->tune_ms.size(); k++) {
+            if (!accepted[k]) continue;
+            bool dup = false;
+            for (size_t q : top) {
+                const laph::Sched &a = p->tune_cand[q], &b = p->tune_cand[k];
+                if (a.tile_cols == b.tile_cols && a.sum_sites == b.sum_sites && a.chunk_sites == b.chunk_sites &&
+                    a.per_chunk == b.per_chunk && a.order == b.order && a.rows2 == b.rows2 &&
+                    a.chunk_sites_b == b.chunk_sites_b) {
+                    p->tune_ms[q] = std::min(p->tune_ms[q], p->tune_ms[k]);   // the same schedule timed again
+                    dup = true;
+                }
+            }
+            if (!dup) top.push_back(k);
+            std::sort(top.begin(), top.end(), [&](size_t a, size_t b) { return p->tune_ms[a] < p->tune_ms[b]; });
+            if (top.size() > 3) top.pop_back();
+        }
+        for (int rep = 0; rep < 2 && top.size() > 1; rep++)
+            for (size_t k : top) {
+                TCK(apply(p->tune_cand[k]));
+                float ms = 0.f;
+                TRC(tune_time(p, ts, &ms));
+                p->tune_ms[k] = std::min(p->tune_ms[k], ms);
+            }
+        if (!top.empty()) {
+            best = top[0];
+            for (size_t k : top)
+                if (p->tune_ms[k] < p->tune_ms[best]) best = k;
         }
     }
     TCK(apply(p->tune_cand[best]));
