@@ -301,7 +301,7 @@ typedef struct {
     int layout;      /* tensor-core modes: how the complex product is laid out on the real tensor cores.
                         0 (default): every complex column of the phased operand is two real rows (re, im) of the
                         MMA's B operand, 128 complex rows per tile; 1: every complex row of the diquark / meson
-                        operand is two real rows of the MMA's A operand (tensor-memory lanes 2r, 2r+1), 64 complex
+                        operand is two real rows of the MMA's A operand (tensor-memory lanes r, 64+r), 64 complex
                         rows per tile, and the phased operand's stage images are half as large */
     int chunk_sites_b; /* tensor-core modes: drain interval of the tiles that hold no meson rows (0: chunk_sites).
                           Baryon and triplet sums are incoherent, so their error grows more slowly with the interval

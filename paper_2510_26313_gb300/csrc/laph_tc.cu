@@ -99,7 +99,7 @@ static_assert(A_LO + KSTAGE <= A_SLOT_COLS && A_COL + 2 * A_SLOT_COLS == TMEM_CO
 // Sizes that follow from the tile width NC (complex columns) and the layout
 // of the complex product.  RD false: every complex column is two real B rows
 // (re-row, im-row), UMMA N = 2 NC, and a tile has 128 complex rows; RD true:
-// every complex row is two real A rows (tensor-memory lanes 2r, 2r+1), UMMA
+// every complex row r is two real A rows (tensor-memory lanes r and 64 + r), UMMA
 // N = NC, and a tile has 64 complex rows.  Tensor memory: the accumulator in
 // columns [0, B_ROWS), the FP32 running sums in [B_ROWS, 2 B_ROWS), the two
 // A slots from column 416.
@@ -402,8 +402,13 @@ __device__ __forceinline__ int next_tile(const Ctx c, Ring &rt, bool &ok)
 
 // The 12 K entries of sites 4h..4h+3 of one row, from the block slots of
 // phi_i (pu) and phi_j (pv), split into hi and lo words.  kind: 2 diquark,
-// 1 meson (conj(phi_i)), 0 no row (zeros).
-template <int ELEM>
+// 1 meson (conj(phi_i)), 0 no row (zeros).  FORM: how an entry x of the
+// complex operand becomes a pair of real K entries: 0 (re, im), the
+// column-doubled layout; in the row-doubled layout 1 (re, -im) for the re-row
+// and 2 (im, re) for the im-row of a complex row, so that with B rows
+// (Psi_re, Psi_im) the re-row gives the real part of the product and the
+// im-row its imaginary part.
+template <int ELEM, int FORM>
 __device__ __forceinline__ void a_quarter(int kind, const uint8_t *pu, const uint8_t *pv, uint32_t (&hi)[12],
                                           uint32_t (&lo)[12])
 {
@@ -429,49 +434,10 @@ __device__ __forceinline__ void a_quarter(int kind, const uint8_t *pu, const uin
                 d = make_float2(u[e].x, -u[e].y);
             else
                 d = make_float2(0.f, 0.f);
+            if (FORM == 1) d = make_float2(d.x, -d.y);
+            if (FORM == 2) d = make_float2(d.y, d.x);
             split2<ELEM>(d.x, d.y, hi[6 * m + e], lo[6 * m + e]);
         }
-    }
-}
-
-// Row-doubled layout: lanes 2r (part 0) and 2r+1 (part 1) hold the two real
-// rows of complex row r.  Each lane forms half of the row's 12 K entries of
-// sites 4h..4h+3 (part p: sites 4h+2p, 4h+2p+1), the pair exchanges them, and
-// every lane splits all 12 in its own form: (re, -im) for the re-row, (im, re)
-// for the im-row, so that with B rows (Psi_re, Psi_im) the re-row gives the
-// real part of the product and the im-row its imaginary part.
-template <int ELEM>
-__device__ __forceinline__ void a_pair(int kind, int part, const uint8_t *pu, const uint8_t *pv, uint32_t (&hi)[12],
-                                       uint32_t (&lo)[12])
-{
-    float2 u[6], v[6], mine[6], other[6];
-#pragma unroll
-    for (int h = 0; h < 3; h++) {
-        const float4 a = reinterpret_cast<const float4 *>(pu)[3 * part + h];
-        const float4 b = reinterpret_cast<const float4 *>(pv)[3 * part + h];
-        u[2 * h] = make_float2(a.x, a.y);
-        u[2 * h + 1] = make_float2(a.z, a.w);
-        v[2 * h] = make_float2(b.x, b.y);
-        v[2 * h + 1] = make_float2(b.z, b.w);
-    }
-#pragma unroll
-    for (int e = 0; e < 6; e++) {
-        float2 x;
-        if (kind == 2)
-            x = cross8(u + 3 * (e / 3), v + 3 * (e / 3), e % 3);
-        else if (kind == 1)
-            x = make_float2(u[e].x, -u[e].y);
-        else
-            x = make_float2(0.f, 0.f);
-        mine[e] = x;
-        other[e] = make_float2(__shfl_xor_sync(0xffffffffu, x.x, 1), __shfl_xor_sync(0xffffffffu, x.y, 1));
-    }
-    // entries 0..5 belong to sites 4h, 4h+1 (part 0's), 6..11 to sites 4h+2, 4h+3 (part 1's)
-#pragma unroll
-    for (int e = 0; e < 12; e++) {
-        const float2 x = e < 6 ? (part == 0 ? mine[e] : other[e]) : (part == 0 ? other[e - 6] : mine[e - 6]);
-        const float re = part == 0 ? x.x : x.y, im = part == 0 ? -x.y : x.x;
-        split2<ELEM>(re, im, hi[e], lo[e]);
     }
 }
 
@@ -604,7 +570,9 @@ __global__ void __launch_bounds__(Roles<RD>::NTHREADS, 1) tc_kernel(const KParam
     } else if (warp < N_AWARPS) {
         // ---------------------------------------------------------- A producers
         const int quad = warp & 3, half = (warp >> 2) & 1, grp = warp >> 3;
-        const int r = RD ? (quad * 32 + lane) >> 1 : quad * 32 + lane;   // the lane's (complex) row of the tile
+        // the lane's (complex) row of the tile; row-doubled layout: lane quadrants 0, 1 hold the re-rows of the
+        // tile's 64 complex rows, quadrants 2, 3 their im-rows
+        const int r = RD ? 32 * (quad & 1) + lane : quad * 32 + lane;
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
         const uint32_t ta0 = tmem + lane_base + A_COL + (uint32_t)grp * A_SLOT_COLS + 12u * half;
         uint32_t G = 0;   // global index of the tile's first stage
@@ -661,10 +629,12 @@ __global__ void __launch_bounds__(Roles<RD>::NTHREADS, 1) tc_kernel(const KParam
                 }
                 const uint8_t *buf = smem + s * kp.stage_bytes;
                 uint32_t hi[12], lo[12];
-                if (RD)
-                    a_pair<ELEM>(kind, lane & 1, buf + off_u, buf + off_v, hi, lo);
+                if (!RD)
+                    a_quarter<ELEM, 0>(kind, buf + off_u, buf + off_v, hi, lo);
+                else if (quad < 2)
+                    a_quarter<ELEM, 1>(kind, buf + off_u, buf + off_v, hi, lo);
                 else
-                    a_quarter<ELEM>(kind, buf + off_u, buf + off_v, hi, lo);
+                    a_quarter<ELEM, 2>(kind, buf + off_u, buf + off_v, hi, lo);
                 if (!warp_wait(c, &S->empty[s2], ph2)) {
                     ok = false;
                     break;
@@ -697,7 +667,7 @@ __global__ void __launch_bounds__(Roles<RD>::NTHREADS, 1) tc_kernel(const KParam
         const int quad = warp & 3;
         constexpr int N_EH = R::EPI_WARPS / 4;            // epilogue warps per lane quadrant
         const int eh = (warp - N_AWARPS) >> 2;            // this warp's share: 16-column blocks b with b % N_EH == eh
-        const int r = RD ? (quad * 32 + lane) >> 1 : quad * 32 + lane;   // the lane's (complex) row of the tile
+        const int r = RD ? 32 * (quad & 1) + lane : quad * 32 + lane;   // the lane's (complex) row of the tile
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
         uint32_t gc = 0, gc1 = 0;   // drains done of the low / high column half
         bool ok = true;
@@ -771,12 +741,10 @@ __global__ void __launch_bounds__(Roles<RD>::NTHREADS, 1) tc_kernel(const KParam
                 tmem_ld16(tmem + lane_base + SUM_COL + 16u * b, v);
                 tmem_wait_ld();
                 if (RD) {
-                    // lane 2r holds the real parts of complex row r, lane 2r+1
-                    // the imaginary parts: the pair's even lane writes
+                    // lane quadrants 0, 1 hold the real parts of the complex
+                    // rows, quadrants 2, 3 the imaginary parts: each writes its half
 #pragma unroll
                     for (int u = 0; u < 16; u++) {
-                        const uint32_t o = __shfl_xor_sync(0xffffffffu, v[u], 1);
-                        if (lane & 1) continue;
                         const int cc = cskip + 16 * b + u;
                         if (!rvalid || cc >= ncols) continue;
                         const int col = td.col0 + cc;
@@ -790,7 +758,7 @@ __global__ void __launch_bounds__(Roles<RD>::NTHREADS, 1) tc_kernel(const KParam
                             if (k <= pj) continue;
                             e = (long long)p * n_trip + binom3(k) + q;
                         }
-                        part[e] = make_float2(__uint_as_float(v[u]), __uint_as_float(o));
+                        reinterpret_cast<float *>(part + e)[quad >> 1] = __uint_as_float(v[u]);
                     }
                     continue;
                 }
