@@ -41,13 +41,16 @@ WORKLOADS = {
 }
 METRIC = "baryon+meson block complex TFLOP/s at L=32,N=64,Np=19; tensor-pipe %; rel err vs FP64"
 
-# DRAM bytes (read + write) of tc_kernel per byte of B-operand stage images it consumes, from the ncu capture
-# summarised in profiles/tc_kernel_L24_T2_N64_P19_full.md (1.915 GB of DRAM traffic for 2 x 12 x 1728 stage images
-# of 39,936 B, tc_kernel<0,3,104,0>); the contraction's DRAM traffic is dominated by those images, so a launch's
-# traffic is this ratio times its image bytes.  It holds for the captured kernel only (layout 0, 104 columns): for
-# another tile shape the line reports no traffic.  To be retaken whenever the kernel changes.
-TC_DRAM_PER_IMAGE_BYTE = 1.915e9 / (2 * 12 * 1728 * 39936)
-TC_CAPTURED_SHAPE = (128, 104)   # (tile rows, tile columns) of the captured kernel
+# DRAM bytes (read + write) of tc_kernel per byte of B-operand stage images it consumes, from the ncu captures
+# summarised in profiles/, by (tile rows, tile columns): tc_kernel_L24_T2_N64_P19_full.md (1.941 GB for 2 x 12 x 1728
+# stage images of 39,936 B, tc_kernel<0,3,104,0>) and tc_kernel_rowdoubled208_L24_T2_N64_P19_full.md (1.071 GB for
+# 2 x 6 x 1728 images of 39,936 B, tc_kernel<0,3,208,1>).  The contraction's DRAM traffic is dominated by those images,
+# so a launch's traffic is the ratio times its image bytes; a plan of another tile shape reports no traffic.  To be
+# retaken whenever the kernel changes.
+TC_DRAM_PER_IMAGE_BYTE = {(128, 104): 1.941e9 / (2 * 12 * 1728 * 39936),
+                          (64, 208): 1.071e9 / (2 * 6 * 1728 * 39936)}
+TC_PROFILE = {(128, 104): "profiles/tc_kernel_L24_T2_N64_P19_full.md",
+              (64, 208): "profiles/tc_kernel_rowdoubled208_L24_T2_N64_P19_full.md"}
 
 
 def momenta_for(name):
@@ -900,12 +903,13 @@ def main():
         n_ct = -(-(N * P) // nc)
         img_b = 192 * nc if desc["tile_rows"] == 64 else 384 * nc  # one stage image (layout 1: one B row per column)
         images = T * n_ct * (-(-(3 * V) // 24)) * img_b            # stage images read per step
-        captured = (desc["tile_rows"], nc) == TC_CAPTURED_SHAPE
+        shape = (desc["tile_rows"], nc)
+        ratio = TC_DRAM_PER_IMAGE_BYTE.get(shape)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": TC_DRAM_PER_IMAGE_BYTE * images / n_con if captured else None,
-                "traffic_source": ("per tc_kernel launch: DRAM bytes per stage-image byte from the ncu capture at "
-                                   "L=24, T=2 (profiles/tc_kernel_L24_T2_N64_P19_full.md) x this launch's image bytes"
-                                   if captured else "no capture of this tile shape"),
+                "frac": achieved / peak, "traffic": ratio * images / n_con if ratio else None,
+                "traffic_source": (f"per tc_kernel launch: DRAM bytes per stage-image byte from the ncu capture at "
+                                   f"L=24, T=2 ({TC_PROFILE[shape]}) x this launch's image bytes"
+                                   if ratio else "no capture of this tile shape"),
                 "peak_source": f"{peak_src} bf16 dense sustained (cuBLAS); FP16 runs at the bf16 rate",
                 "note": "achieved counts algorithmic flops; the 3-term split executes 3x that on the tensor pipe"}
         # B-operand stage images: HBM-bound, algorithmic bytes = images written + phi read once
