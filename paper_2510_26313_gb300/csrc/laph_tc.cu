@@ -19,10 +19,9 @@
 // sums tolerate a longer interval) into a second tensor-memory region of
 // FP32 running sums kept by CUDA cores with round-to-nearest.  A tile covers
 // one block of sites (at most sc_stages K stages); at its end the running
-// sums are stored as FP32
-// partials, and reduce_kernel adds the partials of all site blocks of an
-// output in FP64, in block order, scales them back and writes the
-// complex128 output.  At chunk boundaries the MMAs of the two column halves
+// sums are stored as FP32 partials, and reduce_kernel adds the partials of
+// all site blocks of an output in FP64, in block order, scales them back and
+// writes the complex128 (or complex64) output.  At chunk boundaries the MMAs of the two column halves
 // of the accumulator are issued and committed separately, so that the drain
 // of one half overlaps the MMAs of the other.
 //
