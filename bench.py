@@ -718,13 +718,11 @@ def run_lanczos(args):
     return 0
 
 
-def run_ragged(args):
-    """--workload ragged: 200 ragged instances (L in {16,24,32}, N in [24,96], P in {1,7,19,33},
-    T in 1..8) in one plan; the same instances as 200 separate plans for comparison."""
+def measure_ragged(laph, count, mode, chunk_sites, steps, warmup, check=True):
+    """`count` seeded ragged instances (L in {16,24,32}, N in [24,96], P in {1,7,19,33}, T in 1..8) in one plan,
+    then the same instances as one plan each; with `check`, the FP64 oracle on timeslice 0 of the three smallest."""
     import torch
-    from paper_2510_26313_gb300 import binding as laph
-    torch.cuda.set_device(0)
-    insts = synth.ragged_instances(200)
+    insts = synth.ragged_instances(count)
     specs = [(i.L, i.T, i.N, i.momenta) for i in insts]
     flops_step = sum(i.T * flops_per_timeslice(i.L, i.N, i.P) for i in insts)
     gen = torch.Generator(device="cuda")
@@ -733,11 +731,11 @@ def run_ragged(args):
     for i in insts:
         z = torch.randn((i.T, i.N, i.V, 3, 2), generator=gen, device="cuda", dtype=torch.float32)
         phis.append(torch.view_as_complex(z).contiguous() / math.sqrt(3 * i.V))
-    plan = laph.Plan(specs, mode=args.mode, flags=laph.PLAN_TIMING, chunk_sites=args.chunk_sites)
+    plan = laph.Plan(specs, mode=mode, flags=laph.PLAN_TIMING, chunk_sites=chunk_sites)
     Bs, Ms = plan.alloc_outputs()
     ws = plan.alloc_workspace()
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         plan.execute(phis, Bs, Ms, ws, stream=stream)
     torch.cuda.synchronize()
     if plan.device_status() != laph.LAPH_OK:
@@ -747,17 +745,16 @@ def run_ragged(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         plan.execute(phis, Bs, Ms, ws, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     n_con = plan.contraction_launches()
-    k_ms = sum(plan.kernel_times(args.steps * n_con)) / args.steps
-    # accuracy on the smallest instances (timeslice 0) against the FP64 oracle
+    k_ms = sum(plan.kernel_times(steps * n_con)) / steps
     rel = []
-    if not args.no_cpu_baseline:
+    if check:
         small = sorted(range(len(insts)), key=lambda n: insts[n].T * flops_per_timeslice(insts[n].L, insts[n].N, insts[n].P))[:3]
         for n in small:
             B0, M0, _, _, _ = oracle_sample(phis[n][0].cpu().numpy().astype(np.complex64), insts[n].L, insts[n].momenta)
@@ -765,7 +762,7 @@ def run_ragged(args):
     # the same instances, one plan each, executed back to back
     del ws
     torch.cuda.empty_cache()
-    single = [laph.Plan([sp], mode=args.mode, chunk_sites=args.chunk_sites) for sp in specs]
+    single = [laph.Plan([sp], mode=mode, chunk_sites=chunk_sites) for sp in specs]
     sws = torch.empty(max(pl.workspace_size() for pl in single), dtype=torch.uint8, device="cuda")  # shared, stream-ordered
     for n, pl in enumerate(single):
         pl.execute([phis[n]], [Bs[n]], [Ms[n]], sws, stream=stream)
@@ -776,23 +773,79 @@ def run_ragged(args):
     e1.record(stream)
     torch.cuda.synchronize()
     ms_single = e0.elapsed_time(e1)
+    out = {"value": flops_step / (ms / 1e3) / 1e12, "ms_per_step": ms, "kernel_ms": k_ms,
+           "kernel_tflops": flops_step / (k_ms / 1e3) / 1e12, "flops_step": flops_step,
+           "timeslices": sum(i.T for i in insts), "per_instance_plans": {"ms_per_step": ms_single,
+                                                                          "value": flops_step / (ms_single / 1e3) / 1e12},
+           "rel_err": rel, "clocks": clk, "contraction_launches": n_con,
+           "gpu_launches": plan.launches_per_execute() * steps, "schedule": schedule_of(plan, False),
+           "device_status": plan.device_status()}
+    for pl in single:
+        pl.close()
+    plan.close()
+    return out
+
+
+def run_ragged(args):
+    """--workload ragged: 200 ragged instances (L in {16,24,32}, N in [24,96], P in {1,7,19,33},
+    T in 1..8) in one plan; the same instances as 200 separate plans for comparison."""
+    import torch
+    from paper_2510_26313_gb300 import binding as laph
+    torch.cuda.set_device(0)
+    r = measure_ragged(laph, 200, args.mode, args.chunk_sites, args.steps, args.warmup, not args.no_cpu_baseline)
     peaks, _ = measured_peaks()
     peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
     line = {
-        "metric": "ragged batch complex TFLOP/s (200 instances, one plan)", "value": flops_step / (ms / 1e3) / 1e12,
-        "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "metric": "ragged batch complex TFLOP/s (200 instances, one plan)", "value": r["value"],
+        "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": f"{args.mode}->f32/f64",
         "data": "synthetic (seeded complex Gaussian, not orthonormalised)",
         "config": {"workload": "200 ragged instances: L in {16,24,32}, N in [24,96], P in {1,7,19,33}, T in 1..8",
-                   "timeslices": sum(i.T for i in insts), "mode": args.mode},
-        "roofline": {"bound": "tensor", "achieved": flops_step / (k_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                     "frac": flops_step / (k_ms / 1e3) / 1e12 / peak, "traffic": None},
-        "per_instance_plans": {"ms_per_step": ms_single, "value": flops_step / (ms_single / 1e3) / 1e12},
-        "gpu_launches": plan.launches_per_execute() * args.steps, "clocks": clk, "rel_err": rel,
-        "contraction_launches": n_con, "kernel_ms": k_ms, "schedule": schedule_of(plan, False),
+                   "timeslices": r["timeslices"], "mode": args.mode},
+        "roofline": {"bound": "tensor", "achieved": r["kernel_tflops"], "peak": peak, "unit": "TFLOP/s",
+                     "frac": r["kernel_tflops"] / peak, "traffic": None},
+        "per_instance_plans": r["per_instance_plans"],
+        "gpu_launches": r["gpu_launches"], "clocks": r["clocks"], "rel_err": r["rel_err"],
+        "contraction_launches": r["contraction_launches"], "kernel_ms": r["kernel_ms"], "schedule": r["schedule"],
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def measure_lanczos(laph, cfg, steps, warmup, seed):
+    """One batched Lanczos solve of configuration `cfg` (see LANCZOS) on seeded smoothed links, timed: timeslices
+    per second, the phases, the eigenvalue range and the largest residual norm."""
+    import torch
+    L, T, n_ev, m, d, lo = cfg["L"], cfg["T"], cfg["n_ev"], cfg["m"], cfg["degree"], cfg["lo"]
+    V = L ** 3
+    U = synth.random_links_device(L, T, cfg["eps"], seed)
+    evecs = torch.empty((T, n_ev, V, 3), dtype=torch.complex64, device="cuda")
+    ws = torch.empty(laph.lanczos_workspace_size(L, T, n_ev, m, d, lo), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        laph.lanczos(U, L, n_ev, m, cheb_degree=d, cheb_lo=lo, out=evecs, workspace=ws, stream=stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    stats = []
+    e0.record(stream)
+    for _ in range(steps):
+        st = {}
+        _, ev, res = laph.lanczos(U, L, n_ev, m, cheb_degree=d, cheb_lo=lo, out=evecs, workspace=ws, stream=stream,
+                                  stats=st)
+        stats.append(st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    ev = ev.cpu().numpy() if hasattr(ev, "cpu") else np.asarray(ev)
+    res = res.cpu().numpy() if hasattr(res, "cpu") else np.asarray(res)
+    out = {"value": T / (ms / 1e3), "unit": "timeslices/s", "ms_per_solve": ms,
+           "filter_ms": sum(s["apply_ms"] for s in stats) / steps, "orth_ms": sum(s["orth_ms"] for s in stats) / steps,
+           "eigenvalues": [float(ev.min()), float(ev.max())], "max_residual": float(res.max()),
+           "config": {k: cfg[k] for k in ("L", "T", "n_ev", "m", "degree", "lo")}}
+    del ws, evecs, U
+    torch.cuda.empty_cache()
+    return out
 
 
 def main():
@@ -806,6 +859,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-extra-aux", action="store_true",
+                    help="skip the ragged-batch and eigensolver side measurements (thousands of launches: keep them "
+                         "out of profiler launch lists)")
     ap.add_argument("--ref-triples", type=int, default=6000)
     ap.add_argument("--chunk-sites", type=int, default=0)
     ap.add_argument("--sum-sites", type=int, default=0)
@@ -1001,6 +1057,14 @@ def main():
             aux["triplets"] = {"timeslices": min(4, T), "ms": tr["ms_per_step"], "kernel_ms": tr["kernel_ms"],
                                "value": tr["value"], "kernel_tflops": tr["kernel_tflops"], "unit": "TFLOP/s",
                                "rel_err": tr.get("rel_err"), "device_status": tr["device_status"]}
+        # the ragged batch (200 instances in one plan, and as 200 plans) and the LapH eigensolver at its benchmark
+        # configuration, so that the default run records them too
+        if args.mode in ("f16x3", "bf16x3") and args.workload == "metric" and not args.no_extra_aux:
+            rg = measure_ragged(laph, 200, args.mode, args.chunk_sites, 2, 1, check=not args.no_cpu_baseline)
+            aux["ragged_200"] = {k: rg[k] for k in ("value", "ms_per_step", "kernel_tflops", "timeslices",
+                                                      "per_instance_plans", "rel_err", "device_status")}
+            aux["ragged_200"]["unit"] = "TFLOP/s"
+            aux["lanczos"] = measure_lanczos(laph, LANCZOS["lanczos"], 2, 1, synth.SEED_BASE + 21)
 
     # ---- accuracy and CPU baseline on timeslice 0 (rank 0 only)
     rel = None
