@@ -812,6 +812,40 @@ def run_ragged(args):
     return 0
 
 
+def measure_medium_fp32(laph, steps, warmup, check=True):
+    """The FP32 CUDA-core path (the plain FP32 GPU path) at the medium configuration (L=24, T=48, N=32, 7 momenta);
+    with `check`, the FP64 oracle on timeslice 0."""
+    import torch
+    L, T, N, _ = WORKLOADS["medium"]
+    mom = momenta_for("medium")
+    P = int(mom.shape[0])
+    phi_h = synth.random_phi(L, N, T=T, instance=0)
+    phi = torch.from_numpy(phi_h).cuda()
+    plan = laph.Plan([(L, T, N, mom)], mode="fp32")
+    Bs, Ms = plan.alloc_outputs()
+    ws = plan.alloc_workspace()
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        plan.execute([phi], Bs, Ms, ws, stream=stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        plan.execute([phi], Bs, Ms, ws, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    out = {"value": T * flops_per_timeslice(L, N, P) / (ms / 1e3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
+           "workload": f"L={L},T={T},N={N},P={P}", "device_status": plan.device_status()}
+    if check:
+        B0, M0, _, _, _ = oracle_sample(phi_h[0], L, mom)
+        out["rel_err"] = {"B": rel_frob(Bs[0][0].cpu().numpy(), B0), "M": rel_frob(Ms[0][0].cpu().numpy(), M0),
+                          "timeslice": 0}
+    plan.close()
+    return out
+
+
 def measure_lanczos(laph, cfg, steps, warmup, seed):
     """One batched Lanczos solve of configuration `cfg` (see LANCZOS) on seeded smoothed links, timed: timeslices
     per second, the phases, the eigenvalue range and the largest residual norm."""
@@ -860,8 +894,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-extra-aux", action="store_true",
-                    help="skip the ragged-batch and eigensolver side measurements (thousands of launches: keep them "
-                         "out of profiler launch lists)")
+                    help="skip the ragged-batch, eigensolver and FP32 medium-configuration side measurements "
+                         "(thousands of launches: keep them out of profiler launch lists)")
     ap.add_argument("--ref-triples", type=int, default=6000)
     ap.add_argument("--chunk-sites", type=int, default=0)
     ap.add_argument("--sum-sites", type=int, default=0)
@@ -1065,6 +1099,7 @@ def main():
                                                       "per_instance_plans", "rel_err", "device_status")}
             aux["ragged_200"]["unit"] = "TFLOP/s"
             aux["lanczos"] = measure_lanczos(laph, LANCZOS["lanczos"], 2, 1, synth.SEED_BASE + 21)
+            aux["medium_fp32"] = measure_medium_fp32(laph, 3, 2, check=not args.no_cpu_baseline)
 
     # ---- accuracy and CPU baseline on timeslice 0 (rank 0 only)
     rel = None
