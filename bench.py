@@ -705,7 +705,7 @@ def run_lanczos(args):
                    "orth_ms": orth_ms, "orth_gbs": orth_gbs,
                    "setup_ms": sum(s["setup_ms"] for s in stats) / args.steps,
                    "ritz_ms": sum(s["ritz_ms"] for s in stats) / args.steps,
-                   "other_ms": ms - apply_ms - orth_ms},
+                   "other_ms": ms - apply_ms - orth_ms, "host_steps": max(s["host_steps"] for s in stats)},
         "convergence": {"max_resid": float(res.max()), "median_resid": float(np.median(res)),
                         "ev_min": float(ev.min()), "ev_max": float(ev.max())},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(sum(s["launches"] for s in stats)), "clocks": clk,
@@ -875,6 +875,7 @@ def measure_lanczos(laph, cfg, steps, warmup, seed):
     res = res.cpu().numpy() if hasattr(res, "cpu") else np.asarray(res)
     out = {"value": T / (ms / 1e3), "unit": "timeslices/s", "ms_per_solve": ms,
            "filter_ms": sum(s["apply_ms"] for s in stats) / steps, "orth_ms": sum(s["orth_ms"] for s in stats) / steps,
+           "ritz_ms": sum(s["ritz_ms"] for s in stats) / steps, "host_steps": max(s["host_steps"] for s in stats),
            "eigenvalues": [float(ev.min()), float(ev.max())], "max_residual": float(res.max()),
            "config": {k: cfg[k] for k in ("L", "T", "n_ev", "m", "degree", "lo")}}
     del ws, evecs, U

@@ -231,8 +231,9 @@ typedef struct {
 /* Where the time of one laph_lanczos call goes, from CUDA events recorded on
  * its stream: the whole call; the setup (workspace, start vectors); the
  * applications of -Delta (or of the filter); the orthogonalisation with the
- * norm of each new basis vector (including its read-back to the host); the
- * Ritz vectors, Rayleigh quotients and residuals.  Launches of this
+ * norm and the Lanczos coefficients of each new basis vector; the Ritz
+ * vectors, Rayleigh quotients and residuals (with the read-back of the
+ * coefficients and the host tridiagonal solver).  Launches of this
  * library's kernels, of which the Laplacian launches (each over one filter
  * group of timeslices, or all T without a filter, one vector each). */
 typedef struct {
@@ -247,6 +248,8 @@ typedef struct {
                            and every link SU(3) to FP32 accuracy: third row within 2e-6 of
                            conj(row0 x row1)) */
     int ts_group;       /* timeslices per filter group used (T without a filter) */
+    int host_steps;     /* 1: a timeslice met an invariant subspace, so the Krylov steps ran a second time with
+                           the host reading the coefficients after every step (the figures above cover both runs) */
 } laph_lanczos_stats;
 
 /* Bytes of device workspace laph_lanczos needs (about 8 T 3 L^3 (n_krylov +
@@ -263,8 +266,12 @@ LAPH_API int laph_lanczos_workspace_size(int L, int T, int n_ev, const laph_lanc
  * (resid may be NULL); stats (may be NULL) receives the timings above.
  * workspace: device memory of laph_lanczos_workspace_size bytes, 256-byte
  * aligned (workspace_bytes its size), or NULL to have the call allocate it on
- * `stream` and free it before returning.  Synchronises the stream once per
- * Krylov step and blocks until done.  LAPH_ERR_ARG for bad parameters
+ * `stream` and free it before returning.  The Krylov steps run without host
+ * synchronisation: the coefficients stay on the device and are read back
+ * once, after the last step.  If a timeslice met an invariant subspace (its
+ * new vector vanished), the steps run again from the same start vectors with
+ * the stream synchronised after every step, so that the host can give that
+ * timeslice a fresh vector (stats->host_steps).  Blocks until done.  LAPH_ERR_ARG for bad parameters
  * (2 <= L <= 512, 1 <= T <= 65535, n_ev <= n_krylov, the bounds on n_krylov
  * and the filter above, ts_group < 0, link_rows other than 0, 2, 3), for
  * null or misaligned (8-byte) pointers and when the host tridiagonal solver does not converge,

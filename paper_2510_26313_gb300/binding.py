@@ -69,7 +69,8 @@ class laph_lanczos_params(ctypes.Structure):
 class laph_lanczos_stats(ctypes.Structure):
     _fields_ = [("total_ms", ctypes.c_double), ("setup_ms", ctypes.c_double), ("apply_ms", ctypes.c_double),
                 ("orth_ms", ctypes.c_double), ("ritz_ms", ctypes.c_double), ("launches", ctypes.c_int64),
-                ("apply_launches", ctypes.c_int64), ("links_two_rows", ctypes.c_int), ("ts_group", ctypes.c_int)]
+                ("apply_launches", ctypes.c_int64), ("links_two_rows", ctypes.c_int), ("ts_group", ctypes.c_int),
+                ("host_steps", ctypes.c_int)]
 
 
 def lib() -> ctypes.CDLL:

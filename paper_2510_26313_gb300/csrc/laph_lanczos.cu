@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(LAP_THREADS) update_kernel(const float2 *__res
     }
 }
 
-// out[t] = w[t] * scale[t] (scale from the host, FP64).
+// out[t] = w[t] * scale[t] (scale per timeslice, FP64).
 // copy: a second destination (may be null), [T][K].
 __global__ void scale_kernel(const float2 *__restrict__ w, long long ts_w, float2 *__restrict__ out, long long ts_out,
                              long long K, const double *__restrict__ scale, float2 *__restrict__ copy)
@@ -472,6 +472,30 @@ __global__ void scale_kernel(const float2 *__restrict__ w, long long ts_w, float
     const float2 r = make_float2(v.x * s, v.y * s);
     out[t * ts_out + e] = r;
     if (copy) copy[t * K + e] = r;
+}
+
+// alpha[t][j] = Re <v_j, A v_j>: row j of the first Gram-Schmidt pass's
+// coefficients (dots, [T][ld]).
+__global__ void take_alpha_kernel(const double2 *__restrict__ dots, int ld, int j, double *__restrict__ alpha, int m,
+                                  int T)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < T) alpha[(long long)t * m + j] = dots[(long long)t * ld + j].x;
+}
+
+// beta[t][j] = |w| after both Gram-Schmidt passes (norm2 = |w|^2), the scale
+// 1/|w| of the next basis vector, and in *brk the earliest step at which |w|
+// fell below 1e-6 max(1, |alpha|) (an invariant subspace; only when check).
+__global__ void take_beta_kernel(const double *__restrict__ norm2, const double *__restrict__ alpha, int j, int m,
+                                 int T, int check, double *__restrict__ beta, double *__restrict__ scale,
+                                 int *__restrict__ brk)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const double a = alpha[(long long)t * m + j], b = sqrt(fmax(norm2[t], 0.0));
+    beta[(long long)t * m + j] = b;
+    scale[t] = b > 1e-30 ? 1.0 / b : 0.0;
+    if (check && b < 1e-6 * fmax(1.0, fabs(a))) atomicMin(brk, j);
 }
 
 // X[t][r] = sum_j S[t][j][r] basis[t][j] for r < nr (S real, [T][m][nr]); each
@@ -729,7 +753,8 @@ namespace {
 // m + 1 vectors of every timeslice; after the Ritz vectors have been formed it
 // is reused for (-Delta) applied to them.
 struct LzLayout {
-    size_t Us, basis, w, ya, yb, yc, vin, X, dots, dscale, dnorm, dS, dred, dlam, dperm, dflag, total;
+    size_t Us, basis, w, ya, yb, yc, vin, X, dots, dscale, dnorm, dS, dred, dlam, dperm, dflag, dalpha, dbeta, dbrk,
+        total;
 };
 
 LzLayout lz_layout(long long K, int T, int m, int nr)
@@ -757,6 +782,9 @@ LzLayout lz_layout(long long K, int T, int m, int nr)
     l.dlam = take(sizeof(double) * (size_t)T * nr);
     l.dperm = take(sizeof(int) * (size_t)T * nr);
     l.dflag = take(sizeof(int));
+    l.dalpha = take(sizeof(double) * (size_t)T * m);
+    l.dbeta = take(sizeof(double) * (size_t)T * m);
+    l.dbrk = take(sizeof(int));
     l.total = off;
     return l;
 }
@@ -800,6 +828,8 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
     cudaStream_t s = (cudaStream_t)stream;
     char *ws = (char *)workspace, *owned = nullptr;
     cudaEvent_t ev[7] = {};   // call start, loop start, iteration (apply, orth, end), loop end, call end
+    std::vector<cudaEvent_t> step_ev;   // with stats: per Krylov step without host synchronisation, apply start,
+                                        // apply end, orthogonalisation end
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t filter = nullptr;
@@ -835,11 +865,13 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
     const bool pairs = V % 2 == 0;
     float2 *Ud, *basis, *w, *ya, *yb, *yc, *vin, *X, *Y;
     double2 *dots;
-    double *dscale, *dnorm, *dS, *dred, *dlam;
-    int *dperm;
+    double *dscale, *dnorm, *dS, *dred, *dlam, *dalpha, *dbeta;
+    int *dperm, *dbrk;
 
     if (stats) {
         for (auto &e : ev) LCK(cudaEventCreate(&e));
+        step_ev.assign(3 * (size_t)m, nullptr);
+        for (auto &e : step_ev) LCK(cudaEventCreate(&e));
         LCK(cudaEventRecord(ev[0], s));
     }
     if (!ws) {
@@ -862,6 +894,9 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
     dred = (double *)(ws + lay.dred);
     dlam = (double *)(ws + lay.dlam);
     dperm = (int *)(ws + lay.dperm);
+    dalpha = (double *)(ws + lay.dalpha);
+    dbeta = (double *)(ws + lay.dbeta);
+    dbrk = (int *)(ws + lay.dbrk);
 
     {
         // the operator on the newest basis vector v (of every timeslice) -> w
@@ -944,14 +979,42 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
             for (int t = 0; t < T; t++) h_norm[t] = tmp[2 * t];
             return e;
         };
-        // basis vector j = w * h_scale
-        auto store = [&](int j) -> cudaError_t {
-            cudaError_t e = cudaMemcpyAsync(dscale, h_scale.data(), sizeof(double) * T, cudaMemcpyHostToDevice, s);
-            if (e != cudaSuccess) return e;
+        // the same two passes for the steps without host synchronisation: the
+        // first pass's coefficient of basis vector j becomes alpha[t][j], |w|
+        // of the result beta[t][j], 1/|w| the scale of basis vector j + 1
+        // (dscale), and a step that meets an invariant subspace is noted in dbrk
+        auto orthogonalise_dev = [&](int j) -> cudaError_t {
+            const unsigned bt = (unsigned)((T + 127) / 128);
+            cudaError_t e = cudaSuccess;
+            for (int pass = 0; pass < 2 && e == cudaSuccess; pass++) {
+                e = cudaMemsetAsync(dots, 0, sizeof(double2) * (m + 1) * T, s);
+                if (e == cudaSuccess && pass == 1) e = cudaMemsetAsync(dnorm, 0, sizeof(double) * T, s);
+                if (e != cudaSuccess) break;
+                dots_kernel<<<dim3(blocks_dot, T), LAP_THREADS, 0, s>>>(basis, ts_b, w, K, K, j + 1, dots, m + 1);
+                update_kernel<<<dim3(blocks_upd, T), LAP_THREADS, sizeof(float2) * (j + 1), s>>>(
+                    basis, ts_b, w, K, K, j + 1, dots, m + 1, pass == 1 ? dnorm : nullptr);
+                if (pass == 0) take_alpha_kernel<<<bt, 128, 0, s>>>(dots, m + 1, j, dalpha, m, T);
+                e = cudaGetLastError();
+                st.launches += pass == 0 ? 3 : 2;
+            }
+            if (e == cudaSuccess) {
+                take_beta_kernel<<<bt, 128, 0, s>>>(dnorm, dalpha, j, m, T, j + 1 < m ? 1 : 0, dbeta, dscale, dbrk);
+                e = cudaGetLastError();
+                st.launches++;
+            }
+            return e;
+        };
+        // basis vector j = w * dscale (the scales already on the device)
+        auto store_dev = [&](int j) -> cudaError_t {
             scale_kernel<<<dim3(blocks_e, T), LAP_THREADS, 0, s>>>(w, K, basis + (long long)j * K, ts_b, K, dscale,
                                                                    d > 0 ? vin : nullptr);
             st.launches++;
             return cudaGetLastError();
+        };
+        // basis vector j = w * h_scale
+        auto store = [&](int j) -> cudaError_t {
+            cudaError_t e = cudaMemcpyAsync(dscale, h_scale.data(), sizeof(double) * T, cudaMemcpyHostToDevice, s);
+            return e == cudaSuccess ? store_dev(j) : e;
         };
 
         // the links in the solver's layout; two rows suffice when they are SU(3)
@@ -981,57 +1044,95 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
             LCK(e2);
             LCK(cudaGraphInstantiate(&filter, graph, 0));
         }
-        // start vectors: seeded pattern, normalised
-        LCK(laph::launch_fill_pattern(w, K * T, prm->seed ? prm->seed : 12345u, s));
-        st.launches++;
-        LCK(norm_w());
-        for (int t = 0; t < T; t++) h_scale[t] = 1.0 / std::sqrt(std::max(h_norm[t], 1e-300));
-        LCK(store(0));
-        if (stats) LCK(cudaEventRecord(ev[1], s));
-        for (int j = 0; j < m; j++) {
-            if (stats) LCK(cudaEventRecord(ev[2], s));
-            LCK(apply(basis + (long long)j * K));
-            if (stats) LCK(cudaEventRecord(ev[3], s));
-            LCK(orthogonalise(j + 1));
-            if (stats) {
-                float a = 0.f, o = 0.f;
-                LCK(cudaEventRecord(ev[4], s));
-                LCK(cudaEventSynchronize(ev[4]));
-                LCK(cudaEventElapsedTime(&a, ev[2], ev[3]));
-                LCK(cudaEventElapsedTime(&o, ev[3], ev[4]));
-                st.apply_ms += a;
-                st.orth_ms += o;
-            }
-            bool broke = false;
-            for (int t = 0; t < T; t++) {
-                const double a = h_dots[2 * ((size_t)t * (m + 1) + j)], b = std::sqrt(std::max(h_norm[t], 0.0));
-                alpha[(size_t)t * m + j] = a;
-                beta[(size_t)t * m + j] = b;
-                h_scale[t] = b > 1e-30 ? 1.0 / b : 0.0;
-                if (b < 1e-6 * std::max(1.0, std::fabs(a))) broke = true;
-            }
-            if (j + 1 == m) break;
-            if (broke) {
-                // an invariant subspace: the timeslices concerned continue from a
-                // fresh vector orthogonal to their basis, with a zero coupling
-                LCK(laph::launch_fill_pattern(ya, K * T, 777u + (unsigned)j, s));
-                st.launches++;
-                for (int t = 0; t < T; t++) {
-                    const double a = alpha[(size_t)t * m + j];
-                    if (beta[(size_t)t * m + j] < 1e-6 * std::max(1.0, std::fabs(a))) {
-                        LCK(cudaMemcpyAsync(w + (long long)t * K, ya + (long long)t * K, sizeof(float2) * K,
-                                            cudaMemcpyDeviceToDevice, s));
-                        beta[(size_t)t * m + j] = 0.0;
-                    }
+        // The Krylov steps.  First without host synchronisation: the
+        // coefficients alpha, beta and the next vector's scale stay on the
+        // device, and come back once after the last step.  If a timeslice met
+        // an invariant subspace on the way, the steps run again from the same
+        // start vectors (every launch is deterministic, so they repeat up to
+        // that step) with the host reading the coefficients after every step
+        // and giving the timeslices concerned a fresh vector.
+        for (int attempt = 0; attempt < 2; attempt++) {
+            const bool host_steps = attempt == 1;
+            // start vectors: seeded pattern, normalised
+            LCK(laph::launch_fill_pattern(w, K * T, prm->seed ? prm->seed : 12345u, s));
+            st.launches++;
+            LCK(norm_w());
+            for (int t = 0; t < T; t++) h_scale[t] = 1.0 / std::sqrt(std::max(h_norm[t], 1e-300));
+            LCK(store(0));
+            if (stats && attempt == 0) LCK(cudaEventRecord(ev[1], s));
+            if (!host_steps) {
+                LCK(cudaMemsetAsync(dbrk, 0x7f, sizeof(int), s));   // 0x7f7f7f7f: no step
+                for (int j = 0; j < m; j++) {
+                    if (stats) LCK(cudaEventRecord(step_ev[3 * (size_t)j], s));
+                    LCK(apply(basis + (long long)j * K));
+                    if (stats) LCK(cudaEventRecord(step_ev[3 * (size_t)j + 1], s));
+                    LCK(orthogonalise_dev(j));
+                    if (stats) LCK(cudaEventRecord(step_ev[3 * (size_t)j + 2], s));
+                    if (j + 1 < m) LCK(store_dev(j + 1));
                 }
-                const std::vector<double> keep = h_dots;
-                LCK(orthogonalise(j + 1));
-                h_dots = keep;
-                for (int t = 0; t < T; t++) h_scale[t] = 1.0 / std::sqrt(std::max(h_norm[t], 1e-300));
+                if (stats) LCK(cudaEventRecord(ev[5], s));
+                int h_brk = 0;
+                LCK(cudaMemcpyAsync(alpha.data(), dalpha, sizeof(double) * T * m, cudaMemcpyDeviceToHost, s));
+                LCK(cudaMemcpyAsync(beta.data(), dbeta, sizeof(double) * T * m, cudaMemcpyDeviceToHost, s));
+                LCK(cudaMemcpyAsync(&h_brk, dbrk, sizeof(int), cudaMemcpyDeviceToHost, s));
+                LCK(cudaStreamSynchronize(s));
+                if (stats)
+                    for (int j = 0; j < m; j++) {
+                        float a = 0.f, o = 0.f;
+                        LCK(cudaEventElapsedTime(&a, step_ev[3 * (size_t)j], step_ev[3 * (size_t)j + 1]));
+                        LCK(cudaEventElapsedTime(&o, step_ev[3 * (size_t)j + 1], step_ev[3 * (size_t)j + 2]));
+                        st.apply_ms += a;
+                        st.orth_ms += o;
+                    }
+                if (h_brk >= m) break;
+                st.host_steps = 1;
+                continue;
             }
-            LCK(store(j + 1));
+            for (int j = 0; j < m; j++) {
+                if (stats) LCK(cudaEventRecord(ev[2], s));
+                LCK(apply(basis + (long long)j * K));
+                if (stats) LCK(cudaEventRecord(ev[3], s));
+                LCK(orthogonalise(j + 1));
+                if (stats) {
+                    float a = 0.f, o = 0.f;
+                    LCK(cudaEventRecord(ev[4], s));
+                    LCK(cudaEventSynchronize(ev[4]));
+                    LCK(cudaEventElapsedTime(&a, ev[2], ev[3]));
+                    LCK(cudaEventElapsedTime(&o, ev[3], ev[4]));
+                    st.apply_ms += a;
+                    st.orth_ms += o;
+                }
+                bool broke = false;
+                for (int t = 0; t < T; t++) {
+                    const double a = h_dots[2 * ((size_t)t * (m + 1) + j)], b = std::sqrt(std::max(h_norm[t], 0.0));
+                    alpha[(size_t)t * m + j] = a;
+                    beta[(size_t)t * m + j] = b;
+                    h_scale[t] = b > 1e-30 ? 1.0 / b : 0.0;
+                    if (b < 1e-6 * std::max(1.0, std::fabs(a))) broke = true;
+                }
+                if (j + 1 == m) break;
+                if (broke) {
+                    // an invariant subspace: the timeslices concerned continue from a
+                    // fresh vector orthogonal to their basis, with a zero coupling
+                    LCK(laph::launch_fill_pattern(ya, K * T, 777u + (unsigned)j, s));
+                    st.launches++;
+                    for (int t = 0; t < T; t++) {
+                        const double a = alpha[(size_t)t * m + j];
+                        if (beta[(size_t)t * m + j] < 1e-6 * std::max(1.0, std::fabs(a))) {
+                            LCK(cudaMemcpyAsync(w + (long long)t * K, ya + (long long)t * K, sizeof(float2) * K,
+                                                cudaMemcpyDeviceToDevice, s));
+                            beta[(size_t)t * m + j] = 0.0;
+                        }
+                    }
+                    const std::vector<double> keep = h_dots;
+                    LCK(orthogonalise(j + 1));
+                    h_dots = keep;
+                    for (int t = 0; t < T; t++) h_scale[t] = 1.0 / std::sqrt(std::max(h_norm[t], 1e-300));
+                }
+                LCK(store(j + 1));
+            }
+            if (stats) LCK(cudaEventRecord(ev[5], s));
         }
-        if (stats) LCK(cudaEventRecord(ev[5], s));
         // Ritz pairs of the tridiagonal matrices; the wanted end: the smallest
         // eigenvalues of -Delta, the largest of the filter (times (-1)^d: T_d
         // grows with sign (-1)^d below the damped interval)
@@ -1130,6 +1231,8 @@ int laph_lanczos(const void *U, int L, int T, int n_ev, const laph_lanczos_param
     }
 done:
     for (auto &e : ev)
+        if (e) cudaEventDestroy(e);
+    for (auto &e : step_ev)
         if (e) cudaEventDestroy(e);
     if (filter) cudaGraphExecDestroy(filter);
     if (graph) cudaGraphDestroy(graph);

@@ -109,18 +109,22 @@ def test_lanczos_with_and_without_the_chebyshev_filter_at_L8(laph, degree, link_
     vecs, ev, res = laph.lanczos(torch.from_numpy(U).cuda(), L, n_ev, m, cheb_degree=degree, cheb_lo=1.45,
                                  link_rows=link_rows, stats=st)
     assert st["links_two_rows"] == (link_rows == 2 or (link_rows == 0 and degree == 0))
+    assert st["host_steps"] == 0   # no invariant subspace: the steps ran without host synchronisation
     check_against_dense(U, L, n_ev, ev, vecs.cpu().numpy(), res)
 
 
 def test_lanczos_breakdown_on_the_degenerate_free_field(laph):
     """U = 1 at L = 3: eigenvalues 0 (x3), 3 (x18), 6 (x36), 9 (x24).  A Krylov space of one start vector holds
     one vector per eigenspace, so the iteration breaks down and continues from fresh vectors; with 3 L^3 steps
-    every eigenvector is found."""
+    every eigenvector is found.  The breakdown is detected on the device after the steps that ran without host
+    synchronisation, which then run again with the host deciding after every step."""
     import torch
     L = 3
     V = L ** 3
     U = np.broadcast_to(np.eye(3, dtype=np.complex64), (2, 3, V, 3, 3)).copy()
-    vecs, ev, res = laph.lanczos(torch.from_numpy(U).cuda(), L, 24, 3 * V)
+    st = {}
+    vecs, ev, res = laph.lanczos(torch.from_numpy(U).cuda(), L, 24, 3 * V, stats=st)
+    assert st["host_steps"] == 1
     ref = np.array([0.0] * 3 + [3.0] * 18 + [6.0] * 3)
     np.testing.assert_allclose(ev, np.broadcast_to(ref, ev.shape), atol=5e-5)
     assert res.max() <= 1e-3
