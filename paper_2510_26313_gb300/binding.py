@@ -168,13 +168,59 @@ def triple_index(i: int, j: int, k: int) -> int:
     return int(lib().laph_triple_index(i, j, k))
 
 
-def _check_phi(phi, L):
+def _on_current_device(t) -> bool:
     import torch
-    if not (phi.is_cuda and phi.dtype == torch.complex64 and phi.is_contiguous()):
-        raise ValueError("phi must be a contiguous complex64 CUDA tensor [T][N][L^3][3]")
+    return t.device.index == torch.cuda.current_device()
+
+
+def _check_tensor(t, dtype, shape, name):
+    """t must be a contiguous CUDA tensor of `dtype` and exactly `shape` on the current CUDA device: the C side
+    reads or writes exactly that many elements there and cannot check the size of a device buffer."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous {dtype} CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not _on_current_device(t):
+        raise ValueError(f"{name} must be on the current CUDA device")
+
+
+def _check_workspace(ws, nbytes, name="workspace"):
+    """A device workspace of at least `nbytes` bytes on the current CUDA device (None when nbytes is 0)."""
+    import torch
+    if nbytes == 0 and ws is None:
+        return
+    if not (isinstance(ws, torch.Tensor) and ws.is_cuda and ws.is_contiguous() and _on_current_device(ws)):
+        raise ValueError(f"{name} must be a contiguous CUDA tensor on the current device ({nbytes} bytes)")
+    if ws.numel() * ws.element_size() < nbytes:
+        raise ValueError(f"{name} holds {ws.numel() * ws.element_size()} bytes, {nbytes} are needed")
+
+
+def _check_phi(phi, L, T=None, N=None, name="phi"):
+    """A field complex64 [T][N][L^3][3] on the current CUDA device; T and N are checked when given."""
+    import torch
+    if not (isinstance(phi, torch.Tensor) and phi.is_cuda and phi.dtype == torch.complex64 and phi.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous complex64 CUDA tensor [T][N][L^3][3]")
     if phi.dim() != 4 or phi.shape[2] != L ** 3 or phi.shape[3] != 3:
-        raise ValueError(f"phi must be [T][N][L^3][3], got {tuple(phi.shape)} for L={L}")
+        raise ValueError(f"{name} must be [T][N][L^3][3], got {tuple(phi.shape)} for L={L}")
+    if (T is not None and phi.shape[0] != T) or (N is not None and phi.shape[1] != N):
+        raise ValueError(f"{name} must be [{T}][{N}][{L ** 3}][3], got {tuple(phi.shape)}")
+    if not _on_current_device(phi):
+        raise ValueError(f"{name} must be on the current CUDA device")
     return int(phi.shape[0]), int(phi.shape[1])
+
+
+def _check_host_phi(a, shape, name):
+    """A host field: a contiguous complex64 numpy array or CPU tensor of exactly `shape` (the C side copies
+    that many bytes from it)."""
+    import torch
+    if isinstance(a, torch.Tensor):
+        ok = not a.is_cuda and a.dtype == torch.complex64 and a.is_contiguous() and tuple(a.shape) == tuple(shape)
+    else:
+        ok = isinstance(a, np.ndarray) and a.dtype == np.complex64 and a.flags.c_contiguous and \
+            tuple(a.shape) == tuple(shape)
+    if not ok:
+        raise ValueError(f"{name} must be a contiguous host complex64 buffer of shape {tuple(shape)}")
 
 
 def phase_table(L: int, momenta, device=None):
@@ -182,6 +228,8 @@ def phase_table(L: int, momenta, device=None):
     import torch
     mom = _momenta(momenta)
     out = torch.empty((mom.shape[0], L ** 3), dtype=torch.complex128, device=device or "cuda")
+    if not _on_current_device(out):
+        raise ValueError("the phase table is computed on the current CUDA device")
     _check(lib().laph_phase_table(L, mom.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), mom.shape[0],
                                   _ptr(out), _stream(None)), "laph_phase_table")
     return out
@@ -193,6 +241,7 @@ def diquarks(phi, L: int, out=None, stream=None):
     T, N = _check_phi(phi, L)
     if out is None:
         out = torch.empty((T, N * (N - 1) // 2, L ** 3, 3), dtype=torch.complex64, device=phi.device)
+    _check_tensor(out, torch.complex64, (T, N * (N - 1) // 2, L ** 3, 3), "out")
     _check(lib().laph_diquarks(_ptr(phi), L, T, N, _ptr(out), _stream(stream)), "laph_diquarks")
     return out
 
@@ -200,9 +249,13 @@ def diquarks(phi, L: int, out=None, stream=None):
 def baryon_dense(packed, N: int, out=None, stream=None):
     """complex128 [T][P][N][N][N] from the packed [T][P][C(N,3)] form."""
     import torch
+    if not (isinstance(packed, torch.Tensor) and packed.dim() == 3):
+        raise ValueError("packed must be a complex128 CUDA tensor [T][P][C(N,3)]")
     T, P = int(packed.shape[0]), int(packed.shape[1])
+    _check_tensor(packed, torch.complex128, (T, P, N * (N - 1) * (N - 2) // 6), "packed")
     if out is None:
         out = torch.empty((T, P, N, N, N), dtype=torch.complex128, device=packed.device)
+    _check_tensor(out, torch.complex128, (T, P, N, N, N), "out")
     _check(lib().laph_baryon_dense(_ptr(packed), T, N, P, _ptr(out), _stream(stream)), "laph_baryon_dense")
     return out
 
@@ -214,6 +267,7 @@ def baryon_blocks(phi, L: int, momenta, mode="f16x3", out=None, stream=None):
     mom = _momenta(momenta)
     if out is None:
         out = torch.empty((T, mom.shape[0], N * (N - 1) * (N - 2) // 6), dtype=torch.complex128, device=phi.device)
+    _check_tensor(out, torch.complex128, (T, mom.shape[0], N * (N - 1) * (N - 2) // 6), "out")
     rc = lib().laph_baryon_blocks(_ptr(phi), L, T, N, mom.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                   mom.shape[0], _ptr(out), _mode(mode), _stream(stream))
     _check(rc, "laph_baryon_blocks")
@@ -227,6 +281,7 @@ def meson_blocks(phi, L: int, momenta, mode="f16x3", out=None, stream=None):
     mom = _momenta(momenta)
     if out is None:
         out = torch.empty((T, mom.shape[0], N, N), dtype=torch.complex128, device=phi.device)
+    _check_tensor(out, torch.complex128, (T, mom.shape[0], N, N), "out")
     rc = lib().laph_meson_blocks(_ptr(phi), L, T, N, mom.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                  mom.shape[0], _ptr(out), _mode(mode), _stream(stream))
     _check(rc, "laph_meson_blocks")
@@ -249,6 +304,7 @@ def triplet_blocks(phi, psi, chi, L: int, momenta, mode="f16x3", out=None, strea
     mom = _momenta(momenta)
     if out is None:
         out = torch.empty((T, mom.shape[0], N, N, N), dtype=torch.complex128, device=phi.device)
+    _check_tensor(out, torch.complex128, (T, mom.shape[0], N, N, N), "out")
     rc = lib().laph_triplet_blocks(_ptr(phi), _ptr(psi), _ptr(chi), L, T, N,
                                    mom.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), mom.shape[0], _ptr(out),
                                    _mode(mode), _stream(stream))
@@ -263,6 +319,7 @@ def doublet_blocks(phi, psi, L: int, momenta, mode="f16x3", out=None, stream=Non
     mom = _momenta(momenta)
     if out is None:
         out = torch.empty((T, mom.shape[0], N, N), dtype=torch.complex128, device=phi.device)
+    _check_tensor(out, torch.complex128, (T, mom.shape[0], N, N), "out")
     rc = lib().laph_doublet_blocks(_ptr(phi), _ptr(psi), L, T, N, mom.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                    mom.shape[0], _ptr(out), _mode(mode), _stream(stream))
     _check(rc, "laph_doublet_blocks")
@@ -280,6 +337,7 @@ def projection(v, s, L: int, momenta=((0, 0, 0),), mode="f16x3", out=None, strea
     mom = _momenta(momenta)
     if out is None:
         out = torch.empty((T, mom.shape[0], Nv, Ns), dtype=torch.complex128, device=v.device)
+    _check_tensor(out, torch.complex128, (T, mom.shape[0], Nv, Ns), "out")
     rc = lib().laph_projection(_ptr(v), _ptr(s), L, T, Nv, Ns, mom.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                mom.shape[0], _ptr(out), _mode(mode), _stream(stream))
     _check(rc, "laph_projection")
@@ -292,6 +350,8 @@ def _check_links(U, L):
         raise ValueError("U must be a contiguous complex64 CUDA tensor [T][3][L^3][3][3]")
     if U.dim() != 5 or tuple(U.shape[1:]) != (3, L ** 3, 3, 3):
         raise ValueError(f"U must have shape [T][3][{L ** 3}][3][3], got {tuple(U.shape)}")
+    if not _on_current_device(U):
+        raise ValueError("U must be on the current CUDA device")
     return U.shape[0]
 
 
@@ -304,6 +364,7 @@ def laplacian(U, f, L: int, out=None, stream=None):
         raise ValueError("f and U must have the same timeslices and device")
     if out is None:
         out = torch.empty_like(f)
+    _check_tensor(out, torch.complex64, tuple(f.shape), "out")
     rc = lib().laph_laplacian(_ptr(U), _ptr(f), _ptr(out), L, T, nvec, _stream(stream))
     _check(rc, "laph_laplacian")
     return out
@@ -332,6 +393,9 @@ def lanczos(U, L: int, n_ev: int, n_krylov: int, cheb_degree: int = 0, cheb_lo: 
     T = _check_links(U, L)
     if out is None:
         out = torch.empty((T, n_ev, L ** 3, 3), dtype=torch.complex64, device=U.device)
+    _check_tensor(out, torch.complex64, (T, n_ev, L ** 3, 3), "out")
+    if workspace is not None:
+        _check_workspace(workspace, 0)
     p = laph_lanczos_params(n_krylov, cheb_degree, cheb_lo, seed, ts_group, int(pdl), link_rows)
     ws = ctypes.c_void_p(workspace.data_ptr()) if workspace is not None else None
     ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
@@ -365,11 +429,8 @@ def _check_out(out, shape, phi, name):
     """An output tensor must be exactly what the C side will write: complex128, contiguous, the stated
     shape, on phi's device, which must be the current device."""
     import torch
-    if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.complex128 and out.is_contiguous()):
-        raise ValueError(f"{name} must be a contiguous complex128 CUDA tensor")
-    if tuple(out.shape) != tuple(shape):
-        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(out.shape)}")
-    if out.device != phi.device or phi.device.index != torch.cuda.current_device():
+    _check_tensor(out, torch.complex128, shape, name)
+    if out.device != phi.device:
         raise ValueError(f"{name} and phi must be on the current CUDA device")
 
 
@@ -574,9 +635,16 @@ class Plan:
             arr[n] = None if t is None else t.data_ptr()
         return arr
 
+    def _check_inputs(self, phis, workspace, nbytes):
+        """One field per instance, of the instance's shape, and a workspace of the plan's size."""
+        if phis is None or len(phis) != len(self.instances):
+            raise ValueError(f"{len(self.instances)} fields are needed, one per instance")
+        _check_workspace(workspace, nbytes)
+
     def execute(self, phis, Bs, Ms, workspace, stream=None):
-        for (L, T, N, _), phi in zip(self.instances, phis):
-            _check_phi(phi, L)
+        self._check_inputs(phis, workspace, self.workspace_size())
+        for n, ((L, T, N, _), phi) in enumerate(zip(self.instances, phis)):
+            _check_phi(phi, L, T, N, f"phi[{n}]")
         self._check_outputs(Bs, Ms)
         pa = self._ptr_array(phis)
         ba = self._ptr_array(Bs) if Bs is not None else None
@@ -587,9 +655,14 @@ class Plan:
     def execute_fields(self, fields, outs, workspace, stream=None):
         """LAPH_PLAN_FIELDS plans: fields[n] = (phi, psi, chi) for triplets, (phi, psi) for
         doublets; outs[n] the instance's B3 or M2."""
+        self._check_inputs(fields, workspace, self.workspace_size())
         flat = []
-        for (L, T, N, _), fs in zip(self.instances, fields):
-            _check_fields(tuple(fs), L, same_n=not (self.flags & PLAN_SKIP_B))
+        per = 2 if self.flags & PLAN_SKIP_B else 3
+        for n, ((L, T, N, _), fs) in enumerate(zip(self.instances, fields)):
+            if len(fs) != per:
+                raise ValueError(f"fields[{n}] must hold {per} fields")
+            for q, f in enumerate(fs):
+                _check_phi(f, L, T, (self.n_col[n] or N) if q == 1 and per == 2 else N, f"fields[{n}][{q}]")
             flat.extend(fs)
         if self.flags & PLAN_SKIP_M:
             self._check_outputs(outs, None)
@@ -606,6 +679,9 @@ class Plan:
             if a is None:
                 return None
             return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+        self._check_inputs(phis_host, workspace, self.host_workspace_size())
+        for n, ((L, T, N, _), a) in enumerate(zip(self.instances, phis_host)):
+            _check_host_phi(a, (T, N, L ** 3, 3), f"phi[{n}]")
         self._check_outputs(Bs_host, Ms_host, host=True)
         pa = (ctypes.c_void_p * len(phis_host))(*[addr(a) for a in phis_host])
         ba = (ctypes.c_void_p * len(Bs_host))(*[addr(a) for a in Bs_host]) if Bs_host is not None else None

@@ -217,8 +217,8 @@ def test_product_path_does_not_reference_the_oracle():
 
 
 def test_binding_validates_links_and_vectors_before_calling_the_library(lib):
-    """The Laplacian and Lanczos wrappers refuse host tensors, wrong dtypes and wrong shapes with ValueError (no
-    library call, no GPU needed)."""
+    """The Laplacian, Lanczos and block wrappers refuse host tensors, wrong dtypes and wrong shapes with ValueError
+    (no library call, no GPU needed)."""
     import numpy as np
     torch = pytest.importorskip("torch")
     from paper_2510_26313_gb300 import binding
@@ -233,6 +233,15 @@ def test_binding_validates_links_and_vectors_before_calling_the_library(lib):
         binding.lanczos(U.to(torch.complex128), L, 4, 20)
     with pytest.raises(ValueError):
         binding.lanczos(U[:, :2].contiguous(), L, 4, 20)                     # two directions
+    phi = torch.zeros((1, 4, L ** 3, 3), dtype=torch.complex64)          # host field
+    mom = [(0, 0, 0)]
+    for call in (lambda: binding.baryon_blocks(phi, L, mom), lambda: binding.meson_blocks(phi, L, mom),
+                 lambda: binding.diquarks(phi, L), lambda: binding.triplet_blocks(phi, phi, phi, L, mom),
+                 lambda: binding.doublet_blocks(phi, phi, L, mom), lambda: binding.projection(phi, phi, L),
+                 lambda: binding.blocks_noalloc(phi, L, mom, None, None),
+                 lambda: binding.baryon_dense(torch.zeros((1, 1, 4), dtype=torch.complex128), 4)):
+        with pytest.raises(ValueError):
+            call()
     n = binding.lanczos_workspace_size(L, 1, 4, 20)
     assert n >= 8 * 3 * L ** 3 * (20 + 1 + 4)
     with pytest.raises(binding.LaphError):
