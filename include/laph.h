@@ -334,8 +334,9 @@ LAPH_API int laph_plan_workspace_size(const laph_plan *plan, size_t *bytes);
 /* Runs the whole batch on `stream`: phi[n], out_B[n], out_M[n] are device
  * pointers for instance n (layouts above; out_B/out_M ignored when skipped).
  * No allocation, no host synchronisation: safe inside stream capture.
- * Returns LAPH_ERR_WORKSPACE if the workspace is NULL/misaligned while
- * workspace_size > 0. */
+ * The current device must be the one the plan was created on (LAPH_ERR_ARG
+ * otherwise).  Returns LAPH_ERR_WORKSPACE if the workspace is NULL/misaligned
+ * while workspace_size > 0. */
 LAPH_API int laph_plan_execute(laph_plan *plan, const void *const *phi, void *const *out_B, void *const *out_M,
                       void *workspace, void *stream);
 
@@ -353,8 +354,10 @@ LAPH_API int laph_plan_execute_fields(laph_plan *plan, const void *const *fields
  * is copied in, computed, and out_B_host[n]/out_M_host[n] (complex128, or
  * complex64 with LAPH_PLAN_OUT_C64) are copied back, timeslice chunk by chunk with copies overlapping compute.
  * Device staging comes from `workspace`, which must hold
- * laph_plan_host_workspace_size bytes.  Returns after the stream is
- * synchronised. */
+ * laph_plan_host_workspace_size bytes (256-byte aligned), on the plan's
+ * device, which must be current (LAPH_ERR_ARG otherwise).  Returns after the
+ * stream is synchronised, on failure too: copies queued before a failure
+ * finish before the call returns, so the host buffers are free to reuse. */
 LAPH_API int laph_plan_host_workspace_size(const laph_plan *plan, size_t *bytes);
 LAPH_API int laph_plan_execute_host(laph_plan *plan, const void *const *phi_host, void *const *out_B_host,
                            void *const *out_M_host, void *workspace, void *stream);
@@ -436,11 +439,13 @@ typedef struct {
  * cap); then, from the fastest, half and twice the site-block size of the
  * FP64 reduction; then half and 1.5 times the drain interval (for all
  * tiles; chunk_sites_b is kept as given); finally the three fastest accepted
- * schedules are timed twice more and each keeps its lowest time.  A drain
+ * schedules and the default schedule (the one a plan without the flag runs)
+ * are timed twice more and each keeps its lowest time.  The fastest replaces
+ * the default only if it is more than 1% faster.  A drain
  * interval is accepted only if the relative error of (instance 0, timeslice 0)
  * against the FP32 CUDA-core path stays within 5e-6 (half the 1e-5 bound) or
  * within the default interval's own error; plans of several fields keep the
- * default interval.  The fastest accepted candidate is applied (see
+ * default interval.  The schedule chosen so is applied (see
  * laph_plan_describe, laph_plan_schedule, laph_plan_sum_sites).
  * Writes min(cap, number of candidates) records; *n_candidates (may be NULL)
  * receives the number of candidates (0 without LAPH_PLAN_AUTOTUNE). */

@@ -928,9 +928,18 @@ static int ring_times(const std::vector<cudaEvent_t> &b, const std::vector<cudaE
 // the error of (instance 0, timeslice 0) against the FP32 CUDA-core path (its
 // accuracy probe) stays within TUNE_ERR_LIMIT or within the default's own
 // probe error; plans of several fields have no FP32 path and keep the default
-// interval.  Finally the three fastest accepted schedules are timed twice
-// more, each keeps its lowest time, and the fastest is applied.
+// interval.  Finally the three fastest accepted schedules and the default one
+// are timed twice more, each keeps its lowest time, and the fastest is applied
+// if it beats the default by more than TUNE_MARGIN (else the default is).
 constexpr double TUNE_ERR_LIMIT = 5e-6;   // half the 1e-5 bound of the split-precision modes
+// A tuned schedule replaces the default one only if it is faster by more than
+// this fraction.  Near-ties are timing noise (at the 64-timeslice L=32
+// workload layout 1 with 208 columns and layout 0 with 104 came within 0.3% of
+// each other, and the choice flipped from box to box), and the default's
+// smaller chunks overlap the copies of laph_plan_execute_host better (there
+// layout 1's chunks of 25 timeslices left 4-5 ms more of copying exposed per
+// execute than the default's 10).
+constexpr double TUNE_MARGIN = 0.01;
 
 struct TuneState {
     std::vector<void *> phi, ob, om;
@@ -1114,24 +1123,36 @@ static int autotune(laph_plan *p, const laph::Sched &def, const std::function<cu
         }
         // 4: the three fastest accepted schedules are timed twice more, and
         // each keeps the lowest of its times, so that one noisy timing does
-        // not decide between close candidates
+        // not decide between close candidates; the default schedule (candidate
+        // 0) is timed again with them and keeps its place unless the fastest
+        // beats it by more than TUNE_MARGIN
+        auto same = [&](size_t qa, size_t qb) {
+            const laph::Sched &a = p->tune_cand[qa], &b = p->tune_cand[qb];
+            return a.tile_cols == b.tile_cols && a.sum_sites == b.sum_sites && a.chunk_sites == b.chunk_sites &&
+                   a.per_chunk == b.per_chunk && a.order == b.order && a.rows2 == b.rows2 &&
+                   a.chunk_sites_b == b.chunk_sites_b;
+        };
         std::vector<size_t> top;
         for (size_t k = 0; k < p->tune_ms.size(); k++) {
             if (!accepted[k]) continue;
             bool dup = false;
-            for (size_t q : top) {
-                const laph::Sched &a = p->tune_cand[q], &b = p->tune_cand[k];
-                if (a.tile_cols == b.tile_cols && a.sum_sites == b.sum_sites && a.chunk_sites == b.chunk_sites &&
-                    a.per_chunk == b.per_chunk && a.order == b.order && a.rows2 == b.rows2 &&
-                    a.chunk_sites_b == b.chunk_sites_b) {
+            for (size_t q : top)
+                if (same(q, k)) {
                     p->tune_ms[q] = std::min(p->tune_ms[q], p->tune_ms[k]);   // the same schedule timed again
                     dup = true;
                 }
-            }
             if (!dup) top.push_back(k);
             std::sort(top.begin(), top.end(), [&](size_t a, size_t b) { return p->tune_ms[a] < p->tune_ms[b]; });
             if (top.size() > 3) top.pop_back();
         }
+        size_t def_k = 0;
+        bool def_in_top = false;
+        for (size_t q : top)
+            if (same(q, 0)) {
+                def_k = q;
+                def_in_top = true;
+            }
+        if (!def_in_top) top.push_back(0);
         for (int rep = 0; rep < 2 && top.size() > 1; rep++)
             for (size_t k : top) {
                 TCK(apply(p->tune_cand[k]));
@@ -1139,11 +1160,10 @@ static int autotune(laph_plan *p, const laph::Sched &def, const std::function<cu
                 TRC(tune_time(p, ts, &ms));
                 p->tune_ms[k] = std::min(p->tune_ms[k], ms);
             }
-        if (!top.empty()) {
-            best = top[0];
-            for (size_t k : top)
-                if (p->tune_ms[k] < p->tune_ms[best]) best = k;
-        }
+        best = top[0];
+        for (size_t k : top)
+            if (p->tune_ms[k] < p->tune_ms[best]) best = k;
+        if (!same(best, def_k) && p->tune_ms[best] > (1.0 - TUNE_MARGIN) * p->tune_ms[def_k]) best = def_k;
     }
     TCK(apply(p->tune_cand[best]));
     TCK(cudaMemsetAsync(p->d_status, 0, sizeof(int), ts.st));
@@ -1308,14 +1328,17 @@ int laph_plan_host_workspace_size(const laph_plan *plan, size_t *bytes)
     return LAPH_OK;
 }
 
-int laph_plan_execute_host(laph_plan *plan, const void *const *phi_host, void *const *out_B_host,
-                           void *const *out_M_host, void *workspace, void *stream)
+// laph_plan_execute_host without the clean-up after a failure
+static int execute_host_body(laph_plan *plan, const void *const *phi_host, void *const *out_B_host, void *const *out_M_host,
+                      void *workspace, cudaStream_t s)
 {
-    if (!plan || !phi_host || !workspace || ((uintptr_t)workspace) % 256) return LAPH_ERR_ARG;
+    if (!phi_host || !workspace || ((uintptr_t)workspace) % 256) return LAPH_ERR_ARG;
     if (plan->flags & LAPH_PLAN_FIELDS) return LAPH_ERR_UNSUPPORTED;
     const bool needB = !(plan->flags & LAPH_PLAN_SKIP_B), needM = !(plan->flags & LAPH_PLAN_SKIP_M);
     if ((needB && !out_B_host) || (needM && !out_M_host)) return LAPH_ERR_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
+    int cur = 0;
+    CK(cudaGetDevice(&cur));
+    if (cur != plan->device) return LAPH_ERR_ARG;
     char *ws = (char *)workspace;
     size_t off = ((plan->ws_bytes + 255) / 256) * 256;
     std::vector<const void *> dphi(plan->n_inst);
@@ -1410,6 +1433,22 @@ int laph_plan_execute_host(laph_plan *plan, const void *const *phi_host, void *c
     CK(cudaStreamSynchronize(plan->d2h));
     CK(cudaStreamSynchronize(s));
     return LAPH_OK;
+}
+
+int laph_plan_execute_host(laph_plan *plan, const void *const *phi_host, void *const *out_B_host,
+                           void *const *out_M_host, void *workspace, void *stream)
+{
+    if (!plan) return LAPH_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int rc = execute_host_body(plan, phi_host, out_B_host, out_M_host, workspace, s);
+    if (rc != LAPH_OK) {
+        // copies queued before the failure still read or write the caller's
+        // host buffers: they finish before the caller gets the buffers back
+        if (plan->h2d) cudaStreamSynchronize(plan->h2d);
+        if (plan->d2h) cudaStreamSynchronize(plan->d2h);
+        cudaStreamSynchronize(s);
+    }
+    return rc;
 }
 
 int laph_get_device_status(laph_plan *plan, void *stream, int *status)
