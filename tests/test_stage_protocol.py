@@ -12,6 +12,10 @@ that every producer reads exactly its stage's landed data, that no copy starts i
 read or still being filled, that no barrier phase receives more arrivals than it expects and that nothing
 deadlocks, for ring depths 2..6.  The data barriers are indexed by stage modulo 2 NS, so each serves one
 producer group; indexing them by buffer (stage modulo NS) breaks for odd NS, which the negative control shows.
+
+The second model is the accumulator drain handshake between the MMA warp and the epilogue warps (two column halves,
+per-tile drain intervals, four or eight epilogue warps); its negative controls are an acc_empty barrier counting one
+arrival, a wait on the wrong parity, and an epilogue that derives its chunks from another drain interval.
 """
 import random
 
@@ -127,3 +131,162 @@ def test_negative_control_data_barriers_per_buffer_break_for_odd_depth():
         except AssertionError:
             failures += 1
     assert failures > 0
+
+
+# ---------------------------------------------------------------------------
+# The accumulator drain handshake between the MMA warp and the epilogue warps.
+#
+# The accumulator is used as two column halves h (one when the tile is narrow).
+# Per drain chunk of a tile, the MMA warp, for each half in order, waits on
+# acc_empty[h] with parity (g_h & 1) ^ 1 before the chunk's first MMAs into it,
+# and after the chunk's last MMAs into it commits acc_full[h] (the commit
+# arrives once those MMAs have completed, in issue order); the stages between
+# write both halves.  Every epilogue warp, per chunk and half, waits on
+# acc_full[h] with parity g_h & 1, reads the half, and arrives on acc_empty[h]
+# (count: the number of epilogue warps).  The drain interval of a tile is
+# chunk_stages, or chunk_stages_b for tiles without meson rows; both sides
+# must derive the same chunk count from it.
+
+
+def drain_programs(tiles, chunk, chunk_b, epi_chunk_b=None):
+    """MMA and epilogue op lists for a tile sequence [(nst, meson, nh)]."""
+    mma, epi = [], []
+    for t, (nst, meson, nh) in enumerate(tiles):
+        cs = chunk if meson else chunk_b
+        ce = chunk if meson else (chunk_b if epi_chunk_b is None else epi_chunk_b)
+        n_ch = -(-nst // cs)
+        for ch in range(n_ch):
+            n_in = min(cs, nst - ch * cs)       # stages of this chunk
+            for h in range(nh):
+                mma.append(("wait_empty", h))
+                mma.append(("write", h, (t, ch)))
+                if n_in == 1:
+                    mma.append(("commit", h, (t, ch)))
+            if n_in > 2:
+                mma.append(("write_both", nh, (t, ch)))
+            if n_in > 1:
+                for h in range(nh):
+                    mma.append(("write", h, (t, ch)))
+                    mma.append(("commit", h, (t, ch)))
+        for ch in range(-(-nst // ce)):
+            for h in range(nh):
+                epi.append(("wait_full", h, (t, ch)))
+                epi.append(("arrive", h, (t, ch)))
+    return mma, epi
+
+
+def simulate_drain(tiles, epi_warps, chunk, chunk_b, seed, empty_count=None, mma_parity_flip=False,
+                   epi_chunk_b=None):
+    rng = random.Random(seed)
+    acc_full = [Bar(1), Bar(1)]
+    acc_empty = [Bar(empty_count or epi_warps) for _ in range(2)]
+    mma_ops, epi_ops = drain_programs(tiles, chunk, chunk_b, epi_chunk_b)
+    owner = [None, None]            # chunk whose sums are in the half
+    committed = [None, None]        # chunk whose MMAs into the half have completed
+    drained = [{}, {}]              # chunk -> epilogue warps that have read and released it
+    pending = []                    # commits issued, not yet arrived (they arrive in order)
+    g_mma = [0, 0]
+    pc_mma = 0
+    warps = [{"pc": 0, "g": [0, 0]} for _ in range(epi_warps)]
+    for _ in range(200000):
+        if pc_mma == len(mma_ops) and not pending and all(w["pc"] == len(epi_ops) for w in warps):
+            return
+        acts = []
+        if pc_mma < len(mma_ops):
+            op = mma_ops[pc_mma]
+            if op[0] != "wait_empty":
+                acts.append(("mma",))
+            else:
+                h = op[1]
+                par = (g_mma[h] & 1) ^ (0 if mma_parity_flip else 1)
+                if acc_empty[h].try_wait(par):
+                    acts.append(("mma",))
+        if pending:
+            acts.append(("arrive_commit",))
+        for i, w in enumerate(warps):
+            if w["pc"] == len(epi_ops):
+                continue
+            op = epi_ops[w["pc"]]
+            if op[0] == "arrive" or acc_full[op[1]].try_wait(w["g"][op[1]] & 1):
+                acts.append(("epi", i))
+        assert acts, "deadlock"
+        act = rng.choice(acts)
+        if act[0] == "mma":
+            op = mma_ops[pc_mma]
+            pc_mma += 1
+            if op[0] == "wait_empty":
+                h = op[1]
+                prev = owner[h]
+                if prev is not None:
+                    assert len(drained[h].get(prev, ())) == epi_warps, \
+                        f"half {h}: chunk {prev} overwritten before every epilogue warp drained it"
+            elif op[0] == "write":
+                h, cid = op[1], op[2]
+                assert owner[h] in (None, cid) or len(drained[h].get(owner[h], ())) == epi_warps, \
+                    f"half {h} written while chunk {owner[h]} is undrained"
+                owner[h] = cid
+                committed[h] = None
+            elif op[0] == "write_both":
+                for h in range(op[1]):
+                    assert owner[h] == op[2], f"middle stage of chunk {op[2]} without the half {h}"
+            else:
+                h, cid = op[1], op[2]
+                pending.append((h, cid))
+                g_mma[h] += 1
+        elif act[0] == "arrive_commit":
+            h, cid = pending.pop(0)
+            committed[h] = cid
+            acc_full[h].arrive()
+        else:
+            w = warps[act[1]]
+            op = epi_ops[w["pc"]]
+            w["pc"] += 1
+            h, cid = op[1], op[2]
+            if op[0] == "wait_full":
+                assert owner[h] == cid and committed[h] == cid, \
+                    f"epilogue read half {h} for chunk {cid}, but it holds {owner[h]} (completed: {committed[h]})"
+            else:
+                drained[h].setdefault(cid, set()).add(act[1])
+                w["g"][h] += 1
+                acc_empty[h].arrive()
+    raise AssertionError("no progress")
+
+
+def random_tiles(rng, n):
+    # (K stages, has meson rows, column halves)
+    return [(rng.randint(1, 40), rng.random() < 0.3, rng.choice([1, 2, 2])) for _ in range(n)]
+
+
+@pytest.mark.parametrize("epi_warps", [4, 8])
+@pytest.mark.parametrize("chunk,chunk_b", [(16, 16), (16, 24), (8, 16), (1, 1), (3, 2)])
+def test_drain_handshake(epi_warps, chunk, chunk_b):
+    for seed in range(60):
+        rng = random.Random(1000 + seed)
+        simulate_drain(random_tiles(rng, 6), epi_warps, chunk, chunk_b, seed)
+
+
+def _fails(**kw):
+    failures = 0
+    for seed in range(60):
+        rng = random.Random(2000 + seed)
+        try:
+            simulate_drain(random_tiles(rng, 6), 8, 16, 24, seed, **kw)
+        except AssertionError:
+            failures += 1
+    return failures
+
+
+def test_negative_control_acc_empty_counting_one_warp():
+    """acc_empty expecting one arrival instead of one per epilogue warp: the MMAs overwrite a half that other
+    epilogue warps have not drained yet."""
+    assert _fails(empty_count=1) > 0
+
+
+def test_negative_control_mma_waits_on_the_wrong_parity():
+    assert _fails(mma_parity_flip=True) == 60
+
+
+def test_negative_control_epilogue_with_another_drain_interval():
+    """The epilogue deriving its chunk count from chunk_stages where the MMA used chunk_stages_b (tiles without
+    meson rows): the two sides disagree on the chunks and the handshake breaks."""
+    assert _fails(epi_chunk_b=16) > 0
