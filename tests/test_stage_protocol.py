@@ -16,6 +16,7 @@ producer group; indexing them by buffer (stage modulo NS) breaks for odd NS, whi
 The second model is the accumulator drain handshake between the MMA warp and the epilogue warps (two column halves,
 per-tile drain intervals, four or eight epilogue warps); its negative controls are an acc_empty barrier counting one
 arrival, a wait on the wrong parity, and an epilogue that derives its chunks from another drain interval.
+The third is the tile ring through which the loader hands tile ids to the other roles.
 """
 import random
 
@@ -290,3 +291,71 @@ def test_negative_control_epilogue_with_another_drain_interval():
     """The epilogue deriving its chunk count from chunk_stages where the MMA used chunk_stages_b (tiles without
     meson rows): the two sides disagree on the chunks and the handshake breaks."""
     assert _fails(epi_chunk_b=16) > 0
+
+
+# ---------------------------------------------------------------------------
+# The tile ring: the loader claims tile ids from the global counter and
+# publishes them through TRING shared slots; every reader warp (A producers,
+# epilogue, MMA) takes every entry in order and frees it at once.  The loader
+# waits on tempty[slot] with parity (round & 1) ^ 1, writes the id, arrives on
+# tfull[slot]; a reader waits on tfull[slot] with parity round & 1, reads,
+# arrives on tempty[slot] (count: the number of readers).  The last entry is
+# -1, after which every role stops.
+
+
+def simulate_tile_ring(n_tiles, n_readers, ring, seed, empty_count=None):
+    rng = random.Random(seed)
+    tfull = [Bar(1) for _ in range(ring)]
+    tempty = [Bar(empty_count or n_readers) for _ in range(ring)]
+    slot_val = [None] * ring
+    loader = {"k": 0, "done": False}
+    readers = [{"k": 0, "seen": [], "done": False} for _ in range(n_readers)]
+    for _ in range(100000):
+        if loader["done"] and all(r["done"] for r in readers):
+            for r in readers:
+                assert r["seen"] == list(range(n_tiles)), "a reader saw tiles out of order or lost one"
+            return
+        acts = []
+        k = loader["k"]
+        if not loader["done"] and tempty[k % ring].try_wait(((k // ring) & 1) ^ 1):
+            acts.append(("load",))
+        for i, r in enumerate(readers):
+            k = r["k"]
+            if not r["done"] and tfull[k % ring].try_wait((k // ring) & 1):
+                acts.append(("read", i))
+        assert acts, "deadlock"
+        act = rng.choice(acts)
+        if act[0] == "load":
+            k = loader["k"]
+            slot_val[k % ring] = k if k < n_tiles else -1
+            tfull[k % ring].arrive()
+            loader["k"] += 1
+            loader["done"] = k >= n_tiles
+        else:
+            r = readers[act[1]]
+            k = r["k"]
+            v = slot_val[k % ring]
+            assert v == (k if k < n_tiles else -1), f"reader {act[1]} took entry {k} but read tile {v}"
+            tempty[k % ring].arrive()
+            r["k"] += 1
+            if v < 0:
+                r["done"] = True
+            else:
+                r["seen"].append(v)
+    raise AssertionError("no progress")
+
+
+@pytest.mark.parametrize("n_readers", [21, 25])   # 16 A producers + 4 or 8 epilogue warps + the MMA warp
+def test_tile_ring(n_readers):
+    for seed in range(40):
+        simulate_tile_ring(13, n_readers, 4, seed)
+
+
+def test_negative_control_tile_ring_freed_by_fewer_readers():
+    failures = 0
+    for seed in range(40):
+        try:
+            simulate_tile_ring(13, 21, 4, seed, empty_count=20)
+        except AssertionError:
+            failures += 1
+    assert failures > 0
