@@ -140,7 +140,11 @@ LAPH_API const char *laph_status_string(int status);
 /* Text of the last failed CUDA call on this thread ("" if none). */
 LAPH_API const char *laph_last_cuda_error(void);
 
-/* Library ABI version (major*10000 + minor*100 + patch). */
+/* Library ABI version (major*10000 + minor*100 + patch).  1.1 added the
+ * fields laph_plan_options.chunk_sites_b, laph_tune_record.chunk_sites_b and
+ * laph_lanczos_stats.host_steps (the structs grew at their ends), the flag
+ * LAPH_PLAN_OUT_C64 and laph_plan_drain_sites; a caller built against 1.0
+ * passes structs that are too small for a 1.1 library. */
 LAPH_API int laph_version(void);
 
 /* ---- K-a: momentum phase table --------------------------------------- */

@@ -171,7 +171,7 @@ const char *laph_status_string(int status)
 
 const char *laph_last_cuda_error(void) { return g_last_cuda; }
 
-int laph_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+int laph_version(void) { return 1 * 10000 + 1 * 100 + 0; }
 
 int laph_phase_table(int L, const int32_t *momenta, int n_mom, void *out, void *stream)
 {
