@@ -14,6 +14,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblaph_gb300.so")
+ABI_VERSION = 10100   # laph_version() of the library whose structures this binding declares
 
 LAPH_OK = 0
 LAPH_ERR_ARG = -1
@@ -134,6 +135,10 @@ def lib() -> ctypes.CDLL:
             f = getattr(L, name)
             f.restype = res
             f.argtypes = args
+        # the ctypes structures above have the sizes of this ABI version; an older build would write past them
+        if L.laph_version() != ABI_VERSION:
+            raise RuntimeError(f"CUDA library {LIB_PATH} has ABI version {L.laph_version()}, the binding expects "
+                               f"{ABI_VERSION}: rebuild it with __graft_entry__.build()")
         _lib = L
     return _lib
 
