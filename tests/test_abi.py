@@ -247,3 +247,34 @@ def test_binding_validates_links_and_vectors_before_calling_the_library(lib):
     with pytest.raises(binding.LaphError):
         binding.lanczos_workspace_size(L, 1, 30, 20)                         # n_ev > n_krylov
     assert np.isfinite(n)
+
+
+def test_binding_structures_match_the_header(tmp_path):
+    """Every struct the binding declares with ctypes has the size and field offsets that a C compiler gives the
+    same struct from include/laph.h (a mismatch would let the library write past a Python-side structure)."""
+    import shutil
+    import subprocess
+    from paper_2510_26313_gb300 import binding
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [binding.laph_instance, binding.laph_plan_options, binding.laph_tune_record,
+               binding.laph_lanczos_params, binding.laph_lanczos_stats]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "laph.h"', 'int main(void) {']
+    for st in structs:
+        name = st.__name__
+        lines.append(f'    printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in st._fields_:
+            lines.append(f'    printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ['    return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    c_side = {(a, b): int(c) for a, b, c in (l.split() for l in out if l.strip())}
+    for st in structs:
+        name = st.__name__
+        assert c_side[(name, "size")] == ctypes.sizeof(st), name
+        for field, _ in st._fields_:
+            assert c_side[(name, field)] == getattr(st, field).offset, (name, field)
