@@ -38,6 +38,9 @@ def test_library_exports_every_declared_symbol(lib):
     assert len(names) >= 15
     for n in names:
         assert hasattr(lib, n), f"{n} declared in laph.h but not exported by {binding.LIB_PATH}"
+        # the binding sets result and argument types for every entry point (an untyped ctypes call would pass and
+        # return plain ints, truncating 64-bit pointers and sizes)
+        assert getattr(lib, n).argtypes is not None and getattr(lib, n).restype is not None, n
 
 
 def test_triple_index_is_colex(lib):
